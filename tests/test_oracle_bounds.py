@@ -1,0 +1,155 @@
+"""Pins of the oracle's FP64 bounds (Thm. "bound_dev", eq. "epsrade"), the stopping
+test of Algorithm 1, and the progressive loop.
+
+Special cases with closed forms (C = 0, w = 0, R~ = 0), the equivalence of the
+stopping line with the inequality chain in the proof of Prop. "main", the
+monotonicity of eta, its large-m limit 2 A, and the schedule
+(delta_i = delta / 2^i, m_i = m0 2^(i-1)).  End to end: on a graph small enough
+for exact set betweenness, the certified set reaches (1 - 1/e - eps) of the
+brute-force optimum.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_03651_gb300 import inputs as I
+
+A = 1 - math.exp(-1)
+
+
+def L_of(delta, i):
+    return math.log(5 * 2**i / delta)
+
+
+@pytest.mark.parametrize("m,i", [(1000, 1), (64000, 7), (10**6, 3)])
+def test_zero_coverage_closed_forms(m, i):
+    # C = 0: xi = nu = 2 L/m.  A = 0, w = 0: Rt = 0, R = 2 L/m,
+    # eta = 4 L/m + sqrt(2 L (2L/m + 8L/m) / m) + L/(3m) = (4 + sqrt(20) + 1/3) L/m
+    stop, b = O.bounds(0, m, 0, 10, 0, 0, 0.1, 0.1, i)
+    L = L_of(0.1, i)
+    assert b["C"] == 0 and b["A"] == 0 and b["w"] == 0
+    assert b["xi"] == pytest.approx(2 * L / m, rel=1e-14)
+    assert b["nu"] == pytest.approx(2 * L / m, rel=1e-14)
+    assert b["Rt"] == 0
+    assert b["R"] == pytest.approx(2 * L / m, rel=1e-14)
+    assert b["eta"] == pytest.approx((4 + math.sqrt(20) + 1 / 3) * L / m, rel=1e-14)
+    assert not stop  # C = 0 can never be certified
+
+
+def test_no_variance_keeps_amcera():
+    stop, b = O.bounds(500, 1000, 1234, 10, 0, 0, 0.1, 0.1, 2)
+    assert b["Rt"] == b["A"] == pytest.approx(1234 / (10 * 1000), rel=1e-15)
+    assert b["C"] == 0.5
+
+
+def test_scaled_inputs():
+    # every bound depends on the sample through C, A, w and m only
+    s1, b1 = O.bounds(300, 1000, 200, 10, 900, 3, 0.05, 0.1, 2)
+    s2, b2 = O.bounds(600, 2000, 400, 10, 1800, 3, 0.05, 0.1, 2)
+    for key in ("C", "A", "w"):
+        assert b1[key] == pytest.approx(b2[key], rel=1e-15)
+    assert b2["eta"] < b1["eta"] and b2["xi"] < b1["xi"]
+
+
+def test_stop_equals_prop_main_chain():
+    """Alg. 1's test a((a-eps) xi + eta) <= eps C is the middle inequality of the proof of
+    Prop. "main": C/a + xi <= (C - eta)/(a - eps)."""
+    rng = np.random.default_rng(0)
+    agree = 0
+    for _ in range(3000):
+        m = int(rng.integers(1000, 10**7))
+        cov = int(rng.integers(0, m + 1))
+        t = int(rng.integers(1, 100))
+        Rsum = int(rng.integers(0, 5 * t * math.isqrt(m) + 1))
+        Wnum = int(rng.integers(0, 4 * m + 1))
+        b = int(rng.integers(0, 20))
+        eps = float(rng.uniform(0.001, 0.5))
+        i = int(rng.integers(1, 12))
+        stop, v = O.bounds(cov, m, Rsum, t, Wnum, b, eps, 0.1, i)
+        lhs = v["C"] / A + v["xi"]
+        rhs = (v["C"] - v["eta"]) / (A - eps)
+        if abs(lhs - rhs) < 1e-9 * max(1.0, abs(lhs)):
+            continue  # rounding decides at the boundary
+        assert stop == (lhs <= rhs)
+        agree += stop
+    assert agree > 0
+
+
+def test_eta_monotone_and_limit():
+    base = dict(covered=4000, m=10000, Rsum=300, t=10, Wnum=20000, b=4, eps=0.05, delta=0.1, i=3)
+    def eta(**kw):
+        a = dict(base, **kw)
+        return O.bounds(a["covered"], a["m"], a["Rsum"], a["t"], a["Wnum"], a["b"], a["eps"], a["delta"], a["i"])[1]
+    e0 = eta()["eta"]
+    assert eta(Rsum=600)["eta"] > e0
+    assert eta(Wnum=40000)["eta"] > e0
+    assert eta(b=8)["eta"] > e0
+    assert eta(i=4)["eta"] > e0  # smaller delta_i
+    # fixed C, A, w: eta -> 2 A as m grows (numerators scaled with m)
+    for m in (10**6, 10**8, 10**10):
+        s = m // 10000
+        v = eta(covered=4000 * s, m=m, Rsum=300 * s, Wnum=20000 * s)
+        assert v["A"] == pytest.approx(0.003)
+    assert v["eta"] == pytest.approx(2 * 0.003, rel=0.05)
+
+
+def test_run_schedule_and_first_stop():
+    g = O.Graph.of(I.ba(300, 3, 2))
+    r = g.run(k=5, eps=0.2, delta=0.1, t=10, seed=3, m0=500)
+    assert r["status"] == O.OK
+    log = r["log"]
+    for row_i, row in enumerate(log, start=1):
+        assert row[0] == row_i and row[1] == 500 * 2 ** (row_i - 1)
+        stop, b = O.bounds(int(row[2]), int(row[1]), int(row[3]), 10, int(row[4]), int(row[5]), 0.2, 0.1, row_i)
+        assert stop == bool(row[14])
+        assert b["eta"] == row[13] and b["xi"] == row[10]
+    assert all(row[14] == 0 for row in log[:-1]) and log[-1][14] == 1
+    assert r["m_final"] == log[-1][1] and r["covered"] == log[-1][2]
+
+
+def test_run_not_certified_on_empty_hyperedges():
+    # complete graph: every hyper-edge is empty, C = 0 forever
+    n = 8
+    e = np.array([(a, b) for a in range(n) for b in range(a + 1, n)], np.int32)
+    g = O.Graph.of(I.from_edges(n, e[:, 0], e[:, 1], False))
+    r = g.run(k=2, eps=0.1, delta=0.1, t=4, seed=1, m0=100, m_cap=1600)
+    assert r["status"] == O.ENOTCERTIFIED and r["m_final"] == 1600 and r["covered"] == 0
+    assert len(r["S"]) == 0
+
+
+def test_run_rejects_bad_arguments():
+    g = O.Graph.of(I.ba(30, 2, 1))
+    for kw in (dict(k=0), dict(eps=0.0), dict(eps=0.7), dict(delta=1.0), dict(t=0)):
+        args = dict(k=3, eps=0.1, delta=0.1, t=4, seed=1)
+        args.update(kw)
+        with pytest.raises(O.OracleError):
+            g.run(**args)
+
+
+def test_certified_set_is_within_guarantee_on_tiny_graph():
+    """Prop. "main": C(S) >= (1 - 1/e - eps) C(S*), checked with exact set betweenness."""
+    nx = pytest.importorskip("networkx")
+    g = I.ba(14, 2, 6)
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    for v in range(g.n):
+        for w in g.col[g.off[v]:g.off[v + 1]]:
+            G.add_edge(v, int(w))
+    pairs = {}
+    for s in range(g.n):
+        for t in range(g.n):
+            if s != t:
+                pairs[(s, t)] = [set(p[1:-1]) for p in nx.all_shortest_paths(G, s, t)]
+    def B(S):
+        S = set(S)
+        return sum(sum(1 for p in ps if p & S) / len(ps) for ps in pairs.values()) / (g.n * (g.n - 1))
+    k, eps = 2, 0.3
+    opt = max(B(S) for S in itertools.combinations(range(g.n), k))
+    og = O.Graph.of(g)
+    for seed in range(3):
+        r = og.run(k=k, eps=eps, delta=0.1, t=10, seed=seed, m0=1000)
+        assert r["status"] == O.OK
+        assert B(r["S"]) >= (1 - 1 / math.e - eps) * opt
