@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Sampled paths/s of one CentRA sample-and-cover round on GB300.
+
+A step is one pass of the whole hot path over one batch: draw M pairs,
+count shortest paths, walk one uniform shortest path per pair, append the
+hyper-edges, build the node -> sample incidence, greedyCover(k), the t sign
+vectors and AMCERA numerators, and the FP64 bounds / stopping test (one round
+of Algorithm 1 at m = M).  Every step uses a fresh job with its own seed so no
+step reuses another's samples.  The graph (synthetic R-MAT scale 18 LCC,
+stand-in for the paper's SNAP graphs) stays resident in HBM.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle (the plain
+single-threaded C statement of the method) on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2306_03651_gb300 import inputs as I  # noqa: E402
+
+WORKLOADS = {
+    "rmat18": ("R-MAT scale 18 (262,144 ids), edge factor 16, (.57,.19,.19,.05), undirected, dedup, no self-loops, LCC",
+               I.rmat18_lcc),
+    "ba2000": ("Barabasi-Albert n=2000, 4 edges per new node, seed 1", I.ba_2000),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="rmat18", choices=sorted(WORKLOADS))
+    ap.add_argument("--m", type=int, default=65536, help="pairs sampled per step")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- gpu arm
+def gpu_step(P, graph, wl, M, seed):
+    job = P.Job(graph, seed, wl.t)
+    job.set_timing(True)
+    job.sample(M)
+    S, cov = job.greedy_cover(wl.k)
+    Rnum, Wnum, b = job.mcera(wl.k)
+    stop, bd = P.bounds(cov, M, int(Rnum.sum()), wl.t, Wnum, b, wl.eps, wl.delta, 1)
+    st = job.stats()
+    job.close()
+    return st, (S, cov, Rnum, Wnum, b, stop, bd)
+
+
+def merge_stats(acc, st):
+    for k, v in st.items():
+        a = acc.setdefault(k, dict(launches=0, ms=0.0, timed=0, units=0))
+        for f in a:
+            a[f] += v[f]
+
+
+def run_gpu(args, rank, world):
+    import torch
+    import paper_2306_03651_gb300 as P
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    desc, make = WORKLOADS[args.workload]
+    wl = make()
+    g = wl.graph
+    graph = P.Graph.of(g)
+    M = args.m
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
+    seed0 = 1_000_003 * (rank + 1)
+    for w in range(args.warmup):
+        gpu_step(P, graph, wl, M, seed0 + w)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    stats, times = {}, []
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        st, _ = gpu_step(P, graph, wl, M, seed0 + 1000 + s)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+        merge_stats(stats, st)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = total_ms / args.steps
+    value = world * M * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers: graph upload from
+    # pinned memory, the round, results back to the host
+    e2e = None
+    if not args.no_e2e:
+        off_h = torch.from_numpy(g.off).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        torch.cuda.synchronize()
+        et = []
+        for s in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            gg = P.Graph(g.n, off_h.numpy(), col_h.numpy(), g.directed)
+            job = P.Job(gg, seed0 + 2000 + s, wl.t)
+            job.sample(M)
+            S, cov = job.greedy_cover(wl.k)
+            Rnum, Wnum, b = job.mcera(wl.k)
+            P.bounds(cov, M, int(Rnum.sum()), wl.t, Wnum, b, wl.eps, wl.delta, 1)
+            job.close()
+            gg.close()
+            torch.cuda.synchronize()
+            et.append(time.perf_counter() - t1)
+        e_tot = sum(et)
+        if world > 1:
+            t = torch.tensor([e_tot], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_tot = float(t.item())
+        e2e = {"value": world * M * args.steps / e_tot, "unit": "paths/s",
+               "h2d_bytes_per_step": int(g.off.nbytes + g.col.nbytes),
+               "d2h_bytes_per_step": int(4 * wl.k + 8 * wl.t + 8 + 4 + 8 + 4)}
+
+    # roofline: the kernel class with the most device time; its algorithmic
+    # bytes are counted by the kernels themselves
+    import json as _json
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            pk = _json.load(f)
+        peak, peak_src = float(pk["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    byte_classes = ("expand_pull", "expand_push", "level_finalize", "cone", "cone_sigma")
+    dom = max(stats, key=lambda k: stats[k]["ms"])
+    roof = None
+    if stats[dom]["ms"] > 0:
+        avg_ms = stats[dom]["ms"] / max(stats[dom]["timed"], 1)
+        per_launch_bytes = stats[dom]["units"] / max(stats[dom]["launches"], 1)
+        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if dom in byte_classes else None
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
+                "avg_launch_ms": avg_ms, "launches": stats[dom]["launches"]}
+    launches = int(sum(v["launches"] for v in stats.values()))
+    out = {
+        "metric": "sampled paths/s", "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}; one Algorithm-1 round per step at m={M} pairs, "
+                               f"k={wl.k}, t={wl.t}, eps={wl.eps}, delta={wl.delta}",
+                   "n": g.n, "arcs": g.nnz, "pairs_per_step": M, "l2": "flushed (256 MB write) between steps",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+        "wall_s": wall,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "units": v["units"]}
+                    for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},
+    }
+    return out, wl
+
+
+# ---------------------------------------------------------------- cpu oracle
+def oracle_rate(wl, seconds: float, seed: int = 424242):
+    """The oracle (single thread) on a bounded sample: pairs, walks, greedyCover, AMCERA, bounds."""
+    import oracle as O
+
+    og = O.Graph.of(wl.graph)
+    probe = O.Job(og, seed, wl.t)
+    t0 = time.perf_counter()
+    probe.sample(4)
+    per = max((time.perf_counter() - t0) / 4, 1e-6)
+    count = int(max(8, min(200000, seconds / per)))
+    job = O.Job(og, seed + 1, wl.t)
+    t0 = time.perf_counter()
+    job.sample(count)
+    S, cov = job.greedy_cover(wl.k)
+    Rn, Wn, b = job.mcera(wl.k)
+    O.bounds(cov, count, int(Rn.sum()), wl.t, Wn, b, wl.eps, wl.delta, 1)
+    el = time.perf_counter() - t0
+    return count / el, count, el
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        desc, make = WORKLOADS[args.workload]
+        wl = make()
+        for _ in range(args.warmup):
+            oracle_rate(wl, min(2.0, args.cpu_seconds / 4))
+        rates, counts, els = [], [], []
+        for _ in range(args.steps):
+            r, c, e = oracle_rate(wl, args.cpu_seconds / max(args.steps, 1))
+            rates.append(r)
+            counts.append(c)
+            els.append(e)
+        tot = sum(counts) / sum(els)
+        sample = f"{sum(counts)} pairs over {args.steps} steps ({sum(els):.1f} s), each step one oracle round"
+        print(json.dumps({
+            "impl": "reference", "metric": "sampled paths/s", "value": tot, "unit": "paths/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(els) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {desc}; one Algorithm-1 round per step (bounded sample), "
+                                   f"k={wl.k}, t={wl.t}", "n": wl.graph.n, "arcs": wl.graph.nnz},
+            "cpu_baseline": {"value": tot, "unit": "paths/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": tot, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out, wl = run_gpu(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            r, c, e = oracle_rate(wl, args.cpu_seconds)
+            out["cpu_baseline"] = {"value": r, "unit": "paths/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"{c} pairs of the same workload, one oracle round ({e:.1f} s)"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,147 @@
+/*
+ * cen.h -- C ABI of the GB300 CentRA sample-and-cover library (libcen.so).
+ *
+ * CentRA (Pellegrina, "Efficient Centrality Maximization with Rademacher
+ * Averages", KDD'23) approximates the size-k node set of maximum set
+ * betweenness: it draws random shortest paths (hyper-edges), runs greedy
+ * max-coverage on them, bounds the supremum deviation with Monte Carlo
+ * Rademacher averages, and doubles the sample until its stopping rule certifies
+ * a (1 - 1/e - eps)-approximation with probability >= 1 - delta (Algorithm 1).
+ *
+ * Conventions for every entry point:
+ *   - Return value: int status, CEN_OK (0) or a negative CEN_E* code; the
+ *     message of the last failure on the calling thread is in cen_last_error().
+ *     No C++ exception crosses this boundary.
+ *   - Node ids are int32 in [0, n); CSR offsets are int64.
+ *   - Pointers documented as "host" must be host memory; "device" must be
+ *     device memory of the current CUDA device.  Output arrays are owned by
+ *     the caller; every handle is owned by the library until its _free call.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     returns only after its GPU work on that stream is complete.
+ *   - A job handle is not thread-safe; distinct jobs may be used from distinct
+ *     threads.  All device memory is allocated by the library, stream-ordered.
+ *   - Randomness is Philox4x32-10 keyed by the job seed with counter
+ *     (j_lo, j_hi, purpose, attempt) for sample j: results depend only on
+ *     (graph, seed, parameters), never on launch configuration or timing.
+ */
+#ifndef CEN_H
+#define CEN_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CEN_OK 0
+#define CEN_EINVAL (-1)        /* bad argument or malformed graph */
+#define CEN_ENOMEM (-2)        /* device allocation failed */
+#define CEN_ECUDA (-3)         /* a CUDA runtime call or kernel failed */
+#define CEN_EOVERFLOW (-4)     /* a sampled pair has >= 2^128 shortest paths */
+#define CEN_ENOTCERTIFIED (-5) /* cen_run: the next sample size would exceed m_cap */
+#define CEN_ETIMEOUT (-6)      /* a bounded device-side wait ran out */
+
+#define CEN_LOG_COLS 16 /* per-round log row, see cen_run */
+
+typedef struct cen_graph cen_graph;
+typedef struct cen_job cen_job;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int cen_version(void);
+
+/* Text of the last failure on the calling thread ("" if none). */
+const char *cen_last_error(void);
+
+/* Graph G = (V, E) of Sec. 3.1, as a canonical CSR: off[n+1] (int64, off[0] =
+ * 0, nondecreasing, off[n] = nnz), col[nnz] (int32), every row strictly
+ * ascending, no self-loops.  Undirected graphs list both arcs of each edge
+ * and set directed = 0; directed graphs list out-arcs.  `on_device` says
+ * whether off/col are device (1) or host (0) pointers; they are copied, the
+ * caller keeps them.  The copy is validated on the GPU; a malformed CSR gives
+ * CEN_EINVAL.  n >= 2.  For directed graphs the in-arc CSR is built on the GPU. */
+int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
+                   void *stream, cen_graph **out);
+int cen_graph_free(cen_graph *g);
+int cen_graph_info(const cen_graph *g, int32_t *n, int64_t *nnz, int *directed);
+
+/* A job holds the growing sample H (Alg. 1 "H_i") for one (graph, seed, t).
+ * t >= 1 is the number of Rademacher vectors (rows of sigma, Sec. 3.2). */
+int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, cen_job **out);
+int cen_job_free(cen_job *job);
+/* m = samples drawn so far; members = sum of |h| over them. */
+int cen_job_size(const cen_job *job, uint64_t *m, int64_t *members);
+
+/* Alg. 1 "sampleHEs(H, m_new)" for set betweenness (Sec. 3.1, Sec. 5):
+ * appends samples j = m .. m+m_new-1.  Sample j draws s uniform in V and t
+ * uniform in V \ {s}; counts shortest paths from s (BFS, exact, to 2^128);
+ * draws one shortest s->t path uniformly by a backward walk from t; and
+ * appends the path's interior nodes (s->t order) as hyper-edge h_j (empty if
+ * t is unreachable or adjacent).  Also extends the sign matrix sigma by the
+ * columns j (Alg. 1 "sampleRadeVars", extended rather than redrawn).
+ * CEN_EOVERFLOW if some pair has >= 2^128 shortest paths (job unchanged). */
+int cen_sample(cen_job *job, uint64_t m_new);
+
+/* Alg. 1 "greedyCover(k, H)" (Sec. 3.1): k times add the node covering the
+ * most still-uncovered samples (lowest id on ties); stop early when that
+ * count is 0.  S_out[k] (host) receives the picks in order, *S_size their
+ * number, *covered = |{j : h_j meets S}| = m * C_H(S). */
+int cen_greedy_cover(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered);
+
+/* AMCERA numerators (Sec. 4.1, Alg. 1 lines computing r_j^u and r_j), all
+ * integers: with R_q^u = sum_{j: u in h_j} sigma_{q,j} (= m r_q^u),
+ * Rnum_out[q] (host, t entries) = sum of the <= k largest positive R_q^u,
+ * *Wnum_out = sum of the k largest c_u = |{j: u in h_j}|, *b_out = max |h_j|.
+ * Then AMCERA = sum_q Rnum_q / (t m) and the wimpy variance w = b Wnum / m. */
+int cen_mcera(cen_job *job, int32_t k, int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out);
+
+/* Host FP64 bounds of Thm. "bound_dev" (eq. "epsrade", ln(5/delta_i)) and the
+ * stopping test of Alg. 1 at iteration i >= 1 (delta_i = delta / 2^i).
+ * out[8] = C, AMCERA, w, nu, xi, R~, R, eta.  *stop = 1 iff
+ * (1-1/e)((1-1/e-eps) xi + eta) <= eps C.  Pure host code; no GPU work. */
+int cen_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
+               double delta, int32_t i, double *out, int32_t *stop);
+
+/* Algorithm 1 end to end on one graph: m_i = m0 2^(i-1) samples in round i,
+ * greedyCover, AMCERA, bounds, stop test.  Requires k >= 1, t >= 1,
+ * 0 < eps < 1 - 1/e, 0 < delta < 1, 1 <= m0 <= m_cap.  S_out (host, capacity
+ * k), *S_size, *covered, *m_final, *rounds describe the last round; log (host,
+ * may be NULL) receives min(rounds, max_rounds) rows of CEN_LOG_COLS doubles:
+ * i, m_i, covered, Rsum, Wnum, b, C, AMCERA, w, nu, xi, R~, R, eta, stop, |S|.
+ * Returns CEN_OK when certified, CEN_ENOTCERTIFIED when the next sample size
+ * would exceed m_cap (outputs then describe the last round), or an error. */
+int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+            uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
+            int32_t *rounds, double *log, int32_t max_rounds);
+
+/* ---- inspection (copies device state to host; for tests and tooling) ---- */
+/* hoff[m+1], hmem[members], s[m], t[m], d[m] (d = -1 when unreachable); any may be NULL. */
+int cen_job_copy_samples(const cen_job *job, int64_t *hoff, int32_t *hmem, int32_t *s, int32_t *t, int32_t *d);
+/* The node -> samples incidence built by the last greedy/mcera call: noff[n+1],
+ * nsamp[members] (each node's sample ids, as a set: order within a row is
+ * unspecified).  Either may be NULL. */
+int cen_job_copy_incidence(const cen_job *job, int64_t *noff, int32_t *nsamp);
+/* R[q * n + u] (int32, t x n) and c[n] from the last cen_mcera call. */
+int cen_job_copy_rade(const cen_job *job, int32_t *R, int32_t *c);
+/* Packed sign words of samples [0, m): words[j * ceil(t/32) + w], bit q%32 of word q/32 set iff sigma_{q,j} = +1. */
+int cen_job_copy_signs(const cen_job *job, uint32_t *words);
+
+/* ---- instrumentation ---- */
+/* Per-kernel-class launch counts, device time and work units since the job
+ * was created (or last reset).  Device time is recorded only while
+ * timing is enabled (CUDA events around each launch on the job stream). */
+#define CEN_NKCLASS 16
+typedef struct cen_kstat {
+  char name[32];
+  uint64_t launches;
+  double ms;          /* sum of event-timed durations (timing enabled only) */
+  uint64_t timed;     /* launches that were event-timed */
+  uint64_t units;     /* work units counted by the kernel (class-specific) */
+} cen_kstat;
+int cen_job_set_timing(cen_job *job, int enable);
+int cen_job_stats(cen_job *job, cen_kstat *out /* [CEN_NKCLASS] */, int32_t *nclasses);
+int cen_job_reset_stats(cen_job *job);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

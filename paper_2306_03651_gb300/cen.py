@@ -1,0 +1,270 @@
+"""ctypes binding of libcen.so (include/cen.h), the GB300 CentRA library.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The raw C entry points are exported under their C names (``cen_sample`` ...);
+``Graph``, ``Job``, ``run`` and ``bounds`` wrap them with numpy / torch
+arguments.  Streams default to torch's current CUDA stream.
+
+Importing this module loads ``libcen.so``, compiling it with nvcc first when
+it is absent; if that fails the import raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcen.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
+
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LOG_COLS = ("i", "m", "covered", "Rsum", "Wnum", "b", "C", "A", "w", "nu", "xi", "Rt", "R", "eta", "stop", "S_size")
+NKCLASS = 16
+
+
+class CenError(RuntimeError):
+    def __init__(self, rc: int, msg: str):
+        super().__init__(f"{msg} (status {rc})")
+        self.rc = rc
+
+
+class cen_kstat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
+                ("timed", ctypes.c_uint64), ("units", ctypes.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        from . import _build
+        try:
+            _build.build()
+        except Exception as e:  # no CUDA library means no product path
+            raise ImportError(f"libcen.so is missing and could not be built: {e}") from e
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, u64, dbl, vp, ip = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double,
+                                  ctypes.c_void_p, ctypes.c_int)
+    pvp = ctypes.POINTER(ctypes.c_void_p)
+    sigs = {
+        "cen_version": ([], ip),
+        "cen_last_error": ([], ctypes.c_char_p),
+        "cen_graph_load": ([vp, vp, i32, i64, ip, ip, vp, pvp], ip),
+        "cen_graph_free": ([vp], ip),
+        "cen_graph_info": ([vp, vp, vp, vp], ip),
+        "cen_job_create": ([vp, u64, i32, vp, pvp], ip),
+        "cen_job_free": ([vp], ip),
+        "cen_job_size": ([vp, vp, vp], ip),
+        "cen_sample": ([vp, u64], ip),
+        "cen_greedy_cover": ([vp, i32, vp, vp, vp], ip),
+        "cen_mcera": ([vp, i32, vp, vp, vp], ip),
+        "cen_bounds": ([u64, u64, i64, i32, i64, i32, dbl, dbl, i32, vp, vp], ip),
+        "cen_run": ([vp, i32, dbl, dbl, i32, u64, u64, u64, vp, vp, vp, vp, vp, vp, vp, i32], ip),
+        "cen_job_copy_samples": ([vp, vp, vp, vp, vp, vp], ip),
+        "cen_job_copy_incidence": ([vp, vp, vp], ip),
+        "cen_job_copy_rade": ([vp, vp, vp], ip),
+        "cen_job_copy_signs": ([vp, vp], ip),
+        "cen_job_set_timing": ([vp, ip], ip),
+        "cen_job_stats": ([vp, vp, vp], ip),
+        "cen_job_reset_stats": ([vp], ip),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+        globals()[name] = f
+    return lib
+
+
+_lib = _load()
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/cen.h."""
+    with open(HEADER) as f:
+        src = f.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cen_[a-z0-9_]+)\s*\(", src)))
+
+
+def last_error() -> str:
+    return (_lib.cen_last_error() or b"").decode()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise CenError(rc, f"{what}: {last_error()}")
+
+
+def _p(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def current_stream():
+    """torch's current CUDA stream handle (or None when torch/CUDA is absent)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class Graph:
+    """Device-resident canonical CSR graph (``cen_graph_load``)."""
+
+    def __init__(self, n: int, off, col, directed: bool = False, stream=None):
+        self.n = int(n)
+        self.directed = bool(directed)
+        self.stream = stream if stream is not None else current_stream()
+        if _is_torch_cuda(off):
+            on_dev, poff, pcol = 1, off.data_ptr(), col.data_ptr()
+            nnz = int(col.numel())
+            self._keep = (off, col)
+        else:
+            off = np.ascontiguousarray(off, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            on_dev, poff, pcol = 0, _p(off), _p(col)
+            nnz = int(off[-1])
+            self._keep = (off, col)
+        self.nnz = nnz
+        h = ctypes.c_void_p()
+        _check(_lib.cen_graph_load(poff, pcol, self.n, nnz, int(directed), on_dev, self.stream, ctypes.byref(h)),
+               "cen_graph_load")
+        self.h = h
+        self._keep = None
+
+    @classmethod
+    def of(cls, g, stream=None):
+        """From any object with n, off, col, directed (e.g. the inputs module's Graph)."""
+        return cls(g.n, g.off, g.col, g.directed, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.cen_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Job:
+    """The growing sample of one CentRA run (``cen_job_*``)."""
+
+    def __init__(self, graph: Graph, seed: int, t: int, stream=None):
+        self.graph = graph
+        self.seed = int(seed)
+        self.t = int(t)
+        self.nw = (self.t + 31) // 32
+        self.stream = stream if stream is not None else graph.stream
+        h = ctypes.c_void_p()
+        _check(_lib.cen_job_create(graph.h, self.seed, self.t, self.stream, ctypes.byref(h)), "cen_job_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.cen_job_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def size(self):
+        m, mem = ctypes.c_uint64(), ctypes.c_int64()
+        _check(_lib.cen_job_size(self.h, ctypes.byref(m), ctypes.byref(mem)), "cen_job_size")
+        return m.value, mem.value
+
+    @property
+    def m(self) -> int:
+        return self.size()[0]
+
+    def sample(self, m_new: int):
+        _check(_lib.cen_sample(self.h, int(m_new)), "cen_sample")
+
+    def greedy_cover(self, k: int):
+        S = np.empty(k, np.int32)
+        size, cov = ctypes.c_int32(), ctypes.c_uint64()
+        _check(_lib.cen_greedy_cover(self.h, k, _p(S), ctypes.byref(size), ctypes.byref(cov)), "cen_greedy_cover")
+        return S[: size.value].copy(), cov.value
+
+    def mcera(self, k: int):
+        Rnum = np.empty(self.t, np.int64)
+        W, b = ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.cen_mcera(self.h, k, _p(Rnum), ctypes.byref(W), ctypes.byref(b)), "cen_mcera")
+        return Rnum, W.value, b.value
+
+    def samples(self):
+        m, mem = self.size()
+        hoff = np.empty(m + 1, np.int64)
+        hmem = np.empty(max(mem, 1), np.int32)
+        s, t, d = (np.empty(max(m, 1), np.int32) for _ in range(3))
+        _check(_lib.cen_job_copy_samples(self.h, _p(hoff), _p(hmem), _p(s), _p(t), _p(d)), "cen_job_copy_samples")
+        return dict(hoff=hoff, hmem=hmem[:mem], s=s[:m], t=t[:m], d=d[:m])
+
+    def incidence(self):
+        _, mem = self.size()
+        noff = np.empty(self.graph.n + 1, np.int64)
+        nsamp = np.empty(max(mem, 1), np.int32)
+        _check(_lib.cen_job_copy_incidence(self.h, _p(noff), _p(nsamp)), "cen_job_copy_incidence")
+        return noff, nsamp[:mem]
+
+    def rade(self):
+        R = np.empty((self.t, self.graph.n), np.int32)
+        c = np.empty(self.graph.n, np.int32)
+        _check(_lib.cen_job_copy_rade(self.h, _p(R), _p(c)), "cen_job_copy_rade")
+        return R, c
+
+    def signs(self):
+        m = self.m
+        w = np.empty((max(m, 1), self.nw), np.uint32)
+        _check(_lib.cen_job_copy_signs(self.h, _p(w)), "cen_job_copy_signs")
+        return w[:m]
+
+    def set_timing(self, enable: bool):
+        _check(_lib.cen_job_set_timing(self.h, int(enable)), "cen_job_set_timing")
+
+    def reset_stats(self):
+        _check(_lib.cen_job_reset_stats(self.h), "cen_job_reset_stats")
+
+    def stats(self) -> dict:
+        arr = (cen_kstat * NKCLASS)()
+        nc = ctypes.c_int32()
+        _check(_lib.cen_job_stats(self.h, arr, ctypes.byref(nc)), "cen_job_stats")
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, timed=arr[i].timed,
+                                           units=arr[i].units) for i in range(nc.value)}
+
+
+def bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i):
+    """``cen_bounds``: (stop, dict C, A, w, nu, xi, Rt, R, eta)."""
+    out = np.zeros(8, np.float64)
+    stop = ctypes.c_int32()
+    _check(_lib.cen_bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i, _p(out), ctypes.byref(stop)), "cen_bounds")
+    return bool(stop.value), dict(zip(("C", "A", "w", "nu", "xi", "Rt", "R", "eta"), out.tolist()))
+
+
+def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: int = 1000, m_cap: int = 1 << 30,
+        stream=None, max_rounds: int = 64) -> dict:
+    """``cen_run`` (Algorithm 1): certified top-k set; status OK or ENOTCERTIFIED."""
+    S = np.empty(k, np.int32)
+    size, rounds = ctypes.c_int32(), ctypes.c_int32()
+    cov, mf = ctypes.c_uint64(), ctypes.c_uint64()
+    log = np.zeros((max_rounds, 16), np.float64)
+    st = stream if stream is not None else graph.stream
+    rc = _lib.cen_run(graph.h, k, eps, delta, t, seed, m0, m_cap, st, _p(S), ctypes.byref(size), ctypes.byref(cov),
+                      ctypes.byref(mf), ctypes.byref(rounds), _p(log), max_rounds)
+    if rc not in (OK, ENOTCERTIFIED):
+        _check(rc, "cen_run")
+    return dict(status=rc, S=S[: size.value].copy(), covered=cov.value, m_final=mf.value, rounds=rounds.value,
+                log=log[: min(rounds.value, max_rounds)].copy())

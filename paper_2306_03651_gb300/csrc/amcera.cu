@@ -1,0 +1,179 @@
+// AMCERA numerators (Sec. 4.1; Alg. 1 lines computing r_j^u, r_j and the average).
+//
+// R_q^u = sum over samples j holding u of sigma_{q,j} = 2 P_q^u - c_u, where
+// P_q^u counts u's samples whose sign bit q is set.  The sup over |S| <= k of
+// sum_{u in S} R_q^u is the sum of the <= k largest positive R_q^u (the
+// objective is additive in S), found per row by an exact MSB-first radix
+// select; the same select over c_u gives the wimpy-variance numerator.
+#include "job.cuh"
+
+namespace cen {
+
+// Warp per node u with c_u > 0: lanes take 32 incident samples at a time; for
+// each sign word the warp ballots bit q across the 32 samples and lane q adds
+// the popcount.
+__global__ void __launch_bounds__(256) k_rade(int32_t n, int t, int nw, const int64_t *__restrict__ noff,
+                                              const int32_t *__restrict__ nsamp, const uint32_t *__restrict__ sign,
+                                              int32_t *R, unsigned long long *units) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long scanned = 0;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += nwarps) {
+    const int64_t r0 = noff[u], r1 = noff[u + 1];
+    const int32_t cu = (int32_t)(r1 - r0);
+    if (cu == 0) continue;  // R rows are zero-filled
+    for (int w = 0; w < nw; ++w) {
+      int32_t P = 0;
+      for (int64_t base = r0; base < r1; base += 32) {
+        const int64_t i = base + lane;
+        const uint32_t x = i < r1 ? sign[(int64_t)nsamp[i] * nw + w] : 0u;
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+          const int c = __popc(__ballot_sync(0xffffffffu, (x >> q) & 1u));
+          if (lane == q) P += c;
+        }
+      }
+      const int q = 32 * w + lane;
+      if (q < t) R[(int64_t)q * n + u] = 2 * P - cu;
+    }
+    scanned += (unsigned long long)cu;
+  }
+  if (lane == 0 && scanned) atomicAdd(units, scanned);
+}
+
+// ------------------------------------------------------------ radix select
+// Per row: prefix/mask of the k-th largest positive value found so far, the
+// count still to take (krem) and the sum of values already known to be in.
+struct SelRow {
+  uint32_t prefix, mask;
+  int32_t krem;
+  int32_t done;
+  long long sum;
+};
+
+__global__ void k_sel_init(SelRow *rows, int nrows, int32_t k) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x)
+    rows[r] = SelRow{0u, 0u, k, 0, 0ll};
+}
+
+// Histogram of digit `shift` over positive values matching the row's prefix.
+__global__ void __launch_bounds__(256) k_sel_hist(const int32_t *__restrict__ vals, int64_t n, int nrows, int shift,
+                                                  const SelRow *__restrict__ rows, unsigned int *hcnt,
+                                                  unsigned long long *hsum) {
+  __shared__ unsigned int sc[256];
+  __shared__ unsigned long long ss[256];
+  const int r = blockIdx.y;
+  const SelRow row = rows[r];
+  if (row.done) return;
+  sc[threadIdx.x] = 0;
+  ss[threadIdx.x] = 0;
+  __syncthreads();
+  const int32_t *v = vals + (int64_t)r * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = v[i];
+    if (x > 0 && ((uint32_t)x & row.mask) == row.prefix) {
+      const uint32_t d = ((uint32_t)x >> shift) & 255u;
+      atomicAdd(&sc[d], 1u);
+      atomicAdd(&ss[d], (unsigned long long)x);
+    }
+  }
+  __syncthreads();
+  if (sc[threadIdx.x]) {
+    atomicAdd(&hcnt[r * 256 + threadIdx.x], sc[threadIdx.x]);
+    atomicAdd(&hsum[r * 256 + threadIdx.x], ss[threadIdx.x]);
+  }
+}
+
+// One thread per row: walk digits from the top, take whole buckets while
+// they fit in krem, descend into the bucket that crosses krem.
+__global__ void k_sel_step(int nrows, int shift, SelRow *rows, unsigned int *hcnt, unsigned long long *hsum) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  SelRow row = rows[r];
+  if (!row.done) {
+    long long total = 0;
+    for (int d = 0; d < 256; ++d) total += hcnt[r * 256 + d];
+    if (total <= row.krem) {  // every matching value is in
+      for (int d = 0; d < 256; ++d) row.sum += (long long)hsum[r * 256 + d];
+      row.krem = 0;
+      row.done = 1;
+    } else {
+      for (int d = 255; d >= 0; --d) {
+        const int c = (int)hcnt[r * 256 + d];
+        if (c < row.krem) {
+          row.krem -= c;
+          row.sum += (long long)hsum[r * 256 + d];
+        } else {
+          row.prefix |= (uint32_t)d << shift;
+          row.mask |= 255u << shift;
+          break;
+        }
+      }
+      if (shift == 0) {  // prefix is now the exact k-th value; krem copies of it remain
+        row.sum += (long long)row.krem * (long long)row.prefix;
+        row.krem = 0;
+        row.done = 1;
+      }
+    }
+    rows[r] = row;
+  }
+  for (int d = 0; d < 256; ++d) {
+    hcnt[r * 256 + d] = 0;
+    hsum[r * 256 + d] = 0;
+  }
+}
+
+// Sum of the <= k largest positive entries of each of `nrows` rows of length n.
+static void topk_positive_sum(cen_job *job, const int32_t *vals, int64_t n, int nrows, int32_t k, long long *out_host) {
+  cudaStream_t st = job->st;
+  Stats *S = &job->stats;
+  job->selst.ensure(sizeof(SelRow) * (size_t)nrows, st);
+  job->selh.ensure((size_t)nrows * 256 * (4 + 8), st);
+  SelRow *rows = job->selst.as<SelRow>();
+  unsigned int *hcnt = job->selh.as<unsigned int>();
+  unsigned long long *hsum = (unsigned long long *)(hcnt + (size_t)nrows * 256);
+  CEN_CK(cudaMemsetAsync(job->selh.p, 0, (size_t)nrows * 256 * 12, st));
+  launch(S, K_SELECT, st, [&] { k_sel_init<<<grid_for(nrows, 128), 128, 0, st>>>(rows, nrows, k); });
+  const int bx = grid_for((size_t)n, 256 * 8, 512);
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    launch(S, K_SELECT, st, [&] {
+      k_sel_hist<<<dim3(bx, nrows), 256, 0, st>>>(vals, n, nrows, shift, rows, hcnt, hsum);
+    });
+    launch(S, K_SELECT, st, [&] { k_sel_step<<<grid_for(nrows, 64), 64, 0, st>>>(nrows, shift, rows, hcnt, hsum); });
+  }
+  SelRow *h = (SelRow *)host_staging(job, sizeof(SelRow) * (size_t)nrows);
+  CEN_CK(cudaMemcpyAsync(h, rows, sizeof(SelRow) * (size_t)nrows, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrows; ++r) out_host[r] = h[r].sum;
+}
+
+void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
+  CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_mcera: k must be >= 1");
+  build_incidence(job);
+  cudaStream_t st = job->st;
+  Stats *S = &job->stats;
+  const int32_t n = job->g->n;
+  const int t = job->t;
+  job->R.ensure(4 * (size_t)n * t, st);
+  CEN_CK(cudaMemsetAsync(job->R.p, 0, 4 * (size_t)n * t, st));
+  launch(S, K_RADE, st, [&] {
+    k_rade<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(n, t, job->nw, job->noff.as<int64_t>(),
+                                                                      job->nsamp.as<int32_t>(),
+                                                                      job->sign.as<uint32_t>(), job->R.as<int32_t>(),
+                                                                      (unsigned long long *)(job->stats.d_units + K_RADE));
+  });
+  std::vector<long long> rn(t);
+  topk_positive_sum(job, job->R.as<int32_t>(), n, t, k, rn.data());
+  for (int q = 0; q < t; ++q) Rnum[q] = rn[q];
+  long long w = 0;
+  topk_positive_sum(job, job->c.as<int32_t>(), n, 1, k, &w);
+  *Wnum = w;
+  int hb = 0;
+  CEN_CK(cudaMemcpyAsync(host_staging(job, 4), job->bmax.p, 4, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  memcpy(&hb, host_staging(job, 4), 4);
+  *b = job->m ? hb : 0;
+  job->rade_valid_k = k;
+}
+
+}  // namespace cen

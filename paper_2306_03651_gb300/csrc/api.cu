@@ -1,0 +1,349 @@
+// C ABI of libcen (include/cen.h): argument checks, handle lifetimes,
+// Algorithm 1's progressive loop and the FP64 bounds.  Every entry point
+// converts internal failures into a status code and a thread-local message.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "job.cuh"
+
+namespace cen {
+const std::string &last_error();
+
+void *host_staging(cen_job *job, size_t bytes) {
+  if (bytes > job->host_bytes) {
+    if (job->host) cudaFreeHost(job->host);
+    job->host = nullptr;
+    job->host_bytes = 0;
+    size_t cap = 4096;
+    while (cap < bytes) cap *= 2;
+    CEN_CK(cudaMallocHost(&job->host, cap));
+    job->host_bytes = cap;
+  }
+  return job->host;
+}
+
+// Thm. "bound_dev" (eq. "epsrade") with ln(5/delta_i) and the xi / stopping
+// lines of Alg. 1.  Evaluation order (a = 1 - 1/e, L = ln(5/delta_i), Lm = L/m):
+//   C = covered/m;  A = Rsum/(t m);  w = (b Wnum)/m
+//   xi = sqrt(Lm Lm + (2 C L)/(a m)) + Lm;   nu = C/a + xi
+//   Rt = A + sqrt((4 w L)/(t m));   R = Rt + sqrt(Lm Lm + (2 L Rt)/m) + Lm
+//   eta = 2 R + sqrt((2 L (nu + 4 R))/m) + L/(3 m)
+//   stop <=> a ((a - eps) xi + eta) <= eps C
+static int bounds_fp64(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
+                       double delta, int32_t i, double *out) {
+  const double a = 1.0 - exp(-1.0);
+  const double md = (double)m;
+  const double L = log(5.0 / ldexp(delta, -i));
+  const double Lm = L / md;
+  const double C = (double)covered / md;
+  const double A = (double)Rsum / ((double)t * md);
+  const double w = ((double)b * (double)Wnum) / md;
+  const double xi = sqrt(Lm * Lm + (2.0 * C * L) / (a * md)) + Lm;
+  const double nu = C / a + xi;
+  const double Rt = A + sqrt((4.0 * w * L) / ((double)t * md));
+  const double R = Rt + sqrt(Lm * Lm + (2.0 * L * Rt) / md) + Lm;
+  const double eta = 2.0 * R + sqrt((2.0 * L * (nu + 4.0 * R)) / md) + L / (3.0 * md);
+  out[0] = C;
+  out[1] = A;
+  out[2] = w;
+  out[3] = nu;
+  out[4] = xi;
+  out[5] = Rt;
+  out[6] = R;
+  out[7] = eta;
+  return (a * ((a - eps) * xi + eta) <= eps * C) ? 1 : 0;
+}
+
+}  // namespace cen
+
+using cen::Error;
+
+#define CEN_API_BEGIN try {
+#define CEN_API_END                                  \
+  return CEN_OK;                                     \
+  }                                                  \
+  catch (const Error &e) {                           \
+    cen::set_last_error(e.msg);                      \
+    return e.code;                                   \
+  }                                                  \
+  catch (const std::bad_alloc &) {                   \
+    cen::set_last_error("host allocation failed");   \
+    return CEN_ENOMEM;                               \
+  }                                                  \
+  catch (...) {                                      \
+    cen::set_last_error("unexpected internal error"); \
+    return CEN_ECUDA;                                \
+  }
+
+extern "C" {
+
+int cen_version(void) { return 100; }
+
+const char *cen_last_error(void) { return cen::last_error().c_str(); }
+
+int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
+                   void *stream, cen_graph **out) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(out && off && (col || nnz == 0), CEN_EINVAL, "cen_graph_load: null argument");
+  CEN_REQUIRE(n >= 2 && nnz >= 0, CEN_EINVAL, "cen_graph_load: need n >= 2 and nnz >= 0");
+  *out = nullptr;
+  cen_graph *g = new cen_graph();
+  g->n = n;
+  g->nnz = nnz;
+  g->directed = directed ? 1 : 0;
+  g->st = (cudaStream_t)stream;
+  try {
+    cen::graph_build(g, off, col, on_device != 0, nullptr);
+  } catch (...) {
+    delete g;
+    throw;
+  }
+  *out = g;
+  CEN_API_END
+}
+
+int cen_graph_free(cen_graph *g) {
+  CEN_API_BEGIN
+  if (g) {
+    cudaStream_t st = g->st;
+    delete g;
+    CEN_CK(cudaStreamSynchronize(st));
+  }
+  CEN_API_END
+}
+
+int cen_graph_info(const cen_graph *g, int32_t *n, int64_t *nnz, int *directed) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(g, CEN_EINVAL, "cen_graph_info: null graph");
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (directed) *directed = g->directed;
+  CEN_API_END
+}
+
+int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, cen_job **out) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(g && out, CEN_EINVAL, "cen_job_create: null argument");
+  CEN_REQUIRE(t >= 1 && t <= 4096, CEN_EINVAL, "cen_job_create: need 1 <= t <= 4096");
+  *out = nullptr;
+  cen_job *job = new cen_job();
+  job->g = g;
+  job->seed = seed;
+  job->t = t;
+  job->nw = (t + 31) / 32;
+  job->st = (cudaStream_t)stream;
+  try {
+    job->stats.init(job->st);
+  } catch (...) {
+    delete job;
+    throw;
+  }
+  *out = job;
+  CEN_API_END
+}
+
+int cen_job_free(cen_job *job) {
+  CEN_API_BEGIN
+  if (job) {
+    cudaStream_t st = job->st;
+    cudaStreamSynchronize(st);
+    void *h = job->host;
+    delete job;
+    CEN_CK(cudaStreamSynchronize(st));
+    if (h) cudaFreeHost(h);
+  }
+  CEN_API_END
+}
+
+int cen_job_size(const cen_job *job, uint64_t *m, int64_t *members) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_job_size: null job");
+  if (m) *m = job->m;
+  if (members) *members = job->members;
+  CEN_API_END
+}
+
+int cen_sample(cen_job *job, uint64_t m_new) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_sample: null job");
+  CEN_REQUIRE(job->m + m_new < (1ull << 31), CEN_EINVAL, "cen_sample: at most 2^31 - 1 samples per job");
+  cen::sample_append(job, m_new);
+  job->stats.resolve();
+  CEN_API_END
+}
+
+int cen_greedy_cover(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && S_out && S_size && covered, CEN_EINVAL, "cen_greedy_cover: null argument");
+  cen::greedy_cover(job, k, S_out, S_size, covered);
+  job->stats.resolve();
+  CEN_API_END
+}
+
+int cen_mcera(cen_job *job, int32_t k, int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && Rnum_out && Wnum_out && b_out, CEN_EINVAL, "cen_mcera: null argument");
+  cen::mcera(job, k, Rnum_out, Wnum_out, b_out);
+  job->stats.resolve();
+  CEN_API_END
+}
+
+int cen_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
+               double delta, int32_t i, double *out, int32_t *stop) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(out && stop && m >= 1 && t >= 1 && i >= 1 && delta > 0 && delta < 1, CEN_EINVAL,
+              "cen_bounds: need m >= 1, t >= 1, i >= 1, 0 < delta < 1");
+  *stop = cen::bounds_fp64(covered, m, Rsum, t, Wnum, b, eps, delta, i, out);
+  CEN_API_END
+}
+
+int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+            uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
+            int32_t *rounds, double *log, int32_t max_rounds) {
+  cen_job *job = nullptr;
+  int rc = CEN_OK;
+  try {
+    const double a = 1.0 - exp(-1.0);
+    CEN_REQUIRE(g && S_out && S_size && covered && m_final && rounds, CEN_EINVAL, "cen_run: null argument");
+    CEN_REQUIRE(k >= 1 && t >= 1 && eps > 0.0 && eps < a && delta > 0.0 && delta < 1.0 && m0 >= 1 && m_cap >= m0,
+                CEN_EINVAL, "cen_run: need k >= 1, t >= 1, 0 < eps < 1-1/e, 0 < delta < 1, 1 <= m0 <= m_cap");
+    int crc = cen_job_create(g, seed, t, stream, &job);
+    if (crc) return crc;
+    std::vector<int64_t> Rnum(t);
+    uint64_t m_prev = 0, m_i = m0;
+    rc = CEN_ENOTCERTIFIED;
+    for (int32_t i = 1;; ++i) {
+      cen::sample_append(job, m_i - m_prev);
+      uint64_t cov = 0;
+      cen::greedy_cover(job, k, S_out, S_size, &cov);
+      int64_t Wnum = 0;
+      int32_t b = 0;
+      cen::mcera(job, k, Rnum.data(), &Wnum, &b);
+      int64_t Rsum = 0;
+      for (int q = 0; q < t; ++q) Rsum += Rnum[q];
+      double bd[8];
+      const int stop = cen::bounds_fp64(cov, m_i, Rsum, t, Wnum, b, eps, delta, i, bd);
+      if (log && i <= max_rounds) {
+        double *row = log + (size_t)(i - 1) * CEN_LOG_COLS;
+        row[0] = i;
+        row[1] = (double)m_i;
+        row[2] = (double)cov;
+        row[3] = (double)Rsum;
+        row[4] = (double)Wnum;
+        row[5] = b;
+        for (int q = 0; q < 8; ++q) row[6 + q] = bd[q];
+        row[14] = stop;
+        row[15] = *S_size;
+      }
+      *covered = cov;
+      *m_final = m_i;
+      *rounds = i;
+      if (stop) {
+        rc = CEN_OK;
+        break;
+      }
+      if (m_i > m_cap / 2) {
+        rc = CEN_ENOTCERTIFIED;
+        cen::set_last_error("cen_run: not certified within m_cap samples");
+        break;
+      }
+      m_prev = m_i;
+      m_i *= 2;
+    }
+  } catch (const Error &e) {
+    cen::set_last_error(e.msg);
+    rc = e.code;
+  } catch (...) {
+    cen::set_last_error("unexpected internal error");
+    rc = CEN_ECUDA;
+  }
+  if (job) cen_job_free(job);
+  return rc;
+}
+
+int cen_job_copy_samples(const cen_job *job, int64_t *hoff, int32_t *hmem, int32_t *s, int32_t *t, int32_t *d) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_job_copy_samples: null job");
+  cudaStream_t st = job->st;
+  if (hoff) {
+    if (job->m)
+      CEN_CK(cudaMemcpyAsync(hoff, job->hoff.p, 8 * (job->m + 1), cudaMemcpyDeviceToHost, st));
+    else
+      hoff[0] = 0;
+  }
+  if (hmem && job->members) CEN_CK(cudaMemcpyAsync(hmem, job->hmem.p, 4 * job->members, cudaMemcpyDeviceToHost, st));
+  if (s && job->m) CEN_CK(cudaMemcpyAsync(s, job->ps.p, 4 * job->m, cudaMemcpyDeviceToHost, st));
+  if (t && job->m) CEN_CK(cudaMemcpyAsync(t, job->pt.p, 4 * job->m, cudaMemcpyDeviceToHost, st));
+  if (d && job->m) CEN_CK(cudaMemcpyAsync(d, job->pd.p, 4 * job->m, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  CEN_API_END
+}
+
+int cen_job_copy_incidence(const cen_job *job, int64_t *noff, int32_t *nsamp) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && job->inc_m == job->m, CEN_EINVAL,
+              "cen_job_copy_incidence: no incidence for the current sample (call cen_greedy_cover or cen_mcera)");
+  cudaStream_t st = job->st;
+  if (noff) CEN_CK(cudaMemcpyAsync(noff, job->noff.p, 8 * ((size_t)job->g->n + 1), cudaMemcpyDeviceToHost, st));
+  if (nsamp && job->members)
+    CEN_CK(cudaMemcpyAsync(nsamp, job->nsamp.p, 4 * job->members, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  CEN_API_END
+}
+
+int cen_job_copy_rade(const cen_job *job, int32_t *R, int32_t *c) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && job->rade_valid_k >= 0 && job->inc_m == job->m, CEN_EINVAL,
+              "cen_job_copy_rade: call cen_mcera first");
+  cudaStream_t st = job->st;
+  if (R) CEN_CK(cudaMemcpyAsync(R, job->R.p, 4 * (size_t)job->g->n * job->t, cudaMemcpyDeviceToHost, st));
+  if (c) CEN_CK(cudaMemcpyAsync(c, job->c.p, 4 * (size_t)job->g->n, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  CEN_API_END
+}
+
+int cen_job_copy_signs(const cen_job *job, uint32_t *words) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && words, CEN_EINVAL, "cen_job_copy_signs: null argument");
+  if (job->m)
+    CEN_CK(cudaMemcpyAsync(words, job->sign.p, 4 * (size_t)job->nw * job->m, cudaMemcpyDeviceToHost, job->st));
+  CEN_CK(cudaStreamSynchronize(job->st));
+  CEN_API_END
+}
+
+int cen_job_set_timing(cen_job *job, int enable) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_job_set_timing: null job");
+  CEN_CK(cudaStreamSynchronize(job->st));
+  job->stats.resolve();
+  job->stats.timing = enable != 0;
+  CEN_API_END
+}
+
+int cen_job_stats(cen_job *job, cen_kstat *out, int32_t *nclasses) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && out && nclasses, CEN_EINVAL, "cen_job_stats: null argument");
+  CEN_CK(cudaStreamSynchronize(job->st));
+  job->stats.resolve();
+  uint64_t units[cen::K_COUNT];
+  CEN_CK(cudaMemcpy(units, job->stats.d_units, sizeof(units), cudaMemcpyDeviceToHost));
+  for (int c = 0; c < cen::K_COUNT; ++c) {
+    out[c] = job->stats.k[c];
+    out[c].units = units[c];
+  }
+  *nclasses = cen::K_COUNT;
+  CEN_API_END
+}
+
+int cen_job_reset_stats(cen_job *job) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_job_reset_stats: null job");
+  CEN_CK(cudaStreamSynchronize(job->st));
+  job->stats.reset(job->st);
+  CEN_CK(cudaStreamSynchronize(job->st));
+  CEN_API_END
+}
+
+}  // extern "C"

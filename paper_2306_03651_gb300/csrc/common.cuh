@@ -1,0 +1,222 @@
+// Shared internals of libcen: error handling, stream-ordered device buffers,
+// the Philox4x32-10 generator, warp helpers and per-kernel accounting.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "cen.h"
+
+namespace cen {
+
+// ----------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string &msg);
+void set_last_error(const std::string &msg);
+
+#define CEN_CK(call)                                                                              \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      ::cen::fail(e_ == cudaErrorMemoryAllocation ? CEN_ENOMEM : CEN_ECUDA,                       \
+                  std::string(#call) + ": " + cudaGetErrorString(e_) + " (" + __FILE__ + ":" +      \
+                      std::to_string(__LINE__) + ")");                                            \
+  } while (0)
+
+#define CEN_REQUIRE(cond, code, text) \
+  do {                                \
+    if (!(cond)) ::cen::fail((code), (text)); \
+  } while (0)
+
+// ------------------------------------------------ stream-ordered buffers
+// Device memory owned by the library, allocated and freed in stream order.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    bytes = 0;
+  }
+  // Ensure capacity >= need bytes; keeps the first `keep` bytes of old content.
+  void ensure(size_t need, cudaStream_t s, size_t keep = 0) {
+    st = s;
+    if (need <= bytes && p) return;
+    size_t cap = bytes ? bytes : 256;
+    while (cap < need) cap = cap + cap / 2 + 256;
+    void *np = nullptr;
+    CEN_CK(cudaMallocAsync(&np, cap, s));
+    if (p && keep) CEN_CK(cudaMemcpyAsync(np, p, keep < bytes ? keep : bytes, cudaMemcpyDeviceToDevice, s));
+    if (p) CEN_CK(cudaFreeAsync(p, s));
+    p = np;
+    bytes = cap;
+  }
+  template <class T>
+  T *as() const { return static_cast<T *>(p); }
+};
+
+// ------------------------------------------------------------- Philox
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11): each round
+// multiplies counter words 0 and 2 by the two round multipliers, the high
+// halves are mixed with words 1 and 3 and the round key; the key advances by
+// the two Weyl increments.  Counter for sample j: (j_lo, j_hi, purpose, word3).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+constexpr uint32_t kPurposeS = 0u, kPurposeT = 1u, kPurposeWalk0 = 2u, kPurposeSign = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(kPhiloxM0, c.x), lo0 = kPhiloxM0 * c.x;
+    const uint32_t hi1 = __umulhi(kPhiloxM1, c.z), lo1 = kPhiloxM1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += kPhiloxW0;
+    k.y += kPhiloxW1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 philox_block(uint64_t seed, uint64_t j, uint32_t purpose, uint32_t w3) {
+  return philox(make_uint4((uint32_t)j, (uint32_t)(j >> 32), purpose, w3),
+                make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+typedef unsigned __int128 u128;
+
+// Uniform integer in [0, B), 1 <= B <= 2^64 - 1: bitmask rejection with
+// mask = 2^ceil(log2 B) - 1 over the low 64 bits of block (j, purpose, a).
+__device__ __forceinline__ uint64_t uniform_below64(uint64_t seed, uint64_t j, uint32_t purpose, uint64_t B) {
+  const int bits = (B <= 1) ? 0 : 64 - __clzll((long long)(B - 1));
+  const uint64_t mask = bits == 64 ? ~0ull : ((1ull << bits) - 1ull);
+  for (uint32_t a = 0;; ++a) {
+    const uint4 x = philox_block(seed, j, purpose, a);
+    const uint64_t v = ((uint64_t)x.x | ((uint64_t)x.y << 32)) & mask;
+    if (v < B) return v;
+  }
+}
+
+// Same rule for 1 <= B < 2^128: 64 bits while B <= 2^64, else all 128 bits.
+__device__ __forceinline__ u128 uniform_below128(uint64_t seed, uint64_t j, uint32_t purpose, u128 B) {
+  const u128 bm1 = B - 1;
+  const uint64_t hi = (uint64_t)(bm1 >> 64), lo = (uint64_t)bm1;
+  const int bits = B <= 1 ? 0 : (hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo));
+  const u128 mask = bits == 128 ? ~(u128)0 : (((u128)1 << bits) - 1);
+  const bool wide = B > ((u128)1 << 64);
+  for (uint32_t a = 0;; ++a) {
+    const uint4 x = philox_block(seed, j, purpose, a);
+    u128 v = (u128)x.x | ((u128)x.y << 32);
+    if (wide) v |= ((u128)x.z << 64) | ((u128)x.w << 96);
+    v &= mask;
+    if (v < B) return v;
+  }
+}
+
+// ----------------------------------------------------------- warp helpers
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_or64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ------------------------------------------------------- accounting
+enum KClass : int {
+  K_PAIRS = 0,   // pair draw + wave init
+  K_TCHECK,      // target check before each level
+  K_PUSH,        // top-down level expansion
+  K_PULL,        // bottom-up level expansion
+  K_LEVEL_FIN,   // level finalize (mask, visited, frontier list)
+  K_CONE,        // backward cone pass
+  K_SIGMA,       // path counts on the cone
+  K_WALK,        // backward walk + hyper-edge write
+  K_APPEND,      // lengths / offsets of new samples
+  K_SIGN,        // sign words
+  K_TRANSPOSE,   // node -> sample incidence
+  K_GREEDY,      // greedy argmax + update
+  K_RADE,        // R_q^u accumulation
+  K_SELECT,      // top-k positive sums
+  K_GRAPH,       // graph validation / in-CSR
+  K_MISC,        // scans, fills
+  K_COUNT
+};
+static_assert(K_COUNT <= CEN_NKCLASS, "too many kernel classes");
+extern const char *const kClassNames[K_COUNT];
+
+struct Stats {
+  cen_kstat k[CEN_NKCLASS];
+  bool timing = false;
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  uint64_t *d_units = nullptr;  // device counters [K_COUNT]
+  Stats();
+  ~Stats();
+  void init(cudaStream_t st);
+  cudaEvent_t ev();
+  void begin(int cls, cudaStream_t st, cudaEvent_t *a, cudaEvent_t *b);
+  void end(int cls, cudaStream_t st, cudaEvent_t a, cudaEvent_t b);
+  void resolve();  // stream must be synchronized
+  void reset(cudaStream_t st);
+};
+
+// Launch bookkeeping: counts every launch of a class and, with timing on,
+// brackets it by events on the launch stream.
+template <class F>
+inline void launch(Stats *S, int cls, cudaStream_t st, F &&f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (S) S->begin(cls, st, &a, &b);
+  f();
+  CEN_CK(cudaGetLastError());
+  if (S) S->end(cls, st, a, b);
+}
+
+inline int grid_for(size_t items, int per_block, int cap = 152 * 32) {
+  size_t g = (items + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > (size_t)cap) g = cap;
+  return (int)g;
+}
+
+// ------------------------------------------------------------- prims
+// Device-wide exclusive scan of `n` int64 values (in may equal out); writes
+// the total to *d_total (device) when non-null.
+void exclusive_scan_i64(const int64_t *in, int64_t *out, size_t n, int64_t *d_total, DevBuf &tmp, cudaStream_t st,
+                        Stats *S);
+// Exclusive scan of int32 counts into int64 offsets (out has n+1 entries, out[n] = total).
+void counts_to_offsets(const int32_t *cnt, int64_t *out, size_t n, DevBuf &tmp, cudaStream_t st, Stats *S);
+// Stable LSD radix sort of (key, value) uint32 pairs by key, keys < 2^key_bits.
+// Result lands in keys/vals (ping-pong through the scratch buffers).
+void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, DevBuf &k2, DevBuf &v2, DevBuf &hist,
+                      DevBuf &tmp, cudaStream_t st, Stats *S);
+
+}  // namespace cen
+
+// -------------------------------------------------------- opaque handles
+struct cen_graph {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int directed = 0;
+  cudaStream_t st = nullptr;
+  cen::DevBuf off, col, roff, rcol;  // roff/rcol empty when undirected (alias off/col)
+  const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
+  const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
+};

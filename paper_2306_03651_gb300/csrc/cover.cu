@@ -1,0 +1,156 @@
+// Node -> sample incidence and greedyCover(k, H) (Sec. 3.1; Alg. 1 line "greedyCover").
+#include "job.cuh"
+
+namespace cen {
+
+// ------------------------------------------------------- incidence
+__global__ void k_count_members(const int32_t *__restrict__ hmem, int64_t total, int32_t *c) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&c[hmem[i]], 1);
+}
+
+// Thread per sample: each member u gets j appended to row u (order within a
+// row follows atomic arrival; every consumer of the rows is order-free).
+__global__ void k_scatter_members(const int64_t *__restrict__ hoff, const int32_t *__restrict__ hmem, uint64_t m,
+                                  const int64_t *__restrict__ noff, int32_t *cursor, int32_t *nsamp) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (uint64_t)gridDim.x * blockDim.x) {
+    for (int64_t e = hoff[j]; e < hoff[j + 1]; ++e) {
+      const int32_t u = hmem[e];
+      const int32_t pos = atomicAdd(&cursor[u], 1);
+      nsamp[noff[u] + pos] = (int32_t)j;
+    }
+  }
+}
+
+void build_incidence(cen_job *job) {
+  if (job->inc_m == job->m) return;
+  cudaStream_t st = job->st;
+  Stats *S = &job->stats;
+  const int32_t n = job->g->n;
+  job->c.ensure(4 * (size_t)n, st);
+  job->cursor.ensure(4 * (size_t)n, st);
+  job->noff.ensure(8 * ((size_t)n + 1), st);
+  job->nsamp.ensure(4 * (size_t)(job->members + 1), st);
+  CEN_CK(cudaMemsetAsync(job->c.p, 0, 4 * (size_t)n, st));
+  CEN_CK(cudaMemsetAsync(job->cursor.p, 0, 4 * (size_t)n, st));
+  if (job->members)
+    launch(S, K_TRANSPOSE, st, [&] {
+      k_count_members<<<grid_for((size_t)job->members, 256), 256, 0, st>>>(job->hmem.as<int32_t>(), job->members,
+                                                                         job->c.as<int32_t>());
+    });
+  counts_to_offsets(job->c.as<int32_t>(), job->noff.as<int64_t>(), (size_t)n, job->scan_tmp, st, S);
+  if (job->m)
+    launch(S, K_TRANSPOSE, st, [&] {
+      k_scatter_members<<<grid_for(job->m, 256), 256, 0, st>>>(job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
+                                                               job->m, job->noff.as<int64_t>(),
+                                                               job->cursor.as<int32_t>(), job->nsamp.as<int32_t>());
+    });
+  job->inc_m = job->m;
+}
+
+// ---------------------------------------------------------------- greedy
+// Control words: key[2] (ping-pong argmax keys), covered count, picks, done.
+struct GreedyCtl {
+  unsigned long long key[2];
+  unsigned long long covered;
+  int size;
+  int done;
+  int S[1];  // k entries follow
+};
+
+__global__ void k_gain_init(const int32_t *__restrict__ c, int32_t *gain, int32_t n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) gain[i] = c[i];
+}
+
+// argmax over nodes of key = gain << 32 | (2^32 - 1 - u): the max key has the
+// largest gain and, among equal gains, the lowest id.
+__global__ void __launch_bounds__(256) k_greedy_argmax(const int32_t *__restrict__ gain, int32_t n, GreedyCtl *ctl,
+                                                       int slot) {
+  if (ctl->done) return;
+  unsigned long long best = 0;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+    const unsigned long long k = ((unsigned long long)(uint32_t)gain[u] << 32) | (0xFFFFFFFFu - (uint32_t)u);
+    best = k > best ? k : best;
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+    best = y > best ? y : best;
+  }
+  __shared__ unsigned long long wb[8];
+  if ((threadIdx.x & 31) == 0) wb[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = wb[w] > best ? wb[w] : best;
+    if (best) atomicMax(&ctl->key[slot], best);
+  }
+}
+
+// Warp per incident sample of the pick u*: a still-uncovered sample becomes
+// covered and every member's gain drops by one.
+__global__ void __launch_bounds__(256) k_greedy_update(const int64_t *__restrict__ noff,
+                                                       const int32_t *__restrict__ nsamp,
+                                                       const int64_t *__restrict__ hoff,
+                                                       const int32_t *__restrict__ hmem, int32_t *gain,
+                                                       uint32_t *covered, GreedyCtl *ctl, int slot, int it) {
+  if (ctl->done) return;
+  const unsigned long long key = ctl->key[slot];
+  const uint32_t g = (uint32_t)(key >> 32);
+  if (g == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->done = 1;
+    return;
+  }
+  const int32_t u = (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->S[it] = u;
+    ctl->size = it + 1;
+    ctl->covered += g;
+    ctl->key[slot ^ 1] = 0;  // reset the other slot for the next argmax
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t r0 = noff[u], r1 = noff[u + 1];
+  for (int64_t q = r0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); q < r1; q += nwarps) {
+    const int32_t j = nsamp[q];
+    const uint32_t mask = 1u << (j & 31);
+    if (covered[j >> 5] & mask) continue;  // j occurs once in row u: only this warp can set its bit now
+    if (lane == 0) atomicOr(&covered[j >> 5], mask);
+    for (int64_t e = hoff[j] + lane; e < hoff[j + 1]; e += 32) atomicSub(&gain[hmem[e]], 1);
+  }
+}
+
+void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered) {
+  CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_greedy_cover: k must be >= 1");
+  build_incidence(job);
+  cudaStream_t st = job->st;
+  Stats *St = &job->stats;
+  const int32_t n = job->g->n;
+  job->gain.ensure(4 * (size_t)n, st);
+  job->covered.ensure(4 * ((job->m + 31) / 32 + 1), st);
+  const size_t cbytes = sizeof(GreedyCtl) + 4 * (size_t)k;
+  job->gctl.ensure(cbytes, st);
+  CEN_CK(cudaMemsetAsync(job->covered.p, 0, 4 * ((job->m + 31) / 32 + 1), st));
+  CEN_CK(cudaMemsetAsync(job->gctl.p, 0, cbytes, st));
+  GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
+  launch(St, K_GREEDY, st,
+         [&] { k_gain_init<<<grid_for(n, 256), 256, 0, st>>>(job->c.as<int32_t>(), job->gain.as<int32_t>(), n); });
+  const int gblocks = grid_for((size_t)n, 256, 152 * 4);
+  for (int it = 0; it < k; ++it) {
+    const int slot = it & 1;
+    launch(St, K_GREEDY, st,
+           [&] { k_greedy_argmax<<<gblocks, 256, 0, st>>>(job->gain.as<int32_t>(), n, ctl, slot); });
+    launch(St, K_GREEDY, st, [&] {
+      k_greedy_update<<<152 * 4, 256, 0, st>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
+                                                job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
+                                                job->gain.as<int32_t>(), job->covered.as<uint32_t>(), ctl, slot, it);
+    });
+  }
+  char *h = (char *)host_staging(job, cbytes);
+  CEN_CK(cudaMemcpyAsync(h, ctl, cbytes, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  const GreedyCtl *hc = (const GreedyCtl *)h;
+  *S_size = hc->size;
+  *covered = hc->covered;
+  for (int i = 0; i < hc->size; ++i) S[i] = hc->S[i];
+}
+
+}  // namespace cen

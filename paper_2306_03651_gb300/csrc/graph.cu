@@ -1,0 +1,92 @@
+// Graph upload: canonical-CSR validation on the GPU and, for directed graphs,
+// the in-arc CSR (a stable sort of arcs by head keeps each row ascending).
+#include "job.cuh"
+
+namespace cen {
+
+// One warp per row: offsets monotone and in range, heads in [0, n), no
+// self-loop, strictly ascending.  bad |= 1 on any violation.
+__global__ void k_validate_csr(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int *bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (off[0] != 0 || off[n] != nnz) atomicOr(bad, 1);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+    const int64_t b = off[v], e = off[v + 1];
+    if (b > e || b < 0 || e > nnz) {
+      if (lane == 0) atomicOr(bad, 1);
+      continue;
+    }
+    bool ok = true;
+    for (int64_t i = b + lane; i < e; i += 32) {
+      const int32_t c = col[i];
+      ok &= (c >= 0 && c < n && c != (int32_t)v);
+      if (i > b) ok &= (col[i - 1] < c);
+    }
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(bad, 1);
+  }
+}
+
+// Arc list in CSR order: key = head, value = tail.
+__global__ void k_arcs_by_tail(const int64_t *off, const int32_t *col, int32_t n, uint32_t *key, uint32_t *val,
+                               int32_t *indeg) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+    for (int64_t i = off[v] + lane; i < off[v + 1]; i += 32) {
+      key[i] = (uint32_t)col[i];
+      val[i] = (uint32_t)v;
+      atomicAdd(&indeg[col[i]], 1);
+    }
+  }
+}
+
+void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_device, Stats *S) {
+  cudaStream_t st = g->st;
+  const int32_t n = g->n;
+  const int64_t nnz = g->nnz;
+  g->off.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
+  g->col.ensure(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), st);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CEN_CK(cudaMemcpyAsync(g->off.p, off, sizeof(int64_t) * ((size_t)n + 1), kind, st));
+  if (nnz) CEN_CK(cudaMemcpyAsync(g->col.p, col, sizeof(int32_t) * (size_t)nnz, kind, st));
+  DevBuf bad;
+  bad.ensure(sizeof(int), st);
+  CEN_CK(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+  launch(S, K_GRAPH, st, [&] {
+    k_validate_csr<<<grid_for((size_t)n, 8), 256, 0, st>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), n, nnz,
+                                                          bad.as<int>());
+  });
+  int hbad = 0;
+  CEN_CK(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  CEN_REQUIRE(hbad == 0, CEN_EINVAL,
+              "cen_graph_load: CSR is not canonical (offsets, ids in [0,n), no self-loops, rows strictly ascending)");
+  if (!g->directed || nnz == 0) {
+    if (g->directed) {  // no arcs: in-CSR is all zeros
+      g->roff.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
+      CEN_CK(cudaMemsetAsync(g->roff.p, 0, sizeof(int64_t) * ((size_t)n + 1), st));
+      g->rcol.ensure(4, st);
+    }
+    return;
+  }
+  DevBuf key, val, k2, v2, hist, tmp, indeg;
+  key.ensure(4 * (size_t)nnz, st);
+  val.ensure(4 * (size_t)nnz, st);
+  indeg.ensure(4 * (size_t)n, st);
+  CEN_CK(cudaMemsetAsync(indeg.p, 0, 4 * (size_t)n, st));
+  launch(S, K_GRAPH, st, [&] {
+    k_arcs_by_tail<<<grid_for((size_t)n, 8), 256, 0, st>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), n,
+                                                           key.as<uint32_t>(), val.as<uint32_t>(), indeg.as<int32_t>());
+  });
+  int bits = 1;
+  while (bits < 31 && (1u << bits) < (uint32_t)n) ++bits;
+  radix_sort_pairs(key.as<uint32_t>(), val.as<uint32_t>(), (size_t)nnz, bits, k2, v2, hist, tmp, st, S);
+  g->roff.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
+  counts_to_offsets(indeg.as<int32_t>(), g->roff.as<int64_t>(), (size_t)n, tmp, st, S);
+  g->rcol.ensure(4 * (size_t)nnz, st);
+  CEN_CK(cudaMemcpyAsync(g->rcol.p, val.p, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
+  CEN_CK(cudaStreamSynchronize(st));
+}
+
+}  // namespace cen

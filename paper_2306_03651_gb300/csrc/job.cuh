@@ -1,0 +1,67 @@
+// Internal layout of a CentRA job (the growing sample H and its workspaces).
+#pragma once
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cen {
+
+// Workspace of the bit-parallel sampler.  A wave handles W = 64 G samples;
+// every per-vertex set is G 64-bit words (bit b of word g = slot 64 g + b),
+// stored vertex-major: word (v, g) at index v * G + g.
+struct WaveWS {
+  int G = 0;                                  // words per vertex in the current wave
+  DevBuf vis;                                 // [n][G] reached so far
+  std::vector<std::unique_ptr<DevBuf>> lev;   // lev[L]: [n][G] nodes at distance exactly L
+  DevBuf lev_ptrs;                            // device array of lev[L] pointers
+  int lev_ptrs_n = 0;
+  DevBuf tmp;                                 // [n][G] cone accumulation, kept zero between uses
+  DevBuf sig64;                               // [n][W] path counts (64-bit)
+  DevBuf sig128;                              // [n][64] path counts (128-bit, re-run of flagged slots)
+  DevBuf ovf;                                 // [n][G] path-count overflow flags
+  DevBuf slots;                               // per slot: j (u64), s, t, d (int32)
+  DevBuf ctl;                                 // control block (see sampler.cu)
+  DevBuf flist;                               // frontier node list [n]
+  DevBuf jlist;                               // explicit sample ids for a re-run
+};
+
+}  // namespace cen
+
+struct cen_job {
+  const cen_graph *g = nullptr;
+  uint64_t seed = 0;
+  int32_t t = 0;
+  int32_t nw = 0;  // sign words per sample = ceil(t / 32)
+  cudaStream_t st = nullptr;
+  uint64_t m = 0;         // samples
+  int64_t members = 0;    // sum of |h|
+  // sample store (device): hoff[m+1], hmem[members], per-sample s, t, d, sign words
+  cen::DevBuf hoff, hmem, ps, pt, pd, sign, bmax;
+  // node -> sample incidence (rebuilt lazily when m changed)
+  cen::DevBuf c, noff, nsamp, cursor;
+  uint64_t inc_m = ~0ull;
+  // greedy workspace
+  cen::DevBuf gain, covered, gctl;
+  // AMCERA workspace
+  cen::DevBuf R, selh, selst;
+  int32_t rade_valid_k = -1;
+  // sampler workspace
+  cen::WaveWS ws;
+  // scratch for scans
+  cen::DevBuf scan_tmp;
+  // pinned host staging
+  void *host = nullptr;
+  size_t host_bytes = 0;
+  cen::Stats stats;
+  size_t sigma_budget = (size_t)16 << 30;  // bytes allowed for the [n][W] path-count table
+};
+
+namespace cen {
+void sample_append(cen_job *job, uint64_t m_new);
+void build_incidence(cen_job *job);
+void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered);
+void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b);
+void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_device, Stats *S);
+void *host_staging(cen_job *job, size_t bytes);
+}  // namespace cen

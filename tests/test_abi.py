@@ -1,0 +1,66 @@
+"""CPU checks of the boundary: libcen.so loads, exports every function that
+include/cen.h declares, rejects bad arguments without touching a GPU, and its
+host FP64 bounds (Thm. "bound_dev", Alg. 1 stopping test) equal the oracle's
+bit for bit."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2306_03651_gb300 as P
+
+
+def test_library_exports_every_header_function():
+    names = P.header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(P._lib, n)]
+    assert missing == []
+
+
+def test_version_and_error_text():
+    assert P.cen_version() >= 100
+    assert isinstance(P.last_error(), str)
+
+
+def test_bounds_rejects_bad_arguments():
+    out = np.zeros(8)
+    stop = ctypes.c_int32()
+    for args in [(0, 0, 0, 10, 0, 0, 0.1, 0.1, 1),   # m = 0
+                 (0, 10, 0, 0, 0, 0, 0.1, 0.1, 1),   # t = 0
+                 (0, 10, 0, 5, 0, 0, 0.1, 1.5, 1),   # delta >= 1
+                 (0, 10, 0, 5, 0, 0, 0.1, 0.1, 0)]:  # i = 0
+        assert P.cen_bounds(*args, out.ctypes.data, ctypes.byref(stop)) == P.EINVAL
+    assert "cen_bounds" in P.last_error()
+
+
+def test_bounds_match_oracle_bit_for_bit():
+    rng = np.random.default_rng(3)
+    for _ in range(2000):
+        m = int(rng.integers(1, 10**8))
+        cov = int(rng.integers(0, m + 1))
+        t = int(rng.integers(1, 200))
+        Rsum = int(rng.integers(0, t * m // 10 + 1))
+        Wnum = int(rng.integers(0, 50 * m))
+        b = int(rng.integers(0, 60))
+        eps = float(rng.uniform(1e-4, 0.6))
+        delta = float(rng.uniform(1e-6, 0.99))
+        i = int(rng.integers(1, 40))
+        s1, b1 = P.bounds(cov, m, Rsum, t, Wnum, b, eps, delta, i)
+        s2, b2 = O.bounds(cov, m, Rsum, t, Wnum, b, eps, delta, i)
+        assert s1 == s2
+        for k in b1:
+            assert b1[k] == b2[k] or (math.isnan(b1[k]) and math.isnan(b2[k])), k
+
+
+def test_null_handles_rejected():
+    S = np.zeros(4, np.int32)
+    size, cov = ctypes.c_int32(), ctypes.c_uint64()
+    assert P.cen_greedy_cover(None, 4, S.ctypes.data, ctypes.byref(size), ctypes.byref(cov)) == P.EINVAL
+    assert P.cen_sample(None, 10) == P.EINVAL
+    h = ctypes.c_void_p()
+    assert P.cen_job_create(None, 1, 4, None, ctypes.byref(h)) == P.EINVAL
+    off = np.array([0, 1], np.int64)
+    col = np.array([0], np.int32)
+    assert P.cen_graph_load(off.ctypes.data, col.ctypes.data, 1, 1, 0, 0, None, ctypes.byref(h)) == P.EINVAL

@@ -1,0 +1,269 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, bit for bit.
+
+Sampler (pairs, distances, path counts incl. the 128-bit range, backward
+walk, hyper-edge store), incidence, greedyCover, sign words, AMCERA
+numerators and Algorithm 1 end to end.  Small graphs span several waves and a
+ragged last wave; the R-MAT scale-18 LCC workload is checked on sampled
+outputs the oracle computes one by one, plus properties that hold at any size.
+"""
+import ctypes
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_03651_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2306_03651_gb300")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "ba2000_run.json")
+
+
+def small_graphs():
+    star = I.from_edges(9, [0] * 8, list(range(1, 9)), False)
+    kn = 7
+    e = np.array([(a, b) for a in range(kn) for b in range(a + 1, kn)], np.int32)
+    comp = I.from_edges(kn, e[:, 0], e[:, 1], False)
+    dpath = I.from_edges(6, [0, 1, 2, 3, 4], [1, 2, 3, 4, 5], True)
+    return {
+        "ba2000": I.ba(2000, 4, 1),
+        "ba300": I.ba(300, 3, 7),
+        "rmat12_dir": I.rmat(12, 8, seed=3, directed=True, keep_lcc=False),
+        "rmat12_lcc": I.rmat(12, 8, seed=3),
+        "grid_rewired": I.grid_rewired(48, 48, 0.02, 5),
+        "star": star,
+        "complete": comp,
+        "dpath": dpath,
+    }
+
+
+GRAPHS = small_graphs()
+
+
+def oracle_samples(g, seed, m, t=10):
+    og = O.Graph.of(g)
+    job = O.Job(og, seed, t)
+    job.sample(m)
+    return og, job, job.hypergraph()
+
+
+def assert_same_samples(a, b):
+    for key in ("hoff", "s", "t", "d"):
+        assert np.array_equal(a[key], b[key]), key
+    assert np.array_equal(a["hmem"], b["hmem"])
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_sample_parity(name):
+    g = GRAPHS[name]
+    m = 2600 if g.n > 50 else 700
+    _, _, ref = oracle_samples(g, 11, m)
+    job = P.Job(P.Graph.of(g), 11, 10)
+    job.sample(m)
+    assert_same_samples(job.samples(), ref)
+
+
+def test_sample_split_invariance():
+    g = GRAPHS["ba300"]
+    _, _, ref = oracle_samples(g, 5, 1000)
+    for splits in ([1000], [1, 63, 936], [64, 64, 200, 672], [999, 1]):
+        job = P.Job(P.Graph.of(g), 5, 10)
+        for s in splits:
+            job.sample(s)
+        assert_same_samples(job.samples(), ref)
+
+
+def test_path_counts_beyond_64_bits():
+    """40x40 grid: pairs with C(dx+dy, dx) >= 2^64 shortest paths take the 128-bit re-run."""
+    W = 40
+    g = I.grid_rewired(W, W, 0.0, 1)
+    seed, m = 21, 400
+    big = 0
+    for j in range(m):
+        s, t = O.pair(seed, j, W * W)
+        dx, dy = abs(s % W - t % W), abs(s // W - t // W)
+        big += math.comb(dx + dy, dx) >= 2**64
+    assert big > 0
+    _, _, ref = oracle_samples(g, seed, m)
+    job = P.Job(P.Graph.of(g), seed, 10)
+    job.sample(m)
+    assert_same_samples(job.samples(), ref)
+
+
+def test_path_counts_beyond_128_bits_overflow():
+    W = 70
+    g = I.grid_rewired(W, W, 0.0, 1)
+    seed = 3
+    jbad = None
+    for j in range(20000):
+        s, t = O.pair(seed, j, W * W)
+        dx, dy = abs(s % W - t % W), abs(s // W - t // W)
+        if math.comb(dx + dy, dx) >= 2**128:
+            jbad = j
+            break
+    assert jbad is not None
+    job = P.Job(P.Graph.of(g), seed, 4)
+    if jbad > 0:
+        job.sample(jbad)
+    with pytest.raises(P.CenError) as ei:
+        job.sample(1)
+    assert ei.value.rc == P.EOVERFLOW
+    assert job.m == jbad  # the job is unchanged by the failed call
+
+
+def incidence_rows(h, n):
+    rows = [[] for _ in range(n)]
+    for j in range(len(h["hoff"]) - 1):
+        for u in h["hmem"][h["hoff"][j]:h["hoff"][j + 1]]:
+            rows[u].append(j)
+    return rows
+
+
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_dir", "grid_rewired"])
+def test_greedy_incidence_mcera_parity(name):
+    g = GRAPHS[name]
+    m, t = 3000, 40
+    og, ojob, ref = oracle_samples(g, 9, m, t)
+    job = P.Job(P.Graph.of(g), 9, t)
+    job.sample(m)
+    for k in (1, 5, 17, 60):
+        S, cov = job.greedy_cover(k)
+        S2, cov2 = ojob.greedy_cover(k)
+        assert S.tolist() == S2.tolist() and cov == cov2
+    noff, nsamp = job.incidence()
+    rows = incidence_rows(ref, g.n)
+    for u in range(g.n):
+        assert sorted(nsamp[noff[u]:noff[u + 1]].tolist()) == rows[u]
+    words = job.signs()
+    for j in range(0, m, 7):
+        assert np.array_equal(words[j], O.sign_words(9, j, t))
+    for k in (1, 10, 100):
+        Rn, Wn, b = job.mcera(k)
+        Rn2, Wn2, b2 = ojob.mcera(k)
+        assert np.array_equal(Rn, Rn2) and Wn == Wn2 and b == b2
+    R, c = job.rade()
+    R2, c2 = ojob.rade_matrix()
+    assert np.array_equal(R, R2.T) and np.array_equal(c, c2)
+
+
+def test_run_matches_oracle_golden_on_ba2000():
+    with open(GOLDEN) as f:
+        gold = json.load(f)
+    w = I.ba_2000()
+    r = P.run(P.Graph.of(w.graph), w.k, w.eps, w.delta, w.t, w.seed, m0=w.m0)
+    assert r["status"] == gold["status"]
+    assert r["S"].tolist() == gold["S"]
+    assert r["covered"] == gold["covered"] and r["m_final"] == gold["m_final"] and r["rounds"] == gold["rounds"]
+    log = [[float.fromhex(x) for x in row] for row in gold["log_hex"]]
+    assert np.array_equal(r["log"], np.array(log))
+
+
+def test_run_not_certified_on_complete_graph():
+    g = GRAPHS["complete"]
+    r = P.run(P.Graph.of(g), 2, 0.1, 0.1, 4, 1, m0=100, m_cap=1600)
+    ro = O.Graph.of(g).run(2, 0.1, 0.1, 4, 1, m0=100, m_cap=1600)
+    assert r["status"] == P.ENOTCERTIFIED == ro["status"]
+    assert r["m_final"] == ro["m_final"] == 1600 and r["covered"] == 0
+
+
+def test_run_argument_checks():
+    gg = P.Graph.of(GRAPHS["ba300"])
+    for kw in (dict(k=0), dict(eps=0.0), dict(eps=0.7), dict(delta=1.0), dict(t=0)):
+        args = dict(k=3, eps=0.1, delta=0.1, t=4, seed=1)
+        args.update(kw)
+        with pytest.raises(P.CenError) as ei:
+            P.run(gg, **args)
+        assert ei.value.rc == P.EINVAL
+
+
+def test_graph_load_rejects_malformed_and_accepts_device_arrays():
+    torch = pytest.importorskip("torch")
+    g = GRAPHS["ba300"]
+    bad = g.col.copy()
+    r0, r1 = g.off[5], g.off[6]
+    bad[r0], bad[r0 + 1] = bad[r0 + 1], bad[r0]  # unsorted row
+    with pytest.raises(P.CenError) as ei:
+        P.Graph(g.n, g.off, bad, False)
+    assert ei.value.rc == P.EINVAL
+    loop = g.col.copy()
+    loop[r0] = 5  # self-loop in row 5 (row stays sorted only if 5 < next; validation must still fail)
+    with pytest.raises(P.CenError):
+        P.Graph(g.n, g.off, loop, False)
+    dg = P.Graph(g.n, torch.from_numpy(g.off).cuda(), torch.from_numpy(g.col).cuda(), False)
+    job = P.Job(dg, 3, 8)
+    job.sample(300)
+    _, _, ref = oracle_samples(g, 3, 300, 8)
+    assert_same_samples(job.samples(), ref)
+
+
+def test_stats_and_timing():
+    g = GRAPHS["ba2000"]
+    job = P.Job(P.Graph.of(g), 1, 10)
+    job.set_timing(True)
+    job.sample(2048)
+    job.greedy_cover(10)
+    job.mcera(10)
+    st = job.stats()
+    assert st["pairs"]["launches"] >= 1 and st["walk"]["launches"] >= 1
+    assert st["expand_pull"]["launches"] + st["expand_push"]["launches"] >= 1
+    assert st["walk"]["ms"] > 0 and st["walk"]["timed"] == st["walk"]["launches"]
+    job.reset_stats()
+    assert job.stats()["walk"]["launches"] == 0
+
+
+# ---------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def rmat18():
+    return I.rmat18_lcc()
+
+
+def test_rmat18_sampled_parity_and_properties(rmat18):
+    """R-MAT scale 18 LCC at the benchmark's wave size: sampled hyper-edges vs the
+    oracle one by one; every hyper-edge is a shortest path's interior."""
+    g = rmat18.graph
+    m = 4096
+    job = P.Job(P.Graph.of(g), rmat18.seed, rmat18.t)
+    job.sample(m)
+    h = job.samples()
+    og = O.Graph.of(g)
+    rng = np.random.default_rng(0)
+    picks = sorted(set(rng.choice(m, 40, replace=False).tolist()) | {0, 2047, 2048, m - 1})
+    for j in picks:
+        rc, s, t, d, path = og.hyperedge(rmat18.seed, j)
+        assert rc == O.OK
+        assert (h["s"][j], h["t"][j], h["d"][j]) == (s, t, d)
+        assert h["hmem"][h["hoff"][j]:h["hoff"][j + 1]].tolist() == path
+    # properties at any size: connected graph, lengths d - 1, consecutive nodes adjacent
+    assert np.all(h["d"] >= 1)
+    assert np.array_equal(np.diff(h["hoff"]), np.maximum(h["d"] - 1, 0))
+    def has_arc(a, b):
+        row = g.col[g.off[a]:g.off[a + 1]]
+        i = int(np.searchsorted(row, b))
+        return i < len(row) and row[i] == b
+    for j in range(0, m, 37):
+        full = [h["s"][j]] + h["hmem"][h["hoff"][j]:h["hoff"][j + 1]].tolist() + [h["t"][j]]
+        assert len(set(full)) == len(full)
+        for a, b in zip(full, full[1:]):
+            assert has_arc(a, b)
+    # greedy at full size: picks and coverage consistent with the hyper-edges
+    S, cov = job.greedy_cover(rmat18.k)
+    mem = [set(h["hmem"][h["hoff"][j]:h["hoff"][j + 1]].tolist()) for j in range(m)]
+    Sset = set(S.tolist())
+    assert cov == sum(1 for x in mem if x & Sset)
+    chosen, covered = [], np.zeros(m, bool)
+    for u in S.tolist():
+        gains = np.zeros(g.n, np.int64)
+        for j in np.flatnonzero(~covered):
+            for x in mem[j]:
+                gains[x] += 1
+        assert gains[u] == gains.max() and u == int(np.argmax(gains))
+        for j in np.flatnonzero(~covered):
+            if u in mem[j]:
+                covered[j] = True
+        chosen.append(u)
+        if len(chosen) >= 5:
+            break
