@@ -211,12 +211,27 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, De
 }  // namespace cen
 
 // -------------------------------------------------------- opaque handles
+// Rows longer than kHeavyRow arcs are also split into kChunk-arc pieces so
+// that one long row is spread over many warps (see the *_heavy kernels).
+namespace cen {
+constexpr int kHeavyRow = 256;
+constexpr int kChunk = 256;
+struct ChunkTable {
+  DevBuf w, beg;    // chunk -> row id, first arc
+  int64_t count = 0;
+  const int32_t *rows() const { return w.as<int32_t>(); }
+  const int64_t *begins() const { return beg.as<int64_t>(); }
+};
+}  // namespace cen
+
 struct cen_graph {
   int32_t n = 0;
   int64_t nnz = 0;
   int directed = 0;
   cudaStream_t st = nullptr;
   cen::DevBuf off, col, roff, rcol;  // roff/rcol empty when undirected (alias off/col)
+  cen::ChunkTable out_chunks, in_chunks_own;  // in_chunks_own used only when directed
   const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
   const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
+  const cen::ChunkTable &in_chunks() const { return directed ? in_chunks_own : out_chunks; }
 };

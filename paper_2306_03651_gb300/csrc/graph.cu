@@ -41,6 +41,43 @@ __global__ void k_arcs_by_tail(const int64_t *off, const int32_t *col, int32_t n
   }
 }
 
+// Chunk table of the rows longer than kHeavyRow: row v contributes
+// ceil(deg/kChunk) chunks starting at off[v], off[v]+kChunk, ...
+__global__ void k_chunk_count(const int64_t *off, int32_t n, int32_t *cnt) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const int64_t d = off[v + 1] - off[v];
+    cnt[v] = d > kHeavyRow ? (int32_t)((d + kChunk - 1) / kChunk) : 0;
+  }
+}
+__global__ void k_chunk_fill(const int64_t *off, int32_t n, const int64_t *coff, int32_t *cw, int64_t *cbeg) {
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    for (int64_t c = coff[v]; c < coff[v + 1]; ++c) {
+      cw[c] = v;
+      cbeg[c] = off[v] + (c - coff[v]) * kChunk;
+    }
+  }
+}
+
+static void build_chunks(const int64_t *off, int32_t n, ChunkTable &T, cudaStream_t st, Stats *S) {
+  DevBuf cnt, coff, tmp;
+  cnt.ensure(4 * (size_t)n, st);
+  coff.ensure(8 * ((size_t)n + 1), st);
+  launch(S, K_GRAPH, st, [&] { k_chunk_count<<<grid_for(n, 256), 256, 0, st>>>(off, n, cnt.as<int32_t>()); });
+  counts_to_offsets(cnt.as<int32_t>(), coff.as<int64_t>(), (size_t)n, tmp, st, S);
+  int64_t total = 0;
+  CEN_CK(cudaMemcpyAsync(&total, coff.as<int64_t>() + n, 8, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  T.count = total;
+  T.w.ensure(4 * (size_t)(total + 1), st);
+  T.beg.ensure(8 * (size_t)(total + 1), st);
+  if (total)
+    launch(S, K_GRAPH, st, [&] {
+      k_chunk_fill<<<grid_for(n, 256), 256, 0, st>>>(off, n, coff.as<int64_t>(), T.w.as<int32_t>(),
+                                                     T.beg.as<int64_t>());
+    });
+  CEN_CK(cudaStreamSynchronize(st));
+}
+
 void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_device, Stats *S) {
   cudaStream_t st = g->st;
   const int32_t n = g->n;
@@ -62,11 +99,13 @@ void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_d
   CEN_CK(cudaStreamSynchronize(st));
   CEN_REQUIRE(hbad == 0, CEN_EINVAL,
               "cen_graph_load: CSR is not canonical (offsets, ids in [0,n), no self-loops, rows strictly ascending)");
+  build_chunks(g->off.as<int64_t>(), n, g->out_chunks, st, S);
   if (!g->directed || nnz == 0) {
     if (g->directed) {  // no arcs: in-CSR is all zeros
       g->roff.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
       CEN_CK(cudaMemsetAsync(g->roff.p, 0, sizeof(int64_t) * ((size_t)n + 1), st));
       g->rcol.ensure(4, st);
+      build_chunks(g->roff.as<int64_t>(), n, g->in_chunks_own, st, S);
     }
     return;
   }
@@ -86,6 +125,7 @@ void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_d
   counts_to_offsets(indeg.as<int32_t>(), g->roff.as<int64_t>(), (size_t)n, tmp, st, S);
   g->rcol.ensure(4 * (size_t)nnz, st);
   CEN_CK(cudaMemcpyAsync(g->rcol.p, val.p, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
+  build_chunks(g->roff.as<int64_t>(), n, g->in_chunks_own, st, S);
   CEN_CK(cudaStreamSynchronize(st));
 }
 

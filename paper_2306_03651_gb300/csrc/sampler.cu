@@ -133,6 +133,10 @@ __global__ void __launch_bounds__(256) k_expand_pull(const int64_t *__restrict__
     }
     ++opened;
     const int64_t e0 = roff[w], e1 = roff[w + 1];
+    if (e1 - e0 > kHeavyRow) {  // long rows: k_expand_pull_heavy ORs their chunks in
+      if (a == 0) nxt[w * G + g] = 0;
+      continue;
+    }
     uint64_t acc = 0;
     for (int64_t base = e0; base < e1; base += (int64_t)A * 8) {
 #pragma unroll
@@ -161,6 +165,41 @@ __global__ void __launch_bounds__(256) k_expand_pull(const int64_t *__restrict__
     atomicAdd(units, verts * 16ull * G + opened * 16ull + scanned * (4ull + 8ull * G));
 }
 
+// Bottom-up over the chunks of long rows: warp per chunk, OR of the chunk's
+// in-neighbour level words, merged into the node's next word.
+__global__ void __launch_bounds__(256) k_expand_pull_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
+                                                           const int64_t *__restrict__ cbeg,
+                                                           const int64_t *__restrict__ roff,
+                                                           const int32_t *__restrict__ rcol, int G, int gshift,
+                                                           const uint64_t *__restrict__ lev, uint64_t *nxt,
+                                                           const uint64_t *__restrict__ vis,
+                                                           const Ctl *__restrict__ ctl, unsigned long long *units) {
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+  const uint64_t act = ctl->active[g];
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
+    const int32_t w = cw[q];
+    const uint64_t unv = act & ~vis[(int64_t)w * G + g];
+    bytes += 8ull * G;
+    if (!__any_sync(0xffffffffu, unv != 0)) continue;
+    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[w + 1]);
+    uint64_t acc = 0;
+    for (int64_t base = e0; base < e1; base += (int64_t)A * 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t i = base + (int64_t)u * A + a;
+        if (i < e1) acc |= lev[(int64_t)rcol[i] * G + g];
+      }
+    }
+    for (int o = G; o < 32; o <<= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+    const uint64_t nb = acc & unv;
+    if (a == 0 && nb) atomicOr((unsigned long long *)&nxt[(int64_t)w * G + g], (unsigned long long)nb);
+    bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G) + 16ull * G;
+  }
+  if (lane == 0 && bytes) atomicAdd(units, bytes);
+}
+
 // Top-down: every frontier node v ORs its active level-L words into the
 // next-level words of its out-neighbours.
 __global__ void __launch_bounds__(256) k_expand_push(const int64_t *__restrict__ off, const int32_t *__restrict__ col,
@@ -174,9 +213,10 @@ __global__ void __launch_bounds__(256) k_expand_push(const int64_t *__restrict__
   unsigned long long scanned = 0;
   for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < fcount; q += nwarps) {
     const int32_t v = flist[q];
+    const int64_t e0 = off[v], e1 = off[v + 1];
+    if (e1 - e0 > kHeavyRow) continue;  // long rows: k_expand_push_heavy
     const uint64_t f = lev[(int64_t)v * G + g] & act;
     if (!__any_sync(0xffffffffu, f != 0)) continue;
-    const int64_t e0 = off[v], e1 = off[v + 1];
     for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -190,6 +230,37 @@ __global__ void __launch_bounds__(256) k_expand_push(const int64_t *__restrict__
     scanned += 16ull + 8ull * G + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
   }
   if (lane == 0 && scanned) atomicAdd(units, scanned);
+}
+
+// Top-down over the chunks of long out-rows: a chunk of a frontier node pushes
+// its active level words to the chunk's out-neighbours.
+__global__ void __launch_bounds__(256) k_expand_push_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
+                                                           const int64_t *__restrict__ cbeg,
+                                                           const int64_t *__restrict__ off,
+                                                           const int32_t *__restrict__ col, int G, int gshift,
+                                                           const uint64_t *__restrict__ lev, uint64_t *nxt,
+                                                           const Ctl *__restrict__ ctl, unsigned long long *units) {
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+  const uint64_t act = ctl->active[g];
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
+    const int32_t v = cw[q];
+    const uint64_t f = lev[(int64_t)v * G + g] & act;
+    bytes += 8ull * G;
+    if (!__any_sync(0xffffffffu, f != 0)) continue;
+    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, off[v + 1]);
+    for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = base + (int64_t)u * A + a;
+        if (i < e1 && f) atomicOr((unsigned long long *)&nxt[(int64_t)col[i] * G + g], (unsigned long long)f);
+      }
+    }
+    const int nzw = __popc(__ballot_sync(0xffffffffu, f != 0 && a == 0));
+    bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
+  }
+  if (lane == 0 && bytes) atomicAdd(units, bytes);
 }
 
 // Thread per word: keep only newly reached active slots, mark them reached,
@@ -320,6 +391,7 @@ __global__ void __launch_bounds__(256) k_cone_push(int32_t n, int G, int gshift,
     const uint64_t c = up[x * G + g];
     if (!__any_sync(0xffffffffu, c != 0)) continue;
     const int64_t e0 = roff[x], e1 = roff[x + 1];
+    if (e1 - e0 > kHeavyRow) continue;  // long rows: k_cone_push_heavy
     for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -335,6 +407,35 @@ __global__ void __launch_bounds__(256) k_cone_push(int32_t n, int G, int gshift,
   if (lane == 0) atomicAdd(units, scanned + verts * 8ull * G);
 }
 
+// Chunks of long rows: cone words of x at level L+1 go to the chunk's in-neighbours.
+__global__ void __launch_bounds__(256) k_cone_push_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
+                                                         const int64_t *__restrict__ cbeg,
+                                                         const int64_t *__restrict__ roff,
+                                                         const int32_t *__restrict__ rcol, int G, int gshift,
+                                                         const uint64_t *__restrict__ up, uint64_t *tmp,
+                                                         unsigned long long *units) {
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
+    const int32_t x = cw[q];
+    const uint64_t c = up[(int64_t)x * G + g];
+    bytes += 8ull * G;
+    if (!__any_sync(0xffffffffu, c != 0)) continue;
+    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[x + 1]);
+    for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = base + (int64_t)u * A + a;
+        if (i < e1 && c) atomicOr((unsigned long long *)&tmp[(int64_t)rcol[i] * G + g], (unsigned long long)c);
+      }
+    }
+    const int nzw = __popc(__ballot_sync(0xffffffffu, c != 0 && a == 0));
+    bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
+  }
+  if (lane == 0 && bytes) atomicAdd(units, bytes);
+}
+
 // Thread per word: lev[L] &= tmp; tmp = 0.
 __global__ void k_cone_fin(int64_t words, uint64_t *__restrict__ lev, uint64_t *__restrict__ tmp) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
@@ -346,55 +447,99 @@ __global__ void k_cone_fin(int64_t words, uint64_t *__restrict__ lev, uint64_t *
 }
 
 // ------------------------------------------------------------- counts
-// Warp per node w on level L: for every word g with cone slots c, sum the
-// counts of cone in-neighbours on level L-1 into per-slot shared
-// accumulators; wrap-around (>= 2^64) sets the slot's overflow flag.
-__global__ void __launch_bounds__(256) k_cone_sigma64(int32_t n, int G, int W, const int64_t *__restrict__ roff,
+// Path counts on the cone, level L from level L-1.  Lane layout (g, a) as in
+// the expansion.  Warp per node w with cone slots c (word g): the counts of
+// those slots are zeroed, then every in-neighbour v with cone slots f = c &
+// levP[v] adds its counts with 64-bit atomics; a wrap-around (true sum >=
+// 2^64) or an overflowed predecessor sets the slot's overflow flag.  Long
+// rows only get zeroed here; k_cone_sigma64_heavy adds their chunks.
+__device__ __forceinline__ unsigned long long sigma_arcs(int64_t e0, int64_t e1, int A, int a, int G, int g, int W,
+                                                         int64_t w, uint64_t c, const int32_t *__restrict__ rcol,
+                                                         const uint64_t *__restrict__ levP,
+                                                         uint64_t *__restrict__ sig,
+                                                         const uint64_t *__restrict__ ovf, uint64_t &myovf) {
+  unsigned long long bytes = 0;
+  for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = base + (int64_t)u * A + a;
+      if (i >= e1) continue;
+      const int32_t v = rcol[i];
+      uint64_t f = levP[(int64_t)v * G + g] & c;
+      if (!f) continue;
+      myovf |= ovf[(int64_t)v * G + g] & f;
+      bytes += 8ull;
+      while (f) {
+        const int b = __ffsll((long long)f) - 1;
+        f &= f - 1;
+        const unsigned long long x = sig[(int64_t)v * W + 64 * g + b];
+        const unsigned long long old = atomicAdd((unsigned long long *)&sig[w * W + 64 * g + b], x);
+        if (old + x < old) myovf |= 1ull << b;
+        bytes += 24ull;
+      }
+    }
+  }
+  return bytes;
+}
+
+__global__ void __launch_bounds__(256) k_cone_sigma64(int32_t n, int G, int gshift, int W,
+                                                      const int64_t *__restrict__ roff,
                                                       const int32_t *__restrict__ rcol,
                                                       const uint64_t *__restrict__ levL,
                                                       const uint64_t *__restrict__ levP, uint64_t *__restrict__ sig,
                                                       uint64_t *__restrict__ ovf, unsigned long long *units) {
-  __shared__ unsigned long long acc[8][64];
-  __shared__ unsigned long long ovm[8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long scanned = 0;
+  unsigned long long bytes = 0, verts = 0;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nwarps) {
-    for (int g = 0; g < G; ++g) {
-      const uint64_t c = levL[w * G + g];
-      if (!c) continue;
-      acc[warp][lane] = 0;
-      acc[warp][lane + 32] = 0;
-      if (lane == 0) ovm[warp] = 0;
-      __syncwarp();
-      const int64_t e0 = roff[w], e1 = roff[w + 1];
-      for (int64_t i = e0 + lane; i < e1; i += 32) {
-        const int32_t v = rcol[i];
-        uint64_t f = levP[(int64_t)v * G + g] & c;
-        if (!f) continue;
-        const uint64_t of = ovf[(int64_t)v * G + g] & f;
-        if (of) atomicOr(&ovm[warp], (unsigned long long)of);
-        while (f) {
-          const int b = __ffsll((long long)f) - 1;
-          f &= f - 1;
-          const unsigned long long x = sig[(int64_t)v * W + 64 * g + b];
-          const unsigned long long old = atomicAdd(&acc[warp][b], x);
-          if (old + x < old) atomicOr(&ovm[warp], 1ull << b);
-        }
-      }
-      scanned += 16ull + (uint64_t)(e1 - e0) * 20ull + 16ull * (uint64_t)__popcll(c);
-      __syncwarp();
-      if ((c >> lane) & 1) sig[w * W + 64 * g + lane] = acc[warp][lane];
-      if ((c >> (lane + 32)) & 1) sig[w * W + 64 * g + lane + 32] = acc[warp][lane + 32];
-      if (lane == 0 && (ovm[warp] & c)) atomicOr((unsigned long long *)&ovf[w * G + g], ovm[warp] & c);
-      __syncwarp();
+    ++verts;
+    const uint64_t c = levL[w * G + g];
+    if (!__any_sync(0xffffffffu, c != 0)) continue;
+    for (uint64_t z = c; z; z &= z - 1) {
+      const int b = __ffsll((long long)z) - 1;
+      if ((b & (A - 1)) == a) sig[w * W + 64 * g + b] = 0;
     }
+    __syncwarp();
+    const int64_t e0 = roff[w], e1 = roff[w + 1];
+    if (e1 - e0 > kHeavyRow) continue;
+    uint64_t myovf = 0;
+    bytes += sigma_arcs(e0, e1, A, a, G, g, W, w, c, rcol, levP, sig, ovf, myovf);
+    if (a == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
+    for (int o = G; o < 32; o <<= 1) myovf |= __shfl_xor_sync(0xffffffffu, myovf, o);
+    if (a == 0 && myovf) atomicOr((unsigned long long *)&ovf[w * G + g], (unsigned long long)myovf);
   }
-  // bytes: the level words of every node (8 G) plus, per cone word, offsets,
-  // per in-arc the arc (4), level word (8) and overflow word (8), and one
-  // 8-byte count read and write per cone slot (contributing counts are
-  // counted once per slot, not per arc, as lower bound)
-  if (lane == 0) atomicAdd(units, scanned + (unsigned long long)(blockIdx.x == 0 && threadIdx.x == 0) * n * 8ull * G);
+  // bytes: every node's cone words (8 G); per opened node its offsets and,
+  // per in-arc, the arc (4) and the tail's cone words (8 G); per contributing
+  // (arc, slot) the tail's overflow word share, its count and the atomic add
+  bytes = warp_sum(bytes);
+  if (lane == 0) atomicAdd(units, bytes + verts * 8ull * G);
+}
+
+__global__ void __launch_bounds__(256) k_cone_sigma64_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
+                                                            const int64_t *__restrict__ cbeg, int G, int gshift,
+                                                            int W, const int64_t *__restrict__ roff,
+                                                            const int32_t *__restrict__ rcol,
+                                                            const uint64_t *__restrict__ levL,
+                                                            const uint64_t *__restrict__ levP,
+                                                            uint64_t *__restrict__ sig, uint64_t *__restrict__ ovf,
+                                                            unsigned long long *units) {
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
+    const int64_t w = cw[q];
+    const uint64_t c = levL[w * G + g];
+    if (a == 0) bytes += 8ull;
+    if (!__any_sync(0xffffffffu, c != 0)) continue;
+    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[w + 1]);
+    uint64_t myovf = 0;
+    bytes += sigma_arcs(e0, e1, A, a, G, g, W, w, c, rcol, levP, sig, ovf, myovf);
+    if (a == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
+    for (int o = G; o < 32; o <<= 1) myovf |= __shfl_xor_sync(0xffffffffu, myovf, o);
+    if (a == 0 && myovf) atomicOr((unsigned long long *)&ovf[w * G + g], (unsigned long long)myovf);
+  }
+  bytes = warp_sum(bytes);
+  if (lane == 0 && bytes) atomicAdd(units, bytes);
 }
 
 // 128-bit counts for a re-run wave (G = 1): lane handles slots lane and
@@ -687,11 +832,23 @@ struct Sampler {
           k_expand_push<<<grid_for((size_t)fcount * 32, 256, 152 * 64), 256, 0, st>>>(
               off, col, flist, G, gshift, cur, nxt, ctl, units(K_PUSH));
         });
+        const ChunkTable &oc = g->out_chunks;
+        if (oc.count)
+          launch(S, K_PUSH, st, [&] {
+            k_expand_push_heavy<<<grid_for((size_t)oc.count * 32, 256, 152 * 64), 256, 0, st>>>(
+                oc.count, oc.rows(), oc.begins(), off, col, G, gshift, cur, nxt, ctl, units(K_PUSH));
+          });
       } else {
         launch(S, K_PULL, st, [&] {
           k_expand_pull<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(
               roff, rcol, n, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
         });
+        const ChunkTable &ic = g->in_chunks();
+        if (ic.count)
+          launch(S, K_PULL, st, [&] {
+            k_expand_pull_heavy<<<grid_for((size_t)ic.count * 32, 256, 152 * 64), 256, 0, st>>>(
+                ic.count, ic.rows(), ic.begins(), roff, rcol, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
+          });
       }
       CEN_CK(cudaMemsetAsync(&ctl->alive, 0, sizeof(ctl->alive) + sizeof(ctl->farcs) + sizeof(ctl->total) +
                                                  sizeof(ctl->fcount), st));
@@ -726,6 +883,12 @@ struct Sampler {
           k_cone_push<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(n, G, gshift, roff, rcol, up, tmp,
                                                                                units(K_CONE));
         });
+        const ChunkTable &ic = g->in_chunks();
+        if (ic.count)
+          launch(S, K_CONE, st, [&] {
+            k_cone_push_heavy<<<grid_for((size_t)ic.count * 32, 256, 152 * 64), 256, 0, st>>>(
+                ic.count, ic.rows(), ic.begins(), roff, rcol, G, gshift, up, tmp, units(K_CONE));
+          });
       }
       launch(S, K_CONE, st, [&] { k_cone_fin<<<grid_for(words, 256, 152 * 16), 256, 0, st>>>((int64_t)words, lev, tmp); });
     }
@@ -738,14 +901,24 @@ struct Sampler {
     uint64_t *ovf = job->ws.ovf.as<uint64_t>();
     for (int L = 1; L <= Lmax; ++L) {
       uint64_t *lv = level(L), *lp = level(L - 1);
-      launch(S, K_SIGMA, st, [&] {
-        if constexpr (sizeof(T) == 8)
+      if constexpr (sizeof(T) == 8) {
+        launch(S, K_SIGMA, st, [&] {
           k_cone_sigma64<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(
-              n, G, W, roff, rcol, lv, lp, (uint64_t *)sig, ovf, units(K_SIGMA));
-        else
+              n, G, gshift, W, roff, rcol, lv, lp, (uint64_t *)sig, ovf, units(K_SIGMA));
+        });
+        const ChunkTable &ic = g->in_chunks();
+        if (ic.count)
+          launch(S, K_SIGMA, st, [&] {
+            k_cone_sigma64_heavy<<<grid_for((size_t)ic.count * 32, 256, 152 * 64), 256, 0, st>>>(
+                ic.count, ic.rows(), ic.begins(), G, gshift, W, roff, rcol, lv, lp, (uint64_t *)sig, ovf,
+                units(K_SIGMA));
+          });
+      } else {
+        launch(S, K_SIGMA, st, [&] {
           k_cone_sigma128<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(n, roff, rcol, lv, lp,
                                                                                    (u128 *)sig, ovf);
-      });
+        });
+      }
     }
     publish_levels(Lmax);
     launch(S, K_WALK, st, [&] {

@@ -78,8 +78,8 @@ def test_sample_split_invariance():
 
 
 def test_path_counts_beyond_64_bits():
-    """40x40 grid: pairs with C(dx+dy, dx) >= 2^64 shortest paths take the 128-bit re-run."""
-    W = 40
+    """60x60 grid: pairs with C(dx+dy, dx) >= 2^64 shortest paths take the 128-bit re-run."""
+    W = 60
     g = I.grid_rewired(W, W, 0.0, 1)
     seed, m = 21, 400
     big = 0
