@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(256) k_cone_sigma64(int32_t n, int G, int gshi
     if (e1 - e0 > kHeavyRow) continue;
     uint64_t myovf = 0;
     bytes += sigma_arcs(e0, e1, A, a, G, g, W, w, c, rcol, levP, sig, ovf, myovf);
-    if (a == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
+    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
     for (int o = G; o < 32; o <<= 1) myovf |= __shfl_xor_sync(0xffffffffu, myovf, o);
     if (a == 0 && myovf) atomicOr((unsigned long long *)&ovf[w * G + g], (unsigned long long)myovf);
   }
@@ -529,12 +529,12 @@ __global__ void __launch_bounds__(256) k_cone_sigma64_heavy(int64_t nchunks, con
   for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
     const int64_t w = cw[q];
     const uint64_t c = levL[w * G + g];
-    if (a == 0) bytes += 8ull;
+    if (lane == 0) bytes += 8ull * G;
     if (!__any_sync(0xffffffffu, c != 0)) continue;
     const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[w + 1]);
     uint64_t myovf = 0;
     bytes += sigma_arcs(e0, e1, A, a, G, g, W, w, c, rcol, levP, sig, ovf, myovf);
-    if (a == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
+    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
     for (int o = G; o < 32; o <<= 1) myovf |= __shfl_xor_sync(0xffffffffu, myovf, o);
     if (a == 0 && myovf) atomicOr((unsigned long long *)&ovf[w * G + g], (unsigned long long)myovf);
   }
