@@ -113,6 +113,27 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
             uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
             int32_t *rounds, double *log, int32_t max_rounds);
 
+/* Allocation-free sum of the <= k largest positive entries of each row: the
+ * per-vector sup that cen_mcera computes (Rnum), for callers that supply their
+ * own matrix.  The paper has no counterpart; this entry point exists for
+ * callers that cannot allocate device memory, e.g. code running while another
+ * runtime or pool owns every byte of the device, or host callbacks in which
+ * cudaMalloc/cudaFree are not allowed because they would synchronize the
+ * device.  It allocates nothing: its scratch is one static device array
+ * (about 390 KB, held by every GPU that loads the library until exit) sized
+ * for at most 128 rows.
+ *   vals  device, int32 [nrows][n] row-major (only entries > 0 count);
+ *   n >= 0, 1 <= nrows <= 128, k >= 1, otherwise CEN_EINVAL;
+ *   out   host, int64 [nrows]: out[r] = sum of the min(k, #positive) largest
+ *         positive entries of row r (0 for a row without positives).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array, which keeps the last call's contents
+ * (each call clears what must start at zero): calls that overlap on the GPU,
+ * from any stream or thread, race.  Returns after the work on `stream` is done. */
+int cen_topk_positive_sum_noalloc(const int32_t *vals, int64_t n, int32_t nrows, int32_t k, int64_t *out,
+                                  void *stream);
+
 /* ---- inspection (copies device state to host; for tests and tooling) ---- */
 /* hoff[m+1], hmem[members], s[m], t[m], d[m] (d = -1 when unreachable); any may be NULL. */
 int cen_job_copy_samples(const cen_job *job, int64_t *hoff, int32_t *hmem, int32_t *s, int32_t *t, int32_t *d);

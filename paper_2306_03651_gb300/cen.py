@@ -68,6 +68,7 @@ def _load():
         "cen_job_set_timing": ([vp, ip], ip),
         "cen_job_stats": ([vp, vp, vp], ip),
         "cen_job_reset_stats": ([vp], ip),
+        "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)

@@ -5,6 +5,8 @@
 // sum_{u in S} R_q^u is the sum of the <= k largest positive R_q^u (the
 // objective is additive in S), found per row by an exact MSB-first radix
 // select; the same select over c_u gives the wimpy-variance numerator.
+#include <mutex>
+
 #include "job.cuh"
 
 namespace cen {
@@ -177,3 +179,79 @@ void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
 }
 
 }  // namespace cen
+
+// ---------------------------------------------------------------------------
+// Allocation-free top-k positive sums (no counterpart in the paper).
+//
+// Same kernels as the select inside cen_mcera, but the scratch (per-row
+// select state and the 256-bucket count/sum histograms) lives in one
+// file-scope __device__ array, so a call allocates no device memory.  Every
+// call on a device shares that array; calls that overlap on the GPU race.
+namespace cen {
+
+constexpr int kNoAllocMaxRows = 128;
+struct NoAllocScratch {
+  SelRow rows[kNoAllocMaxRows];
+  unsigned int hcnt[kNoAllocMaxRows * 256];
+  unsigned long long hsum[kNoAllocMaxRows * 256];
+};
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device.  The host-side name is only a stand-in for the symbol.
+static NoAllocScratch *noalloc_scratch() {
+  int dev = -1;
+  CEN_CK(cudaGetDevice(&dev));
+  CEN_REQUIRE(dev >= 0 && dev < kNoAllocMaxDevices, CEN_EINVAL, "cen_topk_positive_sum_noalloc: device id too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      fail(CEN_ECUDA, std::string("cen_topk_positive_sum_noalloc: cudaGetSymbolAddress failed: ") +
+                          cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  return static_cast<NoAllocScratch *>(g_noalloc_addr[dev]);
+}
+
+}  // namespace cen
+
+extern "C" int cen_topk_positive_sum_noalloc(const int32_t *vals, int64_t n, int32_t nrows, int32_t k, int64_t *out,
+                                             void *stream) {
+  using namespace cen;
+  try {
+    CEN_REQUIRE(vals && out, CEN_EINVAL, "cen_topk_positive_sum_noalloc: null argument");
+    CEN_REQUIRE(nrows >= 1 && nrows <= kNoAllocMaxRows, CEN_EINVAL,
+                "cen_topk_positive_sum_noalloc: nrows must be in [1, 128] (size of the static scratch)");
+    CEN_REQUIRE(n >= 0 && k >= 1, CEN_EINVAL, "cen_topk_positive_sum_noalloc: need n >= 0 and k >= 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    NoAllocScratch *sc = noalloc_scratch();
+    // the histograms must start at zero; the row states are written by k_sel_init
+    CEN_CK(cudaMemsetAsync(sc->hcnt, 0, sizeof(sc->hcnt) + sizeof(sc->hsum), st));
+    launch(nullptr, K_SELECT, st, [&] { k_sel_init<<<grid_for(nrows, 128), 128, 0, st>>>(sc->rows, nrows, k); });
+    const int bx = grid_for((size_t)(n > 0 ? n : 1), 256 * 8, 512);
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      launch(nullptr, K_SELECT, st, [&] {
+        k_sel_hist<<<dim3(bx, nrows), 256, 0, st>>>(vals, n, nrows, shift, sc->rows, sc->hcnt, sc->hsum);
+      });
+      launch(nullptr, K_SELECT, st,
+             [&] { k_sel_step<<<grid_for(nrows, 64), 64, 0, st>>>(nrows, shift, sc->rows, sc->hcnt, sc->hsum); });
+    }
+    SelRow h[kNoAllocMaxRows];
+    CEN_CK(cudaMemcpyAsync(h, sc->rows, sizeof(SelRow) * (size_t)nrows, cudaMemcpyDeviceToHost, st));
+    CEN_CK(cudaStreamSynchronize(st));
+    for (int r = 0; r < nrows; ++r) out[r] = h[r].sum;
+    return CEN_OK;
+  } catch (const Error &e) {
+    set_last_error(e.msg);
+    return e.code;
+  } catch (...) {
+    set_last_error("cen_topk_positive_sum_noalloc: unexpected internal error");
+    return CEN_ECUDA;
+  }
+}
