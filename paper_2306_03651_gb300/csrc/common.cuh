@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "cen.h"
@@ -63,6 +64,11 @@ struct DevBuf {
   }
   template <class T>
   T *as() const { return static_cast<T *>(p); }
+  void swap(DevBuf &o) {
+    std::swap(p, o.p);
+    std::swap(bytes, o.bytes);
+    std::swap(st, o.st);
+  }
 };
 
 // ------------------------------------------------------------- Philox
@@ -188,6 +194,10 @@ inline void launch(Stats *S, int cls, cudaStream_t st, F &&f) {
   CEN_CK(cudaGetLastError());
   if (S) S->end(cls, st, a, b);
 }
+
+// Blocks of `block` threads that are resident at once on the current device
+// (SM count x blocks per SM for this kernel), cached per kernel.
+int resident_grid(const void *kernel, int block);
 
 inline int grid_for(size_t items, int per_block, int cap = 152 * 32) {
   size_t g = (items + per_block - 1) / per_block;

@@ -16,14 +16,16 @@ struct WaveWS {
   std::vector<std::unique_ptr<DevBuf>> lev;   // lev[L]: [n][G] nodes at distance exactly L
   DevBuf lev_ptrs;                            // device array of lev[L] pointers
   int lev_ptrs_n = 0;
-  DevBuf tmp;                                 // [n][G] cone accumulation, kept zero between uses
+  DevBuf tmp;                                 // [n][G] cone scratch, kept zero between uses
   DevBuf sig64;                               // [n][W] path counts (64-bit)
   DevBuf sig128;                              // [n][64] path counts (128-bit, re-run of flagged slots)
   DevBuf ovf;                                 // [n][G] path-count overflow flags
   DevBuf slots;                               // per slot: j (u64), s, t, d (int32)
   DevBuf ctl;                                 // control block (see sampler.cu)
-  DevBuf flist;                               // frontier node list [n]
   DevBuf jlist;                               // explicit sample ids for a re-run
+  DevBuf arcs;                                // cone arc log of the current wave
+  size_t arc_cap = 0;                         // its capacity in arcs
+  DevBuf arc_range;                           // per level: [first, end) of its logged arcs
 };
 
 }  // namespace cen

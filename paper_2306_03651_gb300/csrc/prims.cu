@@ -3,6 +3,8 @@
 #include <stdio.h>
 
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -79,6 +81,23 @@ void Stats::reset(cudaStream_t st) {
     k[c].units = 0;
   }
   if (d_units) CEN_CK(cudaMemsetAsync(d_units, 0, sizeof(uint64_t) * K_COUNT, st));
+}
+
+// ------------------------------------------------------ occupancy
+int resident_grid(const void *kernel, int block) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, int> cache;
+  int dev = 0;
+  CEN_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({dev, kernel});
+  if (it != cache.end()) return it->second;
+  int sms = 0, per = 0;
+  CEN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CEN_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, block, 0));
+  const int g = sms * (per > 0 ? per : 1);
+  cache[{dev, kernel}] = g;
+  return g;
 }
 
 // -------------------------------------------------------------- scans

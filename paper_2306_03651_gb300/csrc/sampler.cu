@@ -4,11 +4,11 @@
 // (s_b, t_b); all W searches then advance together, one BFS level per step,
 // with every per-vertex set stored as G 64-bit words (bit b%64 of word b/64):
 //   1. discovery: lev[L][v] = slots whose BFS reaches v at distance exactly L.
-//      Before expanding level L, slot b stops if some in-neighbour of t_b is in
-//      lev[L] (then d(s,t) = L+1); the last level is never expanded.
-//   2. cone: walking levels downwards, lev[L] is cut to the nodes that lie on
-//      some shortest s_b -> t_b path (in-neighbours of t_b at level d-1, then
-//      in-neighbours of cone nodes one level lower).
+//      After level L+1 is built, slot b stops when t_b is in it (d = L+1), or
+//      when it is empty (t_b unreachable: Sec. 5 returns the empty set).
+//   2. cone: walking levels downwards, lev[L] is cut to the nodes on some
+//      shortest s_b -> t_b path: t_b on level d, then the in-neighbours on level
+//      L of cone nodes on level L+1.
 //   3. path counts sigma_b[v] (number of shortest s_b -> v paths) on the cone
 //      only, pulled from cone in-neighbours one level lower; every
 //      predecessor of a cone node is itself a cone node, so these equal the
@@ -18,6 +18,11 @@
 //      add sigma of those on level L-1, take the first whose running sum
 //      exceeds r.  The interior nodes are written to the hyper-edge in s->t
 //      order.  A slot whose sigma_t reaches 2^64 is re-run with 128-bit counts.
+//
+// Rows longer than kHeavyRow arcs are handled a second time by *_heavy
+// kernels, one warp per kChunk-arc chunk, merging with atomics; the light
+// kernels skip them.  Lane layout for per-vertex work: g = lane % G (word),
+// a = lane / G (one of A = 32/G arcs handled side by side).
 #include <algorithm>
 #include <cstring>
 
@@ -28,23 +33,41 @@ namespace cen {
 struct Ctl {
   unsigned long long active[32];  // slots still searching
   unsigned long long alive[32];   // slots whose newest level is non-empty
-  unsigned long long farcs;       // out-arcs of the frontier list
+  unsigned long long farcs;       // out-arcs of the newest level (push/pull choice)
   long long total;                // members appended by this wave
-  int fcount;                     // frontier list length
+  unsigned long long arcs;        // cone arcs logged by the cone pass
   int nflag;                      // slots flagged for 128-bit counts
   int err;                        // CEN_* code from device
-  int pad;
   int flagged[2048];
 };
 constexpr int kMaxG = 32;
 constexpr int kMaxW = 64 * kMaxG;
+constexpr int kLevelBlocks = 152 * 8;  // grid of the per-level node sweeps
+constexpr size_t kArcLogCap = (size_t)1 << 24;  // cone arcs logged per wave (24 B each)
+
+// Block-level OR of per-word masks and sum of arc counts, then one global
+// atomic per word and block.
+__device__ __forceinline__ void block_publish(uint64_t alive, unsigned long long arcs, int G, Ctl *ctl) {
+  __shared__ unsigned long long s_alive[32];
+  __shared__ unsigned long long s_arcs;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) s_alive[threadIdx.x] = 0;
+  if (threadIdx.x == 0) s_arcs = 0;
+  __syncthreads();
+  for (int o = G; o < 32; o <<= 1) alive |= __shfl_xor_sync(0xffffffffu, alive, o);
+  arcs = warp_sum(arcs);
+  if (lane < G && alive) atomicOr(&s_alive[lane], (unsigned long long)alive);
+  if (lane == 0 && arcs) atomicAdd(&s_arcs, arcs);
+  __syncthreads();
+  if ((int)threadIdx.x < G && s_alive[threadIdx.x]) atomicOr(&ctl->alive[threadIdx.x], s_alive[threadIdx.x]);
+  if (threadIdx.x == 0 && s_arcs) atomicAdd(&ctl->farcs, s_arcs);
+}
 
 // --------------------------------------------------------------- init
 template <class T>
 __global__ void k_wave_init(int count, uint64_t jbase, const uint64_t *__restrict__ jlist, int32_t n, uint64_t seed,
                             int G, int W, uint64_t *slot_j, int32_t *slot_s, int32_t *slot_t, int32_t *slot_d,
-                            uint64_t *lev0, uint64_t *vis, T *sig, const int64_t *__restrict__ off, int32_t *flist,
-                            Ctl *ctl) {
+                            uint64_t *lev0, uint64_t *vis, T *sig, const int64_t *__restrict__ off, Ctl *ctl) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < W; b += gridDim.x * blockDim.x) {
     if (b >= count) {
       slot_d[b] = -3;
@@ -65,158 +88,192 @@ __global__ void k_wave_init(int count, uint64_t jbase, const uint64_t *__restric
     atomicOr((unsigned long long *)&vis[(int64_t)s * G + g], bit);
     sig[(int64_t)s * W + b] = (T)1;
     atomicOr(&ctl->active[g], bit);
-    const int pos = atomicAdd(&ctl->fcount, 1);
-    flist[pos] = s;
     atomicAdd(&ctl->farcs, (unsigned long long)(off[s + 1] - off[s]));
   }
 }
 
 // ------------------------------------------------------- target check
-// Warp per slot: before level L is expanded, slot b finishes when t_b has an
-// in-neighbour at distance L (d = L+1), or when its level L is empty (t_b is
-// unreachable: Sec. 5 returns the empty set).
+// Thread per slot, after level L was built: t_b on level L ends the search
+// with d = L; an empty level L means t_b is unreachable (d = -1).
 __global__ void k_tcheck(int W, int G, int L, const int32_t *__restrict__ slot_t, int32_t *slot_d,
-                         const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
-                         const uint64_t *__restrict__ lev, Ctl *ctl, int use_alive, unsigned long long *units) {
+                         int32_t *slot_kind, const uint64_t *__restrict__ lev, Ctl *ctl) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < W; b += gridDim.x * blockDim.x) {
+    const int g = b >> 6;
+    const unsigned long long bit = 1ull << (b & 63);
+    if (!(ctl->active[g] & bit)) continue;
+    if (lev[(int64_t)slot_t[b] * G + g] & bit) {
+      slot_d[b] = L;
+      slot_kind[b] = 0;
+      atomicAnd(&ctl->active[g], ~bit);
+    } else if (!(ctl->alive[g] & bit)) {
+      slot_d[b] = -1;
+      atomicAnd(&ctl->active[g], ~bit);
+    }
+  }
+}
+
+// Warp per active slot whose target has at most kHeavyRow in-arcs, before
+// level L is expanded: an in-neighbour of t_b on level L gives d = L+1 and the
+// slot is not expanded further (kind 1: its cone is seeded from those
+// in-neighbours).  Slots with long-row targets are found after the expansion.
+__global__ void k_tcheck_before(int W, int G, int L, const int32_t *__restrict__ slot_t, int32_t *slot_d,
+                                int32_t *slot_kind, const int64_t *__restrict__ roff,
+                                const int32_t *__restrict__ rcol, const uint64_t *__restrict__ lev, Ctl *ctl) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned long long scanned = 0;
   for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < W; b += nwarps) {
     const int g = b >> 6;
     const unsigned long long bit = 1ull << (b & 63);
     if (!(((volatile unsigned long long *)ctl->active)[g] & bit)) continue;
-    if (use_alive && !(ctl->alive[g] & bit)) {
-      if (lane == 0) {
-        slot_d[b] = -1;
-        atomicAnd(&ctl->active[g], ~bit);
-      }
-      continue;
-    }
     const int32_t t = slot_t[b];
     const int64_t e0 = roff[t], e1 = roff[t + 1];
-    bool found = false;
-    for (int64_t base = e0; base < e1 && !found; base += 32) {
-      const int64_t i = base + lane;
-      bool hit = false;
-      if (i < e1) hit = (lev[(int64_t)rcol[i] * G + g] & bit) != 0;
-      found = __any_sync(0xffffffffu, hit);
-      scanned += 32;
-    }
-    if (found && lane == 0) {
+    if (e1 - e0 > kHeavyRow) continue;
+    bool hit = false;
+    for (int64_t i = e0 + lane; i < e1; i += 32) hit |= (lev[(int64_t)rcol[i] * G + g] & bit) != 0;
+    if (__any_sync(0xffffffffu, hit) && lane == 0) {
       slot_d[b] = L + 1;
+      slot_kind[b] = 1;
       atomicAnd(&ctl->active[g], ~bit);
     }
   }
-  if (lane == 0 && scanned) atomicAdd(units, scanned / 32);
 }
 
-// ----------------------------------------------------------- expansion
-// Lane layout for per-vertex word work: g = lane % G (word), a = lane / G
-// (which of the A = 32/G arcs handled in parallel).
 
+// OR of the level-L words (word g) of the tails of arcs [e0, e1): 32 arc ids
+// are loaded at once (coalesced) and handed out by shuffles, so the level
+// rows of up to 8 arcs per lane are in flight together.  Lanes with
+// need == 0 skip their loads.  With early exit, the scan stops after a
+// 32-arc chunk once every bit of `need` is found (across the warp).
+template <bool kEarlyExit>
+__device__ __forceinline__ uint64_t or_tail_words(int64_t e0, int64_t e1, int G, int gshift, int g, int a, int A,
+                                                  uint64_t need, const int32_t *__restrict__ rcol,
+                                                  const uint64_t *__restrict__ lev, unsigned long long &scanned) {
+  const int lane = threadIdx.x & 31;
+  uint64_t acc = 0;
+  for (int64_t base = e0; base < e1; base += 32) {
+    const int32_t myv = base + lane < e1 ? rcol[base + lane] : -1;
+    const int cnt = (int)min((int64_t)32, e1 - base);
+    for (int r0 = 0; r0 < G; r0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int src = ((r0 + u) << (5 - gshift)) + a;  // arc (r0+u)*A + a of this chunk
+        const int32_t v = __shfl_sync(0xffffffffu, myv, src & 31);
+        if (r0 + u < G && src < cnt && need) acc |= lev[(int64_t)v * G + g];
+      }
+    }
+    scanned += (unsigned long long)cnt;
+    if (kEarlyExit) {
+      uint64_t r = acc;
+      for (int o = G; o < 32; o <<= 1) r |= __shfl_xor_sync(0xffffffffu, r, o);
+      if (__all_sync(0xffffffffu, (r & need) == need)) break;
+    }
+  }
+  (void)A;
+  return acc;
+}
+// ----------------------------------------------------------- expansion
 // Bottom-up: every node w with an unreached active slot ORs the level-L words
-// of its in-neighbours (stopping once every unreached slot is found).
+// of its in-neighbours (stopping once every unreached slot is found), and
+// records the new bits: next level, reached set, level-not-empty masks.
 __global__ void __launch_bounds__(256) k_expand_pull(const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
-                                                     int32_t n, int G, int gshift, const uint64_t *__restrict__ lev,
-                                                     uint64_t *__restrict__ nxt, const uint64_t *__restrict__ vis,
-                                                     const Ctl *__restrict__ ctl, unsigned long long *units) {
+                                                     const int64_t *__restrict__ off, int32_t n, int G, int gshift,
+                                                     const uint64_t *__restrict__ lev, uint64_t *__restrict__ nxt,
+                                                     uint64_t *__restrict__ vis, Ctl *ctl,
+                                                     unsigned long long *units) {
   const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
   const uint64_t act = ctl->active[g];
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long scanned = 0, verts = 0, opened = 0;
+  unsigned long long scanned = 0, verts = 0, opened = 0, arcs = 0;
+  uint64_t alive = 0;
   for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nwarps) {
     ++verts;
-    const uint64_t unv = act & ~vis[w * G + g];
+    const uint64_t vw = vis[w * G + g];
+    const uint64_t unv = act & ~vw;
     if (!__any_sync(0xffffffffu, unv != 0)) {
       if (a == 0) nxt[w * G + g] = 0;
       continue;
     }
-    ++opened;
     const int64_t e0 = roff[w], e1 = roff[w + 1];
     if (e1 - e0 > kHeavyRow) {  // long rows: k_expand_pull_heavy ORs their chunks in
       if (a == 0) nxt[w * G + g] = 0;
       continue;
     }
-    uint64_t acc = 0;
-    for (int64_t base = e0; base < e1; base += (int64_t)A * 8) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t i = base + (int64_t)u * A + a;
-        if (i < e1) acc |= lev[(int64_t)rcol[i] * G + g];
-      }
-      if (e1 - e0 > (int64_t)A * 8) {  // long rows: stop once every unreached slot is found
-        uint64_t r = acc;
-        for (int o = G; o < 32; o <<= 1) r |= __shfl_xor_sync(0xffffffffu, r, o);
-        if (__all_sync(0xffffffffu, (r & unv) == unv)) {
-          scanned += (uint64_t)(base + (int64_t)A * 8 - e0);
-          goto reduced;
-        }
-      }
-    }
-    scanned += (uint64_t)(e1 - e0);
-  reduced:
+    ++opened;
+    uint64_t acc = or_tail_words<true>(e0, e1, G, gshift, g, a, A, unv, rcol, lev, scanned);
     for (int o = G; o < 32; o <<= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
-    if (a == 0) nxt[w * G + g] = acc & unv;
+    {
+      const uint64_t nb = acc & unv;
+      if (a == 0) {
+        nxt[w * G + g] = nb;
+        if (nb) vis[w * G + g] = vw | nb;
+      }
+      alive |= nb;
+      if (__any_sync(0xffffffffu, nb != 0) && lane == 0) arcs += (unsigned long long)(off[w + 1] - off[w]);
+    }
   }
+  block_publish(alive, arcs, G, ctl);
   // algorithmic bytes: every node reads its reached word and writes its next
-  // word (16 G); an opened node reads its two offsets (16) and, per scanned
+  // word (16 G); an opened node reads its offsets (16) and, per scanned
   // in-arc, the arc (4) and the tail's level words (8 G)
   if (lane == 0 && verts)
     atomicAdd(units, verts * 16ull * G + opened * 16ull + scanned * (4ull + 8ull * G));
 }
 
-// Bottom-up over the chunks of long rows: warp per chunk, OR of the chunk's
-// in-neighbour level words, merged into the node's next word.
+// Bottom-up over the chunks of long rows: OR of the chunk's in-neighbour level
+// words, merged into the node's next word and reached set.  Chunks of one
+// node may see each other's new bits in its reached word; the union of what
+// they add is still exactly the node's new bits.
 __global__ void __launch_bounds__(256) k_expand_pull_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
                                                            const int64_t *__restrict__ cbeg,
                                                            const int64_t *__restrict__ roff,
                                                            const int32_t *__restrict__ rcol, int G, int gshift,
                                                            const uint64_t *__restrict__ lev, uint64_t *nxt,
-                                                           const uint64_t *__restrict__ vis,
-                                                           const Ctl *__restrict__ ctl, unsigned long long *units) {
+                                                           uint64_t *vis, Ctl *ctl, unsigned long long *units) {
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+  const uint64_t act = ctl->active[g];
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0, arcs = 0;
+  uint64_t alive = 0;
+  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
+    const int32_t w = cw[q];
+    const uint64_t unv = act & ~*(volatile uint64_t *)&vis[(int64_t)w * G + g];
+    if (lane == 0) bytes += 8ull * G;
+    if (!__any_sync(0xffffffffu, unv != 0)) continue;
+    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[w + 1]);
+    unsigned long long sc = 0;
+    uint64_t acc = or_tail_words<true>(e0, e1, G, gshift, g, a, A, unv, rcol, lev, sc);
+    for (int o = G; o < 32; o <<= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
+    const uint64_t nb = acc & unv;
+    uint64_t fresh = 0;
+    if (a == 0 && nb) {
+      const uint64_t old = atomicOr((unsigned long long *)&nxt[(int64_t)w * G + g], (unsigned long long)nb);
+      fresh = nb & ~old;
+      if (fresh) atomicOr((unsigned long long *)&vis[(int64_t)w * G + g], (unsigned long long)fresh);
+    }
+    alive |= fresh;
+    if (__any_sync(0xffffffffu, fresh != 0) && lane == 0) arcs += (unsigned long long)(e1 - e0);
+    if (lane == 0) bytes += 16ull + sc * (4ull + 8ull * G) + 16ull * G;
+  }
+  block_publish(alive, arcs, G, ctl);
+  if (lane == 0 && bytes) atomicAdd(units, bytes);
+}
+
+// Top-down: every node v on level L ORs its active level words into the
+// next-level words of its out-neighbours (next must start zeroed).
+__global__ void __launch_bounds__(256) k_expand_push(const int64_t *__restrict__ off, const int32_t *__restrict__ col,
+                                                     int32_t n, int G, int gshift, const uint64_t *__restrict__ lev,
+                                                     uint64_t *nxt, const Ctl *__restrict__ ctl,
+                                                     unsigned long long *units) {
   const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
   const uint64_t act = ctl->active[g];
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long bytes = 0;
-  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
-    const int32_t w = cw[q];
-    const uint64_t unv = act & ~vis[(int64_t)w * G + g];
-    bytes += 8ull * G;
-    if (!__any_sync(0xffffffffu, unv != 0)) continue;
-    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[w + 1]);
-    uint64_t acc = 0;
-    for (int64_t base = e0; base < e1; base += (int64_t)A * 8) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t i = base + (int64_t)u * A + a;
-        if (i < e1) acc |= lev[(int64_t)rcol[i] * G + g];
-      }
-    }
-    for (int o = G; o < 32; o <<= 1) acc |= __shfl_xor_sync(0xffffffffu, acc, o);
-    const uint64_t nb = acc & unv;
-    if (a == 0 && nb) atomicOr((unsigned long long *)&nxt[(int64_t)w * G + g], (unsigned long long)nb);
-    bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G) + 16ull * G;
-  }
-  if (lane == 0 && bytes) atomicAdd(units, bytes);
-}
-
-// Top-down: every frontier node v ORs its active level-L words into the
-// next-level words of its out-neighbours.
-__global__ void __launch_bounds__(256) k_expand_push(const int64_t *__restrict__ off, const int32_t *__restrict__ col,
-                                                     const int32_t *__restrict__ flist, int G, int gshift,
-                                                     const uint64_t *__restrict__ lev, uint64_t *nxt,
-                                                     const Ctl *__restrict__ ctl, unsigned long long *units) {
-  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
-  const uint64_t act = ctl->active[g];
-  const int fcount = ctl->fcount;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned long long scanned = 0;
-  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < fcount; q += nwarps) {
-    const int32_t v = flist[q];
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+    const uint64_t f = lev[v * G + g] & act;
+    if (lane == 0) bytes += 8ull * G;
+    if (!__any_sync(0xffffffffu, f != 0)) continue;
     const int64_t e0 = off[v], e1 = off[v + 1];
     if (e1 - e0 > kHeavyRow) continue;  // long rows: k_expand_push_heavy
-    const uint64_t f = lev[(int64_t)v * G + g] & act;
-    if (!__any_sync(0xffffffffu, f != 0)) continue;
     for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -224,16 +281,14 @@ __global__ void __launch_bounds__(256) k_expand_push(const int64_t *__restrict__
         if (i < e1 && f) atomicOr((unsigned long long *)&nxt[(int64_t)col[i] * G + g], (unsigned long long)f);
       }
     }
-    // bytes: offsets (16) and level words (8 G) of v; per out-arc the arc (4)
-    // and an 8-byte read-modify-write per non-empty word
+    // bytes: offsets of v; per out-arc the arc (4) and an 8-byte
+    // read-modify-write per non-empty word
     const int nzw = __popc(__ballot_sync(0xffffffffu, f != 0 && a == 0));
-    scanned += 16ull + 8ull * G + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
+    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
   }
-  if (lane == 0 && scanned) atomicAdd(units, scanned);
+  if (lane == 0 && bytes) atomicAdd(units, bytes);
 }
 
-// Top-down over the chunks of long out-rows: a chunk of a frontier node pushes
-// its active level words to the chunk's out-neighbours.
 __global__ void __launch_bounds__(256) k_expand_push_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
                                                            const int64_t *__restrict__ cbeg,
                                                            const int64_t *__restrict__ off,
@@ -247,7 +302,7 @@ __global__ void __launch_bounds__(256) k_expand_push_heavy(int64_t nchunks, cons
   for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
     const int32_t v = cw[q];
     const uint64_t f = lev[(int64_t)v * G + g] & act;
-    bytes += 8ull * G;
+    if (lane == 0) bytes += 8ull * G;
     if (!__any_sync(0xffffffffu, f != 0)) continue;
     const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, off[v + 1]);
     for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
@@ -258,17 +313,16 @@ __global__ void __launch_bounds__(256) k_expand_push_heavy(int64_t nchunks, cons
       }
     }
     const int nzw = __popc(__ballot_sync(0xffffffffu, f != 0 && a == 0));
-    bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
+    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
   }
   if (lane == 0 && bytes) atomicAdd(units, bytes);
 }
 
-// Thread per word: keep only newly reached active slots, mark them reached,
-// collect the non-empty nodes into the frontier list and OR the per-word
-// "level not empty" masks.
+// After a push: keep only newly reached active slots, mark them reached and
+// publish the level masks and out-arc count.
 __global__ void __launch_bounds__(256) k_level_finalize(int32_t n, int G, int gshift, uint64_t *__restrict__ nxt,
                                                         uint64_t *__restrict__ vis, const int64_t *__restrict__ off,
-                                                        int32_t *flist, Ctl *ctl, unsigned long long *units) {
+                                                        Ctl *ctl, unsigned long long *units) {
   const int lane = threadIdx.x & 31;
   const int g = lane & (G - 1);
   const uint64_t act = ctl->active[g];
@@ -280,32 +334,24 @@ __global__ void __launch_bounds__(256) k_level_finalize(int32_t n, int G, int gs
     const int64_t idx = base + lane;
     uint64_t nb = 0;
     if (idx < words) {
-      nb = nxt[idx] & ~vis[idx] & act;
-      nxt[idx] = nb;
-      if (nb) vis[idx] |= nb;
+      const uint64_t x = nxt[idx];
+      if (x) {
+        const uint64_t v = vis[idx];
+        nb = x & ~v & act;
+        nxt[idx] = nb;
+        if (nb) vis[idx] = v | nb;
+      }
     }
     alive |= nb;
     uint64_t any = nb;
     for (int o = 1; o < G; o <<= 1) any |= __shfl_xor_sync(0xffffffffu, any, o);
-    const bool head = (g == 0) && idx < words && any != 0;
-    const unsigned hm = __ballot_sync(0xffffffffu, head);
-    if (hm) {
-      int basepos = 0;
-      if (lane == __ffs(hm) - 1) basepos = atomicAdd(&ctl->fcount, __popc(hm));
-      basepos = __shfl_sync(0xffffffffu, basepos, __ffs(hm) - 1);
-      if (head) {
-        const int32_t w = (int32_t)(idx >> gshift);
-        flist[basepos + __popc(hm & ((1u << lane) - 1u))] = w;
-        arcs += (unsigned long long)(off[w + 1] - off[w]);
-      }
+    if (g == 0 && idx < words && any) {
+      const int64_t w = idx >> gshift;
+      arcs += (unsigned long long)(off[w + 1] - off[w]);
     }
   }
-  for (int o = G; o < 32; o <<= 1) alive |= __shfl_xor_sync(0xffffffffu, alive, o);
-  if (lane < G && alive) atomicOr(&ctl->alive[g], (unsigned long long)alive);
-  arcs = warp_sum(arcs);
-  if (lane == 0 && arcs) atomicAdd(&ctl->farcs, arcs);
-  // bytes: each word is read twice (next, reached) and written twice
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(units, (unsigned long long)words * 32ull);
+  block_publish(alive, arcs, G, ctl);
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(units, (unsigned long long)words * 16ull);
 }
 
 // ------------------------------------------------------ offsets + store
@@ -360,220 +406,279 @@ __global__ void __launch_bounds__(1024) k_wave_append(int count, uint64_t jbase,
 }
 
 // ------------------------------------------------------------------ cone
-// Warp per slot with d-1 == L: in-neighbours of t_b at level L seed the cone.
+// The cone pass also records the cone's arcs: (w on level L, x on level L+1,
+// word g, slots f) meaning sigma_b[x] += sigma_b[w] for every b in f.  The
+// path-count pass then only visits these arcs.
+struct ConeArc {
+  int32_t w, x;
+  int32_t g, pad;
+  uint64_t f;
+};
+struct ArcLog {
+  ConeArc *arcs;
+  unsigned long long *count;  // total appended (may exceed cap: then the log is unusable)
+  unsigned long long cap;
+};
+
+// Thread per kind-0 slot with d == L >= 2: t_b is the cone on its own level;
+// its count starts at zero.
+template <class T>
 __global__ void k_cone_seed(int W, int G, int L, const int32_t *__restrict__ slot_t, const int32_t *__restrict__ slot_d,
-                            const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
-                            const uint64_t *__restrict__ lev, uint64_t *tmp) {
+                            const int32_t *__restrict__ slot_kind, uint64_t *cone, T *sig) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < W; b += gridDim.x * blockDim.x) {
+    if (slot_d[b] != L || L < 2 || slot_kind[b] != 0) continue;
+    const int64_t t = slot_t[b];
+    atomicOr((unsigned long long *)&cone[t * G + (b >> 6)], 1ull << (b & 63));
+    sig[t * W + b] = 0;
+  }
+}
+
+// Warp per kind-1 slot with d - 1 == L >= 1: t_b's count starts at zero and its
+// in-neighbours on level L seed the cone, each arc logged.
+template <class T>
+__global__ void k_cone_seed_pred(int W, int G, int L, const int32_t *__restrict__ slot_t,
+                                 const int32_t *__restrict__ slot_d, const int32_t *__restrict__ slot_kind,
+                                 const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
+                                 const uint64_t *__restrict__ lev, uint64_t *cone, T *sig, ArcLog log) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < W; b += nwarps) {
-    const int d = slot_d[b];
-    if (d < 2 || d - 1 != L) continue;
+    if (slot_d[b] - 1 != L || slot_d[b] < 2 || slot_kind[b] != 1) continue;
     const int g = b >> 6;
     const unsigned long long bit = 1ull << (b & 63);
     const int32_t t = slot_t[b];
-    for (int64_t i = roff[t] + lane; i < roff[t + 1]; i += 32) {
-      const int32_t x = rcol[i];
-      if (lev[(int64_t)x * G + g] & bit) atomicOr((unsigned long long *)&tmp[(int64_t)x * G + g], bit);
-    }
-  }
-}
-
-// Warp per node x: cone words of x at level L+1 go to x's in-neighbours.
-__global__ void __launch_bounds__(256) k_cone_push(int32_t n, int G, int gshift, const int64_t *__restrict__ roff,
-                                                   const int32_t *__restrict__ rcol, const uint64_t *__restrict__ up,
-                                                   uint64_t *tmp, unsigned long long *units) {
-  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long scanned = 0, verts = 0;
-  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
-    ++verts;
-    const uint64_t c = up[x * G + g];
-    if (!__any_sync(0xffffffffu, c != 0)) continue;
-    const int64_t e0 = roff[x], e1 = roff[x + 1];
-    if (e1 - e0 > kHeavyRow) continue;  // long rows: k_cone_push_heavy
-    for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t i = base + (int64_t)u * A + a;
-        if (i < e1 && c) atomicOr((unsigned long long *)&tmp[(int64_t)rcol[i] * G + g], (unsigned long long)c);
+    if (lane == 0) sig[(int64_t)t * W + b] = 0;
+    const int64_t e0 = roff[t], e1 = roff[t + 1];
+    for (int64_t base = e0; base < e1; base += 32) {
+      const int64_t i = base + lane;
+      int32_t w = -1;
+      bool hit = false;
+      if (i < e1) {
+        w = rcol[i];
+        hit = (lev[(int64_t)w * G + g] & bit) != 0;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, hit);
+      if (!m) continue;
+      unsigned long long pos = 0;
+      if (lane == __ffs(m) - 1) pos = atomicAdd(log.count, (unsigned long long)__popc(m));
+      pos = __shfl_sync(0xffffffffu, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
+      if (hit) {
+        atomicOr((unsigned long long *)&cone[(int64_t)w * G + g], bit);
+        if (pos < log.cap) log.arcs[pos] = ConeArc{w, t, g, 0, (uint64_t)bit};
       }
     }
-    const int nzw = __popc(__ballot_sync(0xffffffffu, c != 0 && a == 0));
-    scanned += 16ull + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
   }
-  // bytes: every node's cone words (8 G); a non-empty node's offsets, arcs and
-  // one read-modify-write per non-empty word and arc
-  if (lane == 0) atomicAdd(units, scanned + verts * 8ull * G);
 }
 
-// Chunks of long rows: cone words of x at level L+1 go to the chunk's in-neighbours.
+// Level 1 of the cone: the only predecessor is s_b (count 1), so every cone
+// node on level 1 has count 1 and nothing needs logging.
+template <class T>
+__global__ void k_cone_level1(int64_t words, int G, int gshift, int W, const uint64_t *__restrict__ lev1, T *sig) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t c = lev1[i];
+    if (!c) continue;
+    const int64_t x = i >> gshift;
+    const int g = (int)(i & (G - 1));
+    for (uint64_t z = c; z; z &= z - 1) sig[x * W + 64 * g + (__ffsll((long long)z) - 1)] = (T)1;
+  }
+}
+
+// Arc records are staged per warp in shared memory and appended to the log
+// in batches (one global atomic per batch).
+constexpr int kWarpArcBuf = 64;
+struct WarpArcBuf {
+  ConeArc rec[kWarpArcBuf];
+  int n;
+};
+
+__device__ __forceinline__ void arcbuf_flush(WarpArcBuf &B, const ArcLog &log) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  const int nrec = B.n;
+  if (nrec == 0) return;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(log.count, (unsigned long long)nrec);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int k = lane; k < nrec; k += 32)
+    if (base + k < log.cap) log.arcs[base + k] = B.rec[k];
+  __syncwarp();
+  if (lane == 0) B.n = 0;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void arcbuf_put(WarpArcBuf &B, const ArcLog &log, bool have, const ConeArc &r) {
+  const int lane = threadIdx.x & 31;
+  const unsigned m = __ballot_sync(0xffffffffu, have);
+  if (!m) return;
+  if (B.n + __popc(m) > kWarpArcBuf) arcbuf_flush(B, log);
+  const int pos = B.n + __popc(m & ((1u << lane) - 1u));
+  if (have) B.rec[pos] = r;
+  __syncwarp();
+  if (lane == 0) B.n += __popc(m);
+  __syncwarp();
+}
+
+// Cone slots c of node x on level L+1 mark x's in-neighbours that are on
+// level L for those slots (read first, then one atomic OR if any), and log
+// each such arc.  Arc ids are loaded 32 at a time and shuffled out.
+__device__ __forceinline__ unsigned long long cone_arcs(int64_t e0, int64_t e1, int G, int gshift, int g, int a,
+                                                        uint64_t c, int32_t x, const int32_t *__restrict__ rcol,
+                                                        const uint64_t *__restrict__ lev, uint64_t *cone,
+                                                        WarpArcBuf &B, const ArcLog &log) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long hits = 0;
+  for (int64_t base = e0; base < e1; base += 32) {
+    const int32_t myv = base + lane < e1 ? rcol[base + lane] : -1;
+    const int cnt = (int)min((int64_t)32, e1 - base);
+    for (int r0 = 0; r0 < G; r0 += 4) {
+      int32_t w[4];
+      uint64_t f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int src = ((r0 + u) << (5 - gshift)) + a;
+        w[u] = __shfl_sync(0xffffffffu, myv, src & 31);
+        f[u] = 0;
+        if (r0 + u < G && src < cnt && c) f[u] = lev[(int64_t)w[u] * G + g] & c;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (f[u]) {
+          atomicOr((unsigned long long *)&cone[(int64_t)w[u] * G + g], (unsigned long long)f[u]);
+          ++hits;
+        }
+        arcbuf_put(B, log, f[u] != 0, ConeArc{w[u], x, g, 0, f[u]});
+      }
+    }
+  }
+  return hits;
+}
+
+// Warp per node x on level L+1 with cone slots c: zero x's counts for those
+// slots, then mark and log its cone in-arcs (long rows: k_cone_push_heavy).
+template <class T>
+__global__ void __launch_bounds__(256) k_cone_push(int32_t n, int G, int gshift, int W,
+                                                   const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
+                                                   const uint64_t *__restrict__ up, const uint64_t *__restrict__ lev,
+                                                   uint64_t *cone, T *sig, ArcLog log, unsigned long long *units) {
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+  __shared__ WarpArcBuf s_buf[8];
+  WarpArcBuf &B = s_buf[threadIdx.x >> 5];
+  if (lane == 0) B.n = 0;
+  __syncwarp();
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += nwarps) {
+    const uint64_t c = up[x * G + g];
+    if (lane == 0) bytes += 8ull * G;
+    if (!__any_sync(0xffffffffu, c != 0)) continue;
+    for (uint64_t z = c; z; z &= z - 1) {
+      const int b = __ffsll((long long)z) - 1;
+      if ((b & (A - 1)) == a) sig[x * W + 64 * g + b] = 0;
+    }
+    const int64_t e0 = roff[x], e1 = roff[x + 1];
+    if (e1 - e0 > kHeavyRow) continue;
+    const unsigned long long hits = cone_arcs(e0, e1, G, gshift, g, a, c, (int32_t)x, rcol, lev, cone, B, log);
+    const int nzw = __popc(__ballot_sync(0xffffffffu, c != 0 && a == 0));
+    bytes += 40ull * hits;
+    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * nzw);
+  }
+  arcbuf_flush(B, log);
+  // bytes: every node's cone words (8 G); per non-empty node its offsets and,
+  // per in-arc, the arc (4) and the level word of each non-empty cone word
+  // (8); per hit a 16-byte atomic read-modify-write and a 24-byte arc record
+  bytes = warp_sum(bytes);
+  if (lane == 0 && bytes) atomicAdd(units, bytes);
+}
+
 __global__ void __launch_bounds__(256) k_cone_push_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
                                                          const int64_t *__restrict__ cbeg,
                                                          const int64_t *__restrict__ roff,
                                                          const int32_t *__restrict__ rcol, int G, int gshift,
-                                                         const uint64_t *__restrict__ up, uint64_t *tmp,
+                                                         const uint64_t *__restrict__ up,
+                                                         const uint64_t *__restrict__ lev, uint64_t *cone, ArcLog log,
                                                          unsigned long long *units) {
-  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift;
+  __shared__ WarpArcBuf s_buf[8];
+  WarpArcBuf &B = s_buf[threadIdx.x >> 5];
+  if (lane == 0) B.n = 0;
+  __syncwarp();
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long bytes = 0;
   for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
     const int32_t x = cw[q];
     const uint64_t c = up[(int64_t)x * G + g];
-    bytes += 8ull * G;
-    if (!__any_sync(0xffffffffu, c != 0)) continue;
-    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[x + 1]);
-    for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t i = base + (int64_t)u * A + a;
-        if (i < e1 && c) atomicOr((unsigned long long *)&tmp[(int64_t)rcol[i] * G + g], (unsigned long long)c);
-      }
-    }
-    const int nzw = __popc(__ballot_sync(0xffffffffu, c != 0 && a == 0));
-    bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 16ull * nzw);
-  }
-  if (lane == 0 && bytes) atomicAdd(units, bytes);
-}
-
-// Thread per word: lev[L] &= tmp; tmp = 0.
-__global__ void k_cone_fin(int64_t words, uint64_t *__restrict__ lev, uint64_t *__restrict__ tmp) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t c = tmp[i];
-    const uint64_t l = lev[i];
-    if (l) lev[i] = l & c;
-    if (c) tmp[i] = 0;
-  }
-}
-
-// ------------------------------------------------------------- counts
-// Path counts on the cone, level L from level L-1.  Lane layout (g, a) as in
-// the expansion.  Warp per node w with cone slots c (word g): the counts of
-// those slots are zeroed, then every in-neighbour v with cone slots f = c &
-// levP[v] adds its counts with 64-bit atomics; a wrap-around (true sum >=
-// 2^64) or an overflowed predecessor sets the slot's overflow flag.  Long
-// rows only get zeroed here; k_cone_sigma64_heavy adds their chunks.
-__device__ __forceinline__ unsigned long long sigma_arcs(int64_t e0, int64_t e1, int A, int a, int G, int g, int W,
-                                                         int64_t w, uint64_t c, const int32_t *__restrict__ rcol,
-                                                         const uint64_t *__restrict__ levP,
-                                                         uint64_t *__restrict__ sig,
-                                                         const uint64_t *__restrict__ ovf, uint64_t &myovf) {
-  unsigned long long bytes = 0;
-  for (int64_t base = e0; base < e1; base += (int64_t)A * 4) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t i = base + (int64_t)u * A + a;
-      if (i >= e1) continue;
-      const int32_t v = rcol[i];
-      uint64_t f = levP[(int64_t)v * G + g] & c;
-      if (!f) continue;
-      myovf |= ovf[(int64_t)v * G + g] & f;
-      bytes += 8ull;
-      while (f) {
-        const int b = __ffsll((long long)f) - 1;
-        f &= f - 1;
-        const unsigned long long x = sig[(int64_t)v * W + 64 * g + b];
-        const unsigned long long old = atomicAdd((unsigned long long *)&sig[w * W + 64 * g + b], x);
-        if (old + x < old) myovf |= 1ull << b;
-        bytes += 24ull;
-      }
-    }
-  }
-  return bytes;
-}
-
-__global__ void __launch_bounds__(256) k_cone_sigma64(int32_t n, int G, int gshift, int W,
-                                                      const int64_t *__restrict__ roff,
-                                                      const int32_t *__restrict__ rcol,
-                                                      const uint64_t *__restrict__ levL,
-                                                      const uint64_t *__restrict__ levP, uint64_t *__restrict__ sig,
-                                                      uint64_t *__restrict__ ovf, unsigned long long *units) {
-  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long bytes = 0, verts = 0;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nwarps) {
-    ++verts;
-    const uint64_t c = levL[w * G + g];
-    if (!__any_sync(0xffffffffu, c != 0)) continue;
-    for (uint64_t z = c; z; z &= z - 1) {
-      const int b = __ffsll((long long)z) - 1;
-      if ((b & (A - 1)) == a) sig[w * W + 64 * g + b] = 0;
-    }
-    __syncwarp();
-    const int64_t e0 = roff[w], e1 = roff[w + 1];
-    if (e1 - e0 > kHeavyRow) continue;
-    uint64_t myovf = 0;
-    bytes += sigma_arcs(e0, e1, A, a, G, g, W, w, c, rcol, levP, sig, ovf, myovf);
-    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
-    for (int o = G; o < 32; o <<= 1) myovf |= __shfl_xor_sync(0xffffffffu, myovf, o);
-    if (a == 0 && myovf) atomicOr((unsigned long long *)&ovf[w * G + g], (unsigned long long)myovf);
-  }
-  // bytes: every node's cone words (8 G); per opened node its offsets and,
-  // per in-arc, the arc (4) and the tail's cone words (8 G); per contributing
-  // (arc, slot) the tail's overflow word share, its count and the atomic add
-  bytes = warp_sum(bytes);
-  if (lane == 0) atomicAdd(units, bytes + verts * 8ull * G);
-}
-
-__global__ void __launch_bounds__(256) k_cone_sigma64_heavy(int64_t nchunks, const int32_t *__restrict__ cw,
-                                                            const int64_t *__restrict__ cbeg, int G, int gshift,
-                                                            int W, const int64_t *__restrict__ roff,
-                                                            const int32_t *__restrict__ rcol,
-                                                            const uint64_t *__restrict__ levL,
-                                                            const uint64_t *__restrict__ levP,
-                                                            uint64_t *__restrict__ sig, uint64_t *__restrict__ ovf,
-                                                            unsigned long long *units) {
-  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  unsigned long long bytes = 0;
-  for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nchunks; q += nwarps) {
-    const int64_t w = cw[q];
-    const uint64_t c = levL[w * G + g];
     if (lane == 0) bytes += 8ull * G;
     if (!__any_sync(0xffffffffu, c != 0)) continue;
-    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[w + 1]);
-    uint64_t myovf = 0;
-    bytes += sigma_arcs(e0, e1, A, a, G, g, W, w, c, rcol, levP, sig, ovf, myovf);
-    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * G);
-    for (int o = G; o < 32; o <<= 1) myovf |= __shfl_xor_sync(0xffffffffu, myovf, o);
-    if (a == 0 && myovf) atomicOr((unsigned long long *)&ovf[w * G + g], (unsigned long long)myovf);
+    const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[x + 1]);
+    const unsigned long long hits = cone_arcs(e0, e1, G, gshift, g, a, c, x, rcol, lev, cone, B, log);
+    const int nzw = __popc(__ballot_sync(0xffffffffu, c != 0 && a == 0));
+    bytes += 40ull * hits;
+    if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * nzw);
   }
+  arcbuf_flush(B, log);
   bytes = warp_sum(bytes);
   if (lane == 0 && bytes) atomicAdd(units, bytes);
 }
 
-// 128-bit counts for a re-run wave (G = 1): lane handles slots lane and
-// lane + 32, each summing its cone in-neighbours' counts serially.
-__global__ void __launch_bounds__(256) k_cone_sigma128(int32_t n, const int64_t *__restrict__ roff,
-                                                       const int32_t *__restrict__ rcol,
-                                                       const uint64_t *__restrict__ levL,
-                                                       const uint64_t *__restrict__ levP, u128 *__restrict__ sig,
-                                                       uint64_t *__restrict__ ovf) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n; w += nwarps) {
-    const uint64_t c = levL[w];
-    if (!c) continue;
-    uint64_t myovf = 0;
-    for (int h = 0; h < 2; ++h) {
-      const int b = lane + 32 * h;
-      if (!((c >> b) & 1)) continue;
-      u128 acc = 0;
-      bool of = false;
-      for (int64_t i = roff[w]; i < roff[w + 1]; ++i) {
-        const int32_t v = rcol[i];
-        if (!((levP[v] >> b) & 1)) continue;
-        if ((ovf[v] >> b) & 1) of = true;
-        const u128 x = sig[(int64_t)v * 64 + b];
-        const u128 r = acc + x;
-        if (r < acc) of = true;
-        acc = r;
-      }
-      sig[w * 64 + b] = acc;
-      if (of) myovf |= 1ull << b;
+// Path counts over the logged cone arcs of one level: thread per arc (w, x,
+// g, f): sigma_b[x] += sigma_b[w] for each slot b in f, with 64-bit atomics;
+// a wrap-around (true sum >= 2^64) or an overflowed sigma_b[w] flags slot b
+// of x.  The arcs of a level are read from [range[0], range[1]).
+__global__ void __launch_bounds__(256) k_sigma_arcs64(const ConeArc *__restrict__ arcs,
+                                                      const unsigned long long *__restrict__ range, int G, int W,
+                                                      uint64_t *__restrict__ sig, uint64_t *__restrict__ ovf,
+                                                      unsigned long long *units) {
+  const unsigned long long r0 = range[0], r1 = range[1];
+  unsigned long long bytes = 0;
+  for (unsigned long long i = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const ConeArc e = arcs[i];
+    uint64_t f = e.f;
+    uint64_t of = ovf[(int64_t)e.w * G + e.g] & f;
+    bytes += 32ull;
+    while (f) {
+      const int b = __ffsll((long long)f) - 1;
+      f &= f - 1;
+      const unsigned long long v = sig[(int64_t)e.w * W + 64 * e.g + b];
+      const unsigned long long old = atomicAdd((unsigned long long *)&sig[(int64_t)e.x * W + 64 * e.g + b], v);
+      if (old + v < old) of |= 1ull << b;
+      bytes += 24ull;
     }
-    for (int o = 16; o; o >>= 1) myovf |= __shfl_xor_sync(0xffffffffu, myovf, o);
-    if (lane == 0 && myovf) ovf[w] |= myovf;
+    if (of) atomicOr((unsigned long long *)&ovf[(int64_t)e.x * G + e.g], (unsigned long long)of);
+  }
+  // bytes: the 24-byte record and the tail's overflow word per arc; per slot
+  // the tail's count and a 16-byte atomic read-modify-write
+  bytes = warp_sum(bytes);
+  if ((threadIdx.x & 31) == 0 && bytes) atomicAdd(units, bytes);
+}
+
+// 128-bit variant for a re-run wave: the 128-bit add is two 64-bit atomics
+// (low word, then high word plus carry); all terms are non-negative, so the
+// high word wraps exactly when the true sum reaches 2^128.
+__global__ void __launch_bounds__(256) k_sigma_arcs128(const ConeArc *__restrict__ arcs,
+                                                       const unsigned long long *__restrict__ range, int W,
+                                                       u128 *__restrict__ sig, uint64_t *__restrict__ ovf) {
+  const unsigned long long r0 = range[0], r1 = range[1];
+  for (unsigned long long i = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const ConeArc e = arcs[i];
+    uint64_t f = e.f;
+    uint64_t of = ovf[e.w] & f;
+    while (f) {
+      const int b = __ffsll((long long)f) - 1;
+      f &= f - 1;
+      const u128 v = sig[(int64_t)e.w * W + b];
+      unsigned long long *dst = (unsigned long long *)&sig[(int64_t)e.x * W + b];
+      const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+      const unsigned long long olo = atomicAdd(dst, lo);
+      const unsigned long long add_hi = hi + (olo + lo < olo ? 1ull : 0ull);
+      if (add_hi < hi) of |= 1ull << b;  // hi + carry wrapped
+      if (add_hi) {
+        const unsigned long long ohi = atomicAdd(dst + 1, add_hi);
+        if (ohi + add_hi < ohi) of |= 1ull << b;
+      }
+    }
+    if (of) atomicOr((unsigned long long *)&ovf[e.x], (unsigned long long)of);
   }
 }
 
@@ -582,12 +687,6 @@ __device__ __forceinline__ uint64_t shfl_up_T(uint64_t v, int o) { return __shfl
 __device__ __forceinline__ u128 shfl_up_T(u128 v, int o) {
   const uint64_t lo = __shfl_up_sync(0xffffffffu, (uint64_t)v, o);
   const uint64_t hi = __shfl_up_sync(0xffffffffu, (uint64_t)(v >> 64), o);
-  return ((u128)hi << 64) | lo;
-}
-__device__ __forceinline__ uint64_t shfl_xor_T(uint64_t v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ u128 shfl_xor_T(u128 v, int o) {
-  const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)v, o);
-  const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(v >> 64), o);
   return ((u128)hi << 64) | lo;
 }
 __device__ __forceinline__ u128 shfl_T(u128 v, int src) {
@@ -603,9 +702,9 @@ __device__ __forceinline__ u128 draw_below(uint64_t seed, uint64_t j, uint32_t p
   return uniform_below128(seed, j, p, B);
 }
 
-// Warp per slot (see the file header, step 4).  T = uint64_t: a slot whose
-// sigma_t does not fit is appended to ctl->flagged.  T = u128: such a slot
-// sets ctl->err = CEN_EOVERFLOW.
+// Warp per slot (see the file header, step 4).  Arcs are scanned 128 at a time
+// (4 chunks of 32 loaded together).  T = uint64_t: a slot whose sigma_t
+// overflowed is appended to ctl->flagged.  T = u128: it sets ctl->err.
 template <class T>
 __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ slot_j,
                        const int32_t *__restrict__ slot_t, const int32_t *__restrict__ slot_d,
@@ -623,32 +722,7 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
     const uint64_t bit = 1ull << (b & 63);
     const uint64_t j = slot_j[b];
     int32_t v = slot_t[b];
-    int L = d;
-    // sigma_t = sum over in-neighbours on level d-1 (all of them are cone nodes)
-    T acc = 0;
-    bool of = false;
-    {
-      const uint64_t *lp = levs[L - 1];
-      for (int64_t i = roff[v] + lane; i < roff[v + 1]; i += 32) {
-        const int32_t x = rcol[i];
-        if (lp[(int64_t)x * G + g] & bit) {
-          if (ovf[(int64_t)x * G + g] & bit) of = true;
-          const T y = sig[(int64_t)x * Wst + b];
-          const T r = acc + y;
-          if (r < acc) of = true;
-          acc = r;
-        }
-      }
-      for (int o = 16; o; o >>= 1) {
-        const T y = shfl_xor_T(acc, o);
-        const bool oy = __shfl_xor_sync(0xffffffffu, (int)of, o) != 0;
-        const T r = acc + y;
-        of = of || oy || (r < acc);
-        acc = r;
-      }
-      scanned += (uint64_t)(roff[v + 1] - roff[v]);
-    }
-    if (of) {
+    if (ovf[(int64_t)v * G + g] & bit) {
       if (lane == 0) {
         if (sizeof(T) == 8) {
           const int pos = atomicAdd(&ctl->nflag, 1);
@@ -659,35 +733,45 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
       }
       continue;
     }
-    T sv = acc;
+    T sv = sig[(int64_t)v * Wst + b];
     const int64_t hbase = hoff[j];
     uint32_t step = 0;
+    int L = d;
     while (L >= 2) {
       const T r = draw_below(seed, j, kPurposeWalk0 + step, sv);
       const uint64_t *lp = levs[L - 1];
       T cum = 0;
       int32_t pick = -1;
       const int64_t e0 = roff[v], e1 = roff[v + 1];
-      for (int64_t base = e0; base < e1; base += 32) {
-        const int64_t i = base + lane;
-        int32_t x = -1;
-        T val = 0;
-        if (i < e1) {
-          x = rcol[i];
-          if (lp[(int64_t)x * G + g] & bit) val = sig[(int64_t)x * Wst + b];
+      for (int64_t base = e0; base < e1 && pick < 0; base += 128) {
+        int32_t x[4];
+        T val[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t i = base + 32 * u + lane;
+          x[u] = i < e1 ? rcol[i] : -1;
         }
-        T pre = val;
-        for (int o = 1; o < 32; o <<= 1) {
-          const T y = shfl_up_T(pre, o);
-          if (lane >= o) pre += y;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          val[u] = 0;
+          if (x[u] >= 0 && (lp[(int64_t)x[u] * G + g] & bit)) val[u] = sig[(int64_t)x[u] * Wst + b];
         }
-        const unsigned hit = __ballot_sync(0xffffffffu, (cum + pre) > r);
-        scanned += 1;
-        if (hit) {
-          pick = __shfl_sync(0xffffffffu, x, __ffs(hit) - 1);
-          break;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (pick >= 0) break;
+          T pre = val[u];
+          for (int o = 1; o < 32; o <<= 1) {
+            const T y = shfl_up_T(pre, o);
+            if (lane >= o) pre += y;
+          }
+          const unsigned hit = __ballot_sync(0xffffffffu, (cum + pre) > r);
+          if (hit) {
+            pick = __shfl_sync(0xffffffffu, x[u], __ffs(hit) - 1);
+          } else {
+            cum += shfl_T(pre, 31);
+          }
         }
-        cum += shfl_T(pre, 31);
+        scanned += 128;
       }
       if (pick < 0) {  // cannot happen with consistent counts
         if (lane == 0) atomicExch(&ctl->err, CEN_EINVAL);
@@ -700,7 +784,7 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
       ++step;
     }
   }
-  if (lane == 0 && scanned) atomicAdd(units, scanned);
+  if (lane == 0 && scanned) atomicAdd(units, scanned * 12ull);
 }
 
 // --------------------------------------------------------------- sign words
@@ -739,7 +823,7 @@ struct Sampler {
   Ctl *ctl = nullptr;
   Ctl *hctl = nullptr;  // pinned mirror (header part)
   uint64_t *slot_j = nullptr;
-  int32_t *slot_s = nullptr, *slot_t = nullptr, *slot_d = nullptr;
+  int32_t *slot_s = nullptr, *slot_t = nullptr, *slot_d = nullptr, *slot_kind = nullptr;
 
   unsigned long long *units(int cls) { return (unsigned long long *)(job->stats.d_units + cls); }
 
@@ -749,19 +833,25 @@ struct Sampler {
     while ((1 << gshift) < G) ++gshift;
     W = 64 * G;
     WaveWS &ws = job->ws;
-    ws.G = G;
     const size_t words = (size_t)n * G;
     ws.vis.ensure(words * 8, st);
-    ws.tmp.ensure(words * 8, st);
     ws.ovf.ensure(words * 8, st);
+    if (ws.G != G || !ws.tmp.p) {  // the cone scratch is kept zero between waves of one width
+      ws.tmp.ensure(words * 8, st);
+      CEN_CK(cudaMemsetAsync(ws.tmp.p, 0, words * 8, st));
+    }
+    ws.G = G;
     ws.ctl.ensure(sizeof(Ctl), st);
-    ws.slots.ensure((size_t)kMaxW * (8 + 4 * 3), st);
-    ws.flist.ensure((size_t)std::max<int64_t>(n, kMaxW) * 4, st);  // init lists one source per slot
+    ws.slots.ensure((size_t)kMaxW * (8 + 4 * 4), st);
+    if (ws.arc_cap == 0)  // grows (and the wave is redone) when a wave logs more arcs
+      ws.arc_cap = std::min<size_t>(kArcLogCap, std::max<size_t>((size_t)1 << 16, 2 * words));
+    ws.arcs.ensure(sizeof(ConeArc) * ws.arc_cap, st);
     ctl = ws.ctl.as<Ctl>();
     slot_j = ws.slots.as<uint64_t>();
     slot_s = (int32_t *)(slot_j + kMaxW);
     slot_t = slot_s + kMaxW;
     slot_d = slot_t + kMaxW;
+    slot_kind = slot_d + kMaxW;
     hctl = (Ctl *)host_staging(job, sizeof(Ctl));
   }
 
@@ -801,7 +891,6 @@ struct Sampler {
   int discover(int count, uint64_t jbase, const uint64_t *jlist, T *sig) {
     const size_t words = (size_t)n * G;
     uint64_t *vis = job->ws.vis.as<uint64_t>();
-    int32_t *flist = job->ws.flist.as<int32_t>();
     CEN_CK(cudaMemsetAsync(vis, 0, words * 8, st));
     CEN_CK(cudaMemsetAsync(job->ws.ovf.p, 0, words * 8, st));
     CEN_CK(cudaMemsetAsync(ctl, 0, offsetof(Ctl, flagged), st));
@@ -813,24 +902,24 @@ struct Sampler {
     const int32_t *rcol = g->in_col();
     launch(S, K_PAIRS, st, [&] {
       k_wave_init<T><<<grid_for(W, 256), 256, 0, st>>>(count, jbase, jlist, n, job->seed, G, W, slot_j, slot_s,
-                                                       slot_t, slot_d, lev0, vis, sig, off, flist, ctl);
-    });
-    launch(S, K_TCHECK, st, [&] {
-      k_tcheck<<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, 0, slot_t, slot_d, roff, rcol, lev0, ctl, 0,
-                                                              units(K_TCHECK));
+                                                       slot_t, slot_d, lev0, vis, sig, off, ctl);
     });
     fetch_ctl_head();
     int L = 0;
+    const int nb = grid_for((size_t)n * 32, 256, kLevelBlocks);
     while (any_active()) {
       uint64_t *cur = level(L);
       uint64_t *nxt = level(L + 1);
+      launch(S, K_TCHECK, st, [&] {
+        k_tcheck_before<<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, roff,
+                                                                       rcol, cur, ctl);
+      });
       const bool push = (double)hctl->farcs * 4.0 < (double)g->nnz;
-      const long long fcount = hctl->fcount;
+      CEN_CK(cudaMemsetAsync(&ctl->alive, 0, sizeof(ctl->alive) + sizeof(ctl->farcs), st));
       if (push) {
         CEN_CK(cudaMemsetAsync(nxt, 0, words * 8, st));
         launch(S, K_PUSH, st, [&] {
-          k_expand_push<<<grid_for((size_t)fcount * 32, 256, 152 * 64), 256, 0, st>>>(
-              off, col, flist, G, gshift, cur, nxt, ctl, units(K_PUSH));
+          k_expand_push<<<resident_grid((const void *)k_expand_push, 256), 256, 0, st>>>(off, col, n, G, gshift, cur, nxt, ctl, units(K_PUSH));
         });
         const ChunkTable &oc = g->out_chunks;
         if (oc.count)
@@ -838,27 +927,23 @@ struct Sampler {
             k_expand_push_heavy<<<grid_for((size_t)oc.count * 32, 256, 152 * 64), 256, 0, st>>>(
                 oc.count, oc.rows(), oc.begins(), off, col, G, gshift, cur, nxt, ctl, units(K_PUSH));
           });
+        launch(S, K_LEVEL_FIN, st, [&] {
+          k_level_finalize<<<resident_grid((const void *)k_level_finalize, 256), 256, 0, st>>>(n, G, gshift, nxt, vis, off, ctl,
+                                                                               units(K_LEVEL_FIN));
+        });
       } else {
         launch(S, K_PULL, st, [&] {
-          k_expand_pull<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(
-              roff, rcol, n, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
+          k_expand_pull<<<resident_grid((const void *)k_expand_pull, 256), 256, 0, st>>>(roff, rcol, off, n, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
         });
         const ChunkTable &ic = g->in_chunks();
         if (ic.count)
           launch(S, K_PULL, st, [&] {
-            k_expand_pull_heavy<<<grid_for((size_t)ic.count * 32, 256, 152 * 64), 256, 0, st>>>(
+            k_expand_pull_heavy<<<resident_grid((const void *)k_expand_pull_heavy, 256), 256, 0, st>>>(
                 ic.count, ic.rows(), ic.begins(), roff, rcol, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
           });
       }
-      CEN_CK(cudaMemsetAsync(&ctl->alive, 0, sizeof(ctl->alive) + sizeof(ctl->farcs) + sizeof(ctl->total) +
-                                                 sizeof(ctl->fcount), st));
-      launch(S, K_LEVEL_FIN, st, [&] {
-        k_level_finalize<<<grid_for(words, 256, 152 * 32), 256, 0, st>>>(n, G, gshift, nxt, vis, off, flist, ctl,
-                                                                         units(K_LEVEL_FIN));
-      });
       launch(S, K_TCHECK, st, [&] {
-        k_tcheck<<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, L + 1, slot_t, slot_d, roff, rcol, nxt, ctl,
-                                                                1, units(K_TCHECK));
+        k_tcheck<<<grid_for(W, 256), 256, 0, st>>>(W, G, L + 1, slot_t, slot_d, slot_kind, nxt, ctl);
       });
       fetch_ctl_head();
       ++L;
@@ -867,58 +952,74 @@ struct Sampler {
     return L;
   }
 
-  void cone(int Lmax) {
+  // Cut every level >= 1 to the cone (lev[L] and the zeroed scratch swap
+  // roles), zero the cone's counts (level 1: set them to 1) and log its arcs
+  // above level 1; range[2U], range[2U+1] bound the arcs into level U.
+  // Returns the number of logged arcs (the log is usable iff <= its capacity).
+  template <class T>
+  unsigned long long cone(int Lmax, T *sig) {
     const size_t words = (size_t)n * G;
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
-    uint64_t *tmp = job->ws.tmp.as<uint64_t>();
-    for (int L = Lmax; L >= 0; --L) {
+    WaveWS &ws = job->ws;
+    const int nb = grid_for((size_t)n * 32, 256, kLevelBlocks);
+    ws.arc_range.ensure(sizeof(unsigned long long) * 2 * (size_t)(Lmax + 3), st);
+    unsigned long long *range = ws.arc_range.as<unsigned long long>();
+    CEN_CK(cudaMemsetAsync(range, 0, sizeof(unsigned long long) * 2 * (size_t)(Lmax + 3), st));
+    unsigned long long *count = &ctl->arcs;
+    CEN_CK(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+    const ArcLog log{ws.arcs.as<ConeArc>(), count, (unsigned long long)ws.arc_cap};
+    const ChunkTable &ic = g->in_chunks();
+    for (int L = Lmax; L >= 1; --L) {
       uint64_t *lev = level(L);
+      uint64_t *cone = ws.tmp.as<uint64_t>();
       launch(S, K_CONE, st, [&] {
-        k_cone_seed<<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, roff, rcol, lev, tmp);
+        k_cone_seed<T><<<grid_for(W, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, cone, sig);
       });
+      CEN_CK(cudaMemcpyAsync(range + 2 * (L + 1), count, 8, cudaMemcpyDeviceToDevice, st));
       if (L < Lmax) {
-        uint64_t *up = level(L + 1);
+        const uint64_t *up = level(L + 1);
         launch(S, K_CONE, st, [&] {
-          k_cone_push<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(n, G, gshift, roff, rcol, up, tmp,
-                                                                               units(K_CONE));
+          k_cone_push<T><<<resident_grid((const void *)k_cone_push<T>, 256), 256, 0, st>>>(n, G, gshift, W, roff, rcol, up, lev, cone, sig, log, units(K_CONE));
         });
-        const ChunkTable &ic = g->in_chunks();
         if (ic.count)
           launch(S, K_CONE, st, [&] {
-            k_cone_push_heavy<<<grid_for((size_t)ic.count * 32, 256, 152 * 64), 256, 0, st>>>(
-                ic.count, ic.rows(), ic.begins(), roff, rcol, G, gshift, up, tmp, units(K_CONE));
+            k_cone_push_heavy<<<resident_grid((const void *)k_cone_push_heavy, 256), 256, 0, st>>>(
+                ic.count, ic.rows(), ic.begins(), roff, rcol, G, gshift, up, lev, cone, log, units(K_CONE));
           });
       }
-      launch(S, K_CONE, st, [&] { k_cone_fin<<<grid_for(words, 256, 152 * 16), 256, 0, st>>>((int64_t)words, lev, tmp); });
+      launch(S, K_CONE, st, [&] {
+        k_cone_seed_pred<T><<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, roff,
+                                                                           rcol, lev, cone, sig, log);
+      });
+      CEN_CK(cudaMemcpyAsync(range + 2 * (L + 1) + 1, count, 8, cudaMemcpyDeviceToDevice, st));
+      ws.lev[L]->swap(ws.tmp);  // the cone becomes level L
+      CEN_CK(cudaMemsetAsync(ws.tmp.p, 0, words * 8, st));
     }
+    launch(S, K_CONE, st, [&] {
+      k_cone_level1<T><<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, G, gshift, W, level(1),
+                                                                          sig);
+    });
+    fetch_ctl_head();
+    return hctl->arcs;
   }
 
+  // Path counts level by level over the logged arcs (levels 2 .. Lmax+1;
+  // Lmax+1 holds only targets found before their last expansion).
   template <class T>
   void sigma_and_walk(int count, int Lmax, T *sig) {
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
     uint64_t *ovf = job->ws.ovf.as<uint64_t>();
-    for (int L = 1; L <= Lmax; ++L) {
-      uint64_t *lv = level(L), *lp = level(L - 1);
-      if constexpr (sizeof(T) == 8) {
-        launch(S, K_SIGMA, st, [&] {
-          k_cone_sigma64<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(
-              n, G, gshift, W, roff, rcol, lv, lp, (uint64_t *)sig, ovf, units(K_SIGMA));
-        });
-        const ChunkTable &ic = g->in_chunks();
-        if (ic.count)
-          launch(S, K_SIGMA, st, [&] {
-            k_cone_sigma64_heavy<<<grid_for((size_t)ic.count * 32, 256, 152 * 64), 256, 0, st>>>(
-                ic.count, ic.rows(), ic.begins(), G, gshift, W, roff, rcol, lv, lp, (uint64_t *)sig, ovf,
-                units(K_SIGMA));
-          });
-      } else {
-        launch(S, K_SIGMA, st, [&] {
-          k_cone_sigma128<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(n, roff, rcol, lv, lp,
-                                                                                   (u128 *)sig, ovf);
-        });
-      }
+    const ConeArc *arcs = job->ws.arcs.as<ConeArc>();
+    for (int L = 2; L <= Lmax + 1; ++L) {
+      const unsigned long long *range = job->ws.arc_range.as<unsigned long long>() + 2 * L;
+      launch(S, K_SIGMA, st, [&] {
+        if constexpr (sizeof(T) == 8)
+          k_sigma_arcs64<<<resident_grid((const void *)k_sigma_arcs64, 256), 256, 0, st>>>(arcs, range, G, W, (uint64_t *)sig, ovf, units(K_SIGMA));
+        else
+          k_sigma_arcs128<<<resident_grid((const void *)k_sigma_arcs128, 256), 256, 0, st>>>(arcs, range, W, (u128 *)sig, ovf);
+      });
     }
     publish_levels(Lmax);
     launch(S, K_WALK, st, [&] {
@@ -961,31 +1062,38 @@ void sample_append(cen_job *job, uint64_t m_new) {
   int64_t members = job->members;
   std::vector<uint64_t> flagged_js;
   for (uint64_t j0 = m0; j0 < m1;) {
-    const int G = pick_G(m1 - j0, g->n, job->sigma_budget);
-    sp.setup(G);
+    sp.setup(pick_G(m1 - j0, g->n, job->sigma_budget));
     const int count = (int)std::min<uint64_t>((uint64_t)sp.W, m1 - j0);
     job->ws.sig64.ensure((size_t)g->n * sp.W * 8, st);
     uint64_t *sig = job->ws.sig64.as<uint64_t>();
-    const int Lmax = sp.discover<uint64_t>(count, j0, nullptr, sig);
-    launch(sp.S, K_APPEND, st, [&] {
-      k_wave_append<<<1, 1024, 0, st>>>(count, j0, sp.slot_s, sp.slot_t, sp.slot_d, job->hoff.as<int64_t>(),
-                                        job->ps.as<int32_t>(), job->pt.as<int32_t>(), job->pd.as<int32_t>(),
-                                        job->bmax.as<int>(), sp.ctl);
-    });
-    sp.fetch_ctl_head();
-    const int64_t wave_total = sp.hctl->total;
-    job->hmem.ensure(4 * (size_t)(members + wave_total + 1), st, 4 * (size_t)members);
-    sp.cone(Lmax);
+    int Lmax = 0;
+    int64_t wave_total = 0;
+    for (;;) {  // a wave whose cone arcs overflow the log is redone with a larger log
+      Lmax = sp.discover<uint64_t>(count, j0, nullptr, sig);
+      launch(sp.S, K_APPEND, st, [&] {
+        k_wave_append<<<1, 1024, 0, st>>>(count, j0, sp.slot_s, sp.slot_t, sp.slot_d, job->hoff.as<int64_t>(),
+                                          job->ps.as<int32_t>(), job->pt.as<int32_t>(), job->pd.as<int32_t>(),
+                                          job->bmax.as<int>(), sp.ctl);
+      });
+      sp.fetch_ctl_head();
+      wave_total = sp.hctl->total;
+      job->hmem.ensure(4 * (size_t)(members + wave_total + 1), st, 4 * (size_t)members);
+      const unsigned long long narcs = sp.cone<uint64_t>(Lmax, sig);
+      if (narcs <= job->ws.arc_cap) break;
+      job->ws.arc_cap = (size_t)(narcs + narcs / 4);
+      job->ws.arcs.release();
+      sp.setup(sp.G);
+    }
     sp.sigma_and_walk<uint64_t>(count, Lmax, sig);
     CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CEN_CK(cudaStreamSynchronize(st));
     CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent path counts in the backward walk");
     if (sp.hctl->nflag > 0) {
-      std::vector<uint64_t> js(sp.hctl->nflag);
       std::vector<uint64_t> slot_js(count);
+      std::vector<int> fl(sp.hctl->flagged, sp.hctl->flagged + sp.hctl->nflag);
       CEN_CK(cudaMemcpyAsync(slot_js.data(), sp.slot_j, 8 * (size_t)count, cudaMemcpyDeviceToHost, st));
       CEN_CK(cudaStreamSynchronize(st));
-      for (int q = 0; q < sp.hctl->nflag; ++q) flagged_js.push_back(slot_js[sp.hctl->flagged[q]]);
+      for (int b : fl) flagged_js.push_back(slot_js[b]);
     }
     members += wave_total;
     j0 += (uint64_t)count;
@@ -1004,8 +1112,15 @@ void sample_append(cen_job *job, uint64_t m_new) {
       CEN_CK(cudaStreamSynchronize(st));
       sp.hctl = (Ctl *)host_staging(job, sizeof(Ctl));
       u128 *sig = job->ws.sig128.as<u128>();
-      const int Lmax = sp.discover<u128>(count, 0, job->ws.jlist.as<uint64_t>(), sig);
-      sp.cone(Lmax);
+      int Lmax = 0;
+      for (;;) {
+        Lmax = sp.discover<u128>(count, 0, job->ws.jlist.as<uint64_t>(), sig);
+        const unsigned long long narcs = sp.cone<u128>(Lmax, sig);
+        if (narcs <= job->ws.arc_cap) break;
+        job->ws.arc_cap = (size_t)(narcs + narcs / 4);
+        job->ws.arcs.release();
+        sp.setup(1);
+      }
       sp.sigma_and_walk<u128>(count, Lmax, sig);
       CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, offsetof(Ctl, flagged), cudaMemcpyDeviceToHost, st));
       CEN_CK(cudaStreamSynchronize(st));
