@@ -2,6 +2,7 @@
 // Algorithm 1's progressive loop and the FP64 bounds.  Every entry point
 // converts internal failures into a status code and a thread-local message.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -134,6 +135,10 @@ int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, c
   job->t = t;
   job->nw = (t + 31) / 32;
   job->st = (cudaStream_t)stream;
+  if (const char *e = getenv("CEN_WAVE_WORDS")) {  // wave width in 64-slot words (1..32), a tuning knob
+    const int w = atoi(e);
+    if (w >= 1 && w <= 32) job->max_wave_words = w;
+  }
   try {
     job->stats.init(job->st);
   } catch (...) {

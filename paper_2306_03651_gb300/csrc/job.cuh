@@ -57,6 +57,7 @@ struct cen_job {
   size_t host_bytes = 0;
   cen::Stats stats;
   size_t sigma_budget = (size_t)16 << 30;  // bytes allowed for the [n][W] path-count table
+  int max_wave_words = 32;                 // upper bound on G (wave width / 64)
 };
 
 namespace cen {

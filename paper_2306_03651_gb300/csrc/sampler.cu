@@ -43,6 +43,7 @@ struct Ctl {
 constexpr int kMaxG = 32;
 constexpr int kMaxW = 64 * kMaxG;
 constexpr int kLevelBlocks = 152 * 8;  // grid of the per-level node sweeps
+constexpr int kWalkUnroll = 8;          // 32-arc chunks in flight per walk step
 constexpr size_t kArcLogCap = (size_t)1 << 24;  // cone arcs logged per wave (24 B each)
 
 // Block-level OR of per-word masks and sum of arc counts, then one global
@@ -702,8 +703,8 @@ __device__ __forceinline__ u128 draw_below(uint64_t seed, uint64_t j, uint32_t p
   return uniform_below128(seed, j, p, B);
 }
 
-// Warp per slot (see the file header, step 4).  Arcs are scanned 128 at a time
-// (4 chunks of 32 loaded together).  T = uint64_t: a slot whose sigma_t
+// Warp per slot (see the file header, step 4).  Arcs are scanned 256 at a time
+// (8 chunks of 32 loaded together).  T = uint64_t: a slot whose sigma_t
 // overflowed is appended to ctl->flagged.  T = u128: it sets ctl->err.
 template <class T>
 __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ slot_j,
@@ -743,21 +744,22 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
       T cum = 0;
       int32_t pick = -1;
       const int64_t e0 = roff[v], e1 = roff[v + 1];
-      for (int64_t base = e0; base < e1 && pick < 0; base += 128) {
-        int32_t x[4];
-        T val[4];
+      for (int64_t base = e0; base < e1 && pick < 0; base += 32 * kWalkUnroll) {
+        int32_t x[kWalkUnroll];
+        T val[kWalkUnroll];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kWalkUnroll; ++u) {
           const int64_t i = base + 32 * u + lane;
           x[u] = i < e1 ? rcol[i] : -1;
         }
+        uint64_t hit_bits = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          val[u] = 0;
-          if (x[u] >= 0 && (lp[(int64_t)x[u] * G + g] & bit)) val[u] = sig[(int64_t)x[u] * Wst + b];
-        }
+        for (int u = 0; u < kWalkUnroll; ++u)
+          if (x[u] >= 0 && (lp[(int64_t)x[u] * G + g] & bit)) hit_bits |= 1ull << u;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kWalkUnroll; ++u) val[u] = ((hit_bits >> u) & 1) ? sig[(int64_t)x[u] * Wst + b] : (T)0;
+#pragma unroll
+        for (int u = 0; u < kWalkUnroll; ++u) {
           if (pick >= 0) break;
           T pre = val[u];
           for (int o = 1; o < 32; o <<= 1) {
@@ -771,7 +773,7 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
             cum += shfl_T(pre, 31);
           }
         }
-        scanned += 128;
+        scanned += 32 * kWalkUnroll;
       }
       if (pick < 0) {  // cannot happen with consistent counts
         if (lane == 0) atomicExch(&ctl->err, CEN_EINVAL);
@@ -1032,9 +1034,9 @@ struct Sampler {
 
 }  // namespace
 
-static int pick_G(uint64_t remaining, int32_t n, size_t budget) {
+static int pick_G(uint64_t remaining, int32_t n, size_t budget, int gmax) {
   int G = 1;
-  while (G < kMaxG && (uint64_t)64 * G < remaining) G <<= 1;
+  while (G < kMaxG && G < gmax && (uint64_t)64 * G < remaining) G <<= 1;
   while (G > 1 && (size_t)n * 64 * G * 8 > budget) G >>= 1;
   return G;
 }
@@ -1062,7 +1064,7 @@ void sample_append(cen_job *job, uint64_t m_new) {
   int64_t members = job->members;
   std::vector<uint64_t> flagged_js;
   for (uint64_t j0 = m0; j0 < m1;) {
-    sp.setup(pick_G(m1 - j0, g->n, job->sigma_budget));
+    sp.setup(pick_G(m1 - j0, g->n, job->sigma_budget, job->max_wave_words));
     const int count = (int)std::min<uint64_t>((uint64_t)sp.W, m1 - j0);
     job->ws.sig64.ensure((size_t)g->n * sp.W * 8, st);
     uint64_t *sig = job->ws.sig64.as<uint64_t>();
