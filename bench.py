@@ -35,6 +35,8 @@ WORKLOADS = {
     "rmat18": ("R-MAT scale 18 (262,144 ids), edge factor 16, (.57,.19,.19,.05), undirected, dedup, no self-loops, LCC",
                I.rmat18_lcc),
     "ba2000": ("Barabasi-Albert n=2000, 4 edges per new node, seed 1", I.ba_2000),
+    "grid2048": ("2048x2048 4-neighbour grid, 1% of edges rewired, undirected", I.grid2048_rewired),
+    "rmat22d": ("R-MAT scale 22, edge factor 16, directed, dedup, no self-loops", I.rmat22_directed),
 }
 
 

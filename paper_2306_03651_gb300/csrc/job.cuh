@@ -17,8 +17,10 @@ struct WaveWS {
   DevBuf lev_ptrs;                            // device array of lev[L] pointers
   int lev_ptrs_n = 0;
   DevBuf tmp;                                 // [n][G] cone scratch, kept zero between uses
-  DevBuf sig64;                               // [n][W] path counts (64-bit)
-  DevBuf sig128;                              // [n][64] path counts (128-bit, re-run of flagged slots)
+  DevBuf any;                                 // [n][G] cone slots of each node (all levels)
+  DevBuf base;                                // [n*G+1] exclusive prefix of their popcounts
+  DevBuf cnt;                                 // [n*G] popcounts (scan input)
+  DevBuf sigc;                                // compact path counts, one per (node, cone slot)
   DevBuf ovf;                                 // [n][G] path-count overflow flags
   DevBuf slots;                               // per slot: j (u64), s, t, d (int32)
   DevBuf ctl;                                 // control block (see sampler.cu)
@@ -56,7 +58,7 @@ struct cen_job {
   void *host = nullptr;
   size_t host_bytes = 0;
   cen::Stats stats;
-  size_t sigma_budget = (size_t)16 << 30;  // bytes allowed for the [n][W] path-count table
+  size_t level_budget = (size_t)1 << 30;   // bytes allowed for one [n][G] level array
   int max_wave_words = 32;                 // upper bound on G (wave width / 64)
 };
 

@@ -46,6 +46,18 @@ constexpr int kLevelBlocks = 152 * 8;  // grid of the per-level node sweeps
 constexpr int kWalkUnroll = 8;          // 32-arc chunks in flight per walk step
 constexpr size_t kArcLogCap = (size_t)1 << 24;  // cone arcs logged per wave (24 B each)
 
+// Compact path-count store: only (node, slot) pairs on some cone get a count.
+// any[v*G+g] holds every cone slot of node v (over all levels; a node is on
+// at most one level per slot); base[v*G+g] is the exclusive prefix sum of
+// their popcounts, so slot b of word g of v is entry base + rank of b.
+struct SigIdx {
+  const uint64_t *any;
+  const int64_t *base;
+  __device__ __forceinline__ int64_t operator()(int64_t vg, int b) const {
+    return base[vg] + __popcll(any[vg] & ((1ull << b) - 1ull));
+  }
+};
+
 // Block-level OR of per-word masks and sum of arc counts, then one global
 // atomic per word and block.
 __device__ __forceinline__ void block_publish(uint64_t alive, unsigned long long arcs, int G, Ctl *ctl) {
@@ -65,10 +77,9 @@ __device__ __forceinline__ void block_publish(uint64_t alive, unsigned long long
 }
 
 // --------------------------------------------------------------- init
-template <class T>
 __global__ void k_wave_init(int count, uint64_t jbase, const uint64_t *__restrict__ jlist, int32_t n, uint64_t seed,
                             int G, int W, uint64_t *slot_j, int32_t *slot_s, int32_t *slot_t, int32_t *slot_d,
-                            uint64_t *lev0, uint64_t *vis, T *sig, const int64_t *__restrict__ off, Ctl *ctl) {
+                            uint64_t *lev0, uint64_t *vis, const int64_t *__restrict__ off, Ctl *ctl) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < W; b += gridDim.x * blockDim.x) {
     if (b >= count) {
       slot_d[b] = -3;
@@ -87,7 +98,6 @@ __global__ void k_wave_init(int count, uint64_t jbase, const uint64_t *__restric
     const unsigned long long bit = 1ull << (b & 63);
     atomicOr((unsigned long long *)&lev0[(int64_t)s * G + g], bit);
     atomicOr((unsigned long long *)&vis[(int64_t)s * G + g], bit);
-    sig[(int64_t)s * W + b] = (T)1;
     atomicOr(&ctl->active[g], bit);
     atomicAdd(&ctl->farcs, (unsigned long long)(off[s + 1] - off[s]));
   }
@@ -421,26 +431,23 @@ struct ArcLog {
   unsigned long long cap;
 };
 
-// Thread per kind-0 slot with d == L >= 2: t_b is the cone on its own level;
-// its count starts at zero.
-template <class T>
+// Thread per kind-0 slot with d == L >= 2: t_b is the cone on its own level.
 __global__ void k_cone_seed(int W, int G, int L, const int32_t *__restrict__ slot_t, const int32_t *__restrict__ slot_d,
-                            const int32_t *__restrict__ slot_kind, uint64_t *cone, T *sig) {
+                            const int32_t *__restrict__ slot_kind, uint64_t *cone, uint64_t *any) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < W; b += gridDim.x * blockDim.x) {
     if (slot_d[b] != L || L < 2 || slot_kind[b] != 0) continue;
-    const int64_t t = slot_t[b];
-    atomicOr((unsigned long long *)&cone[t * G + (b >> 6)], 1ull << (b & 63));
-    sig[t * W + b] = 0;
+    const int64_t tg = (int64_t)slot_t[b] * G + (b >> 6);
+    atomicOr((unsigned long long *)&cone[tg], 1ull << (b & 63));
+    atomicOr((unsigned long long *)&any[tg], 1ull << (b & 63));
   }
 }
 
-// Warp per kind-1 slot with d - 1 == L >= 1: t_b's count starts at zero and its
+// Warp per kind-1 slot with d - 1 == L >= 1: t_b gets a count slot, and its
 // in-neighbours on level L seed the cone, each arc logged.
-template <class T>
 __global__ void k_cone_seed_pred(int W, int G, int L, const int32_t *__restrict__ slot_t,
                                  const int32_t *__restrict__ slot_d, const int32_t *__restrict__ slot_kind,
                                  const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
-                                 const uint64_t *__restrict__ lev, uint64_t *cone, T *sig, ArcLog log) {
+                                 const uint64_t *__restrict__ lev, uint64_t *cone, uint64_t *any, ArcLog log) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < W; b += nwarps) {
@@ -448,7 +455,7 @@ __global__ void k_cone_seed_pred(int W, int G, int L, const int32_t *__restrict_
     const int g = b >> 6;
     const unsigned long long bit = 1ull << (b & 63);
     const int32_t t = slot_t[b];
-    if (lane == 0) sig[(int64_t)t * W + b] = 0;
+    if (lane == 0) atomicOr((unsigned long long *)&any[(int64_t)t * G + g], bit);
     const int64_t e0 = roff[t], e1 = roff[t + 1];
     for (int64_t base = e0; base < e1; base += 32) {
       const int64_t i = base + lane;
@@ -465,6 +472,7 @@ __global__ void k_cone_seed_pred(int W, int G, int L, const int32_t *__restrict_
       pos = __shfl_sync(0xffffffffu, pos, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
       if (hit) {
         atomicOr((unsigned long long *)&cone[(int64_t)w * G + g], bit);
+        atomicOr((unsigned long long *)&any[(int64_t)w * G + g], bit);
         if (pos < log.cap) log.arcs[pos] = ConeArc{w, t, g, 0, (uint64_t)bit};
       }
     }
@@ -474,14 +482,18 @@ __global__ void k_cone_seed_pred(int W, int G, int L, const int32_t *__restrict_
 // Level 1 of the cone: the only predecessor is s_b (count 1), so every cone
 // node on level 1 has count 1 and nothing needs logging.
 template <class T>
-__global__ void k_cone_level1(int64_t words, int G, int gshift, int W, const uint64_t *__restrict__ lev1, T *sig) {
+__global__ void k_cone_level1(int64_t words, const uint64_t *__restrict__ lev1, SigIdx ix, T *sig) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t c = lev1[i];
     if (!c) continue;
-    const int64_t x = i >> gshift;
-    const int g = (int)(i & (G - 1));
-    for (uint64_t z = c; z; z &= z - 1) sig[x * W + 64 * g + (__ffsll((long long)z) - 1)] = (T)1;
+    for (uint64_t z = c; z; z &= z - 1) sig[ix(i, __ffsll((long long)z) - 1)] = (T)1;
   }
+}
+
+// Popcount of every cone word (input of the compact index scan).
+__global__ void k_popc_words(int64_t words, const uint64_t *__restrict__ any, int32_t *cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+    cnt[i] = __popcll(any[i]);
 }
 
 // Arc records are staged per warp in shared memory and appended to the log
@@ -525,7 +537,7 @@ __device__ __forceinline__ void arcbuf_put(WarpArcBuf &B, const ArcLog &log, boo
 __device__ __forceinline__ unsigned long long cone_arcs(int64_t e0, int64_t e1, int G, int gshift, int g, int a,
                                                         uint64_t c, int32_t x, const int32_t *__restrict__ rcol,
                                                         const uint64_t *__restrict__ lev, uint64_t *cone,
-                                                        WarpArcBuf &B, const ArcLog &log) {
+                                                        uint64_t *any, WarpArcBuf &B, const ArcLog &log) {
   const int lane = threadIdx.x & 31;
   unsigned long long hits = 0;
   for (int64_t base = e0; base < e1; base += 32) {
@@ -545,6 +557,7 @@ __device__ __forceinline__ unsigned long long cone_arcs(int64_t e0, int64_t e1, 
       for (int u = 0; u < 4; ++u) {
         if (f[u]) {
           atomicOr((unsigned long long *)&cone[(int64_t)w[u] * G + g], (unsigned long long)f[u]);
+          atomicOr((unsigned long long *)&any[(int64_t)w[u] * G + g], (unsigned long long)f[u]);
           ++hits;
         }
         arcbuf_put(B, log, f[u] != 0, ConeArc{w[u], x, g, 0, f[u]});
@@ -554,14 +567,13 @@ __device__ __forceinline__ unsigned long long cone_arcs(int64_t e0, int64_t e1, 
   return hits;
 }
 
-// Warp per node x on level L+1 with cone slots c: zero x's counts for those
-// slots, then mark and log its cone in-arcs (long rows: k_cone_push_heavy).
-template <class T>
-__global__ void __launch_bounds__(256) k_cone_push(int32_t n, int G, int gshift, int W,
-                                                   const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
-                                                   const uint64_t *__restrict__ up, const uint64_t *__restrict__ lev,
-                                                   uint64_t *cone, T *sig, ArcLog log, unsigned long long *units) {
-  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift, A = 32 >> gshift;
+// Warp per node x on level L+1 with cone slots c: mark and log its cone
+// in-arcs (long rows: k_cone_push_heavy).
+__global__ void __launch_bounds__(256) k_cone_push(int32_t n, int G, int gshift, const int64_t *__restrict__ roff,
+                                                   const int32_t *__restrict__ rcol, const uint64_t *__restrict__ up,
+                                                   const uint64_t *__restrict__ lev, uint64_t *cone, uint64_t *any,
+                                                   ArcLog log, unsigned long long *units) {
+  const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift;
   __shared__ WarpArcBuf s_buf[8];
   WarpArcBuf &B = s_buf[threadIdx.x >> 5];
   if (lane == 0) B.n = 0;
@@ -572,21 +584,17 @@ __global__ void __launch_bounds__(256) k_cone_push(int32_t n, int G, int gshift,
     const uint64_t c = up[x * G + g];
     if (lane == 0) bytes += 8ull * G;
     if (!__any_sync(0xffffffffu, c != 0)) continue;
-    for (uint64_t z = c; z; z &= z - 1) {
-      const int b = __ffsll((long long)z) - 1;
-      if ((b & (A - 1)) == a) sig[x * W + 64 * g + b] = 0;
-    }
     const int64_t e0 = roff[x], e1 = roff[x + 1];
     if (e1 - e0 > kHeavyRow) continue;
-    const unsigned long long hits = cone_arcs(e0, e1, G, gshift, g, a, c, (int32_t)x, rcol, lev, cone, B, log);
+    const unsigned long long hits = cone_arcs(e0, e1, G, gshift, g, a, c, (int32_t)x, rcol, lev, cone, any, B, log);
     const int nzw = __popc(__ballot_sync(0xffffffffu, c != 0 && a == 0));
-    bytes += 40ull * hits;
+    bytes += 56ull * hits;
     if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * nzw);
   }
   arcbuf_flush(B, log);
   // bytes: every node's cone words (8 G); per non-empty node its offsets and,
   // per in-arc, the arc (4) and the level word of each non-empty cone word
-  // (8); per hit a 16-byte atomic read-modify-write and a 24-byte arc record
+  // (8); per hit two 16-byte atomic read-modify-writes and a 24-byte record
   bytes = warp_sum(bytes);
   if (lane == 0 && bytes) atomicAdd(units, bytes);
 }
@@ -596,8 +604,8 @@ __global__ void __launch_bounds__(256) k_cone_push_heavy(int64_t nchunks, const 
                                                          const int64_t *__restrict__ roff,
                                                          const int32_t *__restrict__ rcol, int G, int gshift,
                                                          const uint64_t *__restrict__ up,
-                                                         const uint64_t *__restrict__ lev, uint64_t *cone, ArcLog log,
-                                                         unsigned long long *units) {
+                                                         const uint64_t *__restrict__ lev, uint64_t *cone,
+                                                         uint64_t *any, ArcLog log, unsigned long long *units) {
   const int lane = threadIdx.x & 31, g = lane & (G - 1), a = lane >> gshift;
   __shared__ WarpArcBuf s_buf[8];
   WarpArcBuf &B = s_buf[threadIdx.x >> 5];
@@ -611,9 +619,9 @@ __global__ void __launch_bounds__(256) k_cone_push_heavy(int64_t nchunks, const 
     if (lane == 0) bytes += 8ull * G;
     if (!__any_sync(0xffffffffu, c != 0)) continue;
     const int64_t e0 = cbeg[q], e1 = min(e0 + (int64_t)kChunk, roff[x + 1]);
-    const unsigned long long hits = cone_arcs(e0, e1, G, gshift, g, a, c, x, rcol, lev, cone, B, log);
+    const unsigned long long hits = cone_arcs(e0, e1, G, gshift, g, a, c, x, rcol, lev, cone, any, B, log);
     const int nzw = __popc(__ballot_sync(0xffffffffu, c != 0 && a == 0));
-    bytes += 40ull * hits;
+    bytes += 56ull * hits;
     if (lane == 0) bytes += 16ull + (uint64_t)(e1 - e0) * (4ull + 8ull * nzw);
   }
   arcbuf_flush(B, log);
@@ -626,29 +634,31 @@ __global__ void __launch_bounds__(256) k_cone_push_heavy(int64_t nchunks, const 
 // a wrap-around (true sum >= 2^64) or an overflowed sigma_b[w] flags slot b
 // of x.  The arcs of a level are read from [range[0], range[1]).
 __global__ void __launch_bounds__(256) k_sigma_arcs64(const ConeArc *__restrict__ arcs,
-                                                      const unsigned long long *__restrict__ range, int G, int W,
-                                                      uint64_t *__restrict__ sig, uint64_t *__restrict__ ovf,
-                                                      unsigned long long *units) {
+                                                      const unsigned long long *__restrict__ range, int G,
+                                                      SigIdx ix, uint64_t *__restrict__ sig,
+                                                      uint64_t *__restrict__ ovf, unsigned long long *units) {
   const unsigned long long r0 = range[0], r1 = range[1];
   unsigned long long bytes = 0;
   for (unsigned long long i = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const ConeArc e = arcs[i];
+    const int64_t wg = (int64_t)e.w * G + e.g, xg = (int64_t)e.x * G + e.g;
     uint64_t f = e.f;
-    uint64_t of = ovf[(int64_t)e.w * G + e.g] & f;
-    bytes += 32ull;
+    uint64_t of = ovf[wg] & f;
+    bytes += 64ull;
     while (f) {
       const int b = __ffsll((long long)f) - 1;
       f &= f - 1;
-      const unsigned long long v = sig[(int64_t)e.w * W + 64 * e.g + b];
-      const unsigned long long old = atomicAdd((unsigned long long *)&sig[(int64_t)e.x * W + 64 * e.g + b], v);
+      const unsigned long long v = sig[ix(wg, b)];
+      const unsigned long long old = atomicAdd((unsigned long long *)&sig[ix(xg, b)], v);
       if (old + v < old) of |= 1ull << b;
       bytes += 24ull;
     }
-    if (of) atomicOr((unsigned long long *)&ovf[(int64_t)e.x * G + e.g], (unsigned long long)of);
+    if (of) atomicOr((unsigned long long *)&ovf[xg], (unsigned long long)of);
   }
-  // bytes: the 24-byte record and the tail's overflow word per arc; per slot
-  // the tail's count and a 16-byte atomic read-modify-write
+  // bytes: per arc the 24-byte record, the tail's overflow word and the cone
+  // words and bases of both ends; per slot the tail's count and a 16-byte
+  // atomic read-modify-write
   bytes = warp_sum(bytes);
   if ((threadIdx.x & 31) == 0 && bytes) atomicAdd(units, bytes);
 }
@@ -657,19 +667,20 @@ __global__ void __launch_bounds__(256) k_sigma_arcs64(const ConeArc *__restrict_
 // (low word, then high word plus carry); all terms are non-negative, so the
 // high word wraps exactly when the true sum reaches 2^128.
 __global__ void __launch_bounds__(256) k_sigma_arcs128(const ConeArc *__restrict__ arcs,
-                                                       const unsigned long long *__restrict__ range, int W,
+                                                       const unsigned long long *__restrict__ range, int G, SigIdx ix,
                                                        u128 *__restrict__ sig, uint64_t *__restrict__ ovf) {
   const unsigned long long r0 = range[0], r1 = range[1];
   for (unsigned long long i = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < r1;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const ConeArc e = arcs[i];
+    const int64_t wg = (int64_t)e.w * G + e.g, xg = (int64_t)e.x * G + e.g;
     uint64_t f = e.f;
-    uint64_t of = ovf[e.w] & f;
+    uint64_t of = ovf[wg] & f;
     while (f) {
       const int b = __ffsll((long long)f) - 1;
       f &= f - 1;
-      const u128 v = sig[(int64_t)e.w * W + b];
-      unsigned long long *dst = (unsigned long long *)&sig[(int64_t)e.x * W + b];
+      const u128 v = sig[ix(wg, b)];
+      unsigned long long *dst = (unsigned long long *)&sig[ix(xg, b)];
       const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
       const unsigned long long olo = atomicAdd(dst, lo);
       const unsigned long long add_hi = hi + (olo + lo < olo ? 1ull : 0ull);
@@ -679,7 +690,7 @@ __global__ void __launch_bounds__(256) k_sigma_arcs128(const ConeArc *__restrict
         if (ohi + add_hi < ohi) of |= 1ull << b;
       }
     }
-    if (of) atomicOr((unsigned long long *)&ovf[e.x], (unsigned long long)of);
+    if (of) atomicOr((unsigned long long *)&ovf[xg], (unsigned long long)of);
   }
 }
 
@@ -707,7 +718,7 @@ __device__ __forceinline__ u128 draw_below(uint64_t seed, uint64_t j, uint32_t p
 // (8 chunks of 32 loaded together).  T = uint64_t: a slot whose sigma_t
 // overflowed is appended to ctl->flagged.  T = u128: it sets ctl->err.
 template <class T>
-__global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ slot_j,
+__global__ void k_walk(int count, int G, SigIdx ix, const uint64_t *__restrict__ slot_j,
                        const int32_t *__restrict__ slot_t, const int32_t *__restrict__ slot_d,
                        const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
                        const uint64_t *const *__restrict__ levs, const T *__restrict__ sig,
@@ -734,7 +745,7 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
       }
       continue;
     }
-    T sv = sig[(int64_t)v * Wst + b];
+    T sv = sig[ix((int64_t)v * G + g, b & 63)];
     const int64_t hbase = hoff[j];
     uint32_t step = 0;
     int L = d;
@@ -757,7 +768,8 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
         for (int u = 0; u < kWalkUnroll; ++u)
           if (x[u] >= 0 && (lp[(int64_t)x[u] * G + g] & bit)) hit_bits |= 1ull << u;
 #pragma unroll
-        for (int u = 0; u < kWalkUnroll; ++u) val[u] = ((hit_bits >> u) & 1) ? sig[(int64_t)x[u] * Wst + b] : (T)0;
+        for (int u = 0; u < kWalkUnroll; ++u)
+          val[u] = ((hit_bits >> u) & 1) ? sig[ix((int64_t)x[u] * G + g, b & 63)] : (T)0;
 #pragma unroll
         for (int u = 0; u < kWalkUnroll; ++u) {
           if (pick >= 0) break;
@@ -780,7 +792,7 @@ __global__ void k_walk(int count, int G, int Wst, const uint64_t *__restrict__ s
         break;
       }
       if (lane == 0) hmem[hbase + (L - 2)] = pick;
-      sv = sig[(int64_t)pick * Wst + b];
+      sv = sig[ix((int64_t)pick * G + g, b & 63)];
       v = pick;
       --L;
       ++step;
@@ -838,6 +850,9 @@ struct Sampler {
     const size_t words = (size_t)n * G;
     ws.vis.ensure(words * 8, st);
     ws.ovf.ensure(words * 8, st);
+    ws.any.ensure(words * 8, st);
+    ws.base.ensure((words + 1) * 8, st);
+    ws.cnt.ensure(words * 4, st);
     if (ws.G != G || !ws.tmp.p) {  // the cone scratch is kept zero between waves of one width
       ws.tmp.ensure(words * 8, st);
       CEN_CK(cudaMemsetAsync(ws.tmp.p, 0, words * 8, st));
@@ -889,8 +904,7 @@ struct Sampler {
   }
 
   // Discovery for slots [0, count): returns the highest level materialised.
-  template <class T>
-  int discover(int count, uint64_t jbase, const uint64_t *jlist, T *sig) {
+  int discover(int count, uint64_t jbase, const uint64_t *jlist) {
     const size_t words = (size_t)n * G;
     uint64_t *vis = job->ws.vis.as<uint64_t>();
     CEN_CK(cudaMemsetAsync(vis, 0, words * 8, st));
@@ -903,8 +917,8 @@ struct Sampler {
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
     launch(S, K_PAIRS, st, [&] {
-      k_wave_init<T><<<grid_for(W, 256), 256, 0, st>>>(count, jbase, jlist, n, job->seed, G, W, slot_j, slot_s,
-                                                       slot_t, slot_d, lev0, vis, sig, off, ctl);
+      k_wave_init<<<grid_for(W, 256), 256, 0, st>>>(count, jbase, jlist, n, job->seed, G, W, slot_j, slot_s, slot_t,
+                                                    slot_d, lev0, vis, off, ctl);
     });
     fetch_ctl_head();
     int L = 0;
@@ -955,78 +969,107 @@ struct Sampler {
   }
 
   // Cut every level >= 1 to the cone (lev[L] and the zeroed scratch swap
-  // roles), zero the cone's counts (level 1: set them to 1) and log its arcs
+  // roles), record every node's cone slots in `any` and log the cone arcs
   // above level 1; range[2U], range[2U+1] bound the arcs into level U.
   // Returns the number of logged arcs (the log is usable iff <= its capacity).
-  template <class T>
-  unsigned long long cone(int Lmax, T *sig) {
+  unsigned long long cone(int Lmax) {
     const size_t words = (size_t)n * G;
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
     WaveWS &ws = job->ws;
-    const int nb = grid_for((size_t)n * 32, 256, kLevelBlocks);
     ws.arc_range.ensure(sizeof(unsigned long long) * 2 * (size_t)(Lmax + 3), st);
     unsigned long long *range = ws.arc_range.as<unsigned long long>();
     CEN_CK(cudaMemsetAsync(range, 0, sizeof(unsigned long long) * 2 * (size_t)(Lmax + 3), st));
     unsigned long long *count = &ctl->arcs;
     CEN_CK(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+    uint64_t *any = ws.any.as<uint64_t>();
+    CEN_CK(cudaMemsetAsync(any, 0, words * 8, st));
     const ArcLog log{ws.arcs.as<ConeArc>(), count, (unsigned long long)ws.arc_cap};
     const ChunkTable &ic = g->in_chunks();
     for (int L = Lmax; L >= 1; --L) {
       uint64_t *lev = level(L);
       uint64_t *cone = ws.tmp.as<uint64_t>();
       launch(S, K_CONE, st, [&] {
-        k_cone_seed<T><<<grid_for(W, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, cone, sig);
+        k_cone_seed<<<grid_for(W, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, cone, any);
       });
       CEN_CK(cudaMemcpyAsync(range + 2 * (L + 1), count, 8, cudaMemcpyDeviceToDevice, st));
       if (L < Lmax) {
         const uint64_t *up = level(L + 1);
         launch(S, K_CONE, st, [&] {
-          k_cone_push<T><<<resident_grid((const void *)k_cone_push<T>, 256), 256, 0, st>>>(n, G, gshift, W, roff, rcol, up, lev, cone, sig, log, units(K_CONE));
+          k_cone_push<<<resident_grid((const void *)k_cone_push, 256), 256, 0, st>>>(n, G, gshift, roff, rcol, up, lev,
+                                                                                     cone, any, log, units(K_CONE));
         });
         if (ic.count)
           launch(S, K_CONE, st, [&] {
             k_cone_push_heavy<<<resident_grid((const void *)k_cone_push_heavy, 256), 256, 0, st>>>(
-                ic.count, ic.rows(), ic.begins(), roff, rcol, G, gshift, up, lev, cone, log, units(K_CONE));
+                ic.count, ic.rows(), ic.begins(), roff, rcol, G, gshift, up, lev, cone, any, log, units(K_CONE));
           });
       }
       launch(S, K_CONE, st, [&] {
-        k_cone_seed_pred<T><<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, roff,
-                                                                           rcol, lev, cone, sig, log);
+        k_cone_seed_pred<<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, roff, rcol,
+                                                                         lev, cone, any, log);
       });
       CEN_CK(cudaMemcpyAsync(range + 2 * (L + 1) + 1, count, 8, cudaMemcpyDeviceToDevice, st));
       ws.lev[L]->swap(ws.tmp);  // the cone becomes level L
       CEN_CK(cudaMemsetAsync(ws.tmp.p, 0, words * 8, st));
     }
-    launch(S, K_CONE, st, [&] {
-      k_cone_level1<T><<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, G, gshift, W, level(1),
-                                                                          sig);
-    });
     fetch_ctl_head();
     return hctl->arcs;
   }
 
-  // Path counts level by level over the logged arcs (levels 2 .. Lmax+1;
-  // Lmax+1 holds only targets found before their last expansion).
+  // Compact count store for the cone pairs: bases by an exclusive scan of the
+  // popcounts of `any`; counts zeroed, level 1 set to 1.  Returns the index.
   template <class T>
-  void sigma_and_walk(int count, int Lmax, T *sig) {
+  SigIdx sigma_store(T **sig_out) {
+    const size_t words = (size_t)n * G;
+    WaveWS &ws = job->ws;
+    const uint64_t *any = ws.any.as<uint64_t>();
+    int64_t *base = ws.base.as<int64_t>();
+    launch(S, K_SIGMA, st, [&] {
+      k_popc_words<<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, any, ws.cnt.as<int32_t>());
+    });
+    counts_to_offsets(ws.cnt.as<int32_t>(), base, words, job->scan_tmp, st, S);
+    int64_t *h = (int64_t *)host_staging(job, sizeof(Ctl) + 8);
+    CEN_CK(cudaMemcpyAsync(h, base + words, 8, cudaMemcpyDeviceToHost, st));
+    CEN_CK(cudaStreamSynchronize(st));
+    const int64_t pairs = *h;
+    hctl = (Ctl *)host_staging(job, sizeof(Ctl));
+    ws.sigc.ensure(sizeof(T) * (size_t)(pairs + 1), st);
+    CEN_CK(cudaMemsetAsync(ws.sigc.p, 0, sizeof(T) * (size_t)(pairs + 1), st));
+    const SigIdx ix{any, base};
+    T *sig = ws.sigc.as<T>();
+    launch(S, K_SIGMA, st, [&] {
+      k_cone_level1<T><<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, level(1), ix, sig);
+    });
+    *sig_out = sig;
+    return ix;
+  }
+
+  // Path counts level by level over the logged arcs (levels 2 .. Lmax+1;
+  // Lmax+1 holds only targets found before their last expansion), then the walk.
+  template <class T>
+  void sigma_and_walk(int count, int Lmax) {
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
     uint64_t *ovf = job->ws.ovf.as<uint64_t>();
     const ConeArc *arcs = job->ws.arcs.as<ConeArc>();
+    T *sig = nullptr;
+    const SigIdx ix = sigma_store<T>(&sig);
     for (int L = 2; L <= Lmax + 1; ++L) {
       const unsigned long long *range = job->ws.arc_range.as<unsigned long long>() + 2 * L;
       launch(S, K_SIGMA, st, [&] {
         if constexpr (sizeof(T) == 8)
-          k_sigma_arcs64<<<resident_grid((const void *)k_sigma_arcs64, 256), 256, 0, st>>>(arcs, range, G, W, (uint64_t *)sig, ovf, units(K_SIGMA));
+          k_sigma_arcs64<<<resident_grid((const void *)k_sigma_arcs64, 256), 256, 0, st>>>(
+              arcs, range, G, ix, (uint64_t *)sig, ovf, units(K_SIGMA));
         else
-          k_sigma_arcs128<<<resident_grid((const void *)k_sigma_arcs128, 256), 256, 0, st>>>(arcs, range, W, (u128 *)sig, ovf);
+          k_sigma_arcs128<<<resident_grid((const void *)k_sigma_arcs128, 256), 256, 0, st>>>(arcs, range, G, ix,
+                                                                                             (u128 *)sig, ovf);
       });
     }
     publish_levels(Lmax);
     launch(S, K_WALK, st, [&] {
       k_walk<T><<<grid_for((size_t)count * 32, 256), 256, 0, st>>>(
-          count, G, W, slot_j, slot_t, slot_d, roff, rcol, job->ws.lev_ptrs.as<const uint64_t *>(), sig, ovf,
+          count, G, ix, slot_j, slot_t, slot_d, roff, rcol, job->ws.lev_ptrs.as<const uint64_t *>(), sig, ovf,
           job->hoff.as<int64_t>(), job->hmem.as<int32_t>(), job->seed, ctl, units(K_WALK));
     });
   }
@@ -1034,10 +1077,12 @@ struct Sampler {
 
 }  // namespace
 
+// Wave width: up to gmax words, no wider than the samples left need, and with
+// one level array ([n][G] words) within `budget` bytes.
 static int pick_G(uint64_t remaining, int32_t n, size_t budget, int gmax) {
   int G = 1;
   while (G < kMaxG && G < gmax && (uint64_t)64 * G < remaining) G <<= 1;
-  while (G > 1 && (size_t)n * 64 * G * 8 > budget) G >>= 1;
+  while (G > 1 && (size_t)n * G * 8 > budget) G >>= 1;
   return G;
 }
 
@@ -1064,14 +1109,12 @@ void sample_append(cen_job *job, uint64_t m_new) {
   int64_t members = job->members;
   std::vector<uint64_t> flagged_js;
   for (uint64_t j0 = m0; j0 < m1;) {
-    sp.setup(pick_G(m1 - j0, g->n, job->sigma_budget, job->max_wave_words));
+    sp.setup(pick_G(m1 - j0, g->n, job->level_budget, job->max_wave_words));
     const int count = (int)std::min<uint64_t>((uint64_t)sp.W, m1 - j0);
-    job->ws.sig64.ensure((size_t)g->n * sp.W * 8, st);
-    uint64_t *sig = job->ws.sig64.as<uint64_t>();
     int Lmax = 0;
     int64_t wave_total = 0;
     for (;;) {  // a wave whose cone arcs overflow the log is redone with a larger log
-      Lmax = sp.discover<uint64_t>(count, j0, nullptr, sig);
+      Lmax = sp.discover(count, j0, nullptr);
       launch(sp.S, K_APPEND, st, [&] {
         k_wave_append<<<1, 1024, 0, st>>>(count, j0, sp.slot_s, sp.slot_t, sp.slot_d, job->hoff.as<int64_t>(),
                                           job->ps.as<int32_t>(), job->pt.as<int32_t>(), job->pd.as<int32_t>(),
@@ -1080,13 +1123,13 @@ void sample_append(cen_job *job, uint64_t m_new) {
       sp.fetch_ctl_head();
       wave_total = sp.hctl->total;
       job->hmem.ensure(4 * (size_t)(members + wave_total + 1), st, 4 * (size_t)members);
-      const unsigned long long narcs = sp.cone<uint64_t>(Lmax, sig);
+      const unsigned long long narcs = sp.cone(Lmax);
       if (narcs <= job->ws.arc_cap) break;
       job->ws.arc_cap = (size_t)(narcs + narcs / 4);
       job->ws.arcs.release();
       sp.setup(sp.G);
     }
-    sp.sigma_and_walk<uint64_t>(count, Lmax, sig);
+    sp.sigma_and_walk<uint64_t>(count, Lmax);
     CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     CEN_CK(cudaStreamSynchronize(st));
     CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent path counts in the backward walk");
@@ -1104,7 +1147,6 @@ void sample_append(cen_job *job, uint64_t m_new) {
   if (!flagged_js.empty()) {
     std::sort(flagged_js.begin(), flagged_js.end());
     sp.setup(1);
-    job->ws.sig128.ensure((size_t)g->n * 64 * 16, st);
     job->ws.jlist.ensure(8 * 64, st);
     for (size_t q0 = 0; q0 < flagged_js.size(); q0 += 64) {
       const int count = (int)std::min<size_t>(64, flagged_js.size() - q0);
@@ -1113,17 +1155,16 @@ void sample_append(cen_job *job, uint64_t m_new) {
       CEN_CK(cudaMemcpyAsync(job->ws.jlist.p, h, 8 * (size_t)count, cudaMemcpyHostToDevice, st));
       CEN_CK(cudaStreamSynchronize(st));
       sp.hctl = (Ctl *)host_staging(job, sizeof(Ctl));
-      u128 *sig = job->ws.sig128.as<u128>();
       int Lmax = 0;
       for (;;) {
-        Lmax = sp.discover<u128>(count, 0, job->ws.jlist.as<uint64_t>(), sig);
-        const unsigned long long narcs = sp.cone<u128>(Lmax, sig);
+        Lmax = sp.discover(count, 0, job->ws.jlist.as<uint64_t>());
+        const unsigned long long narcs = sp.cone(Lmax);
         if (narcs <= job->ws.arc_cap) break;
         job->ws.arc_cap = (size_t)(narcs + narcs / 4);
         job->ws.arcs.release();
         sp.setup(1);
       }
-      sp.sigma_and_walk<u128>(count, Lmax, sig);
+      sp.sigma_and_walk<u128>(count, Lmax);
       CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, offsetof(Ctl, flagged), cudaMemcpyDeviceToHost, st));
       CEN_CK(cudaStreamSynchronize(st));
       CEN_REQUIRE(sp.hctl->err != CEN_EOVERFLOW, CEN_EOVERFLOW,
