@@ -51,6 +51,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--mode", default="round", choices=["round", "batch", "serve"],
+                    help="round: one Algorithm-1 round per step (default); batch: time to certified eps of the "
+                         "64-job BA workload, one job at a time vs batched; serve: Poisson request stream")
+    ap.add_argument("--batch-jobs", type=int, default=64)
+    ap.add_argument("--batch-workers", type=int, default=8)
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-eps", default="0.01,0.005")
+    ap.add_argument("--serve-workers", type=int, default=8)
     return ap.parse_args()
 
 
@@ -263,10 +271,93 @@ def oracle_rate(wl, seconds: float, seed: int = 424242):
     return count / el, count, el
 
 
+def run_batch_mode(args):
+    """Time to certified eps of the batched workload: every job to certification,
+    one job at a time (the plain form) and batched (cen_run_batch), same results."""
+    import torch
+    import paper_2306_03651_gb300 as P
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    params = I.ba_batch_params(args.batch_jobs)
+    graphs = [P.Graph.of(I.ba(p["n"], p["d"], p["graph_seed"])) for p in params]
+    jobs = [dict(graph=g, k=p["k"], eps=0.01, delta=0.1, t=32, seed=p["job_seed"], m_cap=1 << 27)
+            for g, p in zip(graphs, params)]
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    t0 = time.perf_counter()
+    plain = P.run_batch(jobs, nworkers=1)
+    t_plain = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batched = P.run_batch(jobs, nworkers=args.batch_workers)
+    t_batch = time.perf_counter() - t0
+    clk = clocks.stop()
+    same = all(a["S"].tolist() == b["S"].tolist() and a["m_final"] == b["m_final"] and a["covered"] == b["covered"]
+               for a, b in zip(plain, batched))
+    samples = sum(r["m_final"] for r in batched)
+    print(json.dumps({
+        "metric": "time to certified eps (s)", "value": t_batch, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "scaling": "strong", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{args.batch_jobs} BA jobs, n log-uniform in [1e4, 5e5], 2-8 edges per node, "
+                               f"k in {{10,50,100}}, eps=0.01, delta=0.1, t=32, m0=1000 doubling",
+                   "batched_workers": args.batch_workers},
+        "plain_s": t_plain, "batched_s": t_batch, "speedup": t_plain / t_batch, "identical_results": same,
+        "certified": sum(1 for r in batched if r["status"] == P.OK), "samples_total": samples,
+        "paths_per_s_batched": samples / t_batch, "clocks": clk,
+    }))
+
+
+def run_serve_mode(args):
+    """Poisson request stream on device-resident graphs (BA 2000, R-MAT 18 LCC, 8 of
+    the batched BA graphs); capacity first (all requests at t=0), then arrival
+    rates 0.5 / 0.7 / 0.9 x capacity."""
+    import torch
+    import paper_2306_03651_gb300 as P
+    from paper_2306_03651_gb300 import serve as SV
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    graphs = {"ba2000": P.Graph.of(I.ba(2000, 4, 1)), "rmat18": P.Graph.of(I.rmat18_lcc().graph)}
+    for j, p in enumerate(I.ba_batch_params(8)):
+        graphs[f"ba{j}"] = P.Graph.of(I.ba(p["n"], p["d"], p["graph_seed"]))
+    names = sorted(graphs)
+    eps_list = [float(x) for x in args.serve_eps.split(",")]
+    rng = np.random.default_rng(11)
+    N = args.serve_requests
+    reqs = [SV.Request(rid=i, graph=names[int(rng.integers(len(names)))], k=int(rng.integers(10, 201)),
+                       eps=float(eps_list[int(rng.integers(len(eps_list)))]), delta=0.1, t=10, seed=5000 + i,
+                       m_cap=1 << 27) for i in range(N)]
+    srv = SV.Server(graphs, workers=args.serve_workers)
+    res = srv.serve(reqs)
+    cap = SV.summarize(res)
+    rows = {"capacity": cap}
+    for frac in (0.5, 0.7, 0.9):
+        arr = SV.poisson_arrivals(N, frac * cap["jobs_per_s"], seed=int(frac * 100))
+        for r, a in zip(reqs, arr):
+            r.arrival_s = a
+        res = SV.Server(graphs, workers=args.serve_workers).serve(reqs)
+        rows[f"lambda_{frac}"] = SV.summarize(res)
+    print(json.dumps({
+        "metric": "jobs/s", "value": rows["lambda_0.9"]["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": f"{N} requests, graphs {names}, k ~ U[10,200], eps in {eps_list}, delta=0.1, t=10",
+                   "workers": args.serve_workers},
+        "p50_latency_s": rows["lambda_0.9"]["p50_latency_s"], "p99_latency_s": rows["lambda_0.9"]["p99_latency_s"],
+        "runs": rows,
+    }))
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.mode == "batch":
+        if rank == 0:
+            run_batch_mode(args)
+        return
+    if args.mode == "serve":
+        if rank == 0:
+            run_serve_mode(args)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

@@ -113,6 +113,30 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
             uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
             int32_t *rounds, double *log, int32_t max_rounds);
 
+/* Batched Algorithm 1: `njobs` independent runs of cen_run, each described by
+ * a spec and answered in the result with the same index.  `nworkers` host
+ * threads, each with its own CUDA stream on the caller's current device, take
+ * jobs longest-first (by arc count) so that jobs overlap on the GPU.  Each
+ * job's outputs equal those of cen_run called alone with the same spec.
+ * Caller-owned buffers: results[i].S (capacity specs[i].k) and, optionally,
+ * results[i].log (results[i].max_rounds rows of CEN_LOG_COLS doubles).
+ * Returns CEN_OK once every job has finished (per-job status in results[i]),
+ * or CEN_EINVAL for bad arguments.  start_s/end_s: seconds since the call. */
+typedef struct cen_job_spec {
+  const cen_graph *graph;
+  int32_t k, t;
+  double eps, delta;
+  uint64_t seed, m0, m_cap;
+} cen_job_spec;
+typedef struct cen_job_result {
+  int32_t status, S_size, rounds, max_rounds;
+  uint64_t covered, m_final;
+  int32_t *S;
+  double *log;
+  double start_s, end_s;
+} cen_job_result;
+int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t nworkers, cen_job_result *results);
+
 /* Allocation-free sum of the <= k largest positive entries of each row: the
  * per-vector sup that cen_mcera computes (Rnum), for callers that supply their
  * own matrix.  The paper has no counterpart; this entry point exists for

@@ -31,6 +31,19 @@ class CenError(RuntimeError):
         self.rc = rc
 
 
+class cen_job_spec(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("k", ctypes.c_int32), ("t", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("delta", ctypes.c_double), ("seed", ctypes.c_uint64), ("m0", ctypes.c_uint64),
+                ("m_cap", ctypes.c_uint64)]
+
+
+class cen_job_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("S_size", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("covered", ctypes.c_uint64), ("m_final", ctypes.c_uint64),
+                ("S", ctypes.c_void_p), ("log", ctypes.c_void_p), ("start_s", ctypes.c_double),
+                ("end_s", ctypes.c_double)]
+
+
 class cen_kstat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
                 ("timed", ctypes.c_uint64), ("units", ctypes.c_uint64)]
@@ -69,6 +82,7 @@ def _load():
         "cen_job_stats": ([vp, vp, vp], ip),
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
+        "cen_run_batch": ([vp, i32, i32, vp], ip),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -269,3 +283,30 @@ def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: i
         _check(rc, "cen_run")
     return dict(status=rc, S=S[: size.value].copy(), covered=cov.value, m_final=mf.value, rounds=rounds.value,
                 log=log[: min(rounds.value, max_rounds)].copy())
+
+
+def run_batch(jobs, nworkers: int = 8, max_rounds: int = 64) -> list[dict]:
+    """``cen_run_batch``: `jobs` is a list of dicts with graph (Graph), k, eps, delta, t, seed and optional
+    m0 (1000) / m_cap (2^30).  Returns one dict per job, like ``run`` plus start_s / end_s."""
+    n = len(jobs)
+    specs = (cen_job_spec * max(n, 1))()
+    res = (cen_job_result * max(n, 1))()
+    keep = []
+    for i, j in enumerate(jobs):
+        specs[i] = cen_job_spec(j["graph"].h, j["k"], j["t"], j["eps"], j["delta"], j["seed"], j.get("m0", 1000),
+                                j.get("m_cap", 1 << 30))
+        S = np.empty(j["k"], np.int32)
+        log = np.zeros((max_rounds, 16), np.float64)
+        keep.append((S, log))
+        res[i].S = S.ctypes.data
+        res[i].log = log.ctypes.data
+        res[i].max_rounds = max_rounds
+    _check(_lib.cen_run_batch(specs, n, nworkers, res), "cen_run_batch")
+    out = []
+    for i in range(n):
+        S, log = keep[i]
+        r = res[i]
+        out.append(dict(status=r.status, S=S[: r.S_size].copy(), covered=r.covered, m_final=r.m_final,
+                        rounds=r.rounds, log=log[: min(r.rounds, max_rounds)].copy(), start_s=r.start_s,
+                        end_s=r.end_s))
+    return out

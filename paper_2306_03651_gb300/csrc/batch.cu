@@ -1,0 +1,63 @@
+// Batched Algorithm 1: many independent CentRA jobs driven concurrently.
+//
+// Each worker thread owns one CUDA stream and runs whole jobs (cen_run) on it;
+// jobs are handed out longest-first (by arc count).  Kernels of different
+// jobs overlap on the GPU, host synchronisation of one job hides behind
+// another's kernels, and every job's result is exactly what cen_run gives for
+// it alone: samples, signs and picks depend only on (graph, seed, parameters).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <numeric>
+#include <thread>
+#include <vector>
+
+#include "job.cuh"
+
+extern "C" int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t nworkers, cen_job_result *results) {
+  try {
+    CEN_REQUIRE(specs && results && njobs >= 0 && nworkers >= 1, CEN_EINVAL, "cen_run_batch: bad arguments");
+    for (int32_t i = 0; i < njobs; ++i)
+      CEN_REQUIRE(specs[i].graph && results[i].S, CEN_EINVAL, "cen_run_batch: null graph or S buffer");
+    int dev = 0;
+    CEN_CK(cudaGetDevice(&dev));
+    std::vector<int32_t> order(njobs);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return specs[a].graph->nnz > specs[b].graph->nnz; });
+    std::atomic<int32_t> next{0};
+    const auto t0 = std::chrono::steady_clock::now();
+    auto secs = [&] {
+      return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    auto worker = [&] {
+      if (cudaSetDevice(dev) != cudaSuccess) return;
+      cudaStream_t st = nullptr;
+      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+      for (;;) {
+        const int32_t q = next.fetch_add(1);
+        if (q >= njobs) break;
+        const int32_t i = order[q];
+        const cen_job_spec &sp = specs[i];
+        cen_job_result &r = results[i];
+        r.start_s = secs();
+        r.status = cen_run(sp.graph, sp.k, sp.eps, sp.delta, sp.t, sp.seed, sp.m0, sp.m_cap, st, r.S, &r.S_size,
+                           &r.covered, &r.m_final, &r.rounds, r.log, r.log ? r.max_rounds : 0);
+        r.end_s = secs();
+      }
+      cudaStreamDestroy(st);
+    };
+    for (int32_t i = 0; i < njobs; ++i) results[i].status = CEN_ECUDA;  // until a worker runs it
+    std::vector<std::thread> pool;
+    const int32_t nw = std::min<int32_t>(nworkers, std::max<int32_t>(njobs, 1));
+    for (int32_t w = 0; w < nw; ++w) pool.emplace_back(worker);
+    for (auto &th : pool) th.join();
+    return CEN_OK;
+  } catch (const cen::Error &e) {
+    cen::set_last_error(e.msg);
+    return e.code;
+  } catch (...) {
+    cen::set_last_error("cen_run_batch: unexpected internal error");
+    return CEN_ECUDA;
+  }
+}

@@ -1,0 +1,176 @@
+"""Continuous-batching request loop for CentRA jobs on device-resident graphs.
+
+Requests (graph name, k, eps, delta, t, seed) arrive over time.  A request is
+admitted as soon as a worker is free and its estimated device memory fits in
+the HBM budget; admitted requests run Algorithm 1 concurrently, each on its
+own CUDA stream, so their kernels overlap on the GPU, and each keeps its
+growing sample on the device across its progressive rounds (``cen_run``).
+Finished requests release their memory and worker at once, so waiting ones
+are admitted mid-flight.  A request's result does not depend on what runs
+beside it: samples, signs and picks are functions of (graph, seed, parameters).
+
+Latency is arrival -> completion; the loop reports p50 / p99 latency and jobs/s.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import threading
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import cen as P
+
+
+@dataclass
+class Request:
+    rid: int
+    graph: str
+    k: int
+    eps: float
+    delta: float
+    t: int
+    seed: int
+    arrival_s: float = 0.0
+    m0: int = 1000
+    m_cap: int = 1 << 27
+
+
+@dataclass
+class Result:
+    rid: int
+    status: int
+    S: np.ndarray
+    covered: int
+    m_final: int
+    rounds: int
+    log: np.ndarray
+    arrival_s: float
+    start_s: float
+    end_s: float
+    est_bytes: int
+
+    @property
+    def latency_s(self) -> float:
+        return self.end_s - self.arrival_s
+
+
+def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: float = 8.0, levels: int = 16) -> int:
+    """Upper estimate of one job's device memory (admission policy, not the method).
+
+    Wave workspace: `levels` + 6 arrays of n*G words (G = wave words, at most 32
+    and at most 1 GB per array) and the initial cone-arc log (2 n G records of
+    24 bytes); sample store for m_cap samples: offsets, endpoints, distance,
+    sign words and members (twice: samples and the incidence); AMCERA table
+    R[t][n] and greedy / incidence arrays."""
+    G = 32
+    while G > 1 and n * G * 8 > (1 << 30):
+        G //= 2
+    words = n * G
+    wave = 8 * words * (levels + 6) + 24 * 2 * words
+    nw = (t + 31) // 32
+    store = m_cap * (8 + 12 + 4 * nw) + 2 * 4 * int(m_cap * avg_hyperedge)
+    node = n * (4 * t + 4 * 4 + 8)
+    return int(wave + store + node)
+
+
+class Server:
+    """Admission by HBM budget, one CUDA stream per worker, FIFO order."""
+
+    def __init__(self, graphs: dict, workers: int = 8, hbm_budget_bytes: int | None = None):
+        import torch
+        self.graphs = graphs
+        self.workers = workers
+        if hbm_budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info()
+            hbm_budget_bytes = int(free * 0.8)
+        self.budget = hbm_budget_bytes
+        self.streams = [torch.cuda.Stream() for _ in range(workers)]
+        self._cv = threading.Condition()
+        self._queue: deque = deque()
+        self._in_use = 0
+        self._free_workers = list(range(workers))
+        self._results: list[Result] = []
+        self._t0 = 0.0
+        self.peak_bytes = 0
+        self.peak_running = 0
+
+    def _est(self, r: Request) -> int:
+        g = self.graphs[r.graph]
+        return estimate_job_bytes(g.n, g.nnz, r.t, r.m_cap)
+
+    def _now(self) -> float:
+        return time.perf_counter() - self._t0
+
+    def _run_one(self, w: int, r: Request, est: int, arrival: float):
+        g = self.graphs[r.graph]
+        start = self._now()
+        out = P.run(g, r.k, r.eps, r.delta, r.t, r.seed, m0=r.m0, m_cap=r.m_cap,
+                    stream=ctypes.c_void_p(self.streams[w].cuda_stream))
+        end = self._now()
+        res = Result(r.rid, out["status"], out["S"], out["covered"], out["m_final"], out["rounds"], out["log"],
+                     arrival, start, end, est)
+        with self._cv:
+            self._results.append(res)
+            self._in_use -= est
+            self._free_workers.append(w)
+            self._cv.notify_all()
+
+    def _dispatch(self, total: int):
+        threads = []
+        done = 0
+        while done < total:
+            with self._cv:
+                while True:
+                    if self._queue:
+                        r, est, arr = self._queue[0]
+                        fits = self._in_use + est <= self.budget or self._in_use == 0
+                        if self._free_workers and fits:
+                            self._queue.popleft()
+                            w = self._free_workers.pop()
+                            self._in_use += est
+                            self.peak_bytes = max(self.peak_bytes, self._in_use)
+                            self.peak_running = max(self.peak_running, self.workers - len(self._free_workers))
+                            break
+                    self._cv.wait(timeout=0.05)
+            th = threading.Thread(target=self._run_one, args=(w, r, est, arr), daemon=True)
+            th.start()
+            threads.append(th)
+            done += 1
+        for th in threads:
+            th.join()
+
+    def serve(self, requests: list[Request]) -> list[Result]:
+        """Run a request stream whose arrival_s are offsets from the start; returns results by rid."""
+        reqs = sorted(requests, key=lambda r: r.arrival_s)
+        self._results = []
+        self._t0 = time.perf_counter()
+        disp = threading.Thread(target=self._dispatch, args=(len(reqs),), daemon=True)
+        disp.start()
+        for r in reqs:
+            wait = r.arrival_s - self._now()
+            if wait > 0:
+                time.sleep(wait)
+            with self._cv:
+                self._queue.append((r, self._est(r), self._now()))
+                self._cv.notify_all()
+        disp.join()
+        return sorted(self._results, key=lambda x: x.rid)
+
+
+def summarize(results: list[Result], makespan_s: float | None = None) -> dict:
+    lat = np.array([r.latency_s for r in results])
+    span = makespan_s if makespan_s is not None else max(r.end_s for r in results) - min(r.arrival_s for r in results)
+    return {"jobs": len(results), "jobs_per_s": len(results) / span if span > 0 else math.inf,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "mean_latency_s": float(lat.mean()), "makespan_s": span,
+            "certified": int(sum(1 for r in results if r.status == P.OK))}
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int) -> list[float]:
+    """n arrival offsets of a Poisson process with the given rate (seeded)."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n)).tolist()
