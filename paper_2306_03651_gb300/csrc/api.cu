@@ -139,6 +139,10 @@ int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, c
     const int w = atoi(e);
     if (w >= 1 && w <= 32) job->max_wave_words = w;
   }
+  if (const char *e = getenv("CEN_WAVE_STREAMS")) {  // waves of one cen_sample call in flight (1..8)
+    const int w = atoi(e);
+    if (w >= 1 && w <= 8) job->wave_streams = w;
+  }
   try {
     job->stats.init(job->st);
   } catch (...) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -167,6 +168,7 @@ extern const char *const kClassNames[K_COUNT];
 struct Stats {
   cen_kstat k[CEN_NKCLASS];
   bool timing = false;
+  std::mutex mu;  // wave pipelines of one job launch from several threads
   struct Pending {
     int cls;
     cudaEvent_t a, b;

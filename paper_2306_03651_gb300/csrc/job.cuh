@@ -25,6 +25,24 @@ struct WaveWS {
   DevBuf slots;                               // per slot: j (u64), s, t, d (int32)
   DevBuf ctl;                                 // control block (see sampler.cu)
   DevBuf jlist;                               // explicit sample ids for a re-run
+  DevBuf woff;                                // wave-local member offsets per slot
+  DevBuf lens, exoff, scan_tmp;               // offsets of appended samples (workspace 0)
+  void *host = nullptr;                       // pinned staging for this pipeline
+  size_t host_bytes = 0;
+  cudaStream_t own_stream = nullptr;          // stream of an extra pipeline (null for the job's)
+  // Buffers of an extra pipeline are freed in order on the legacy stream
+  // after that pipeline's own stream has drained, then the stream goes.
+  ~WaveWS() {
+    if (own_stream) {
+      cudaStreamSynchronize(own_stream);
+      for (DevBuf *b : {&vis, &lev_ptrs, &tmp, &any, &base, &cnt, &sigc, &ovf, &slots, &ctl, &jlist, &woff, &lens,
+                        &exoff, &scan_tmp, &arcs, &arc_range})
+        b->st = nullptr;
+      for (auto &l : lev) l->st = nullptr;
+    }
+    if (host) cudaFreeHost(host);
+    if (own_stream) cudaStreamDestroy(own_stream);
+  }
   DevBuf arcs;                                // cone arc log of the current wave
   size_t arc_cap = 0;                         // its capacity in arcs
   DevBuf arc_range;                           // per level: [first, end) of its logged arcs
@@ -50,8 +68,9 @@ struct cen_job {
   // AMCERA workspace
   cen::DevBuf R, selh, selst;
   int32_t rade_valid_k = -1;
-  // sampler workspace
-  cen::WaveWS ws;
+  // sampler pipelines (workspace 0 runs on the job's stream)
+  std::vector<std::unique_ptr<cen::WaveWS>> wws;
+  int wave_streams = 4;  // waves of one cen_sample call run at once
   // scratch for scans
   cen::DevBuf scan_tmp;
   // pinned host staging

@@ -39,7 +39,7 @@ void Stats::init(cudaStream_t st) {
     CEN_CK(cudaMemsetAsync(d_units, 0, sizeof(uint64_t) * K_COUNT, st));
   }
 }
-cudaEvent_t Stats::ev() {
+cudaEvent_t Stats::ev() {  // caller holds mu
   if (!pool.empty()) {
     cudaEvent_t e = pool.back();
     pool.pop_back();
@@ -50,6 +50,7 @@ cudaEvent_t Stats::ev() {
   return e;
 }
 void Stats::begin(int cls, cudaStream_t st, cudaEvent_t *a, cudaEvent_t *b) {
+  std::lock_guard<std::mutex> lock(mu);
   k[cls].launches++;
   if (!timing) return;
   *a = ev();
@@ -57,11 +58,13 @@ void Stats::begin(int cls, cudaStream_t st, cudaEvent_t *a, cudaEvent_t *b) {
   CEN_CK(cudaEventRecord(*a, st));
 }
 void Stats::end(int cls, cudaStream_t st, cudaEvent_t a, cudaEvent_t b) {
-  if (!timing || !a) return;
+  if (!a) return;
+  std::lock_guard<std::mutex> lock(mu);
   CEN_CK(cudaEventRecord(b, st));
   pending.push_back({cls, a, b});
 }
 void Stats::resolve() {
+  std::lock_guard<std::mutex> lock(mu);
   for (auto &p : pending) {
     float ms = 0.f;
     CEN_CK(cudaEventElapsedTime(&ms, p.a, p.b));
@@ -74,6 +77,7 @@ void Stats::resolve() {
 }
 void Stats::reset(cudaStream_t st) {
   resolve();
+  std::lock_guard<std::mutex> lock(mu);
   for (int c = 0; c < CEN_NKCLASS; ++c) {
     k[c].launches = 0;
     k[c].ms = 0;

@@ -24,7 +24,10 @@
 // kernels skip them.  Lane layout for per-vertex work: g = lane % G (word),
 // a = lane / G (one of A = 32/G arcs handled side by side).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <mutex>
+#include <thread>
 
 #include "job.cuh"
 
@@ -366,16 +369,16 @@ __global__ void __launch_bounds__(256) k_level_finalize(int32_t n, int G, int gs
 }
 
 // ------------------------------------------------------ offsets + store
-// One block: slot lengths max(d-1, 0) -> hoff of the wave's samples, per-sample
-// s, t, d, and the running max |h|.
-__global__ void __launch_bounds__(1024) k_wave_append(int count, uint64_t jbase, const int32_t *slot_s,
-                                                      const int32_t *slot_t, const int32_t *slot_d, int64_t *hoff,
-                                                      int32_t *ps, int32_t *pt, int32_t *pd, int *bmax, Ctl *ctl) {
+// One block: per-sample s, t, d of the wave, wave-local member offsets
+// woff[b] (exclusive prefix of max(d-1, 0)), the wave's member total and the
+// running max |h|.
+__global__ void __launch_bounds__(1024) k_wave_lengths(int count, uint64_t jbase, const int32_t *slot_s,
+                                                       const int32_t *slot_t, const int32_t *slot_d, int64_t *woff,
+                                                       int32_t *ps, int32_t *pt, int32_t *pd, int *bmax, Ctl *ctl) {
   __shared__ long long wsum[32];
   __shared__ long long carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  const long long base = hoff[jbase];
   int mymax = 0;
   for (int c0 = 0; c0 < count; c0 += 1024) {
     const int b = c0 + threadIdx.x;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(1024) k_wave_append(int count, uint64_t jbase,
     }
     __syncthreads();
     const long long incl = carry + (warp ? wsum[warp - 1] : 0) + x;
-    if (b < count) hoff[jbase + b + 1] = base + incl;
+    if (b < count) woff[b] = incl - len;
     __syncthreads();
     if (threadIdx.x == 1023) carry = incl;
     __syncthreads();
@@ -414,6 +417,22 @@ __global__ void __launch_bounds__(1024) k_wave_append(int count, uint64_t jbase,
   for (int o = 16; o; o >>= 1) mymax = max(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
   if ((threadIdx.x & 31) == 0 && mymax) atomicMax(bmax, mymax);
   if (threadIdx.x == 0) ctl->total = carry;
+}
+
+// lens[i] = max(d[j0+i] - 1, 0): member counts of samples j0 .. j0+count-1.
+__global__ void k_lengths_of(const int32_t *__restrict__ pd, uint64_t j0, uint64_t count, int32_t *lens) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
+    const int d = pd[j0 + i];
+    lens[i] = d >= 2 ? d - 1 : 0;
+  }
+}
+
+// hoff[j0 + i] = hoff[j0] + ex[i] for i = 1 .. count.
+__global__ void k_hoff_add(int64_t *hoff, uint64_t j0, uint64_t count, const int64_t *__restrict__ ex) {
+  const int64_t base = hoff[j0];
+  for (uint64_t i = 1 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    hoff[j0 + i] = base + ex[i];
 }
 
 // ------------------------------------------------------------------ cone
@@ -717,13 +736,16 @@ __device__ __forceinline__ u128 draw_below(uint64_t seed, uint64_t j, uint32_t p
 // Warp per slot (see the file header, step 4).  Arcs are scanned 256 at a time
 // (8 chunks of 32 loaded together).  T = uint64_t: a slot whose sigma_t
 // overflowed is appended to ctl->flagged.  T = u128: it sets ctl->err.
+// Members of slot b go to out[slot_off[b] ...] when slot_off is given (a
+// wave-local buffer), else to out[hoff[j] ...] (the job's store).
 template <class T>
 __global__ void k_walk(int count, int G, SigIdx ix, const uint64_t *__restrict__ slot_j,
                        const int32_t *__restrict__ slot_t, const int32_t *__restrict__ slot_d,
                        const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
                        const uint64_t *const *__restrict__ levs, const T *__restrict__ sig,
-                       const uint64_t *__restrict__ ovf, const int64_t *__restrict__ hoff, int32_t *hmem,
-                       uint64_t seed, Ctl *ctl, unsigned long long *units) {
+                       const uint64_t *__restrict__ ovf, const int64_t *__restrict__ slot_off,
+                       const int64_t *__restrict__ hoff, int32_t *out, uint64_t seed, Ctl *ctl,
+                       unsigned long long *units) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned long long scanned = 0;
@@ -746,7 +768,7 @@ __global__ void k_walk(int count, int G, SigIdx ix, const uint64_t *__restrict__
       continue;
     }
     T sv = sig[ix((int64_t)v * G + g, b & 63)];
-    const int64_t hbase = hoff[j];
+    const int64_t hbase = slot_off ? slot_off[b] : hoff[j];
     uint32_t step = 0;
     int L = d;
     while (L >= 2) {
@@ -791,7 +813,7 @@ __global__ void k_walk(int count, int G, SigIdx ix, const uint64_t *__restrict__
         if (lane == 0) atomicExch(&ctl->err, CEN_EINVAL);
         break;
       }
-      if (lane == 0) hmem[hbase + (L - 2)] = pick;
+      if (lane == 0) out[hbase + (L - 2)] = pick;
       sv = sig[ix((int64_t)pick * G + g, b & 63)];
       v = pick;
       --L;
@@ -827,8 +849,23 @@ __global__ void k_sign(uint64_t j0, uint64_t count, int t, int nw, uint64_t seed
 // ------------------------------------------------------------------ host
 namespace {
 
+void *ws_staging(WaveWS &ws, size_t bytes) {
+  if (bytes > ws.host_bytes) {
+    if (ws.host) cudaFreeHost(ws.host);
+    ws.host = nullptr;
+    ws.host_bytes = 0;
+    size_t cap = 4096;
+    while (cap < bytes) cap *= 2;
+    CEN_CK(cudaMallocHost(&ws.host, cap));
+    ws.host_bytes = cap;
+  }
+  return ws.host;
+}
+
+// One wave pipeline on one stream with its own workspace.
 struct Sampler {
   cen_job *job;
+  WaveWS *wsp;
   const cen_graph *g;
   cudaStream_t st;
   Stats *S;
@@ -839,6 +876,7 @@ struct Sampler {
   uint64_t *slot_j = nullptr;
   int32_t *slot_s = nullptr, *slot_t = nullptr, *slot_d = nullptr, *slot_kind = nullptr;
 
+  WaveWS &ws() { return *wsp; }
   unsigned long long *units(int cls) { return (unsigned long long *)(job->stats.d_units + cls); }
 
   void setup(int Gwant) {
@@ -846,50 +884,51 @@ struct Sampler {
     gshift = 0;
     while ((1 << gshift) < G) ++gshift;
     W = 64 * G;
-    WaveWS &ws = job->ws;
+    WaveWS &w = ws();
     const size_t words = (size_t)n * G;
-    ws.vis.ensure(words * 8, st);
-    ws.ovf.ensure(words * 8, st);
-    ws.any.ensure(words * 8, st);
-    ws.base.ensure((words + 1) * 8, st);
-    ws.cnt.ensure(words * 4, st);
-    if (ws.G != G || !ws.tmp.p) {  // the cone scratch is kept zero between waves of one width
-      ws.tmp.ensure(words * 8, st);
-      CEN_CK(cudaMemsetAsync(ws.tmp.p, 0, words * 8, st));
+    w.vis.ensure(words * 8, st);
+    w.ovf.ensure(words * 8, st);
+    w.any.ensure(words * 8, st);
+    w.base.ensure((words + 1) * 8, st);
+    w.cnt.ensure(words * 4, st);
+    if (w.G != G || !w.tmp.p) {  // the cone scratch is kept zero between waves of one width
+      w.tmp.ensure(words * 8, st);
+      CEN_CK(cudaMemsetAsync(w.tmp.p, 0, words * 8, st));
     }
-    ws.G = G;
-    ws.ctl.ensure(sizeof(Ctl), st);
-    ws.slots.ensure((size_t)kMaxW * (8 + 4 * 4), st);
-    if (ws.arc_cap == 0)  // grows (and the wave is redone) when a wave logs more arcs
-      ws.arc_cap = std::min<size_t>(kArcLogCap, std::max<size_t>((size_t)1 << 16, 2 * words));
-    ws.arcs.ensure(sizeof(ConeArc) * ws.arc_cap, st);
-    ctl = ws.ctl.as<Ctl>();
-    slot_j = ws.slots.as<uint64_t>();
+    w.G = G;
+    w.ctl.ensure(sizeof(Ctl), st);
+    w.slots.ensure((size_t)kMaxW * (8 + 4 * 4), st);
+    w.woff.ensure((size_t)kMaxW * 8, st);
+    if (w.arc_cap == 0)  // grows (and the wave is redone) when a wave logs more arcs
+      w.arc_cap = std::min<size_t>(kArcLogCap, std::max<size_t>((size_t)1 << 16, 2 * words));
+    w.arcs.ensure(sizeof(ConeArc) * w.arc_cap, st);
+    ctl = w.ctl.as<Ctl>();
+    slot_j = w.slots.as<uint64_t>();
     slot_s = (int32_t *)(slot_j + kMaxW);
     slot_t = slot_s + kMaxW;
     slot_d = slot_t + kMaxW;
     slot_kind = slot_d + kMaxW;
-    hctl = (Ctl *)host_staging(job, sizeof(Ctl));
+    hctl = (Ctl *)ws_staging(w, sizeof(Ctl));
   }
 
   uint64_t *level(int L) {
-    WaveWS &ws = job->ws;
+    WaveWS &w = ws();
     const size_t bytes = (size_t)n * G * 8;
-    while ((int)ws.lev.size() <= L) ws.lev.emplace_back(new DevBuf());
-    ws.lev[L]->ensure(bytes, st);
-    return ws.lev[L]->as<uint64_t>();
+    while ((int)w.lev.size() <= L) w.lev.emplace_back(new DevBuf());
+    w.lev[L]->ensure(bytes, st);
+    return w.lev[L]->as<uint64_t>();
   }
 
   void publish_levels(int Lmax) {
-    WaveWS &ws = job->ws;
+    WaveWS &w = ws();
     std::vector<uint64_t *> ptrs(Lmax + 1);
-    for (int L = 0; L <= Lmax; ++L) ptrs[L] = ws.lev[L]->as<uint64_t>();
-    ws.lev_ptrs.ensure(sizeof(uint64_t *) * (Lmax + 1), st);
-    uint64_t **h = (uint64_t **)host_staging(job, sizeof(uint64_t *) * (Lmax + 1) + sizeof(Ctl));
+    for (int L = 0; L <= Lmax; ++L) ptrs[L] = w.lev[L]->as<uint64_t>();
+    w.lev_ptrs.ensure(sizeof(uint64_t *) * (Lmax + 1), st);
+    uint64_t **h = (uint64_t **)ws_staging(w, sizeof(uint64_t *) * (Lmax + 1) + sizeof(Ctl));
     memcpy(h, ptrs.data(), sizeof(uint64_t *) * (Lmax + 1));
-    CEN_CK(cudaMemcpyAsync(ws.lev_ptrs.p, h, sizeof(uint64_t *) * (Lmax + 1), cudaMemcpyHostToDevice, st));
+    CEN_CK(cudaMemcpyAsync(w.lev_ptrs.p, h, sizeof(uint64_t *) * (Lmax + 1), cudaMemcpyHostToDevice, st));
     CEN_CK(cudaStreamSynchronize(st));
-    hctl = (Ctl *)host_staging(job, sizeof(Ctl));
+    hctl = (Ctl *)ws_staging(w, sizeof(Ctl));
   }
 
   void fetch_ctl_head() {
@@ -898,17 +937,17 @@ struct Sampler {
   }
 
   bool any_active() const {
-    for (int g = 0; g < G; ++g)
-      if (hctl->active[g]) return true;
+    for (int gg = 0; gg < G; ++gg)
+      if (hctl->active[gg]) return true;
     return false;
   }
 
   // Discovery for slots [0, count): returns the highest level materialised.
   int discover(int count, uint64_t jbase, const uint64_t *jlist) {
     const size_t words = (size_t)n * G;
-    uint64_t *vis = job->ws.vis.as<uint64_t>();
+    uint64_t *vis = ws().vis.as<uint64_t>();
     CEN_CK(cudaMemsetAsync(vis, 0, words * 8, st));
-    CEN_CK(cudaMemsetAsync(job->ws.ovf.p, 0, words * 8, st));
+    CEN_CK(cudaMemsetAsync(ws().ovf.p, 0, words * 8, st));
     CEN_CK(cudaMemsetAsync(ctl, 0, offsetof(Ctl, flagged), st));
     uint64_t *lev0 = level(0);
     CEN_CK(cudaMemsetAsync(lev0, 0, words * 8, st));
@@ -922,7 +961,6 @@ struct Sampler {
     });
     fetch_ctl_head();
     int L = 0;
-    const int nb = grid_for((size_t)n * 32, 256, kLevelBlocks);
     while (any_active()) {
       uint64_t *cur = level(L);
       uint64_t *nxt = level(L + 1);
@@ -935,7 +973,8 @@ struct Sampler {
       if (push) {
         CEN_CK(cudaMemsetAsync(nxt, 0, words * 8, st));
         launch(S, K_PUSH, st, [&] {
-          k_expand_push<<<resident_grid((const void *)k_expand_push, 256), 256, 0, st>>>(off, col, n, G, gshift, cur, nxt, ctl, units(K_PUSH));
+          k_expand_push<<<resident_grid((const void *)k_expand_push, 256), 256, 0, st>>>(off, col, n, G, gshift, cur,
+                                                                                         nxt, ctl, units(K_PUSH));
         });
         const ChunkTable &oc = g->out_chunks;
         if (oc.count)
@@ -944,12 +983,13 @@ struct Sampler {
                 oc.count, oc.rows(), oc.begins(), off, col, G, gshift, cur, nxt, ctl, units(K_PUSH));
           });
         launch(S, K_LEVEL_FIN, st, [&] {
-          k_level_finalize<<<resident_grid((const void *)k_level_finalize, 256), 256, 0, st>>>(n, G, gshift, nxt, vis, off, ctl,
-                                                                               units(K_LEVEL_FIN));
+          k_level_finalize<<<resident_grid((const void *)k_level_finalize, 256), 256, 0, st>>>(
+              n, G, gshift, nxt, vis, off, ctl, units(K_LEVEL_FIN));
         });
       } else {
         launch(S, K_PULL, st, [&] {
-          k_expand_pull<<<resident_grid((const void *)k_expand_pull, 256), 256, 0, st>>>(roff, rcol, off, n, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
+          k_expand_pull<<<resident_grid((const void *)k_expand_pull, 256), 256, 0, st>>>(
+              roff, rcol, off, n, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
         });
         const ChunkTable &ic = g->in_chunks();
         if (ic.count)
@@ -976,19 +1016,19 @@ struct Sampler {
     const size_t words = (size_t)n * G;
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
-    WaveWS &ws = job->ws;
-    ws.arc_range.ensure(sizeof(unsigned long long) * 2 * (size_t)(Lmax + 3), st);
-    unsigned long long *range = ws.arc_range.as<unsigned long long>();
+    WaveWS &w = ws();
+    w.arc_range.ensure(sizeof(unsigned long long) * 2 * (size_t)(Lmax + 3), st);
+    unsigned long long *range = w.arc_range.as<unsigned long long>();
     CEN_CK(cudaMemsetAsync(range, 0, sizeof(unsigned long long) * 2 * (size_t)(Lmax + 3), st));
     unsigned long long *count = &ctl->arcs;
     CEN_CK(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
-    uint64_t *any = ws.any.as<uint64_t>();
+    uint64_t *any = w.any.as<uint64_t>();
     CEN_CK(cudaMemsetAsync(any, 0, words * 8, st));
-    const ArcLog log{ws.arcs.as<ConeArc>(), count, (unsigned long long)ws.arc_cap};
+    const ArcLog log{w.arcs.as<ConeArc>(), count, (unsigned long long)w.arc_cap};
     const ChunkTable &ic = g->in_chunks();
     for (int L = Lmax; L >= 1; --L) {
       uint64_t *lev = level(L);
-      uint64_t *cone = ws.tmp.as<uint64_t>();
+      uint64_t *cone = w.tmp.as<uint64_t>();
       launch(S, K_CONE, st, [&] {
         k_cone_seed<<<grid_for(W, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, cone, any);
       });
@@ -1010,11 +1050,32 @@ struct Sampler {
                                                                          lev, cone, any, log);
       });
       CEN_CK(cudaMemcpyAsync(range + 2 * (L + 1) + 1, count, 8, cudaMemcpyDeviceToDevice, st));
-      ws.lev[L]->swap(ws.tmp);  // the cone becomes level L
-      CEN_CK(cudaMemsetAsync(ws.tmp.p, 0, words * 8, st));
+      w.lev[L]->swap(w.tmp);  // the cone becomes level L
+      CEN_CK(cudaMemsetAsync(w.tmp.p, 0, words * 8, st));
     }
     fetch_ctl_head();
     return hctl->arcs;
+  }
+
+  // Discovery + cone, redone with a larger arc log when a wave overflows it.
+  int discover_and_cone(int count, uint64_t jbase, const uint64_t *jlist, int64_t *wave_total) {
+    for (;;) {
+      const int Lmax = discover(count, jbase, jlist);
+      if (wave_total) {
+        launch(S, K_APPEND, st, [&] {
+          k_wave_lengths<<<1, 1024, 0, st>>>(count, jbase, slot_s, slot_t, slot_d, ws().woff.as<int64_t>(),
+                                             job->ps.as<int32_t>(), job->pt.as<int32_t>(), job->pd.as<int32_t>(),
+                                             job->bmax.as<int>(), ctl);
+        });
+        fetch_ctl_head();
+        *wave_total = hctl->total;
+      }
+      const unsigned long long narcs = cone(Lmax);
+      if (narcs <= ws().arc_cap) return Lmax;
+      ws().arc_cap = (size_t)(narcs + narcs / 4);
+      ws().arcs.release();
+      setup(G);
+    }
   }
 
   // Compact count store for the cone pairs: bases by an exclusive scan of the
@@ -1022,22 +1083,22 @@ struct Sampler {
   template <class T>
   SigIdx sigma_store(T **sig_out) {
     const size_t words = (size_t)n * G;
-    WaveWS &ws = job->ws;
-    const uint64_t *any = ws.any.as<uint64_t>();
-    int64_t *base = ws.base.as<int64_t>();
+    WaveWS &w = ws();
+    const uint64_t *any = w.any.as<uint64_t>();
+    int64_t *base = w.base.as<int64_t>();
     launch(S, K_SIGMA, st, [&] {
-      k_popc_words<<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, any, ws.cnt.as<int32_t>());
+      k_popc_words<<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, any, w.cnt.as<int32_t>());
     });
-    counts_to_offsets(ws.cnt.as<int32_t>(), base, words, job->scan_tmp, st, S);
-    int64_t *h = (int64_t *)host_staging(job, sizeof(Ctl) + 8);
+    counts_to_offsets(w.cnt.as<int32_t>(), base, words, w.scan_tmp, st, S);
+    int64_t *h = (int64_t *)ws_staging(w, sizeof(Ctl) + 8);
     CEN_CK(cudaMemcpyAsync(h, base + words, 8, cudaMemcpyDeviceToHost, st));
     CEN_CK(cudaStreamSynchronize(st));
     const int64_t pairs = *h;
-    hctl = (Ctl *)host_staging(job, sizeof(Ctl));
-    ws.sigc.ensure(sizeof(T) * (size_t)(pairs + 1), st);
-    CEN_CK(cudaMemsetAsync(ws.sigc.p, 0, sizeof(T) * (size_t)(pairs + 1), st));
+    hctl = (Ctl *)ws_staging(w, sizeof(Ctl));
+    w.sigc.ensure(sizeof(T) * (size_t)(pairs + 1), st);
+    CEN_CK(cudaMemsetAsync(w.sigc.p, 0, sizeof(T) * (size_t)(pairs + 1), st));
     const SigIdx ix{any, base};
-    T *sig = ws.sigc.as<T>();
+    T *sig = w.sigc.as<T>();
     launch(S, K_SIGMA, st, [&] {
       k_cone_level1<T><<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, level(1), ix, sig);
     });
@@ -1046,17 +1107,18 @@ struct Sampler {
   }
 
   // Path counts level by level over the logged arcs (levels 2 .. Lmax+1;
-  // Lmax+1 holds only targets found before their last expansion), then the walk.
+  // Lmax+1 holds only targets found before their last expansion), then the
+  // walk, writing members to out (at slot_off[b], or at hoff[j] if null).
   template <class T>
-  void sigma_and_walk(int count, int Lmax) {
+  void sigma_and_walk(int count, int Lmax, const int64_t *slot_off, int32_t *out) {
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
-    uint64_t *ovf = job->ws.ovf.as<uint64_t>();
-    const ConeArc *arcs = job->ws.arcs.as<ConeArc>();
+    uint64_t *ovf = ws().ovf.as<uint64_t>();
+    const ConeArc *arcs = ws().arcs.as<ConeArc>();
     T *sig = nullptr;
     const SigIdx ix = sigma_store<T>(&sig);
     for (int L = 2; L <= Lmax + 1; ++L) {
-      const unsigned long long *range = job->ws.arc_range.as<unsigned long long>() + 2 * L;
+      const unsigned long long *range = ws().arc_range.as<unsigned long long>() + 2 * L;
       launch(S, K_SIGMA, st, [&] {
         if constexpr (sizeof(T) == 8)
           k_sigma_arcs64<<<resident_grid((const void *)k_sigma_arcs64, 256), 256, 0, st>>>(
@@ -1069,33 +1131,41 @@ struct Sampler {
     publish_levels(Lmax);
     launch(S, K_WALK, st, [&] {
       k_walk<T><<<grid_for((size_t)count * 32, 256), 256, 0, st>>>(
-          count, G, ix, slot_j, slot_t, slot_d, roff, rcol, job->ws.lev_ptrs.as<const uint64_t *>(), sig, ovf,
-          job->hoff.as<int64_t>(), job->hmem.as<int32_t>(), job->seed, ctl, units(K_WALK));
+          count, G, ix, slot_j, slot_t, slot_d, roff, rcol, ws().lev_ptrs.as<const uint64_t *>(), sig, ovf, slot_off,
+          job->hoff.as<int64_t>(), out, job->seed, ctl, units(K_WALK));
     });
   }
 };
 
-}  // namespace
-
 // Wave width: up to gmax words, no wider than the samples left need, and with
 // one level array ([n][G] words) within `budget` bytes.
-static int pick_G(uint64_t remaining, int32_t n, size_t budget, int gmax) {
+int pick_G(uint64_t remaining, int32_t n, size_t budget, int gmax) {
   int G = 1;
   while (G < kMaxG && G < gmax && (uint64_t)64 * G < remaining) G <<= 1;
   while (G > 1 && (size_t)n * G * 8 > budget) G >>= 1;
   return G;
 }
 
+struct WaveOut {
+  uint64_t j0 = 0;
+  int count = 0, G = 0;
+  int64_t total = 0;
+  DevBuf mem;  // the wave's members, samples in order
+  std::vector<uint64_t> flagged;
+};
+
+}  // namespace
+
+// Alg. 1 "sampleHEs": the new samples are cut into waves; up to
+// job->wave_streams waves run at once, each on its own stream and workspace,
+// writing members to a wave buffer.  Then the offsets of all new samples come
+// from one scan of their lengths and the wave buffers are copied in order, so
+// the store is the same whatever the concurrency.  Pairs whose path count
+// reached 2^64 are re-run with 128-bit counts at the end.
 void sample_append(cen_job *job, uint64_t m_new) {
   if (m_new == 0) return;
   const cen_graph *g = job->g;
   cudaStream_t st = job->st;
-  Sampler sp;
-  sp.job = job;
-  sp.g = g;
-  sp.st = st;
-  sp.S = &job->stats;
-  sp.n = g->n;
   const uint64_t m0 = job->m;
   const uint64_t m1 = m0 + m_new;
   job->hoff.ensure(sizeof(int64_t) * (m1 + 1), st, sizeof(int64_t) * (m0 + 1));
@@ -1106,65 +1176,134 @@ void sample_append(cen_job *job, uint64_t m_new) {
   job->sign.ensure(4 * (size_t)job->nw * m1, st, 4 * (size_t)job->nw * m0);
   job->bmax.ensure(4, st, 4);
   if (m0 == 0) CEN_CK(cudaMemsetAsync(job->bmax.p, 0, 4, st));
-  int64_t members = job->members;
-  std::vector<uint64_t> flagged_js;
+
+  // waves
+  std::vector<std::unique_ptr<WaveOut>> waves;
   for (uint64_t j0 = m0; j0 < m1;) {
-    sp.setup(pick_G(m1 - j0, g->n, job->level_budget, job->max_wave_words));
-    const int count = (int)std::min<uint64_t>((uint64_t)sp.W, m1 - j0);
-    int Lmax = 0;
-    int64_t wave_total = 0;
-    for (;;) {  // a wave whose cone arcs overflow the log is redone with a larger log
-      Lmax = sp.discover(count, j0, nullptr);
-      launch(sp.S, K_APPEND, st, [&] {
-        k_wave_append<<<1, 1024, 0, st>>>(count, j0, sp.slot_s, sp.slot_t, sp.slot_d, job->hoff.as<int64_t>(),
-                                          job->ps.as<int32_t>(), job->pt.as<int32_t>(), job->pd.as<int32_t>(),
-                                          job->bmax.as<int>(), sp.ctl);
-      });
-      sp.fetch_ctl_head();
-      wave_total = sp.hctl->total;
-      job->hmem.ensure(4 * (size_t)(members + wave_total + 1), st, 4 * (size_t)members);
-      const unsigned long long narcs = sp.cone(Lmax);
-      if (narcs <= job->ws.arc_cap) break;
-      job->ws.arc_cap = (size_t)(narcs + narcs / 4);
-      job->ws.arcs.release();
-      sp.setup(sp.G);
-    }
-    sp.sigma_and_walk<uint64_t>(count, Lmax);
-    CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    CEN_CK(cudaStreamSynchronize(st));
-    CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent path counts in the backward walk");
-    if (sp.hctl->nflag > 0) {
-      std::vector<uint64_t> slot_js(count);
-      std::vector<int> fl(sp.hctl->flagged, sp.hctl->flagged + sp.hctl->nflag);
-      CEN_CK(cudaMemcpyAsync(slot_js.data(), sp.slot_j, 8 * (size_t)count, cudaMemcpyDeviceToHost, st));
-      CEN_CK(cudaStreamSynchronize(st));
-      for (int b : fl) flagged_js.push_back(slot_js[b]);
-    }
-    members += wave_total;
+    const int G = pick_G(m1 - j0, g->n, job->level_budget, job->max_wave_words);
+    const int count = (int)std::min<uint64_t>((uint64_t)64 * G, m1 - j0);
+    waves.emplace_back(new WaveOut());
+    waves.back()->j0 = j0;
+    waves.back()->count = count;
+    waves.back()->G = G;
     j0 += (uint64_t)count;
   }
-  // 128-bit re-run of the slots whose path count reached 2^64 (offsets already known)
+  int K = std::max(1, std::min<int>(job->wave_streams, (int)waves.size()));
+  if ((size_t)g->n * 8 * waves[0]->G > ((size_t)256 << 20)) K = 1;  // large graphs: one wave at a time
+  while ((int)job->wws.size() < K) {
+    job->wws.emplace_back(new WaveWS());
+    if (job->wws.size() > 1) CEN_CK(cudaStreamCreateWithFlags(&job->wws.back()->own_stream, cudaStreamNonBlocking));
+  }
+  cudaEvent_t ready;
+  CEN_CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  CEN_CK(cudaEventRecord(ready, st));
+
+  std::atomic<size_t> next{0};
+  std::mutex err_mu;
+  Error first_err{CEN_OK, ""};
+  auto work = [&](int w) {
+    try {
+      WaveWS &wsw = *job->wws[w];
+      Sampler sp;
+      sp.job = job;
+      sp.wsp = &wsw;
+      sp.g = g;
+      sp.st = w == 0 ? st : wsw.own_stream;
+      sp.S = &job->stats;
+      sp.n = g->n;
+      if (w > 0) CEN_CK(cudaStreamWaitEvent(sp.st, ready, 0));
+      for (;;) {
+        {
+          std::lock_guard<std::mutex> lk(err_mu);
+          if (first_err.code != CEN_OK) return;
+        }
+        const size_t q = next.fetch_add(1);
+        if (q >= waves.size()) break;
+        WaveOut &wo = *waves[q];
+        sp.setup(wo.G);
+        const int Lmax = sp.discover_and_cone(wo.count, wo.j0, nullptr, &wo.total);
+        wo.mem.ensure(4 * (size_t)(wo.total + 1), sp.st);
+        sp.sigma_and_walk<uint64_t>(wo.count, Lmax, wsw.woff.as<int64_t>(), wo.mem.as<int32_t>());
+        CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sp.st));
+        CEN_CK(cudaStreamSynchronize(sp.st));
+        CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent path counts in the backward walk");
+        if (sp.hctl->nflag > 0) {
+          std::vector<int> fl(sp.hctl->flagged, sp.hctl->flagged + sp.hctl->nflag);
+          std::vector<uint64_t> slot_js(wo.count);
+          CEN_CK(cudaMemcpyAsync(slot_js.data(), sp.slot_j, 8 * (size_t)wo.count, cudaMemcpyDeviceToHost, sp.st));
+          CEN_CK(cudaStreamSynchronize(sp.st));
+          for (int b : fl) wo.flagged.push_back(slot_js[b]);
+        }
+      }
+      CEN_CK(cudaStreamSynchronize(sp.st));
+    } catch (const Error &e) {
+      std::lock_guard<std::mutex> lk(err_mu);
+      if (first_err.code == CEN_OK) first_err = e;
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(err_mu);
+      if (first_err.code == CEN_OK) first_err = Error{CEN_ECUDA, "cen_sample: unexpected error in a wave worker"};
+    }
+  };
+  int dev = 0;
+  CEN_CK(cudaGetDevice(&dev));
+  std::vector<std::thread> pool;
+  for (int w = 1; w < K; ++w)
+    pool.emplace_back([&, w] {
+      if (cudaSetDevice(dev) != cudaSuccess) return;
+      work(w);
+    });
+  work(0);
+  for (auto &th : pool) th.join();
+  cudaEventDestroy(ready);
+  if (first_err.code != CEN_OK) throw first_err;
+
+  // offsets of the new samples, then the wave buffers in order
+  Stats *S = &job->stats;
+  WaveWS &w0 = *job->wws[0];
+  w0.lens.ensure(4 * (size_t)m_new, st);
+  w0.exoff.ensure(8 * ((size_t)m_new + 1), st);
+  launch(S, K_APPEND, st, [&] {
+    k_lengths_of<<<grid_for(m_new, 256), 256, 0, st>>>(job->pd.as<int32_t>(), m0, m_new, w0.lens.as<int32_t>());
+  });
+  counts_to_offsets(w0.lens.as<int32_t>(), w0.exoff.as<int64_t>(), (size_t)m_new, w0.scan_tmp, st, S);
+  launch(S, K_APPEND, st, [&] {
+    k_hoff_add<<<grid_for(m_new, 256), 256, 0, st>>>(job->hoff.as<int64_t>(), m0, m_new, w0.exoff.as<int64_t>());
+  });
+  int64_t total = 0;
+  for (auto &wo : waves) total += wo->total;
+  const int64_t members = job->members;
+  job->hmem.ensure(4 * (size_t)(members + total + 1), st, 4 * (size_t)members);
+  int64_t pos = members;
+  std::vector<uint64_t> flagged_js;
+  for (auto &wo : waves) {
+    if (wo->total)
+      CEN_CK(cudaMemcpyAsync(job->hmem.as<int32_t>() + pos, wo->mem.p, 4 * (size_t)wo->total,
+                             cudaMemcpyDeviceToDevice, st));
+    pos += wo->total;
+    flagged_js.insert(flagged_js.end(), wo->flagged.begin(), wo->flagged.end());
+  }
+
+  // 128-bit re-run of the slots whose path count reached 2^64 (offsets known)
   if (!flagged_js.empty()) {
     std::sort(flagged_js.begin(), flagged_js.end());
+    Sampler sp;
+    sp.job = job;
+    sp.wsp = &w0;
+    sp.g = g;
+    sp.st = st;
+    sp.S = S;
+    sp.n = g->n;
     sp.setup(1);
-    job->ws.jlist.ensure(8 * 64, st);
+    w0.jlist.ensure(8 * 64, st);
     for (size_t q0 = 0; q0 < flagged_js.size(); q0 += 64) {
       const int count = (int)std::min<size_t>(64, flagged_js.size() - q0);
-      uint64_t *h = (uint64_t *)host_staging(job, 8 * 64);
+      uint64_t *h = (uint64_t *)ws_staging(w0, 8 * 64 + sizeof(Ctl));
       memcpy(h, flagged_js.data() + q0, 8 * (size_t)count);
-      CEN_CK(cudaMemcpyAsync(job->ws.jlist.p, h, 8 * (size_t)count, cudaMemcpyHostToDevice, st));
+      CEN_CK(cudaMemcpyAsync(w0.jlist.p, h, 8 * (size_t)count, cudaMemcpyHostToDevice, st));
       CEN_CK(cudaStreamSynchronize(st));
-      sp.hctl = (Ctl *)host_staging(job, sizeof(Ctl));
-      int Lmax = 0;
-      for (;;) {
-        Lmax = sp.discover(count, 0, job->ws.jlist.as<uint64_t>());
-        const unsigned long long narcs = sp.cone(Lmax);
-        if (narcs <= job->ws.arc_cap) break;
-        job->ws.arc_cap = (size_t)(narcs + narcs / 4);
-        job->ws.arcs.release();
-        sp.setup(1);
-      }
-      sp.sigma_and_walk<u128>(count, Lmax);
+      sp.hctl = (Ctl *)ws_staging(w0, sizeof(Ctl));
+      const int Lmax = sp.discover_and_cone(count, 0, w0.jlist.as<uint64_t>(), nullptr);
+      sp.sigma_and_walk<u128>(count, Lmax, nullptr, job->hmem.as<int32_t>());
       CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, offsetof(Ctl, flagged), cudaMemcpyDeviceToHost, st));
       CEN_CK(cudaStreamSynchronize(st));
       CEN_REQUIRE(sp.hctl->err != CEN_EOVERFLOW, CEN_EOVERFLOW,
@@ -1175,14 +1314,15 @@ void sample_append(cen_job *job, uint64_t m_new) {
   // sign columns of the new samples
   {
     const int nblk = (job->nw + 3) / 4;
-    launch(sp.S, K_SIGN, st, [&] {
+    launch(S, K_SIGN, st, [&] {
       k_sign<<<grid_for(m_new * nblk, 256), 256, 0, st>>>(m0, m_new, job->t, job->nw, job->seed,
                                                           job->sign.as<uint32_t>());
     });
   }
+  for (auto &wo : waves) wo->mem.release();  // stream-ordered after the copies above
   CEN_CK(cudaStreamSynchronize(st));
   job->m = m1;
-  job->members = members;
+  job->members = members + total;
 }
 
 }  // namespace cen
