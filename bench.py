@@ -138,6 +138,21 @@ def dram_traffic(kernel_class: str):
     return None
 
 
+# ----------------------------------------------------------------- replicas
+def rank_seed(rank: int) -> int:
+    """Seed of rank `rank`'s replica: distinct per rank, so replicas draw disjoint sample streams."""
+    return 1_000_003 * (rank + 1)
+
+
+def reduce_max(value: float, device) -> float:
+    """Max of `value` over all ranks (the slowest replica times the job)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------- gpu arm
 def gpu_step(P, graph, wl, M, seed):
     job = P.Job(graph, seed, wl.t)
@@ -170,7 +185,7 @@ def run_gpu(args, rank, world):
     graph = P.Graph.of(g)
     M = args.m
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
-    seed0 = 1_000_003 * (rank + 1)
+    seed0 = rank_seed(rank)
     for w in range(args.warmup):
         gpu_step(P, graph, wl, M, seed0 + w)
     torch.cuda.synchronize()
@@ -194,9 +209,7 @@ def run_gpu(args, rank, world):
     clk = clocks.stop()
     total_ms = float(sum(times))
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = reduce_max(total_ms, "cuda")
         torch.distributed.barrier()
     ms_per_step = total_ms / args.steps
     value = world * M * args.steps / (total_ms / 1e3)
@@ -225,9 +238,7 @@ def run_gpu(args, rank, world):
             et.append(time.perf_counter() - t1)
         e_tot = sum(et)
         if world > 1:
-            t = torch.tensor([e_tot], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_tot = float(t.item())
+            e_tot = reduce_max(e_tot, "cuda")
         e2e = {"value": world * M * args.steps / e_tot, "unit": "paths/s",
                "h2d_bytes_per_step": int(g.off.nbytes + g.col.nbytes),
                "d2h_bytes_per_step": int(4 * wl.k + 8 * wl.t + 8 + 4 + 8 + 4)}

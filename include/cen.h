@@ -170,6 +170,22 @@ int cen_job_copy_rade(const cen_job *job, int32_t *R, int32_t *c);
 /* Packed sign words of samples [0, m): words[j * ceil(t/32) + w], bit q%32 of word q/32 set iff sigma_{q,j} = +1. */
 int cen_job_copy_signs(const cen_job *job, uint32_t *words);
 
+/* ---- tuning (results never depend on these; only speed and memory do) ---- */
+#define CEN_PARAM_WAVE_WORDS 1   /* max samples per wave / 64, 1..32 (default 32) */
+#define CEN_PARAM_WAVE_STREAMS 2 /* waves of one cen_sample call in flight, 1..8 (default 4) */
+#define CEN_PARAM_PUSH_RATIO 3   /* expand top-down while frontier out-arcs * ratio < arcs (default 4) */
+#define CEN_PARAM_LEVEL_BUDGET 4 /* max bytes of one per-level bit array [n][wave words] (default 2^30) */
+int cen_job_set_param(cen_job *job, int32_t param, double value);
+/* Defaults for jobs created later on this graph (cen_job_create, cen_run, cen_run_batch);
+ * they take precedence over the environment (CEN_WAVE_WORDS, CEN_WAVE_STREAMS). */
+int cen_graph_set_param(cen_graph *g, int32_t param, double value);
+
+/* Testing hook (no counterpart in the paper): the n-th device allocation the
+ * library makes from now on (n >= 1, any thread) fails with CEN_ENOMEM as if
+ * the device were out of memory; n = 0 disarms.  Process-wide.  Lets callers
+ * test their handling of a full device without filling one. */
+int cen_debug_fail_alloc(int64_t n);
+
 /* ---- instrumentation ---- */
 /* Per-kernel-class launch counts, device time and work units since the job
  * was created (or last reset).  Device time is recorded only while

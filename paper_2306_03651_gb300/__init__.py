@@ -8,7 +8,7 @@ seeded synthetic graph generators and does not load the CUDA library.
 """
 import importlib
 
-_SUBMODULES = ("cen", "inputs", "serve", "_build")
+_SUBMODULES = ("cen", "inputs", "serve", "tune", "_build")
 
 
 def __getattr__(name):

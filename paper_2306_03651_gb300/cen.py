@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libcen.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+PARAM_WAVE_WORDS, PARAM_WAVE_STREAMS, PARAM_PUSH_RATIO, PARAM_LEVEL_BUDGET = 1, 2, 3, 4
 LOG_COLS = ("i", "m", "covered", "Rsum", "Wnum", "b", "C", "A", "w", "nu", "xi", "Rt", "R", "eta", "stop", "S_size")
 NKCLASS = 16
 
@@ -83,6 +84,9 @@ def _load():
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
         "cen_run_batch": ([vp, i32, i32, vp], ip),
+        "cen_job_set_param": ([vp, i32, dbl], ip),
+        "cen_graph_set_param": ([vp, i32, dbl], ip),
+        "cen_debug_fail_alloc": ([i64], ip),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -159,6 +163,10 @@ class Graph:
     def of(cls, g, stream=None):
         """From any object with n, off, col, directed (e.g. the inputs module's Graph)."""
         return cls(g.n, g.off, g.col, g.directed, stream)
+
+    def set_param(self, param: int, value: float):
+        """Tuning default for jobs created later on this graph (results do not change)."""
+        _check(_lib.cen_graph_set_param(self.h, int(param), float(value)), "cen_graph_set_param")
 
     def close(self):
         if getattr(self, "h", None):
@@ -246,6 +254,15 @@ class Job:
         w = np.empty((max(m, 1), self.nw), np.uint32)
         _check(_lib.cen_job_copy_signs(self.h, _p(w)), "cen_job_copy_signs")
         return w[:m]
+
+    def set_param(self, param: int, value: float):
+        _check(_lib.cen_job_set_param(self.h, int(param), float(value)), "cen_job_set_param")
+
+    def tune(self, wave_words=None, wave_streams=None, push_ratio=None, level_budget=None):
+        for p, v in ((PARAM_WAVE_WORDS, wave_words), (PARAM_WAVE_STREAMS, wave_streams),
+                     (PARAM_PUSH_RATIO, push_ratio), (PARAM_LEVEL_BUDGET, level_budget)):
+            if v is not None:
+                self.set_param(p, v)
 
     def set_timing(self, enable: bool):
         _check(_lib.cen_job_set_timing(self.h, int(enable)), "cen_job_set_timing")

@@ -61,6 +61,30 @@ static int bounds_fp64(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, in
 
 using cen::Error;
 
+static void apply_param(cen_job *job, int32_t param, double value) {
+  switch (param) {
+    case CEN_PARAM_WAVE_WORDS:
+      CEN_REQUIRE(value >= 1 && value <= 32, CEN_EINVAL, "cen_job_set_param: wave words must be in [1, 32]");
+      job->max_wave_words = (int)value;
+      break;
+    case CEN_PARAM_WAVE_STREAMS:
+      CEN_REQUIRE(value >= 1 && value <= 8, CEN_EINVAL, "cen_job_set_param: wave streams must be in [1, 8]");
+      job->wave_streams = (int)value;
+      break;
+    case CEN_PARAM_PUSH_RATIO:
+      CEN_REQUIRE(value > 0 && value <= 1e6, CEN_EINVAL, "cen_job_set_param: push ratio must be in (0, 1e6]");
+      job->push_ratio = value;
+      break;
+    case CEN_PARAM_LEVEL_BUDGET:
+      CEN_REQUIRE(value >= (1 << 20), CEN_EINVAL, "cen_job_set_param: level budget must be >= 1 MiB");
+      job->level_budget = (size_t)value;
+      break;
+    default:
+      cen::fail(CEN_EINVAL, "cen_job_set_param: unknown parameter");
+  }
+}
+
+
 #define CEN_API_BEGIN try {
 #define CEN_API_END                                  \
   return CEN_OK;                                     \
@@ -143,6 +167,8 @@ int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, c
     const int w = atoi(e);
     if (w >= 1 && w <= 8) job->wave_streams = w;
   }
+  for (int p = 1; p <= 4; ++p)  // the graph's tuned defaults override the environment
+    if (g->param[p] != 0) apply_param(job, p, g->param[p]);
   try {
     job->stats.init(job->st);
   } catch (...) {
@@ -343,6 +369,23 @@ int cen_job_stats(cen_job *job, cen_kstat *out, int32_t *nclasses) {
     out[c].units = units[c];
   }
   *nclasses = cen::K_COUNT;
+  CEN_API_END
+}
+
+int cen_job_set_param(cen_job *job, int32_t param, double value) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_job_set_param: null job");
+  apply_param(job, param, value);
+  CEN_API_END
+}
+
+int cen_graph_set_param(cen_graph *g, int32_t param, double value) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(g, CEN_EINVAL, "cen_graph_set_param: null graph");
+  CEN_REQUIRE(param >= 1 && param <= 4, CEN_EINVAL, "cen_graph_set_param: unknown parameter");
+  cen_job probe;  // validates the value with the job rules
+  apply_param(&probe, param, value);
+  g->param[param] = value;
   CEN_API_END
 }
 

@@ -35,6 +35,10 @@ void set_last_error(const std::string &msg);
     if (!(cond)) ::cen::fail((code), (text)); \
   } while (0)
 
+// Testing hook: when armed, the n-th device allocation from now fails with
+// CEN_ENOMEM as if the device were full (see cen_debug_fail_alloc).
+void alloc_fault_tick();
+
 // ------------------------------------------------ stream-ordered buffers
 // Device memory owned by the library, allocated and freed in stream order.
 struct DevBuf {
@@ -57,6 +61,7 @@ struct DevBuf {
     size_t cap = bytes ? bytes : 256;
     while (cap < need) cap = cap + cap / 2 + 256;
     void *np = nullptr;
+    alloc_fault_tick();
     CEN_CK(cudaMallocAsync(&np, cap, s));
     if (p && keep) CEN_CK(cudaMemcpyAsync(np, p, keep < bytes ? keep : bytes, cudaMemcpyDeviceToDevice, s));
     if (p) CEN_CK(cudaFreeAsync(p, s));
@@ -243,6 +248,7 @@ struct cen_graph {
   cudaStream_t st = nullptr;
   cen::DevBuf off, col, roff, rcol;  // roff/rcol empty when undirected (alias off/col)
   cen::ChunkTable out_chunks, in_chunks_own;  // in_chunks_own used only when directed
+  double param[5] = {0, 0, 0, 0, 0};          // tuning defaults for jobs on this graph (0 = unset)
   const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
   const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
   const cen::ChunkTable &in_chunks() const { return directed ? in_chunks_own : out_chunks; }

@@ -71,6 +71,7 @@ struct cen_job {
   // sampler pipelines (workspace 0 runs on the job's stream)
   std::vector<std::unique_ptr<cen::WaveWS>> wws;
   int wave_streams = 4;  // waves of one cen_sample call run at once
+  double push_ratio = 4.0;  // expand top-down while frontier out-arcs * push_ratio < arcs
   // scratch for scans
   cen::DevBuf scan_tmp;
   // pinned host staging

@@ -3,6 +3,7 @@
 #include <stdio.h>
 
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -85,6 +86,13 @@ void Stats::reset(cudaStream_t st) {
     k[c].units = 0;
   }
   if (d_units) CEN_CK(cudaMemsetAsync(d_units, 0, sizeof(uint64_t) * K_COUNT, st));
+}
+
+// ------------------------------------------------------ fault hook
+static std::atomic<long long> g_fail_alloc{0};
+void alloc_fault_tick() {
+  if (g_fail_alloc.load(std::memory_order_relaxed) <= 0) return;
+  if (g_fail_alloc.fetch_sub(1) == 1) fail(CEN_ENOMEM, "device allocation failed (injected by cen_debug_fail_alloc)");
 }
 
 // ------------------------------------------------------ occupancy
@@ -298,3 +306,12 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, size_t n, int key_bits, De
 }
 
 }  // namespace cen
+
+extern "C" int cen_debug_fail_alloc(int64_t n) {
+  if (n < 0) {
+    cen::set_last_error("cen_debug_fail_alloc: n must be >= 0");
+    return CEN_EINVAL;
+  }
+  cen::g_fail_alloc.store(n);
+  return CEN_OK;
+}

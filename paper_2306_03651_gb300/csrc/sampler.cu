@@ -968,7 +968,7 @@ struct Sampler {
         k_tcheck_before<<<grid_for((size_t)W * 32, 256), 256, 0, st>>>(W, G, L, slot_t, slot_d, slot_kind, roff,
                                                                        rcol, cur, ctl);
       });
-      const bool push = (double)hctl->farcs * 4.0 < (double)g->nnz;
+      const bool push = (double)hctl->farcs * job->push_ratio < (double)g->nnz;
       CEN_CK(cudaMemsetAsync(&ctl->alive, 0, sizeof(ctl->alive) + sizeof(ctl->farcs), st));
       if (push) {
         CEN_CK(cudaMemsetAsync(nxt, 0, words * 8, st));

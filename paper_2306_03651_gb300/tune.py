@@ -1,0 +1,57 @@
+"""Autotuner for the sampler's launch parameters.
+
+The wave width (slots per bit-parallel wave), the number of wave pipelines in
+flight and the top-down/bottom-up switch only change speed and memory: every
+configuration yields the same samples.  ``autotune`` times one probe round per
+configuration on the caller's graph, checks that all configurations produced
+identical hyper-edges, and stores the fastest as the graph's default
+(``cen_graph_set_param``) so that later jobs, ``run``, ``run_batch`` and the
+serving loop use it.
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import time
+
+import numpy as np
+
+from . import cen as P
+
+DEFAULT_GRID = dict(wave_words=(8, 16, 32), wave_streams=(1, 2, 4), push_ratio=(2.0, 4.0, 16.0))
+
+
+def _digest(h: dict) -> str:
+    m = hashlib.sha256()
+    for key in ("hoff", "hmem", "s", "t", "d"):
+        m.update(np.ascontiguousarray(h[key]).tobytes())
+    return m.hexdigest()
+
+
+def autotune(graph: "P.Graph", t: int = 10, probe_pairs: int = 8192, seed: int = 987654321, grid: dict | None = None,
+             apply: bool = True) -> dict:
+    """Returns dict(best=config, seconds=..., table=[(config, seconds)], digest=...)."""
+    import torch
+    grid = grid or DEFAULT_GRID
+    keys = sorted(grid)
+    table, digests = [], set()
+    for combo in itertools.product(*(grid[k] for k in keys)):
+        cfg = dict(zip(keys, combo))
+        job = P.Job(graph, seed, t)
+        job.tune(**cfg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        job.sample(probe_pairs)
+        torch.cuda.synchronize()
+        table.append((cfg, time.perf_counter() - t0))
+        digests.add(_digest(job.samples()))
+        job.close()
+    if len(digests) != 1:
+        raise RuntimeError("autotune: configurations disagree on the samples")
+    best, secs = min(table, key=lambda x: x[1])
+    if apply:
+        for name, pid in (("wave_words", P.PARAM_WAVE_WORDS), ("wave_streams", P.PARAM_WAVE_STREAMS),
+                          ("push_ratio", P.PARAM_PUSH_RATIO)):
+            if name in best:
+                graph.set_param(pid, best[name])
+    return dict(best=best, seconds=secs, table=table, digest=digests.pop())

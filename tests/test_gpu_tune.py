@@ -1,0 +1,53 @@
+"""Determinism across every tuning configuration, and the autotuner.
+
+Wave width, wave pipelines in flight and the top-down/bottom-up switch change
+speed only: samples, greedy picks and AMCERA numerators must be identical for
+every configuration (this also covers the order in which concurrent waves
+finish)."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_03651_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+P = pytest.importorskip("paper_2306_03651_gb300")
+
+
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_dir"])
+def test_every_configuration_gives_identical_results(name):
+    g = I.ba(2000, 4, 1) if name == "ba2000" else I.rmat(12, 8, seed=3, directed=True, keep_lcc=False)
+    ojob = O.Job(O.Graph.of(g), 21, 16)
+    ojob.sample(3000)
+    ref = ojob.hypergraph()
+    S_ref, cov_ref = ojob.greedy_cover(12)
+    R_ref = ojob.mcera(12)
+    gg = P.Graph.of(g)
+    for words, streams, push in itertools.product((1, 4, 32), (1, 3), (0.5, 4.0, 1e6)):
+        job = P.Job(gg, 21, 16)
+        job.tune(wave_words=words, wave_streams=streams, push_ratio=push)
+        for chunk in (1000, 1, 1999):
+            job.sample(chunk)
+        h = job.samples()
+        for key in ("hoff", "hmem", "s", "t", "d"):
+            assert np.array_equal(h[key], ref[key]), (words, streams, push, key)
+        S, cov = job.greedy_cover(12)
+        assert S.tolist() == S_ref.tolist() and cov == cov_ref
+        Rn, Wn, b = job.mcera(12)
+        assert np.array_equal(Rn, R_ref[0]) and Wn == R_ref[1] and b == R_ref[2]
+
+
+def test_autotune_sets_graph_defaults_without_changing_results():
+    from paper_2306_03651_gb300 import tune
+    g = I.ba(3000, 3, 9)
+    gg = P.Graph.of(g)
+    before = P.run(gg, 8, 0.15, 0.1, 8, 3, m0=500)
+    res = tune.autotune(gg, t=8, probe_pairs=2048, grid=dict(wave_words=(4, 32), wave_streams=(1, 2),
+                                                              push_ratio=(4.0,)))
+    assert res["best"]["wave_words"] in (4, 32) and len(res["table"]) == 4
+    after = P.run(gg, 8, 0.15, 0.1, 8, 3, m0=500)
+    assert after["S"].tolist() == before["S"].tolist() and np.array_equal(after["log"], before["log"])
+    with pytest.raises(P.CenError):
+        gg.set_param(P.PARAM_WAVE_WORDS, 64)
