@@ -53,6 +53,7 @@ def _load():
         "orc_job_new": ([vp, u64, i32, ctypes.POINTER(vp)], ctypes.c_int),
         "orc_job_free": ([vp], None),
         "orc_job_sample": ([vp, u64], ctypes.c_int),
+        "orc_job_sample_from": ([vp, u64, u64], ctypes.c_int),
         "orc_job_m": ([vp], u64),
         "orc_job_members": ([vp], i64),
         "orc_job_copy": ([vp, vp, vp, vp, vp, vp], None),
@@ -188,6 +189,12 @@ class Job:
         rc = _load().orc_job_sample(self.h, m_new)
         if rc:
             raise OracleError(rc, "sample")
+
+    def sample_from(self, j_first: int, count: int):
+        """Append the samples with ids j_first .. j_first+count-1 (shards by sample index)."""
+        rc = _load().orc_job_sample_from(self.h, j_first, count)
+        if rc:
+            raise OracleError(rc, "sample_from")
 
     def hypergraph(self):
         """Returns dict(hoff, hmem, s, t, d) as numpy arrays."""

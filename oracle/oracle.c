@@ -350,6 +350,8 @@ struct orc_job {
   uint64_t seed;
   int32_t t;
   uint64_t m;
+  uint64_t next_id; /* sample id of the next appended sample (= m unless a range was requested) */
+  uint64_t *ids;    /* sample id of each stored sample */
   uint64_t cap_m;
   int64_t *hoff;     /* [m+1] */
   int32_t *hmem;     /* [hoff[m]] */
@@ -369,6 +371,7 @@ int orc_job_new(const orc_graph *g, uint64_t seed, int32_t t, orc_job **out) {
   job->ps = (int32_t *)malloc(sizeof(int32_t) * job->cap_m);
   job->pt = (int32_t *)malloc(sizeof(int32_t) * job->cap_m);
   job->pd = (int32_t *)malloc(sizeof(int32_t) * job->cap_m);
+  job->ids = (uint64_t *)malloc(sizeof(uint64_t) * job->cap_m);
   job->cap_mem = 4096;
   job->hmem = (int32_t *)malloc(sizeof(int32_t) * (size_t)job->cap_mem);
   *out = job;
@@ -377,11 +380,18 @@ int orc_job_new(const orc_graph *g, uint64_t seed, int32_t t, orc_job **out) {
 
 void orc_job_free(orc_job *job) {
   if (!job) return;
-  free(job->hoff); free(job->hmem); free(job->ps); free(job->pt); free(job->pd);
+  free(job->hoff); free(job->hmem); free(job->ps); free(job->pt); free(job->pd); free(job->ids);
   free(job);
 }
 
 uint64_t orc_job_m(const orc_job *job) { return job->m; }
+
+/* Shards by sample index: append the samples with ids j_first .. j_first+count-1
+ * (the store keeps them in id order after any earlier ones). */
+int orc_job_sample_from(orc_job *job, uint64_t j_first, uint64_t count) {
+  job->next_id = j_first;
+  return orc_job_sample(job, count);
+}
 int64_t orc_job_members(const orc_job *job) { return job->hoff[job->m]; }
 
 void orc_job_copy(const orc_job *job, int64_t *hoff, int32_t *hmem, int32_t *s, int32_t *t, int32_t *d) {
@@ -413,12 +423,14 @@ int orc_job_sample(orc_job *job, uint64_t m_new) {
       job->ps = (int32_t *)realloc(job->ps, sizeof(int32_t) * job->cap_m);
       job->pt = (int32_t *)realloc(job->pt, sizeof(int32_t) * job->cap_m);
       job->pd = (int32_t *)realloc(job->pd, sizeof(int32_t) * job->cap_m);
+      job->ids = (uint64_t *)realloc(job->ids, sizeof(uint64_t) * job->cap_m);
     }
     int32_t s, t, d, len;
     uint64_t walk_arcs = 0;
+    const uint64_t jid = job->next_id;
     w.reached_lt_d = 0;
     w.arcs_expanded = 0;
-    rc = hyperedge_ws(g, job->seed, j, &w, &s, &t, &d, &len, path, &walk_arcs);
+    rc = hyperedge_ws(g, job->seed, jid, &w, &s, &t, &d, &len, path, &walk_arcs);
     if (rc != ORC_OK) break;
     int64_t base = job->hoff[j];
     if (base + len > job->cap_mem) {
@@ -430,6 +442,8 @@ int orc_job_sample(orc_job *job, uint64_t m_new) {
     job->ps[j] = s;
     job->pt[j] = t;
     job->pd[j] = d;
+    job->ids[j] = jid;
+    job->next_id = jid + 1;
     job->work[0] += w.reached_lt_d;
     job->work[1] += w.arcs_expanded;
     job->work[2] += walk_arcs;
@@ -492,7 +506,7 @@ int orc_rade_matrix(const orc_job *job, int32_t *R, int32_t *c) {
   memset(R, 0, sizeof(int32_t) * (size_t)n * (size_t)t);
   memset(c, 0, sizeof(int32_t) * (size_t)n);
   for (uint64_t j = 0; j < job->m; ++j) {
-    orc_sign_words(job->seed, j, t, words);
+    orc_sign_words(job->seed, job->ids[j], t, words);
     for (int64_t e = job->hoff[j]; e < job->hoff[j + 1]; ++e) {
       int32_t u = job->hmem[e];
       c[u] += 1;

@@ -75,6 +75,8 @@ int orc_hyperedge(const orc_graph *g, uint64_t seed, uint64_t j, int32_t *s, int
 int orc_job_new(const orc_graph *g, uint64_t seed, int32_t t, orc_job **out);
 void orc_job_free(orc_job *job);
 int orc_job_sample(orc_job *job, uint64_t m_new);      /* append samples [m, m+m_new) */
+/* append the samples with ids j_first .. j_first+count-1 (shards by sample index) */
+int orc_job_sample_from(orc_job *job, uint64_t j_first, uint64_t count);
 uint64_t orc_job_m(const orc_job *job);
 int64_t orc_job_members(const orc_job *job);           /* sum of |h| */
 /* copy out hoff[m+1], hmem[members], and per-sample s, t, d (any may be NULL) */

@@ -151,6 +151,7 @@ static void topk_positive_sum(cen_job *job, const int32_t *vals, int64_t n, int 
 
 void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
   CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_mcera: k must be >= 1");
+  Range range("cen_mcera");
   build_incidence(job);
   cudaStream_t st = job->st;
   Stats *S = &job->stats;

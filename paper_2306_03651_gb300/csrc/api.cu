@@ -250,6 +250,7 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
     uint64_t m_prev = 0, m_i = m0;
     rc = CEN_ENOTCERTIFIED;
     for (int32_t i = 1;; ++i) {
+      cen::Range round_range("cen_run round");
       cen::sample_append(job, m_i - m_prev);
       uint64_t cov = 0;
       cen::greedy_cover(job, k, S_out, S_size, &cov);

@@ -9,9 +9,19 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cen.h"
 
 namespace cen {
+
+// NVTX range for the profiler timeline (no cost when no tool is attached).
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 // ----------------------------------------------------------------- errors
 struct Error {

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_greedy_update(const int64_t *__restrict
 
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered) {
   CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_greedy_cover: k must be >= 1");
+  Range range("cen_greedy_cover");
   build_incidence(job);
   cudaStream_t st = job->st;
   Stats *St = &job->stats;

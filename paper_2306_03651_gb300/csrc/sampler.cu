@@ -1164,6 +1164,7 @@ struct WaveOut {
 // reached 2^64 are re-run with 128-bit counts at the end.
 void sample_append(cen_job *job, uint64_t m_new) {
   if (m_new == 0) return;
+  Range range("cen_sample");
   const cen_graph *g = job->g;
   cudaStream_t st = job->st;
   const uint64_t m0 = job->m;
@@ -1220,6 +1221,7 @@ void sample_append(cen_job *job, uint64_t m_new) {
         const size_t q = next.fetch_add(1);
         if (q >= waves.size()) break;
         WaveOut &wo = *waves[q];
+        Range wave_range("wave");
         sp.setup(wo.G);
         const int Lmax = sp.discover_and_cone(wo.count, wo.j0, nullptr, &wo.total);
         wo.mem.ensure(4 * (size_t)(wo.total + 1), sp.st);

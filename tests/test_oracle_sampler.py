@@ -238,3 +238,21 @@ def test_work_tallies_match_networkx():
         arcs += sum(int(deg[v]) for v, l in lengths.items() if l < d - 1)
     w = job.work()
     assert w[0] == reached and w[1] == arcs and w[3] == h["hoff"][-1]
+
+
+def test_shards_by_sample_index_concatenate_to_the_whole():
+    """Samples are functions of (seed, j): shards over disjoint index ranges, in order,
+    give the same store as one job (the basis of sharded timing and of replicas)."""
+    g = O.Graph.of(I.ba(300, 3, 2))
+    whole = O.Job(g, 13, 4)
+    whole.sample(500)
+    ref = whole.hypergraph()
+    parts = []
+    for a, b in ((0, 170), (170, 171), (171, 500)):
+        job = O.Job(g, 13, 4)
+        job.sample_from(a, b - a)
+        parts.append(job.hypergraph())
+    assert np.concatenate([p["s"] for p in parts]).tolist() == ref["s"].tolist()
+    assert np.concatenate([p["hmem"] for p in parts]).tolist() == ref["hmem"].tolist()
+    lens = np.concatenate([np.diff(p["hoff"]) for p in parts])
+    assert lens.tolist() == np.diff(ref["hoff"]).tolist()
