@@ -63,6 +63,10 @@ def _load():
         "orc_rade_matrix": ([vp, vp, vp], ctypes.c_int),
         "orc_bounds": ([u64, u64, i64, i32, i64, i32, dbl, dbl, i32, vp], ctypes.c_int),
         "orc_run": ([vp, i32, dbl, dbl, i32, u64, u64, u64, vp, vp, vp, vp, vp, vp, i32], ctypes.c_int),
+        "orc_run_sched": ([vp, i32, dbl, dbl, i32, u64, u64, u64, i32, dbl, vp, vp, vp, vp, vp, vp, i32],
+                          ctypes.c_int),
+        "orc_schedule_guess": ([dbl, dbl, dbl, i32], dbl),
+        "orc_schedule_next": ([i32, dbl, u64, u64, dbl, dbl, dbl, i32], u64),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -152,13 +156,14 @@ class Graph:
                                    ctypes.byref(ln), _p(path))
         return rc, s.value, t.value, d.value, path[: ln.value].tolist() if rc == 0 else []
 
-    def run(self, k, eps, delta, t, seed, m0=1000, m_cap=1 << 26, max_rounds=64):
+    def run(self, k, eps, delta, t, seed, m0=1000, m_cap=1 << 26, max_rounds=64, schedule=0, alpha=1.2):
         S = np.empty(k, np.int32)
         size, rounds = ctypes.c_int32(), ctypes.c_int32()
         cov, mf = ctypes.c_uint64(), ctypes.c_uint64()
         log = np.zeros((max_rounds, 16), np.float64)
-        rc = _load().orc_run(self.h, k, eps, delta, t, seed, m0, m_cap, _p(S), ctypes.byref(size), ctypes.byref(cov),
-                             ctypes.byref(mf), ctypes.byref(rounds), _p(log), max_rounds)
+        rc = _load().orc_run_sched(self.h, k, eps, delta, t, seed, m0, m_cap, schedule, alpha, _p(S),
+                                   ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds),
+                                   _p(log), max_rounds)
         if rc not in (OK, ENOTCERTIFIED):
             raise OracleError(rc, "run")
         return dict(status=rc, S=S[: size.value].copy(), covered=cov.value, m_final=mf.value, rounds=rounds.value,
@@ -245,3 +250,11 @@ def bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i):
     out = np.zeros(8, np.float64)
     stop = _load().orc_bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i, _p(out))
     return bool(stop), dict(zip(("C", "A", "w", "nu", "xi", "Rt", "R", "eta"), out.tolist()))
+
+
+def schedule_guess(C, eps, delta, i) -> float:
+    return float(_load().orc_schedule_guess(C, eps, delta, i))
+
+
+def schedule_next(schedule, alpha, m0, m_prev, C_prev, eps, delta, i) -> int:
+    return int(_load().orc_schedule_next(schedule, alpha, m0, m_prev, C_prev, eps, delta, i))

@@ -595,19 +595,58 @@ int orc_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wn
 }
 
 /* ------------------------------------------------------------- Alg. 1 */
+/* Sec. 4.2 "samplingSchedule", optimistic part: Thm. "bound_dev" with R = 0
+ * and nu = 1 leaves eta(m) = sqrt(2 L / m) + L / (3 m); the smallest m with
+ * eta(m) <= eps C / (1 - 1/e) (the stopping test when xi is negligible) solves
+ * (L/3) y^2 + sqrt(2 L) y - target = 0 for y = 1/sqrt(m).  Returns 0 when C = 0
+ * (no finite guess).  Evaluation order is part of the reading. */
+double orc_schedule_guess(double C, double eps, double delta, int32_t i) {
+  double a = 1.0 - exp(-1.0);
+  double L = log(5.0 / ldexp(delta, -i));
+  double target = eps * C / a;
+  if (!(target > 0.0)) return 0.0;
+  double A3 = L / 3.0;
+  double B = sqrt(2.0 * L);
+  double y = (sqrt(B * B + 4.0 * A3 * target) - B) / (2.0 * A3);
+  return 1.0 / (y * y);
+}
+
+/* Next sample size of the schedule.  Doubling: m0 2^(i-1).  Paper
+ * (schedule 1): round 1 is max(m0, ceil(guess(C = 1))); round i > 1 is
+ * max(ceil(alpha m_{i-1}), ceil(guess(C_{i-1}))). */
+uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev, double eps,
+                           double delta, int32_t i) {
+  if (schedule == 0) return i == 1 ? m0 : 2 * m_prev;
+  double grow = i == 1 ? (double)m0 : ceil(alpha * (double)m_prev);
+  double guess = ceil(orc_schedule_guess(i == 1 ? 1.0 : C_prev, eps, delta, i));
+  double m = grow > guess ? grow : guess;
+  if (i > 1 && m <= (double)m_prev) m = (double)m_prev + 1.0;
+  return m >= 18446744073709551615.0 ? UINT64_MAX : (uint64_t)m;
+}
+
 int orc_run(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
             uint64_t m_cap, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final, int32_t *rounds,
             double *log, int32_t max_rounds) {
+  return orc_run_sched(g, k, eps, delta, t, seed, m0, m_cap, 0, 2.0, S_out, S_size, covered, m_final, rounds, log,
+                       max_rounds);
+}
+
+int orc_run_sched(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+                  uint64_t m_cap, int32_t schedule, double alpha, int32_t *S_out, int32_t *S_size, uint64_t *covered,
+                  uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds) {
   double a = 1.0 - exp(-1.0);
-  if (!g || k < 1 || t < 1 || !(eps > 0.0 && eps < a) || !(delta > 0.0 && delta < 1.0) || m0 < 1 || m_cap < m0)
+  if (!g || k < 1 || t < 1 || !(eps > 0.0 && eps < a) || !(delta > 0.0 && delta < 1.0) || m0 < 1 || m_cap < m0 ||
+      (schedule != 0 && schedule != 1) || (schedule == 1 && !(alpha > 1.0)))
     return ORC_EINVAL;
   orc_job *job;
   int rc = orc_job_new(g, seed, t, &job);
   if (rc) return rc;
   int64_t *Rnum = (int64_t *)malloc(sizeof(int64_t) * (size_t)t);
-  uint64_t m_prev = 0, m_i = m0;
+  uint64_t m_prev = 0;
+  uint64_t m_i = orc_schedule_next(schedule, alpha, m0, 0, 1.0, eps, delta, 1);
   int32_t i = 0;
   rc = ORC_ENOTCERTIFIED;
+  if (m_i > m_cap) m_i = m_cap;
   for (;;) {
     ++i;
     int r = orc_job_sample(job, m_i - m_prev);
@@ -634,9 +673,10 @@ int orc_run(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, 
     *m_final = m_i;
     *rounds = i;
     if (stop) { rc = ORC_OK; break; }
-    if (m_i > m_cap / 2) { rc = ORC_ENOTCERTIFIED; break; } /* next m would exceed m_cap */
+    uint64_t next = orc_schedule_next(schedule, alpha, m0, m_i, bd[0], eps, delta, i + 1);
+    if (next > m_cap) { rc = ORC_ENOTCERTIFIED; break; } /* next m would exceed m_cap */
     m_prev = m_i;
-    m_i = 2 * m_i;
+    m_i = next;
   }
   free(Rnum);
   orc_job_free(job);

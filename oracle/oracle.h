@@ -17,7 +17,9 @@
  *     sigma_sw / sigma_sv, scanning in-neighbours in ascending id order;
  *   - greedyCover: ties to the lowest node id; stops early at zero gain;
  *   - sign matrix: extended (never redrawn) across rounds, keyed by sample;
- *   - schedule: m_i = m0 * 2^(i-1); delta_i = delta / 2^i.
+ *   - schedule: m_i = m0 * 2^(i-1) (doubling), or Sec. 4.2's growth by alpha
+ *     with the optimistic guess (R = 0, nu = 1, target eta = eps C_{i-1} /
+ *     (1 - 1/e), C_0 = 1); delta_i = delta / 2^i.
  *
  * Status codes match the CUDA library's public values.
  */
@@ -109,6 +111,15 @@ int orc_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wn
 int orc_run(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
             uint64_t m_cap, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final, int32_t *rounds,
             double *log, int32_t max_rounds);
+
+/* Sampling schedule (Sec. 4.2): 0 = doubling from m0; 1 = the paper's
+ * geometric growth by alpha combined with the optimistic guess (see oracle.c). */
+double orc_schedule_guess(double C, double eps, double delta, int32_t i);
+uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev, double eps,
+                           double delta, int32_t i);
+int orc_run_sched(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+                  uint64_t m_cap, int32_t schedule, double alpha, int32_t *S_out, int32_t *S_size, uint64_t *covered,
+                  uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds);
 
 #ifdef __cplusplus
 }

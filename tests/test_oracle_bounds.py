@@ -4,7 +4,8 @@ test of Algorithm 1, and the progressive loop.
 Special cases with closed forms (C = 0, w = 0, R~ = 0), the equivalence of the
 stopping line with the inequality chain in the proof of Prop. "main", the
 monotonicity of eta, its large-m limit 2 A, and the schedule
-(delta_i = delta / 2^i, m_i = m0 2^(i-1)).  End to end: on a graph small enough
+(delta_i = delta / 2^i, m_i = m0 2^(i-1)), and Sec. 4.2's schedule (its guess
+solves the no-deviation eta for m; growth by alpha).  End to end: on a graph small enough
 for exact set betweenness, the certified set reaches (1 - 1/e - eps) of the
 brute-force optimum.
 """
@@ -153,3 +154,29 @@ def test_certified_set_is_within_guarantee_on_tiny_graph():
         r = og.run(k=k, eps=eps, delta=0.1, t=10, seed=seed, m0=1000)
         assert r["status"] == O.OK
         assert B(r["S"]) >= (1 - 1 / math.e - eps) * opt
+
+
+@pytest.mark.parametrize("C,eps,i", [(1.0, 0.05, 1), (0.4, 0.01, 3), (0.05, 0.2, 7)])
+def test_schedule_guess_solves_the_optimistic_bound(C, eps, i):
+    """Sec. 4.2: with R = 0 and nu = 1, eta(m) = sqrt(2 L/m) + L/(3 m) equals the
+    target eps C / (1 - 1/e) at the guess, and is above it for smaller m."""
+    m = O.schedule_guess(C, eps, 0.1, i)
+    L = L_of(0.1, i)
+    eta = lambda mm: math.sqrt(2 * L / mm) + L / (3 * mm)
+    assert eta(m) == pytest.approx(eps * C / A, rel=1e-12)
+    assert eta(0.99 * m) > eps * C / A > eta(1.01 * m)
+    assert O.schedule_guess(0.0, eps, 0.1, i) == 0.0
+
+
+def test_paper_schedule_grows_geometrically_and_follows_the_guess():
+    g = O.Graph.of(I.ba(300, 3, 2))
+    r = g.run(k=5, eps=0.2, delta=0.1, t=10, seed=3, m0=500, schedule=1, alpha=1.2)
+    assert r["status"] == O.OK
+    ms = [int(row[1]) for row in r["log"]]
+    assert ms[0] == max(500, math.ceil(O.schedule_guess(1.0, 0.2, 0.1, 1)))
+    for prev, cur, row, i in zip(ms, ms[1:], r["log"], range(2, 99)):
+        assert cur >= math.ceil(1.2 * prev) and cur > prev
+        assert cur == max(math.ceil(1.2 * prev), math.ceil(O.schedule_guess(row[6], 0.2, 0.1, i)))
+    # the doubling schedule is unchanged
+    d = g.run(k=5, eps=0.2, delta=0.1, t=10, seed=3, m0=500)
+    assert [int(row[1]) for row in d["log"]] == [500 * 2 ** q for q in range(len(d["log"]))]
