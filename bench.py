@@ -51,9 +51,15 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--mode", default="round", choices=["round", "batch", "serve"],
+    ap.add_argument("--mode", default="round", choices=["round", "batch", "serve", "tsweep", "schedule"],
                     help="round: one Algorithm-1 round per step (default); batch: time to certified eps of the "
-                         "64-job BA workload, one job at a time vs batched; serve: Poisson request stream")
+                         "64-job BA workload, one job at a time vs batched; serve: Poisson request stream; "
+                         "tsweep: fixed-m rounds over the number t of Rademacher vectors (SD bound and time); "
+                         "schedule: time to certified eps with the doubling and the paper's sample schedule")
+    ap.add_argument("--tsweep-m", type=int, default=500000)
+    ap.add_argument("--tsweep-t", default="1,10,50,100,250,500")
+    ap.add_argument("--tsweep-k", type=int, default=50)
+    ap.add_argument("--schedule-eps", default="0.1,0.05")
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -342,6 +348,86 @@ def run_batch_mode(args):
     }))
 
 
+def run_tsweep_mode(args):
+    """Fixed-m rounds over t (the shape of the paper's Sec. 6 experiment on the impact of t:
+    m = 5e5, delta = 0.05, k = 50): per t, the AMCERA, the SD bound eta and the time of one
+    round (sample, greedyCover, AMCERA, bounds), each step a fresh job with its own seed."""
+    import torch
+    import paper_2306_03651_gb300 as P
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    desc, make = WORKLOADS[args.workload]
+    wl = make()
+    graph = P.Graph.of(wl.graph)
+    M, k, delta = args.tsweep_m, args.tsweep_k, 0.05
+    ts = [int(x) for x in args.tsweep_t.split(",")]
+    rows = []
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    for t in ts:
+        times, etas = [], []
+        for step in range(-1, max(args.steps, 1)):  # step -1 is the warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            job = P.Job(graph, 9000 + 97 * t + step, t)
+            job.sample(M)
+            S, cov = job.greedy_cover(k)
+            Rnum, Wnum, b = job.mcera(k)
+            stop, bd = P.bounds(cov, M, int(Rnum.sum()), t, Wnum, b, 0.05, delta, 1)
+            job.close()
+            el = time.perf_counter() - t0
+            if step >= 0:
+                times.append(el)
+                etas.append(bd)
+        rows.append({"t": t, "round_s": statistics.median(times),
+                     "eta": statistics.median(e["eta"] for e in etas),
+                     "amcera": statistics.median(e["A"] for e in etas),
+                     "R": statistics.median(e["R"] for e in etas),
+                     "C": statistics.median(e["C"] for e in etas)})
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": "fixed-m round time over t", "value": rows[-1]["round_s"], "unit": "s", "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "m": M, "k": k, "delta": delta, "t": ts},
+        "rows": rows, "clocks": clk,
+    }))
+
+
+def run_schedule_mode(args):
+    """Time to certified eps of one job with each sample schedule (doubling from m0 = 1000,
+    and the paper's growth by 1.2 plus the optimistic guess)."""
+    import torch
+    import paper_2306_03651_gb300 as P
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    desc, make = WORKLOADS[args.workload]
+    wl = make()
+    graph = P.Graph.of(wl.graph)
+    P.run(graph, wl.k, 0.2, wl.delta, wl.t, 1, m0=1000)  # warm-up
+    rows = []
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    for eps in (float(x) for x in args.schedule_eps.split(",")):
+        for name, sched in (("doubling", P.SCHEDULE_DOUBLING), ("paper", P.SCHEDULE_PAPER)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = P.run(graph, wl.k, eps, wl.delta, wl.t, wl.seed, m0=1000, m_cap=1 << 30, schedule=sched,
+                      alpha=1.2)
+            el = time.perf_counter() - t0
+            rows.append({"eps": eps, "schedule": name, "status": r["status"], "seconds": el,
+                         "rounds": r["rounds"], "m_final": r["m_final"],
+                         "C": float(r["log"][-1][6]) if r["rounds"] else None})
+    clk = clocks.stop()
+    print(json.dumps({
+        "metric": "time to certified eps (s)", "value": rows[-1]["seconds"], "unit": "s", "n_gpus": 1,
+        "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "k": wl.k, "t": wl.t, "delta": wl.delta},
+        "rows": rows, "clocks": clk,
+    }))
+
+
 def run_serve_mode(args):
     """Poisson request stream on device-resident graphs (BA 2000, R-MAT 18 LCC, 8 of
     the batched BA graphs); capacity first (all requests at t=0), then arrival
@@ -415,6 +501,14 @@ def main():
     if args.mode == "serve":
         if rank == 0:
             run_serve_mode(args)
+        return
+    if args.mode == "tsweep":
+        if rank == 0:
+            run_tsweep_mode(args)
+        return
+    if args.mode == "schedule":
+        if rank == 0:
+            run_schedule_mode(args)
         return
     if args.impl == "reference":
         if rank != 0:

@@ -113,6 +113,24 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
             uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
             int32_t *rounds, double *log, int32_t max_rounds);
 
+/* Sample-size schedules (Sec. 4.2).  DOUBLING: m_i = m0 2^(i-1).  PAPER:
+ * geometric growth by alpha > 1 combined with the optimistic guess: m_1 =
+ * max(m0, ceil(g(1))), m_i = max(ceil(alpha m_{i-1}), ceil(g(C_{i-1})),
+ * m_{i-1} + 1), where g(C) is the m at which sqrt(2L/m) + L/(3m) =
+ * eps C / (1 - 1/e), L = ln(5 / delta_i) (the stopping test's eta with no
+ * observed deviation, R = 0, nu = 1), and C_{i-1} is the coverage fraction of
+ * the previous round's greedy set (g(0) = 0).  A first size beyond m_cap is
+ * clamped to m_cap. */
+#define CEN_SCHEDULE_DOUBLING 0
+#define CEN_SCHEDULE_PAPER 1
+
+/* cen_run with a chosen schedule (alpha is read for CEN_SCHEDULE_PAPER only
+ * and must then exceed 1).  Same outputs and status codes as cen_run, which
+ * is cen_run_sched with CEN_SCHEDULE_DOUBLING. */
+int cen_run_sched(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+                  uint64_t m_cap, int32_t schedule, double alpha, void *stream, int32_t *S_out, int32_t *S_size,
+                  uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds);
+
 /* Batched Algorithm 1: `njobs` independent runs of cen_run, each described by
  * a spec and answered in the result with the same index.  `nworkers` host
  * threads, each with its own CUDA stream on the caller's current device, take
@@ -127,6 +145,8 @@ typedef struct cen_job_spec {
   int32_t k, t;
   double eps, delta;
   uint64_t seed, m0, m_cap;
+  int32_t schedule; /* CEN_SCHEDULE_*; a zeroed field is DOUBLING */
+  double alpha;     /* growth factor of CEN_SCHEDULE_PAPER */
 } cen_job_spec;
 typedef struct cen_job_result {
   int32_t status, S_size, rounds, max_rounds;

@@ -22,6 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 PARAM_WAVE_WORDS, PARAM_WAVE_STREAMS, PARAM_PUSH_RATIO, PARAM_LEVEL_BUDGET = 1, 2, 3, 4
+SCHEDULE_DOUBLING, SCHEDULE_PAPER = 0, 1
 LOG_COLS = ("i", "m", "covered", "Rsum", "Wnum", "b", "C", "A", "w", "nu", "xi", "Rt", "R", "eta", "stop", "S_size")
 NKCLASS = 16
 
@@ -35,7 +36,7 @@ class CenError(RuntimeError):
 class cen_job_spec(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_void_p), ("k", ctypes.c_int32), ("t", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("delta", ctypes.c_double), ("seed", ctypes.c_uint64), ("m0", ctypes.c_uint64),
-                ("m_cap", ctypes.c_uint64)]
+                ("m_cap", ctypes.c_uint64), ("schedule", ctypes.c_int32), ("alpha", ctypes.c_double)]
 
 
 class cen_job_result(ctypes.Structure):
@@ -75,6 +76,7 @@ def _load():
         "cen_mcera": ([vp, i32, vp, vp, vp], ip),
         "cen_bounds": ([u64, u64, i64, i32, i64, i32, dbl, dbl, i32, vp, vp], ip),
         "cen_run": ([vp, i32, dbl, dbl, i32, u64, u64, u64, vp, vp, vp, vp, vp, vp, vp, i32], ip),
+        "cen_run_sched": ([vp, i32, dbl, dbl, i32, u64, u64, u64, i32, dbl, vp, vp, vp, vp, vp, vp, vp, i32], ip),
         "cen_job_copy_samples": ([vp, vp, vp, vp, vp, vp], ip),
         "cen_job_copy_incidence": ([vp, vp, vp], ip),
         "cen_job_copy_rade": ([vp, vp, vp], ip),
@@ -287,15 +289,17 @@ def bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i):
 
 
 def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: int = 1000, m_cap: int = 1 << 30,
-        stream=None, max_rounds: int = 64) -> dict:
-    """``cen_run`` (Algorithm 1): certified top-k set; status OK or ENOTCERTIFIED."""
+        stream=None, max_rounds: int = 64, schedule: int = 0, alpha: float = 1.2) -> dict:
+    """``cen_run`` / ``cen_run_sched`` (Algorithm 1): certified top-k set; status OK or ENOTCERTIFIED.
+    schedule: SCHEDULE_DOUBLING (m0 2^(i-1)) or SCHEDULE_PAPER (growth by alpha plus the optimistic guess)."""
     S = np.empty(k, np.int32)
     size, rounds = ctypes.c_int32(), ctypes.c_int32()
     cov, mf = ctypes.c_uint64(), ctypes.c_uint64()
     log = np.zeros((max_rounds, 16), np.float64)
     st = stream if stream is not None else graph.stream
-    rc = _lib.cen_run(graph.h, k, eps, delta, t, seed, m0, m_cap, st, _p(S), ctypes.byref(size), ctypes.byref(cov),
-                      ctypes.byref(mf), ctypes.byref(rounds), _p(log), max_rounds)
+    rc = _lib.cen_run_sched(graph.h, k, eps, delta, t, seed, m0, m_cap, schedule, alpha, st, _p(S),
+                            ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds), _p(log),
+                            max_rounds)
     if rc not in (OK, ENOTCERTIFIED):
         _check(rc, "cen_run")
     return dict(status=rc, S=S[: size.value].copy(), covered=cov.value, m_final=mf.value, rounds=rounds.value,
@@ -304,14 +308,14 @@ def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: i
 
 def run_batch(jobs, nworkers: int = 8, max_rounds: int = 64) -> list[dict]:
     """``cen_run_batch``: `jobs` is a list of dicts with graph (Graph), k, eps, delta, t, seed and optional
-    m0 (1000) / m_cap (2^30).  Returns one dict per job, like ``run`` plus start_s / end_s."""
+    m0 (1000) / m_cap (2^30) / schedule (0) / alpha (1.2).  Returns one dict per job, like ``run`` plus start_s / end_s."""
     n = len(jobs)
     specs = (cen_job_spec * max(n, 1))()
     res = (cen_job_result * max(n, 1))()
     keep = []
     for i, j in enumerate(jobs):
         specs[i] = cen_job_spec(j["graph"].h, j["k"], j["t"], j["eps"], j["delta"], j["seed"], j.get("m0", 1000),
-                                j.get("m_cap", 1 << 30))
+                                j.get("m_cap", 1 << 30), j.get("schedule", 0), j.get("alpha", 1.2))
         S = np.empty(j["k"], np.int32)
         log = np.zeros((max_rounds, 16), np.float64)
         keep.append((S, log))

@@ -57,6 +57,35 @@ static int bounds_fp64(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, in
   return (a * ((a - eps) * xi + eta) <= eps * C) ? 1 : 0;
 }
 
+// Sample-size schedule of Sec. 4.2.  The optimistic guess is the smallest m
+// at which the stopping test could pass if the sample showed no deviation
+// (R = 0, nu = 1 in Thm. "bound_dev"): eta(m) = sqrt(2L/m) + L/(3m) must reach
+// eps C / (1 - 1/e).  With y = 1/sqrt(m) that is the quadratic
+// (L/3) y^2 + sqrt(2L) y = target, solved for its positive root.
+static double schedule_guess(double C, double eps, double delta, int32_t i) {
+  const double a = 1.0 - exp(-1.0);
+  const double L = log(5.0 / ldexp(delta, -i));
+  const double target = eps * C / a;
+  if (!(target > 0.0)) return 0.0;  // C = 0: no finite guess
+  const double A3 = L / 3.0;
+  const double B = sqrt(2.0 * L);
+  const double y = (sqrt(B * B + 4.0 * A3 * target) - B) / (2.0 * A3);
+  return 1.0 / (y * y);
+}
+
+// m_i for round i.  Schedule 0 doubles from m0.  Schedule 1 grows by alpha
+// and jumps to the guess made from the previous round's coverage C_{i-1}
+// (C = 1 before the first round); it always grows by at least one sample.
+static uint64_t schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev,
+                              double eps, double delta, int32_t i) {
+  if (schedule == 0) return i == 1 ? m0 : 2 * m_prev;
+  const double grow = i == 1 ? (double)m0 : ceil(alpha * (double)m_prev);
+  const double guess = ceil(schedule_guess(i == 1 ? 1.0 : C_prev, eps, delta, i));
+  double m = grow > guess ? grow : guess;
+  if (i > 1 && m <= (double)m_prev) m = (double)m_prev + 1.0;
+  return m >= 18446744073709551615.0 ? UINT64_MAX : (uint64_t)m;
+}
+
 }  // namespace cen
 
 using cen::Error;
@@ -237,6 +266,13 @@ int cen_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wn
 int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
             uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
             int32_t *rounds, double *log, int32_t max_rounds) {
+  return cen_run_sched(g, k, eps, delta, t, seed, m0, m_cap, CEN_SCHEDULE_DOUBLING, 2.0, stream, S_out, S_size,
+                       covered, m_final, rounds, log, max_rounds);
+}
+
+int cen_run_sched(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+                  uint64_t m_cap, int32_t schedule, double alpha, void *stream, int32_t *S_out, int32_t *S_size,
+                  uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds) {
   cen_job *job = nullptr;
   int rc = CEN_OK;
   try {
@@ -244,13 +280,18 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
     CEN_REQUIRE(g && S_out && S_size && covered && m_final && rounds, CEN_EINVAL, "cen_run: null argument");
     CEN_REQUIRE(k >= 1 && t >= 1 && eps > 0.0 && eps < a && delta > 0.0 && delta < 1.0 && m0 >= 1 && m_cap >= m0,
                 CEN_EINVAL, "cen_run: need k >= 1, t >= 1, 0 < eps < 1-1/e, 0 < delta < 1, 1 <= m0 <= m_cap");
+    CEN_REQUIRE(schedule == CEN_SCHEDULE_DOUBLING || (schedule == CEN_SCHEDULE_PAPER && alpha > 1.0), CEN_EINVAL,
+                "cen_run: schedule must be doubling, or the paper's with alpha > 1");
     int crc = cen_job_create(g, seed, t, stream, &job);
     if (crc) return crc;
     std::vector<int64_t> Rnum(t);
-    uint64_t m_prev = 0, m_i = m0;
+    uint64_t m_prev = 0;
+    uint64_t m_i = cen::schedule_next(schedule, alpha, m0, 0, 1.0, eps, delta, 1);
+    if (m_i > m_cap) m_i = m_cap;  // a first guess beyond the cap runs one round at the cap
     rc = CEN_ENOTCERTIFIED;
     for (int32_t i = 1;; ++i) {
       cen::Range round_range("cen_run round");
+      CEN_REQUIRE(m_i < (1ull << 31), CEN_EINVAL, "cen_run: at most 2^31 - 1 samples per job");
       cen::sample_append(job, m_i - m_prev);
       uint64_t cov = 0;
       cen::greedy_cover(job, k, S_out, S_size, &cov);
@@ -280,13 +321,14 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
         rc = CEN_OK;
         break;
       }
-      if (m_i > m_cap / 2) {
+      const uint64_t next = cen::schedule_next(schedule, alpha, m0, m_i, bd[0], eps, delta, i + 1);
+      if (next > m_cap) {
         rc = CEN_ENOTCERTIFIED;
         cen::set_last_error("cen_run: not certified within m_cap samples");
         break;
       }
       m_prev = m_i;
-      m_i *= 2;
+      m_i = next;
     }
   } catch (const Error &e) {
     cen::set_last_error(e.msg);

@@ -170,6 +170,52 @@ def test_run_not_certified_on_complete_graph():
     assert r["m_final"] == ro["m_final"] == 1600 and r["covered"] == 0
 
 
+@pytest.mark.parametrize("name,k,eps,t", [("ba300", 5, 0.2, 10), ("rmat12_lcc", 10, 0.1, 25),
+                                          ("grid_rewired", 4, 0.15, 8)])
+def test_paper_schedule_run_matches_oracle(name, k, eps, t):
+    """Sec. 4.2 schedule (growth by alpha plus the optimistic guess): the sample sizes,
+    every bound of every round, the picks and the status equal the oracle's."""
+    g = GRAPHS[name]
+    r = P.run(P.Graph.of(g), k, eps, 0.1, t, 11, m0=1000, schedule=P.SCHEDULE_PAPER, alpha=1.2)
+    ro = O.Graph.of(g).run(k, eps, 0.1, t, 11, m0=1000, schedule=1, alpha=1.2)
+    assert r["status"] == ro["status"] == P.OK
+    assert r["rounds"] == ro["rounds"] and r["m_final"] == ro["m_final"]
+    assert r["S"].tolist() == ro["S"].tolist() and r["covered"] == ro["covered"]
+    assert np.array_equal(r["log"], ro["log"])
+    b = P.run_batch([dict(graph=P.Graph.of(g), k=k, eps=eps, delta=0.1, t=t, seed=11, m0=1000,
+                          schedule=P.SCHEDULE_PAPER, alpha=1.2)], nworkers=1)[0]
+    assert b["status"] == P.OK and np.array_equal(b["log"], ro["log"])
+
+
+def test_fixed_m_bounds_over_t_match_oracle():
+    """Fixed-m rounds over t (the shape of the t sweep): AMCERA numerators and every FP64
+    bound equal the oracle's for t from 1 to 500, where sign words span 1 to 16 words."""
+    g = GRAPHS["ba2000"]
+    m, k = 2500, 50
+    og = O.Graph.of(g)
+    pg = P.Graph.of(g)
+    for t in (1, 10, 50, 100, 250, 500):
+        ojob = O.Job(og, 31 + t, t)
+        ojob.sample(m)
+        job = P.Job(pg, 31 + t, t)
+        job.sample(m)
+        S, cov = job.greedy_cover(k)
+        S2, cov2 = ojob.greedy_cover(k)
+        assert S.tolist() == S2.tolist() and cov == cov2
+        Rn, Wn, b = job.mcera(k)
+        Rn2, Wn2, b2 = ojob.mcera(k)
+        assert np.array_equal(Rn, Rn2) and Wn == Wn2 and b == b2
+        assert P.bounds(cov, m, int(Rn.sum()), t, Wn, b, 0.05, 0.05, 1) == \
+            O.bounds(cov, m, int(Rn2.sum()), t, Wn2, b2, 0.05, 0.05, 1)
+        job.close()
+
+
+def test_paper_schedule_rejects_alpha_at_most_one():
+    with pytest.raises(P.CenError) as ei:
+        P.run(P.Graph.of(GRAPHS["ba300"]), 3, 0.1, 0.1, 4, 1, schedule=P.SCHEDULE_PAPER, alpha=1.0)
+    assert ei.value.rc == P.EINVAL
+
+
 def test_run_argument_checks():
     gg = P.Graph.of(GRAPHS["ba300"])
     for kw in (dict(k=0), dict(eps=0.0), dict(eps=0.7), dict(delta=1.0), dict(t=0)):
