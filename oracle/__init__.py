@@ -63,10 +63,11 @@ def _load():
         "orc_rade_matrix": ([vp, vp, vp], ctypes.c_int),
         "orc_bounds": ([u64, u64, i64, i32, i64, i32, dbl, dbl, i32, vp], ctypes.c_int),
         "orc_run": ([vp, i32, dbl, dbl, i32, u64, u64, u64, vp, vp, vp, vp, vp, vp, i32], ctypes.c_int),
-        "orc_run_sched": ([vp, i32, dbl, dbl, i32, u64, u64, u64, i32, dbl, vp, vp, vp, vp, vp, vp, i32],
-                          ctypes.c_int),
+        "orc_run_ex": ([vp, i32, dbl, dbl, i32, u64, u64, u64, i32, dbl, i32, vp, vp, vp, vp, vp, vp, i32],
+                       ctypes.c_int),
+        "orc_bounds_hedge": ([u64, u64, i32, i32, dbl, dbl, i32, vp], ctypes.c_int),
         "orc_schedule_guess": ([dbl, dbl, dbl, i32], dbl),
-        "orc_schedule_next": ([i32, dbl, u64, u64, dbl, dbl, dbl, i32], u64),
+        "orc_schedule_next": ([i32, dbl, u64, u64, dbl, dbl, dbl, dbl, dbl, i32], u64),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -156,14 +157,16 @@ class Graph:
                                    ctypes.byref(ln), _p(path))
         return rc, s.value, t.value, d.value, path[: ln.value].tolist() if rc == 0 else []
 
-    def run(self, k, eps, delta, t, seed, m0=1000, m_cap=1 << 26, max_rounds=64, schedule=0, alpha=1.2):
+    def run(self, k, eps, delta, t, seed, m0=1000, m_cap=1 << 26, max_rounds=64, schedule=0, alpha=1.2, rule=0):
+        """Algorithm 1.  schedule 0 doubling / 1 the paper's / 2 the paper's plus extrapolation;
+        rule 0 CentRA / 1 HEDGE-P."""
         S = np.empty(k, np.int32)
         size, rounds = ctypes.c_int32(), ctypes.c_int32()
         cov, mf = ctypes.c_uint64(), ctypes.c_uint64()
         log = np.zeros((max_rounds, 16), np.float64)
-        rc = _load().orc_run_sched(self.h, k, eps, delta, t, seed, m0, m_cap, schedule, alpha, _p(S),
-                                   ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds),
-                                   _p(log), max_rounds)
+        rc = _load().orc_run_ex(self.h, k, eps, delta, t, seed, m0, m_cap, schedule, alpha, rule, _p(S),
+                                ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds),
+                                _p(log), max_rounds)
         if rc not in (OK, ENOTCERTIFIED):
             raise OracleError(rc, "run")
         return dict(status=rc, S=S[: size.value].copy(), covered=cov.value, m_final=mf.value, rounds=rounds.value,
@@ -252,9 +255,16 @@ def bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i):
     return bool(stop), dict(zip(("C", "A", "w", "nu", "xi", "Rt", "R", "eta"), out.tolist()))
 
 
+def bounds_hedge(covered, m, n, k, eps, delta, i):
+    """HEDGE-P: returns (stop, dict of C, L_U, nu_U, eta_U)."""
+    out = np.zeros(4, np.float64)
+    stop = _load().orc_bounds_hedge(covered, m, n, k, eps, delta, i, _p(out))
+    return bool(stop), dict(zip(("C", "LU", "nuU", "etaU"), out.tolist()))
+
+
 def schedule_guess(C, eps, delta, i) -> float:
     return float(_load().orc_schedule_guess(C, eps, delta, i))
 
 
-def schedule_next(schedule, alpha, m0, m_prev, C_prev, eps, delta, i) -> int:
-    return int(_load().orc_schedule_next(schedule, alpha, m0, m_prev, C_prev, eps, delta, i))
+def schedule_next(schedule, alpha, m0, m_prev, C_prev, eps, delta, i, eta_prev=0.0, eta_target=0.0) -> int:
+    return int(_load().orc_schedule_next(schedule, alpha, m0, m_prev, C_prev, eta_prev, eta_target, eps, delta, i))

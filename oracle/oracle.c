@@ -594,6 +594,36 @@ int orc_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wn
   return (a * ((a - eps) * xi + eta) <= eps * C) ? 1 : 0;
 }
 
+/* HEDGE-P (Sec. 6, progressive HEDGE): a union bound over the at most n^k
+ * sets of size <= k of a two-sided Bernstein (Chernoff-type) tail for each
+ * set's coverage, i.i.d. 0/1 terms of mean C(S) and variance
+ * C(S)(1 - C(S)) <= min(C(S*), 1/4).  With L_U = k ln n + ln(2 / delta_i),
+ * every set deviates by at most lam(v) = b + sqrt(b^2 + 2 v L_U / m),
+ * b = L_U / (3 m), the root of m lam^2 = L_U (2 v + 2 lam / 3).  C(S*) is
+ * unknown; on the same event C(S*) <= C_H(S*) + lam(C(S*)) <= C / (1 - 1/e) +
+ * lam(C(S*)) (the greedy set keeps a 1 - 1/e share of the sample optimum), so
+ * C(S*) is at most the larger root nu_U of u = C / (1 - 1/e) + lam(u).  The SD
+ * bound is eta_U = lam(min(nu_U, 1/4)).  HEDGE's sufficient condition is
+ * SD <= eps C(S*) / 2; since C(S*) >= C(S) >= C - SD, it holds once
+ * eta_U <= eps (C - eta_U) / 2.
+ * out[0..3] = C, L_U, nu_U, eta_U; returns stop (0/1). */
+int orc_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,
+                     double *out) {
+  double a = 1.0 - exp(-1.0);
+  double md = (double)m;
+  double C = (double)covered / md;
+  double LU = (double)k * log((double)n) + log(2.0 / ldexp(delta, -i));
+  double Lm = LU / md;
+  double b = LU / (3.0 * md);
+  double c0 = C / a + b;
+  /* (u - c0)^2 = b^2 + 2 u Lm, larger root */
+  double nu = c0 + Lm + sqrt(2.0 * c0 * Lm + Lm * Lm + b * b);
+  double v = nu < 0.25 ? nu : 0.25;
+  double eta = b + sqrt(b * b + 2.0 * v * Lm);
+  out[0] = C; out[1] = LU; out[2] = nu; out[3] = eta;
+  return (eta <= eps * (C - eta) / 2.0) ? 1 : 0;
+}
+
 /* ------------------------------------------------------------- Alg. 1 */
 /* Sec. 4.2 "samplingSchedule", optimistic part: Thm. "bound_dev" with R = 0
  * and nu = 1 leaves eta(m) = sqrt(2 L / m) + L / (3 m); the smallest m with
@@ -611,15 +641,24 @@ double orc_schedule_guess(double C, double eps, double delta, int32_t i) {
   return 1.0 / (y * y);
 }
 
-/* Next sample size of the schedule.  Doubling: m0 2^(i-1).  Paper
- * (schedule 1): round 1 is max(m0, ceil(guess(C = 1))); round i > 1 is
- * max(ceil(alpha m_{i-1}), ceil(guess(C_{i-1}))). */
-uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev, double eps,
-                           double delta, int32_t i) {
+/* Next sample size of the schedule for round i.  Schedule 0 doubles from m0.
+ * Schedule 1 (Sec. 4.2): round 1 is max(m0, ceil(guess(C = 1))); round i > 1
+ * is max(ceil(alpha m_{i-1}), ceil(guess(C_{i-1}))).  Schedule 2 also
+ * extrapolates the previous round's SD bound eta_{i-1} at the rate 1/sqrt(m)
+ * (the rate of both SD bounds, Sec. 6) to the largest eta that passes the
+ * stopping test, eta_target > 0: it adds ceil(m_{i-1} (eta_{i-1} /
+ * eta_target)^2) to the max.  Every schedule grows by at least one sample. */
+uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev,
+                           double eta_prev, double eta_target, double eps, double delta, int32_t i) {
   if (schedule == 0) return i == 1 ? m0 : 2 * m_prev;
   double grow = i == 1 ? (double)m0 : ceil(alpha * (double)m_prev);
   double guess = ceil(orc_schedule_guess(i == 1 ? 1.0 : C_prev, eps, delta, i));
   double m = grow > guess ? grow : guess;
+  if (schedule == 2 && i > 1 && eta_target > 0.0) {
+    double r = eta_prev / eta_target;
+    double ext = ceil((double)m_prev * (r * r));
+    if (ext > m) m = ext;
+  }
   if (i > 1 && m <= (double)m_prev) m = (double)m_prev + 1.0;
   return m >= 18446744073709551615.0 ? UINT64_MAX : (uint64_t)m;
 }
@@ -627,23 +666,23 @@ uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t
 int orc_run(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
             uint64_t m_cap, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final, int32_t *rounds,
             double *log, int32_t max_rounds) {
-  return orc_run_sched(g, k, eps, delta, t, seed, m0, m_cap, 0, 2.0, S_out, S_size, covered, m_final, rounds, log,
-                       max_rounds);
+  return orc_run_ex(g, k, eps, delta, t, seed, m0, m_cap, 0, 2.0, 0, S_out, S_size, covered, m_final, rounds, log,
+                    max_rounds);
 }
 
-int orc_run_sched(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
-                  uint64_t m_cap, int32_t schedule, double alpha, int32_t *S_out, int32_t *S_size, uint64_t *covered,
-                  uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds) {
+int orc_run_ex(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+               uint64_t m_cap, int32_t schedule, double alpha, int32_t rule, int32_t *S_out, int32_t *S_size,
+               uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds) {
   double a = 1.0 - exp(-1.0);
   if (!g || k < 1 || t < 1 || !(eps > 0.0 && eps < a) || !(delta > 0.0 && delta < 1.0) || m0 < 1 || m_cap < m0 ||
-      (schedule != 0 && schedule != 1) || (schedule == 1 && !(alpha > 1.0)))
+      schedule < 0 || schedule > 2 || (schedule != 0 && !(alpha > 1.0)) || (rule != 0 && rule != 1))
     return ORC_EINVAL;
   orc_job *job;
   int rc = orc_job_new(g, seed, t, &job);
   if (rc) return rc;
   int64_t *Rnum = (int64_t *)malloc(sizeof(int64_t) * (size_t)t);
   uint64_t m_prev = 0;
-  uint64_t m_i = orc_schedule_next(schedule, alpha, m0, 0, 1.0, eps, delta, 1);
+  uint64_t m_i = orc_schedule_next(schedule, alpha, m0, 0, 1.0, 0.0, 0.0, eps, delta, 1);
   int32_t i = 0;
   rc = ORC_ENOTCERTIFIED;
   if (m_i > m_cap) m_i = m_cap;
@@ -654,14 +693,21 @@ int orc_run_sched(const orc_graph *g, int32_t k, double eps, double delta, int32
     uint64_t cov;
     r = orc_greedy_cover(job, k, S_out, S_size, &cov);
     if (r) { rc = r; break; }
-    int64_t Wnum;
-    int32_t b;
-    r = orc_mcera(job, k, Rnum, &Wnum, &b);
-    if (r) { rc = r; break; }
-    int64_t Rsum = 0;
-    for (int32_t q = 0; q < t; ++q) Rsum += Rnum[q];
-    double bd[8];
-    int stop = orc_bounds(cov, m_i, Rsum, t, Wnum, b, eps, delta, i, bd);
+    int64_t Wnum = 0, Rsum = 0;
+    int32_t b = 0;
+    double bd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int stop;
+    if (rule == 0) {
+      r = orc_mcera(job, k, Rnum, &Wnum, &b);
+      if (r) { rc = r; break; }
+      for (int32_t q = 0; q < t; ++q) Rsum += Rnum[q];
+      stop = orc_bounds(cov, m_i, Rsum, t, Wnum, b, eps, delta, i, bd);
+    } else {
+      /* HEDGE-P: no AMCERA; the log keeps C, nu_U and eta_U in the C, nu and eta columns */
+      double hb[4];
+      stop = orc_bounds_hedge(cov, m_i, g->n, k, eps, delta, i, hb);
+      bd[0] = hb[0]; bd[3] = hb[2]; bd[7] = hb[3];
+    }
     if (log && i <= max_rounds) {
       double *row = log + (size_t)(i - 1) * 16;
       row[0] = i; row[1] = (double)m_i; row[2] = (double)cov; row[3] = (double)Rsum; row[4] = (double)Wnum;
@@ -673,7 +719,9 @@ int orc_run_sched(const orc_graph *g, int32_t k, double eps, double delta, int32
     *m_final = m_i;
     *rounds = i;
     if (stop) { rc = ORC_OK; break; }
-    uint64_t next = orc_schedule_next(schedule, alpha, m0, m_i, bd[0], eps, delta, i + 1);
+    /* the largest SD bound that passes this round's stopping test */
+    double eta_target = rule == 0 ? eps * bd[0] / a - (a - eps) * bd[4] : eps * bd[0] / (2.0 + eps);
+    uint64_t next = orc_schedule_next(schedule, alpha, m0, m_i, bd[0], bd[7], eta_target, eps, delta, i + 1);
     if (next > m_cap) { rc = ORC_ENOTCERTIFIED; break; } /* next m would exceed m_cap */
     m_prev = m_i;
     m_i = next;

@@ -113,13 +113,22 @@ int orc_run(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, 
             double *log, int32_t max_rounds);
 
 /* Sampling schedule (Sec. 4.2): 0 = doubling from m0; 1 = the paper's
- * geometric growth by alpha combined with the optimistic guess (see oracle.c). */
+ * geometric growth by alpha combined with the optimistic guess; 2 = schedule 1
+ * plus extrapolation of the last SD bound to the stopping threshold at the
+ * 1/sqrt(m) rate (see oracle.c). */
 double orc_schedule_guess(double C, double eps, double delta, int32_t i);
-uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev, double eps,
-                           double delta, int32_t i);
-int orc_run_sched(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
-                  uint64_t m_cap, int32_t schedule, double alpha, int32_t *S_out, int32_t *S_size, uint64_t *covered,
-                  uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds);
+uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev,
+                           double eta_prev, double eta_target, double eps, double delta, int32_t i);
+/* HEDGE-P bounds (union bound over n^k sets of a Bernstein tail; see oracle.c):
+ * out[0..3] = C, L_U, nu_U, eta_U; returns 1 iff eta_U <= eps (C - eta_U) / 2. */
+int orc_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,
+                     double *out);
+/* Algorithm 1 with a schedule and a stopping rule: rule 0 = CentRA (AMCERA and
+ * Thm. "bound_dev"), rule 1 = HEDGE-P (orc_bounds_hedge; no AMCERA; the log's
+ * C, nu and eta columns hold C, nu_U, eta_U and the AMCERA columns are 0). */
+int orc_run_ex(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+               uint64_t m_cap, int32_t schedule, double alpha, int32_t rule, int32_t *S_out, int32_t *S_size,
+               uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds);
 
 #ifdef __cplusplus
 }

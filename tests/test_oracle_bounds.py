@@ -180,3 +180,23 @@ def test_paper_schedule_grows_geometrically_and_follows_the_guess():
     # the doubling schedule is unchanged
     d = g.run(k=5, eps=0.2, delta=0.1, t=10, seed=3, m0=500)
     assert [int(row[1]) for row in d["log"]] == [500 * 2 ** q for q in range(len(d["log"]))]
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_extrapolating_schedule_reaches_the_stopping_threshold(rule):
+    """Schedule 2: the next size scales the last SD bound at the 1/sqrt(m) rate to the
+    largest eta that passes the stopping test (C and xi held at the last round's values)."""
+    g = O.Graph.of(I.rmat(10, 8, seed=2))
+    eps, delta, k = 0.1, 0.1, 8
+    r = g.run(k=k, eps=eps, delta=delta, t=20, seed=4, m0=1000, schedule=2, alpha=1.2, rule=rule)
+    p = g.run(k=k, eps=eps, delta=delta, t=20, seed=4, m0=1000, schedule=1, alpha=1.2, rule=rule)
+    assert r["status"] == p["status"] == O.OK
+    ms = [int(row[1]) for row in r["log"]]
+    for i, (row, nxt) in enumerate(zip(r["log"], ms[1:]), start=1):
+        C, xi, eta, m = row[6], row[10], row[13], row[1]
+        target = eps * C / A - (A - eps) * xi if rule == 0 else eps * C / (2 + eps)
+        # at the next size, eta * sqrt(m / next) would meet the threshold (up to the ceil and the max)
+        assert nxt >= m * (eta / target) ** 2 - 1e-6 * m
+        assert nxt == max(math.ceil(1.2 * m), math.ceil(O.schedule_guess(C, eps, delta, i + 1)),
+                          math.ceil(m * (eta / target) ** 2))
+    assert len(r["log"]) < len(p["log"])
