@@ -376,11 +376,13 @@ def run_tsweep_mode(args):
             stop, bd = P.bounds(cov, M, int(Rnum.sum()), t, Wnum, b, 0.05, delta, 1)
             job.close()
             el = time.perf_counter() - t0
+            bd["etaU"] = P.bounds_hedge(cov, M, wl.graph.n, k, 0.05, delta, 1)[1]["etaU"]
             if step >= 0:
                 times.append(el)
                 etas.append(bd)
         rows.append({"t": t, "round_s": statistics.median(times),
                      "eta": statistics.median(e["eta"] for e in etas),
+                     "eta_union_bound": statistics.median(e["etaU"] for e in etas),
                      "amcera": statistics.median(e["A"] for e in etas),
                      "R": statistics.median(e["R"] for e in etas),
                      "C": statistics.median(e["C"] for e in etas)})
@@ -395,8 +397,10 @@ def run_tsweep_mode(args):
 
 
 def run_schedule_mode(args):
-    """Time to certified eps of one job with each sample schedule (doubling from m0 = 1000,
-    and the paper's growth by 1.2 plus the optimistic guess)."""
+    """Time to certified eps of one job per sample schedule (doubling from m0 = 1000; the paper's
+    growth by 1.2 plus the optimistic guess; that plus the predicted size) and stopping rule
+    (CentRA's AMCERA bounds; HEDGE-P's union bound), the shape of the paper's progressive-sampling
+    comparison."""
     import torch
     import paper_2306_03651_gb300 as P
 
@@ -408,16 +412,22 @@ def run_schedule_mode(args):
     rows = []
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
+    plans = (("doubling", P.SCHEDULE_DOUBLING, "centra", P.RULE_CENTRA),
+             ("paper", P.SCHEDULE_PAPER, "centra", P.RULE_CENTRA),
+             ("predict", P.SCHEDULE_EXTRAPOLATE, "centra", P.RULE_CENTRA),
+             ("doubling", P.SCHEDULE_DOUBLING, "hedge_p", P.RULE_HEDGE_P),
+             ("predict", P.SCHEDULE_EXTRAPOLATE, "hedge_p", P.RULE_HEDGE_P))
     for eps in (float(x) for x in args.schedule_eps.split(",")):
-        for name, sched in (("doubling", P.SCHEDULE_DOUBLING), ("paper", P.SCHEDULE_PAPER)):
+        for name, sched, rname, rule in plans:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             r = P.run(graph, wl.k, eps, wl.delta, wl.t, wl.seed, m0=1000, m_cap=1 << 30, schedule=sched,
-                      alpha=1.2)
+                      alpha=1.2, rule=rule)
             el = time.perf_counter() - t0
-            rows.append({"eps": eps, "schedule": name, "status": r["status"], "seconds": el,
+            rows.append({"eps": eps, "schedule": name, "rule": rname, "status": r["status"], "seconds": el,
                          "rounds": r["rounds"], "m_final": r["m_final"],
-                         "C": float(r["log"][-1][6]) if r["rounds"] else None})
+                         "C": float(r["log"][-1][6]) if r["rounds"] else None,
+                         "eta": float(r["log"][-1][13]) if r["rounds"] else None})
     clk = clocks.stop()
     print(json.dumps({
         "metric": "time to certified eps (s)", "value": rows[-1]["seconds"], "unit": "s", "n_gpus": 1,

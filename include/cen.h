@@ -113,29 +113,64 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
             uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
             int32_t *rounds, double *log, int32_t max_rounds);
 
-/* Sample-size schedules (Sec. 4.2).  DOUBLING: m_i = m0 2^(i-1).  PAPER:
- * geometric growth by alpha > 1 combined with the optimistic guess: m_1 =
- * max(m0, ceil(g(1))), m_i = max(ceil(alpha m_{i-1}), ceil(g(C_{i-1})),
- * m_{i-1} + 1), where g(C) is the m at which sqrt(2L/m) + L/(3m) =
- * eps C / (1 - 1/e), L = ln(5 / delta_i) (the stopping test's eta with no
- * observed deviation, R = 0, nu = 1), and C_{i-1} is the coverage fraction of
- * the previous round's greedy set (g(0) = 0).  A first size beyond m_cap is
- * clamped to m_cap. */
+/* Options of cen_run_ex.  A zeroed struct (or a NULL pointer) is cen_run:
+ * doubling schedule, CentRA's stopping rule.
+ *
+ * Sample-size schedules (Sec. 4.2):
+ *   DOUBLING    m_i = m0 2^(i-1).
+ *   PAPER       growth by alpha > 1 combined with the optimistic guess:
+ *               m_1 = max(m0, ceil(g(1))), m_i = max(ceil(alpha m_{i-1}),
+ *               ceil(g(C_{i-1}))), where g(C) is the m at which
+ *               sqrt(2L/m) + L/(3m) = eps C / (1 - 1/e), L = ln(5 / delta_i)
+ *               (the SD bound with no observed deviation, R = 0, nu = 1) and
+ *               C_{i-1} the previous round's coverage fraction (g(0) = 0).
+ *   EXTRAPOLATE PAPER plus m_pred: the smallest m > m_{i-1} at which round
+ *               i's stopping test passes if the coverage fraction C and the
+ *               wimpy-variance fraction w stay as measured in round i-1 and
+ *               the AMCERA shrinks as 1/sqrt(m) (HEDGE-P: C only); found by
+ *               doubling then bisection, and skipped when C = 0 or no size up
+ *               to 2^40 passes.  Not in the paper: a sharper reading of its
+ *               "adaptive guess" that certifies in a few rounds.
+ * Every schedule grows by at least one sample per round; a first size beyond
+ * m_cap is clamped to m_cap.
+ *
+ * Stopping rules:
+ *   CENTRA   Alg. 1: AMCERA, Thm. "bound_dev", stop iff
+ *            (1-1/e)((1-1/e-eps) xi + eta) <= eps C.
+ *   HEDGE_P  Sec. 6's progressive HEDGE: no AMCERA; the SD bound eta_U of
+ *            cen_bounds_hedge; stop iff eta_U <= eps (C - eta_U) / 2.  The
+ *            log row's C, nu and eta columns hold C, nu_U and eta_U and its
+ *            AMCERA columns (Rsum, Wnum, b, AMCERA, w, xi, R~, R) are 0. */
 #define CEN_SCHEDULE_DOUBLING 0
 #define CEN_SCHEDULE_PAPER 1
+#define CEN_SCHEDULE_EXTRAPOLATE 2
+#define CEN_RULE_CENTRA 0
+#define CEN_RULE_HEDGE_P 1
+typedef struct cen_run_opts {
+  int32_t schedule; /* CEN_SCHEDULE_* */
+  int32_t rule;     /* CEN_RULE_* */
+  double alpha;     /* growth factor of PAPER and EXTRAPOLATE (> 1) */
+} cen_run_opts;
 
-/* cen_run with a chosen schedule (alpha is read for CEN_SCHEDULE_PAPER only
- * and must then exceed 1).  Same outputs and status codes as cen_run, which
- * is cen_run_sched with CEN_SCHEDULE_DOUBLING. */
-int cen_run_sched(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
-                  uint64_t m_cap, int32_t schedule, double alpha, void *stream, int32_t *S_out, int32_t *S_size,
-                  uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds);
+/* cen_run with options (NULL = defaults).  Same outputs and status codes. */
+int cen_run_ex(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+               uint64_t m_cap, const cen_run_opts *opts, void *stream, int32_t *S_out, int32_t *S_size,
+               uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds);
 
-/* Batched Algorithm 1: `njobs` independent runs of cen_run, each described by
+/* HEDGE-P's SD bound (no counterpart formula is printed in the paper; this is a
+ * union bound over the <= n^k sets of size <= k of a two-sided Bernstein tail):
+ * L_U = k ln n + ln(2 / delta_i), delta_i = delta / 2^i; nu_U the largest u
+ * with u = C/(1-1/e) + lam(u); eta_U = lam(min(nu_U, 1/4)), where
+ * lam(v) = L_U/(3m) + sqrt((L_U/(3m))^2 + 2 v L_U / m).  out[4] = C, L_U,
+ * nu_U, eta_U; *stop = 1 iff eta_U <= eps (C - eta_U) / 2.  Host code only. */
+int cen_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,
+                     double *out, int32_t *stop);
+
+/* Batched Algorithm 1: `njobs` independent runs of cen_run_ex, each described by
  * a spec and answered in the result with the same index.  `nworkers` host
  * threads, each with its own CUDA stream on the caller's current device, take
  * jobs longest-first (by arc count) so that jobs overlap on the GPU.  Each
- * job's outputs equal those of cen_run called alone with the same spec.
+ * job's outputs equal those of cen_run_ex called alone with the same spec.
  * Caller-owned buffers: results[i].S (capacity specs[i].k) and, optionally,
  * results[i].log (results[i].max_rounds rows of CEN_LOG_COLS doubles).
  * Returns CEN_OK once every job has finished (per-job status in results[i]),
@@ -145,8 +180,7 @@ typedef struct cen_job_spec {
   int32_t k, t;
   double eps, delta;
   uint64_t seed, m0, m_cap;
-  int32_t schedule; /* CEN_SCHEDULE_*; a zeroed field is DOUBLING */
-  double alpha;     /* growth factor of CEN_SCHEDULE_PAPER */
+  cen_run_opts opts; /* zeroed: doubling schedule, CentRA's rule */
 } cen_job_spec;
 typedef struct cen_job_result {
   int32_t status, S_size, rounds, max_rounds;

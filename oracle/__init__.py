@@ -67,7 +67,7 @@ def _load():
                        ctypes.c_int),
         "orc_bounds_hedge": ([u64, u64, i32, i32, dbl, dbl, i32, vp], ctypes.c_int),
         "orc_schedule_guess": ([dbl, dbl, dbl, i32], dbl),
-        "orc_schedule_next": ([i32, dbl, u64, u64, dbl, dbl, dbl, dbl, dbl, i32], u64),
+        "orc_schedule_next": ([i32, dbl, u64, u64, dbl, u64, dbl, dbl, i32], u64),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -158,7 +158,7 @@ class Graph:
         return rc, s.value, t.value, d.value, path[: ln.value].tolist() if rc == 0 else []
 
     def run(self, k, eps, delta, t, seed, m0=1000, m_cap=1 << 26, max_rounds=64, schedule=0, alpha=1.2, rule=0):
-        """Algorithm 1.  schedule 0 doubling / 1 the paper's / 2 the paper's plus extrapolation;
+        """Algorithm 1.  schedule 0 doubling / 1 the paper's / 2 the paper's plus a predicted size;
         rule 0 CentRA / 1 HEDGE-P."""
         S = np.empty(k, np.int32)
         size, rounds = ctypes.c_int32(), ctypes.c_int32()
@@ -266,5 +266,5 @@ def schedule_guess(C, eps, delta, i) -> float:
     return float(_load().orc_schedule_guess(C, eps, delta, i))
 
 
-def schedule_next(schedule, alpha, m0, m_prev, C_prev, eps, delta, i, eta_prev=0.0, eta_target=0.0) -> int:
-    return int(_load().orc_schedule_next(schedule, alpha, m0, m_prev, C_prev, eta_prev, eta_target, eps, delta, i))
+def schedule_next(schedule, alpha, m0, m_prev, C_prev, eps, delta, i, m_pred=0) -> int:
+    return int(_load().orc_schedule_next(schedule, alpha, m0, m_prev, C_prev, m_pred, eps, delta, i))

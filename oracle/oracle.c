@@ -575,23 +575,31 @@ int orc_mcera(const orc_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32
  *   eta = 2 R + sqrt((2 L (nu + 4 R)) / m) + L / (3 m)
  *   stop  <=>  a ((a - eps) xi + eta) <= eps C        (Alg. 1 stopping line)
  */
+/* Thm. "bound_dev" from the sample's fractions C, A, w at sample size md and
+ * L = ln(5 / delta_i); out[3..7] = nu, xi, Rtilde, R, eta. */
+static void bounds_from_fractions(double C, double A, double w, int32_t t, double md, double L, double *out) {
+  double a = 1.0 - exp(-1.0);
+  double Lm = L / md;
+  double xi = sqrt(Lm * Lm + (2.0 * C * L) / (a * md)) + Lm;
+  double nu = C / a + xi;
+  double Rt = A + sqrt((4.0 * w * L) / ((double)t * md));
+  double R = Rt + sqrt(Lm * Lm + (2.0 * L * Rt) / md) + Lm;
+  double eta = 2.0 * R + sqrt((2.0 * L * (nu + 4.0 * R)) / md) + L / (3.0 * md);
+  out[3] = nu; out[4] = xi; out[5] = Rt; out[6] = R; out[7] = eta;
+}
+
 int orc_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
                double delta, int32_t i, double *out) {
   double a = 1.0 - exp(-1.0);
   double md = (double)m;
   double delta_i = ldexp(delta, -i);
   double L = log(5.0 / delta_i);
-  double Lm = L / md;
   double C = (double)covered / md;
   double A = (double)Rsum / ((double)t * md);
   double w = ((double)b * (double)Wnum) / md;
-  double xi = sqrt(Lm * Lm + (2.0 * C * L) / (a * md)) + Lm;
-  double nu = C / a + xi;
-  double Rt = A + sqrt((4.0 * w * L) / ((double)t * md));
-  double R = Rt + sqrt(Lm * Lm + (2.0 * L * Rt) / md) + Lm;
-  double eta = 2.0 * R + sqrt((2.0 * L * (nu + 4.0 * R)) / md) + L / (3.0 * md);
-  out[0] = C; out[1] = A; out[2] = w; out[3] = nu; out[4] = xi; out[5] = Rt; out[6] = R; out[7] = eta;
-  return (a * ((a - eps) * xi + eta) <= eps * C) ? 1 : 0;
+  out[0] = C; out[1] = A; out[2] = w;
+  bounds_from_fractions(C, A, w, t, md, L, out);
+  return (a * ((a - eps) * out[4] + out[7]) <= eps * C) ? 1 : 0;
 }
 
 /* HEDGE-P (Sec. 6, progressive HEDGE): a union bound over the at most n^k
@@ -607,21 +615,67 @@ int orc_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wn
  * SD <= eps C(S*) / 2; since C(S*) >= C(S) >= C - SD, it holds once
  * eta_U <= eps (C - eta_U) / 2.
  * out[0..3] = C, L_U, nu_U, eta_U; returns stop (0/1). */
-int orc_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,
-                     double *out) {
+/* eta_U and nu_U from the coverage fraction C at sample size md; out[2], out[3] */
+static void hedge_from_fraction(double C, double md, double LU, double *out) {
   double a = 1.0 - exp(-1.0);
-  double md = (double)m;
-  double C = (double)covered / md;
-  double LU = (double)k * log((double)n) + log(2.0 / ldexp(delta, -i));
   double Lm = LU / md;
   double b = LU / (3.0 * md);
   double c0 = C / a + b;
   /* (u - c0)^2 = b^2 + 2 u Lm, larger root */
   double nu = c0 + Lm + sqrt(2.0 * c0 * Lm + Lm * Lm + b * b);
   double v = nu < 0.25 ? nu : 0.25;
-  double eta = b + sqrt(b * b + 2.0 * v * Lm);
-  out[0] = C; out[1] = LU; out[2] = nu; out[3] = eta;
-  return (eta <= eps * (C - eta) / 2.0) ? 1 : 0;
+  out[2] = nu;
+  out[3] = b + sqrt(b * b + 2.0 * v * Lm);
+}
+
+static double hedge_L(int32_t n, int32_t k, double delta, int32_t i) {
+  return (double)k * log((double)n) + log(2.0 / ldexp(delta, -i));
+}
+
+int orc_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,
+                     double *out) {
+  double md = (double)m;
+  double C = (double)covered / md;
+  out[0] = C;
+  out[1] = hedge_L(n, k, delta, i);
+  hedge_from_fraction(C, md, out[1], out);
+  return (out[3] <= eps * (C - out[3]) / 2.0) ? 1 : 0;
+}
+
+/* The prediction of the extrapolating schedule: would round i's stopping test
+ * pass at sample size mp if the coverage fraction C and the wimpy-variance
+ * fraction w stayed as measured at m and the AMCERA shrank as 1/sqrt(m)?
+ * (rule 0; rule 1 keeps C only). */
+static int predicted_stop(int32_t rule, double C, double A, double w, int32_t t, int32_t n, int32_t k, uint64_t m,
+                          uint64_t mp, double eps, double delta, int32_t i) {
+  double a = 1.0 - exp(-1.0);
+  double md = (double)mp;
+  double o[8];
+  if (rule == 0) {
+    double Ap = A * sqrt((double)m / md);
+    bounds_from_fractions(C, Ap, w, t, md, log(5.0 / ldexp(delta, -i)), o);
+    return a * ((a - eps) * o[4] + o[7]) <= eps * C;
+  }
+  hedge_from_fraction(C, md, hedge_L(n, k, delta, i), o);
+  return o[3] <= eps * (C - o[3]) / 2.0;
+}
+
+/* Smallest mp > m at which predicted_stop holds (bisection after doubling),
+ * or 0 when none up to 2^40 does (then the prediction is not used). */
+static uint64_t predict_m(int32_t rule, double C, double A, double w, int32_t t, int32_t n, int32_t k, uint64_t m,
+                          double eps, double delta, int32_t i) {
+  if (!(C > 0.0)) return 0;
+  uint64_t lo = m, hi = 2 * m;
+  while (!predicted_stop(rule, C, A, w, t, n, k, m, hi, eps, delta, i)) {
+    if (hi >= ((uint64_t)1 << 40)) return 0;
+    lo = hi;
+    hi = 2 * hi;
+  }
+  while (hi - lo > 1) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (predicted_stop(rule, C, A, w, t, n, k, m, mid, eps, delta, i)) hi = mid; else lo = mid;
+  }
+  return hi;
 }
 
 /* ------------------------------------------------------------- Alg. 1 */
@@ -643,22 +697,17 @@ double orc_schedule_guess(double C, double eps, double delta, int32_t i) {
 
 /* Next sample size of the schedule for round i.  Schedule 0 doubles from m0.
  * Schedule 1 (Sec. 4.2): round 1 is max(m0, ceil(guess(C = 1))); round i > 1
- * is max(ceil(alpha m_{i-1}), ceil(guess(C_{i-1}))).  Schedule 2 also
- * extrapolates the previous round's SD bound eta_{i-1} at the rate 1/sqrt(m)
- * (the rate of both SD bounds, Sec. 6) to the largest eta that passes the
- * stopping test, eta_target > 0: it adds ceil(m_{i-1} (eta_{i-1} /
- * eta_target)^2) to the max.  Every schedule grows by at least one sample. */
+ * is max(ceil(alpha m_{i-1}), ceil(guess(C_{i-1}))).  Schedule 2 also takes
+ * m_pred (> 0), the size at which round i's stopping test is predicted to
+ * pass from round i-1's summary (predict_m).  Every schedule grows by at least
+ * one sample. */
 uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev,
-                           double eta_prev, double eta_target, double eps, double delta, int32_t i) {
+                           uint64_t m_pred, double eps, double delta, int32_t i) {
   if (schedule == 0) return i == 1 ? m0 : 2 * m_prev;
   double grow = i == 1 ? (double)m0 : ceil(alpha * (double)m_prev);
   double guess = ceil(orc_schedule_guess(i == 1 ? 1.0 : C_prev, eps, delta, i));
   double m = grow > guess ? grow : guess;
-  if (schedule == 2 && i > 1 && eta_target > 0.0) {
-    double r = eta_prev / eta_target;
-    double ext = ceil((double)m_prev * (r * r));
-    if (ext > m) m = ext;
-  }
+  if (schedule == 2 && i > 1 && m_pred > 0 && (double)m_pred > m) m = (double)m_pred;
   if (i > 1 && m <= (double)m_prev) m = (double)m_prev + 1.0;
   return m >= 18446744073709551615.0 ? UINT64_MAX : (uint64_t)m;
 }
@@ -682,7 +731,7 @@ int orc_run_ex(const orc_graph *g, int32_t k, double eps, double delta, int32_t 
   if (rc) return rc;
   int64_t *Rnum = (int64_t *)malloc(sizeof(int64_t) * (size_t)t);
   uint64_t m_prev = 0;
-  uint64_t m_i = orc_schedule_next(schedule, alpha, m0, 0, 1.0, 0.0, 0.0, eps, delta, 1);
+  uint64_t m_i = orc_schedule_next(schedule, alpha, m0, 0, 1.0, 0, eps, delta, 1);
   int32_t i = 0;
   rc = ORC_ENOTCERTIFIED;
   if (m_i > m_cap) m_i = m_cap;
@@ -719,9 +768,8 @@ int orc_run_ex(const orc_graph *g, int32_t k, double eps, double delta, int32_t 
     *m_final = m_i;
     *rounds = i;
     if (stop) { rc = ORC_OK; break; }
-    /* the largest SD bound that passes this round's stopping test */
-    double eta_target = rule == 0 ? eps * bd[0] / a - (a - eps) * bd[4] : eps * bd[0] / (2.0 + eps);
-    uint64_t next = orc_schedule_next(schedule, alpha, m0, m_i, bd[0], bd[7], eta_target, eps, delta, i + 1);
+    uint64_t m_pred = schedule == 2 ? predict_m(rule, bd[0], bd[1], bd[2], t, g->n, k, m_i, eps, delta, i + 1) : 0;
+    uint64_t next = orc_schedule_next(schedule, alpha, m0, m_i, bd[0], m_pred, eps, delta, i + 1);
     if (next > m_cap) { rc = ORC_ENOTCERTIFIED; break; } /* next m would exceed m_cap */
     m_prev = m_i;
     m_i = next;

@@ -114,11 +114,11 @@ int orc_run(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, 
 
 /* Sampling schedule (Sec. 4.2): 0 = doubling from m0; 1 = the paper's
  * geometric growth by alpha combined with the optimistic guess; 2 = schedule 1
- * plus extrapolation of the last SD bound to the stopping threshold at the
- * 1/sqrt(m) rate (see oracle.c). */
+ * plus m_pred, the smallest size at which the next round's stopping test
+ * passes if C and w hold and the AMCERA shrinks as 1/sqrt(m) (see oracle.c). */
 double orc_schedule_guess(double C, double eps, double delta, int32_t i);
 uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev,
-                           double eta_prev, double eta_target, double eps, double delta, int32_t i);
+                           uint64_t m_pred, double eps, double delta, int32_t i);
 /* HEDGE-P bounds (union bound over n^k sets of a Bernstein tail; see oracle.c):
  * out[0..3] = C, L_U, nu_U, eta_U; returns 1 iff eta_U <= eps (C - eta_U) / 2. */
 int orc_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,

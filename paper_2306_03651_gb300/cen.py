@@ -22,7 +22,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 PARAM_WAVE_WORDS, PARAM_WAVE_STREAMS, PARAM_PUSH_RATIO, PARAM_LEVEL_BUDGET = 1, 2, 3, 4
-SCHEDULE_DOUBLING, SCHEDULE_PAPER = 0, 1
+SCHEDULE_DOUBLING, SCHEDULE_PAPER, SCHEDULE_EXTRAPOLATE = 0, 1, 2
+RULE_CENTRA, RULE_HEDGE_P = 0, 1
 LOG_COLS = ("i", "m", "covered", "Rsum", "Wnum", "b", "C", "A", "w", "nu", "xi", "Rt", "R", "eta", "stop", "S_size")
 NKCLASS = 16
 
@@ -33,10 +34,14 @@ class CenError(RuntimeError):
         self.rc = rc
 
 
+class cen_run_opts(ctypes.Structure):
+    _fields_ = [("schedule", ctypes.c_int32), ("rule", ctypes.c_int32), ("alpha", ctypes.c_double)]
+
+
 class cen_job_spec(ctypes.Structure):
     _fields_ = [("graph", ctypes.c_void_p), ("k", ctypes.c_int32), ("t", ctypes.c_int32), ("eps", ctypes.c_double),
                 ("delta", ctypes.c_double), ("seed", ctypes.c_uint64), ("m0", ctypes.c_uint64),
-                ("m_cap", ctypes.c_uint64), ("schedule", ctypes.c_int32), ("alpha", ctypes.c_double)]
+                ("m_cap", ctypes.c_uint64), ("opts", cen_run_opts)]
 
 
 class cen_job_result(ctypes.Structure):
@@ -76,7 +81,8 @@ def _load():
         "cen_mcera": ([vp, i32, vp, vp, vp], ip),
         "cen_bounds": ([u64, u64, i64, i32, i64, i32, dbl, dbl, i32, vp, vp], ip),
         "cen_run": ([vp, i32, dbl, dbl, i32, u64, u64, u64, vp, vp, vp, vp, vp, vp, vp, i32], ip),
-        "cen_run_sched": ([vp, i32, dbl, dbl, i32, u64, u64, u64, i32, dbl, vp, vp, vp, vp, vp, vp, vp, i32], ip),
+        "cen_run_ex": ([vp, i32, dbl, dbl, i32, u64, u64, u64, vp, vp, vp, vp, vp, vp, vp, vp, i32], ip),
+        "cen_bounds_hedge": ([u64, u64, i32, i32, dbl, dbl, i32, vp, vp], ip),
         "cen_job_copy_samples": ([vp, vp, vp, vp, vp, vp], ip),
         "cen_job_copy_incidence": ([vp, vp, vp], ip),
         "cen_job_copy_rade": ([vp, vp, vp], ip),
@@ -288,18 +294,29 @@ def bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i):
     return bool(stop.value), dict(zip(("C", "A", "w", "nu", "xi", "Rt", "R", "eta"), out.tolist()))
 
 
+def bounds_hedge(covered, m, n, k, eps, delta, i):
+    """``cen_bounds_hedge``: (stop, dict C, LU, nuU, etaU) of HEDGE-P's union bound."""
+    out = np.zeros(4, np.float64)
+    stop = ctypes.c_int32()
+    _check(_lib.cen_bounds_hedge(covered, m, n, k, eps, delta, i, _p(out), ctypes.byref(stop)), "cen_bounds_hedge")
+    return bool(stop.value), dict(zip(("C", "LU", "nuU", "etaU"), out.tolist()))
+
+
 def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: int = 1000, m_cap: int = 1 << 30,
-        stream=None, max_rounds: int = 64, schedule: int = 0, alpha: float = 1.2) -> dict:
-    """``cen_run`` / ``cen_run_sched`` (Algorithm 1): certified top-k set; status OK or ENOTCERTIFIED.
-    schedule: SCHEDULE_DOUBLING (m0 2^(i-1)) or SCHEDULE_PAPER (growth by alpha plus the optimistic guess)."""
+        stream=None, max_rounds: int = 64, schedule: int = 0, alpha: float = 1.2, rule: int = 0) -> dict:
+    """``cen_run_ex`` (Algorithm 1): certified top-k set; status OK or ENOTCERTIFIED.
+    schedule: SCHEDULE_DOUBLING (m0 2^(i-1)), SCHEDULE_PAPER (growth by alpha plus the optimistic guess) or
+    SCHEDULE_EXTRAPOLATE (PAPER plus the last SD bound scaled to the stopping threshold);
+    rule: RULE_CENTRA (AMCERA bounds) or RULE_HEDGE_P (union bound)."""
     S = np.empty(k, np.int32)
     size, rounds = ctypes.c_int32(), ctypes.c_int32()
     cov, mf = ctypes.c_uint64(), ctypes.c_uint64()
     log = np.zeros((max_rounds, 16), np.float64)
     st = stream if stream is not None else graph.stream
-    rc = _lib.cen_run_sched(graph.h, k, eps, delta, t, seed, m0, m_cap, schedule, alpha, st, _p(S),
-                            ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds), _p(log),
-                            max_rounds)
+    opts = cen_run_opts(schedule, rule, alpha)
+    rc = _lib.cen_run_ex(graph.h, k, eps, delta, t, seed, m0, m_cap, ctypes.byref(opts), st, _p(S),
+                         ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds), _p(log),
+                         max_rounds)
     if rc not in (OK, ENOTCERTIFIED):
         _check(rc, "cen_run")
     return dict(status=rc, S=S[: size.value].copy(), covered=cov.value, m_final=mf.value, rounds=rounds.value,
@@ -308,14 +325,15 @@ def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: i
 
 def run_batch(jobs, nworkers: int = 8, max_rounds: int = 64) -> list[dict]:
     """``cen_run_batch``: `jobs` is a list of dicts with graph (Graph), k, eps, delta, t, seed and optional
-    m0 (1000) / m_cap (2^30) / schedule (0) / alpha (1.2).  Returns one dict per job, like ``run`` plus start_s / end_s."""
+    m0 (1000) / m_cap (2^30) / schedule (0) / rule (0) / alpha (1.2).  Returns one dict per job, like ``run`` plus start_s / end_s."""
     n = len(jobs)
     specs = (cen_job_spec * max(n, 1))()
     res = (cen_job_result * max(n, 1))()
     keep = []
     for i, j in enumerate(jobs):
         specs[i] = cen_job_spec(j["graph"].h, j["k"], j["t"], j["eps"], j["delta"], j["seed"], j.get("m0", 1000),
-                                j.get("m_cap", 1 << 30), j.get("schedule", 0), j.get("alpha", 1.2))
+                                j.get("m_cap", 1 << 30),
+                                cen_run_opts(j.get("schedule", 0), j.get("rule", 0), j.get("alpha", 1.2)))
         S = np.empty(j["k"], np.int32)
         log = np.zeros((max_rounds, 16), np.float64)
         keep.append((S, log))

@@ -32,29 +32,34 @@ void *host_staging(cen_job *job, size_t bytes) {
 //   Rt = A + sqrt((4 w L)/(t m));   R = Rt + sqrt(Lm Lm + (2 L Rt)/m) + Lm
 //   eta = 2 R + sqrt((2 L (nu + 4 R))/m) + L/(3 m)
 //   stop <=> a ((a - eps) xi + eta) <= eps C
-static int bounds_fp64(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
-                       double delta, int32_t i, double *out) {
+// Thm. "bound_dev" from the sample's fractions C, A (AMCERA), w at sample
+// size md with L = ln(5 / delta_i); writes out[3..7] = nu, xi, R~, R, eta.
+static void bounds_from_fractions(double C, double A, double w, int32_t t, double md, double L, double *out) {
   const double a = 1.0 - exp(-1.0);
-  const double md = (double)m;
-  const double L = log(5.0 / ldexp(delta, -i));
   const double Lm = L / md;
-  const double C = (double)covered / md;
-  const double A = (double)Rsum / ((double)t * md);
-  const double w = ((double)b * (double)Wnum) / md;
   const double xi = sqrt(Lm * Lm + (2.0 * C * L) / (a * md)) + Lm;
   const double nu = C / a + xi;
   const double Rt = A + sqrt((4.0 * w * L) / ((double)t * md));
   const double R = Rt + sqrt(Lm * Lm + (2.0 * L * Rt) / md) + Lm;
   const double eta = 2.0 * R + sqrt((2.0 * L * (nu + 4.0 * R)) / md) + L / (3.0 * md);
-  out[0] = C;
-  out[1] = A;
-  out[2] = w;
   out[3] = nu;
   out[4] = xi;
   out[5] = Rt;
   out[6] = R;
   out[7] = eta;
-  return (a * ((a - eps) * xi + eta) <= eps * C) ? 1 : 0;
+}
+
+static int bounds_fp64(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
+                       double delta, int32_t i, double *out) {
+  const double a = 1.0 - exp(-1.0);
+  const double md = (double)m;
+  const double L = log(5.0 / ldexp(delta, -i));
+  const double C = (double)covered / md;
+  out[0] = C;
+  out[1] = (double)Rsum / ((double)t * md);
+  out[2] = ((double)b * (double)Wnum) / md;
+  bounds_from_fractions(C, out[1], out[2], t, md, L, out);
+  return (a * ((a - eps) * out[4] + out[7]) <= eps * C) ? 1 : 0;
 }
 
 // Sample-size schedule of Sec. 4.2.  The optimistic guess is the smallest m
@@ -75,15 +80,93 @@ static double schedule_guess(double C, double eps, double delta, int32_t i) {
 
 // m_i for round i.  Schedule 0 doubles from m0.  Schedule 1 grows by alpha
 // and jumps to the guess made from the previous round's coverage C_{i-1}
-// (C = 1 before the first round); it always grows by at least one sample.
+// (C = 1 before the first round).  Schedule 2 also jumps to m_pred (> 0), the
+// size at which round i's stopping test is predicted to pass (predict_m).
+// Every schedule grows by at least one sample.
 static uint64_t schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t m_prev, double C_prev,
-                              double eps, double delta, int32_t i) {
-  if (schedule == 0) return i == 1 ? m0 : 2 * m_prev;
+                              uint64_t m_pred, double eps, double delta, int32_t i) {
+  if (schedule == CEN_SCHEDULE_DOUBLING) return i == 1 ? m0 : 2 * m_prev;
   const double grow = i == 1 ? (double)m0 : ceil(alpha * (double)m_prev);
   const double guess = ceil(schedule_guess(i == 1 ? 1.0 : C_prev, eps, delta, i));
   double m = grow > guess ? grow : guess;
+  if (schedule == CEN_SCHEDULE_EXTRAPOLATE && i > 1 && m_pred > 0 && (double)m_pred > m) m = (double)m_pred;
   if (i > 1 && m <= (double)m_prev) m = (double)m_prev + 1.0;
   return m >= 18446744073709551615.0 ? UINT64_MAX : (uint64_t)m;
+}
+
+// HEDGE-P's SD bound (Sec. 6; HEDGE's union bound of Sec. 2).  For one set S
+// the coverage estimate is a mean of m i.i.d. 0/1 terms with variance
+// C(S)(1 - C(S)) <= min(C(S*), 1/4); a two-sided Bernstein tail at level
+// delta_i / n^k, union-bounded over the <= n^k sets of size <= k, gives every
+// set a deviation of at most lam(v) = b + sqrt(b^2 + 2 v L_U / m) with
+// L_U = k ln n + ln(2 / delta_i) and b = L_U / (3 m).  On that event
+// C(S*) <= C / (1 - 1/e) + lam(C(S*)) (greedy keeps 1 - 1/e of the sample
+// optimum), whose largest solution is nu_U; eta_U = lam(min(nu_U, 1/4)).
+// HEDGE's sufficient condition SD <= eps C(S*) / 2 then holds once
+// eta_U <= eps (C - eta_U) / 2, because C(S*) >= C(S) >= C - SD.
+static double hedge_L(int32_t n, int32_t k, double delta, int32_t i) {
+  return (double)k * log((double)n) + log(2.0 / ldexp(delta, -i));
+}
+
+// writes out[2] = nu_U, out[3] = eta_U for coverage fraction C at size md
+static void hedge_from_fraction(double C, double md, double LU, double *out) {
+  const double a = 1.0 - exp(-1.0);
+  const double Lm = LU / md;
+  const double b = LU / (3.0 * md);
+  const double c0 = C / a + b;
+  const double nu = c0 + Lm + sqrt(2.0 * c0 * Lm + Lm * Lm + b * b);  // larger root of (u - c0)^2 = b^2 + 2 u Lm
+  const double v = nu < 0.25 ? nu : 0.25;
+  out[2] = nu;
+  out[3] = b + sqrt(b * b + 2.0 * v * Lm);
+}
+
+static int bounds_hedge_fp64(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta,
+                             int32_t i, double *out) {
+  const double md = (double)m;
+  const double C = (double)covered / md;
+  out[0] = C;
+  out[1] = hedge_L(n, k, delta, i);
+  hedge_from_fraction(C, md, out[1], out);
+  return (out[3] <= eps * (C - out[3]) / 2.0) ? 1 : 0;
+}
+
+// Would round i's stopping test pass at size mp if the coverage fraction C
+// and the wimpy-variance fraction w stayed as measured at size m and the
+// AMCERA A shrank as 1/sqrt(m), the rate of both SD bounds (Sec. 6)?
+// (HEDGE-P keeps C only.)
+static bool predicted_stop(int32_t rule, double C, double A, double w, int32_t t, int32_t n, int32_t k, uint64_t m,
+                           uint64_t mp, double eps, double delta, int32_t i) {
+  const double a = 1.0 - exp(-1.0);
+  const double md = (double)mp;
+  double o[8];
+  if (rule == CEN_RULE_CENTRA) {
+    const double Ap = A * sqrt((double)m / md);
+    bounds_from_fractions(C, Ap, w, t, md, log(5.0 / ldexp(delta, -i)), o);
+    return a * ((a - eps) * o[4] + o[7]) <= eps * C;
+  }
+  hedge_from_fraction(C, md, hedge_L(n, k, delta, i), o);
+  return o[3] <= eps * (C - o[3]) / 2.0;
+}
+
+// Smallest mp > m with predicted_stop (doubling, then bisection), or 0 when
+// none up to 2^40 passes (the prediction is then not used).
+static uint64_t predict_m(int32_t rule, double C, double A, double w, int32_t t, int32_t n, int32_t k, uint64_t m,
+                          double eps, double delta, int32_t i) {
+  if (!(C > 0.0)) return 0;
+  uint64_t lo = m, hi = 2 * m;
+  while (!predicted_stop(rule, C, A, w, t, n, k, m, hi, eps, delta, i)) {
+    if (hi >= (1ull << 40)) return 0;
+    lo = hi;
+    hi *= 2;
+  }
+  while (hi - lo > 1) {
+    const uint64_t mid = lo + (hi - lo) / 2;
+    if (predicted_stop(rule, C, A, w, t, n, k, m, mid, eps, delta, i))
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return hi;
 }
 
 }  // namespace cen
@@ -266,27 +349,39 @@ int cen_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wn
 int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
             uint64_t m_cap, void *stream, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final,
             int32_t *rounds, double *log, int32_t max_rounds) {
-  return cen_run_sched(g, k, eps, delta, t, seed, m0, m_cap, CEN_SCHEDULE_DOUBLING, 2.0, stream, S_out, S_size,
-                       covered, m_final, rounds, log, max_rounds);
+  return cen_run_ex(g, k, eps, delta, t, seed, m0, m_cap, nullptr, stream, S_out, S_size, covered, m_final, rounds,
+                    log, max_rounds);
 }
 
-int cen_run_sched(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
-                  uint64_t m_cap, int32_t schedule, double alpha, void *stream, int32_t *S_out, int32_t *S_size,
-                  uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds) {
+int cen_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,
+                     double *out, int32_t *stop) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(out && stop && m >= 1 && n >= 2 && k >= 1 && i >= 1 && delta > 0 && delta < 1, CEN_EINVAL,
+              "cen_bounds_hedge: need m >= 1, n >= 2, k >= 1, i >= 1, 0 < delta < 1");
+  *stop = cen::bounds_hedge_fp64(covered, m, n, k, eps, delta, i, out);
+  CEN_API_END
+}
+
+int cen_run_ex(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
+               uint64_t m_cap, const cen_run_opts *opts, void *stream, int32_t *S_out, int32_t *S_size,
+               uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds) {
   cen_job *job = nullptr;
   int rc = CEN_OK;
   try {
     const double a = 1.0 - exp(-1.0);
+    const cen_run_opts o = opts ? *opts : cen_run_opts{CEN_SCHEDULE_DOUBLING, CEN_RULE_CENTRA, 0.0};
     CEN_REQUIRE(g && S_out && S_size && covered && m_final && rounds, CEN_EINVAL, "cen_run: null argument");
     CEN_REQUIRE(k >= 1 && t >= 1 && eps > 0.0 && eps < a && delta > 0.0 && delta < 1.0 && m0 >= 1 && m_cap >= m0,
                 CEN_EINVAL, "cen_run: need k >= 1, t >= 1, 0 < eps < 1-1/e, 0 < delta < 1, 1 <= m0 <= m_cap");
-    CEN_REQUIRE(schedule == CEN_SCHEDULE_DOUBLING || (schedule == CEN_SCHEDULE_PAPER && alpha > 1.0), CEN_EINVAL,
-                "cen_run: schedule must be doubling, or the paper's with alpha > 1");
+    CEN_REQUIRE(o.schedule >= CEN_SCHEDULE_DOUBLING && o.schedule <= CEN_SCHEDULE_EXTRAPOLATE &&
+                    (o.schedule == CEN_SCHEDULE_DOUBLING || o.alpha > 1.0),
+                CEN_EINVAL, "cen_run: unknown schedule, or alpha <= 1 for a growing schedule");
+    CEN_REQUIRE(o.rule == CEN_RULE_CENTRA || o.rule == CEN_RULE_HEDGE_P, CEN_EINVAL, "cen_run: unknown rule");
     int crc = cen_job_create(g, seed, t, stream, &job);
     if (crc) return crc;
     std::vector<int64_t> Rnum(t);
     uint64_t m_prev = 0;
-    uint64_t m_i = cen::schedule_next(schedule, alpha, m0, 0, 1.0, eps, delta, 1);
+    uint64_t m_i = cen::schedule_next(o.schedule, o.alpha, m0, 0, 1.0, 0, eps, delta, 1);
     if (m_i > m_cap) m_i = m_cap;  // a first guess beyond the cap runs one round at the cap
     rc = CEN_ENOTCERTIFIED;
     for (int32_t i = 1;; ++i) {
@@ -295,13 +390,21 @@ int cen_run_sched(const cen_graph *g, int32_t k, double eps, double delta, int32
       cen::sample_append(job, m_i - m_prev);
       uint64_t cov = 0;
       cen::greedy_cover(job, k, S_out, S_size, &cov);
-      int64_t Wnum = 0;
+      int64_t Wnum = 0, Rsum = 0;
       int32_t b = 0;
-      cen::mcera(job, k, Rnum.data(), &Wnum, &b);
-      int64_t Rsum = 0;
-      for (int q = 0; q < t; ++q) Rsum += Rnum[q];
-      double bd[8];
-      const int stop = cen::bounds_fp64(cov, m_i, Rsum, t, Wnum, b, eps, delta, i, bd);
+      double bd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      int stop;
+      if (o.rule == CEN_RULE_CENTRA) {
+        cen::mcera(job, k, Rnum.data(), &Wnum, &b);
+        for (int q = 0; q < t; ++q) Rsum += Rnum[q];
+        stop = cen::bounds_fp64(cov, m_i, Rsum, t, Wnum, b, eps, delta, i, bd);
+      } else {  // HEDGE-P needs no AMCERA; its C, nu_U, eta_U go to the C, nu, eta columns
+        double hb[4];
+        stop = cen::bounds_hedge_fp64(cov, m_i, g->n, k, eps, delta, i, hb);
+        bd[0] = hb[0];
+        bd[3] = hb[2];
+        bd[7] = hb[3];
+      }
       if (log && i <= max_rounds) {
         double *row = log + (size_t)(i - 1) * CEN_LOG_COLS;
         row[0] = i;
@@ -321,7 +424,11 @@ int cen_run_sched(const cen_graph *g, int32_t k, double eps, double delta, int32
         rc = CEN_OK;
         break;
       }
-      const uint64_t next = cen::schedule_next(schedule, alpha, m0, m_i, bd[0], eps, delta, i + 1);
+      const uint64_t m_pred =
+          o.schedule == CEN_SCHEDULE_EXTRAPOLATE
+              ? cen::predict_m(o.rule, bd[0], bd[1], bd[2], t, g->n, k, m_i, eps, delta, i + 1)
+              : 0;
+      const uint64_t next = cen::schedule_next(o.schedule, o.alpha, m0, m_i, bd[0], m_pred, eps, delta, i + 1);
       if (next > m_cap) {
         rc = CEN_ENOTCERTIFIED;
         cen::set_last_error("cen_run: not certified within m_cap samples");

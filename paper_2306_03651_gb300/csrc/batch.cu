@@ -41,9 +41,8 @@ extern "C" int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t n
         const cen_job_spec &sp = specs[i];
         cen_job_result &r = results[i];
         r.start_s = secs();
-        r.status = cen_run_sched(sp.graph, sp.k, sp.eps, sp.delta, sp.t, sp.seed, sp.m0, sp.m_cap, sp.schedule,
-                                 sp.alpha, st, r.S, &r.S_size, &r.covered, &r.m_final, &r.rounds, r.log,
-                                 r.log ? r.max_rounds : 0);
+        r.status = cen_run_ex(sp.graph, sp.k, sp.eps, sp.delta, sp.t, sp.seed, sp.m0, sp.m_cap, &sp.opts, st, r.S,
+                              &r.S_size, &r.covered, &r.m_final, &r.rounds, r.log, r.log ? r.max_rounds : 0);
         r.end_s = secs();
       }
       cudaStreamDestroy(st);

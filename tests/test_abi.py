@@ -54,6 +54,22 @@ def test_bounds_match_oracle_bit_for_bit():
             assert b1[k] == b2[k] or (math.isnan(b1[k]) and math.isnan(b2[k])), k
 
 
+def test_hedge_bounds_match_oracle_bit_for_bit():
+    rng = np.random.default_rng(4)
+    for _ in range(2000):
+        m = int(rng.integers(1, 10**9))
+        cov = int(rng.integers(0, m + 1))
+        n = int(rng.integers(2, 10**8))
+        k = int(rng.integers(1, 500))
+        eps = float(rng.uniform(1e-4, 0.6))
+        delta = float(rng.uniform(1e-6, 0.99))
+        i = int(rng.integers(1, 40))
+        assert P.bounds_hedge(cov, m, n, k, eps, delta, i) == O.bounds_hedge(cov, m, n, k, eps, delta, i)
+    out = np.zeros(4)
+    stop = ctypes.c_int32()
+    assert P.cen_bounds_hedge(10, 100, 1, 3, 0.1, 0.1, 1, out.ctypes.data, ctypes.byref(stop)) == P.EINVAL
+
+
 def test_null_handles_rejected():
     S = np.zeros(4, np.int32)
     size, cov = ctypes.c_int32(), ctypes.c_uint64()

@@ -210,10 +210,32 @@ def test_fixed_m_bounds_over_t_match_oracle():
         job.close()
 
 
-def test_paper_schedule_rejects_alpha_at_most_one():
-    with pytest.raises(P.CenError) as ei:
-        P.run(P.Graph.of(GRAPHS["ba300"]), 3, 0.1, 0.1, 4, 1, schedule=P.SCHEDULE_PAPER, alpha=1.0)
-    assert ei.value.rc == P.EINVAL
+@pytest.mark.parametrize("name,k,eps,t,schedule,rule", [
+    ("ba300", 5, 0.2, 10, 0, 1), ("ba300", 5, 0.2, 10, 1, 1), ("ba300", 5, 0.2, 10, 2, 0),
+    ("ba300", 5, 0.2, 10, 2, 1), ("rmat12_lcc", 10, 0.1, 25, 2, 0), ("rmat12_lcc", 10, 0.1, 25, 2, 1),
+    ("grid_rewired", 4, 0.15, 8, 2, 0)])
+def test_schedules_and_hedge_p_rule_match_oracle(name, k, eps, t, schedule, rule):
+    """HEDGE-P (union-bound SD, Sec. 6) and the predicting schedule: every round's
+    sample size and bounds, the picks and the status equal the oracle's."""
+    g = GRAPHS[name]
+    r = P.run(P.Graph.of(g), k, eps, 0.1, t, 5, m0=1000, schedule=schedule, alpha=1.2, rule=rule)
+    ro = O.Graph.of(g).run(k, eps, 0.1, t, 5, m0=1000, schedule=schedule, alpha=1.2, rule=rule)
+    assert r["status"] == ro["status"] == P.OK
+    assert r["S"].tolist() == ro["S"].tolist() and r["m_final"] == ro["m_final"]
+    assert np.array_equal(r["log"], ro["log"])
+    if schedule == 2 and rule == 1:
+        b = P.run_batch([dict(graph=P.Graph.of(g), k=k, eps=eps, delta=0.1, t=t, seed=5, m0=1000,
+                              schedule=schedule, alpha=1.2, rule=rule)], nworkers=1)[0]
+        assert np.array_equal(b["log"], ro["log"])
+
+
+def test_run_rejects_bad_options():
+    gg = P.Graph.of(GRAPHS["ba300"])
+    for kw in (dict(schedule=P.SCHEDULE_PAPER, alpha=1.0), dict(schedule=3), dict(rule=2),
+               dict(schedule=P.SCHEDULE_EXTRAPOLATE, alpha=0.5)):
+        with pytest.raises(P.CenError) as ei:
+            P.run(gg, 3, 0.1, 0.1, 4, 1, **kw)
+        assert ei.value.rc == P.EINVAL
 
 
 def test_run_argument_checks():

@@ -183,20 +183,30 @@ def test_paper_schedule_grows_geometrically_and_follows_the_guess():
 
 
 @pytest.mark.parametrize("rule", [0, 1])
-def test_extrapolating_schedule_reaches_the_stopping_threshold(rule):
-    """Schedule 2: the next size scales the last SD bound at the 1/sqrt(m) rate to the
-    largest eta that passes the stopping test (C and xi held at the last round's values)."""
+def test_predicting_schedule_targets_the_next_stopping_test(rule):
+    """Schedule 2: the next size is the smallest at which the next round's stopping test
+    passes when C and w hold and the AMCERA shrinks as 1/sqrt(m); checked by re-evaluating
+    the oracle's own bounds just above and just below the predicted size, with the sums scaled."""
     g = O.Graph.of(I.rmat(10, 8, seed=2))
-    eps, delta, k = 0.1, 0.1, 8
-    r = g.run(k=k, eps=eps, delta=delta, t=20, seed=4, m0=1000, schedule=2, alpha=1.2, rule=rule)
-    p = g.run(k=k, eps=eps, delta=delta, t=20, seed=4, m0=1000, schedule=1, alpha=1.2, rule=rule)
+    eps, delta, k, t = 0.1, 0.1, 8, 20
+    r = g.run(k=k, eps=eps, delta=delta, t=t, seed=4, m0=1000, schedule=2, alpha=1.2, rule=rule)
+    p = g.run(k=k, eps=eps, delta=delta, t=t, seed=4, m0=1000, schedule=1, alpha=1.2, rule=rule)
     assert r["status"] == p["status"] == O.OK
-    ms = [int(row[1]) for row in r["log"]]
-    for i, (row, nxt) in enumerate(zip(r["log"], ms[1:]), start=1):
-        C, xi, eta, m = row[6], row[10], row[13], row[1]
-        target = eps * C / A - (A - eps) * xi if rule == 0 else eps * C / (2 + eps)
-        # at the next size, eta * sqrt(m / next) would meet the threshold (up to the ceil and the max)
-        assert nxt >= m * (eta / target) ** 2 - 1e-6 * m
-        assert nxt == max(math.ceil(1.2 * m), math.ceil(O.schedule_guess(C, eps, delta, i + 1)),
-                          math.ceil(m * (eta / target) ** 2))
     assert len(r["log"]) < len(p["log"])
+    ms = [int(row[1]) for row in r["log"]]
+
+    def passes(row, mp, i):
+        m, C = row[1], row[6]
+        if rule == 1:
+            return O.bounds_hedge(round(C * mp), mp, g.n, k, eps, delta, i)[0]
+        # integer sums whose fractions are C, A sqrt(m/mp), w at size mp (b = 1 carries w)
+        Rsum = round(row[7] * math.sqrt(m / mp) * t * mp)
+        return O.bounds(round(C * mp), mp, Rsum, t, round(row[8] * mp), 1, eps, delta, i)[0]
+
+    predicted = 0
+    for i, (row, nxt) in enumerate(zip(r["log"], ms[1:]), start=1):
+        floor = max(math.ceil(1.2 * row[1]), math.ceil(O.schedule_guess(row[6], eps, delta, i + 1)))
+        predicted += nxt > floor
+        if nxt > floor:  # the prediction decided: it passes there and not earlier (rounding the sums aside)
+            assert passes(row, math.ceil(nxt * 1.001), i + 1) and not passes(row, math.floor(nxt * 0.999), i + 1)
+    assert predicted >= 1 and all(b > a for a, b in zip(ms, ms[1:]))
