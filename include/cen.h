@@ -229,7 +229,19 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
 #define CEN_PARAM_WAVE_STREAMS 2 /* waves of one cen_sample call in flight, 1..8 (default 4) */
 #define CEN_PARAM_PUSH_RATIO 3   /* expand top-down while frontier out-arcs * ratio < arcs (default 4) */
 #define CEN_PARAM_LEVEL_BUDGET 4 /* max bytes of one per-level bit array [n][wave words] (default 2^30) */
+#define CEN_PARAM_SAMPLER 5      /* 0: balanced bidirectional search, one CTA per sample, with the
+                                    bit-parallel sampler for what exceeds its per-CTA limits (default);
+                                    1: bit-parallel waves only.  Hyper-edges are identical. */
+#define CEN_PARAM_BIDIR_BUDGET 6 /* device bytes for the bidirectional sampler's per-CTA workspace,
+                                    >= 2^20 (default 2^32); fewer CTAs run when it is small */
+#define CEN_PARAM_BIDIR_QUEUE 7  /* nodes one CTA may hold per ball or cone side, 16 .. 2^27 (default
+                                    2^18, at most n); larger searches go to the bit-parallel sampler */
 int cen_job_set_param(cen_job *job, int32_t param, double value);
+/* How the job's samples were drawn so far: samples the bidirectional search
+ * left whole to the bit-parallel sampler (*deferred_search), samples whose walk
+ * it left to it (*deferred_walk), and the CTAs (slots) the bidirectional search
+ * runs on (0 before its first use).  Any pointer may be NULL. */
+int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, int32_t *slots);
 /* Defaults for jobs created later on this graph (cen_job_create, cen_run, cen_run_batch);
  * they take precedence over the environment (CEN_WAVE_WORDS, CEN_WAVE_STREAMS). */
 int cen_graph_set_param(cen_graph *g, int32_t param, double value);
@@ -244,7 +256,7 @@ int cen_debug_fail_alloc(int64_t n);
 /* Per-kernel-class launch counts, device time and work units since the job
  * was created (or last reset).  Device time is recorded only while
  * timing is enabled (CUDA events around each launch on the job stream). */
-#define CEN_NKCLASS 16
+#define CEN_NKCLASS 24
 typedef struct cen_kstat {
   char name[32];
   uint64_t launches;

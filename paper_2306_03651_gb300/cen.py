@@ -22,10 +22,12 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 PARAM_WAVE_WORDS, PARAM_WAVE_STREAMS, PARAM_PUSH_RATIO, PARAM_LEVEL_BUDGET = 1, 2, 3, 4
+PARAM_SAMPLER, PARAM_BIDIR_BUDGET, PARAM_BIDIR_QUEUE = 5, 6, 7
+SAMPLER_BIDIR, SAMPLER_WAVES = 0, 1
 SCHEDULE_DOUBLING, SCHEDULE_PAPER, SCHEDULE_EXTRAPOLATE = 0, 1, 2
 RULE_CENTRA, RULE_HEDGE_P = 0, 1
 LOG_COLS = ("i", "m", "covered", "Rsum", "Wnum", "b", "C", "A", "w", "nu", "xi", "Rt", "R", "eta", "stop", "S_size")
-NKCLASS = 16
+NKCLASS = 24
 
 
 class CenError(RuntimeError):
@@ -89,6 +91,7 @@ def _load():
         "cen_job_copy_signs": ([vp, vp], ip),
         "cen_job_set_timing": ([vp, ip], ip),
         "cen_job_stats": ([vp, vp, vp], ip),
+        "cen_job_sampler_info": ([vp, vp, vp, vp], ip),
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
         "cen_run_batch": ([vp, i32, i32, vp], ip),
@@ -277,6 +280,13 @@ class Job:
 
     def reset_stats(self):
         _check(_lib.cen_job_reset_stats(self.h), "cen_job_reset_stats")
+
+    def sampler_info(self) -> dict:
+        """``cen_job_sampler_info``: deferred_search, deferred_walk, slots."""
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32()
+        _check(_lib.cen_job_sampler_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "cen_job_sampler_info")
+        return dict(deferred_search=a.value, deferred_walk=b.value, slots=c.value)
 
     def stats(self) -> dict:
         arr = (cen_kstat * NKCLASS)()

@@ -191,6 +191,19 @@ static void apply_param(cen_job *job, int32_t param, double value) {
       CEN_REQUIRE(value >= (1 << 20), CEN_EINVAL, "cen_job_set_param: level budget must be >= 1 MiB");
       job->level_budget = (size_t)value;
       break;
+    case CEN_PARAM_SAMPLER:
+      CEN_REQUIRE(value == 0 || value == 1, CEN_EINVAL, "cen_job_set_param: sampler must be 0 or 1");
+      job->sampler = (int)value;
+      break;
+    case CEN_PARAM_BIDIR_BUDGET:
+      CEN_REQUIRE(value >= (1 << 20), CEN_EINVAL, "cen_job_set_param: bidirectional budget must be >= 1 MiB");
+      job->bidir_budget = (size_t)value;
+      break;
+    case CEN_PARAM_BIDIR_QUEUE:
+      CEN_REQUIRE(value >= 16 && value <= (double)(1 << 27), CEN_EINVAL,
+                  "cen_job_set_param: bidirectional queue must be in [16, 2^27]");
+      job->bidir_queue = (int64_t)value;
+      break;
     default:
       cen::fail(CEN_EINVAL, "cen_job_set_param: unknown parameter");
   }
@@ -279,7 +292,7 @@ int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, c
     const int w = atoi(e);
     if (w >= 1 && w <= 8) job->wave_streams = w;
   }
-  for (int p = 1; p <= 4; ++p)  // the graph's tuned defaults override the environment
+  for (int p = 1; p <= 7; ++p)  // the graph's tuned defaults override the environment
     if (g->param[p] != 0) apply_param(job, p, g->param[p]);
   try {
     job->stats.init(job->st);
@@ -529,10 +542,19 @@ int cen_job_set_param(cen_job *job, int32_t param, double value) {
   CEN_API_END
 }
 
+int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, int32_t *slots) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_job_sampler_info: null job");
+  if (deferred_search) *deferred_search = job->bidir_deferred_search;
+  if (deferred_walk) *deferred_walk = job->bidir_deferred_walk;
+  if (slots) *slots = job->bws ? job->bws->nslots : 0;
+  CEN_API_END
+}
+
 int cen_graph_set_param(cen_graph *g, int32_t param, double value) {
   CEN_API_BEGIN
   CEN_REQUIRE(g, CEN_EINVAL, "cen_graph_set_param: null graph");
-  CEN_REQUIRE(param >= 1 && param <= 4, CEN_EINVAL, "cen_graph_set_param: unknown parameter");
+  CEN_REQUIRE(param >= 1 && param <= 7, CEN_EINVAL, "cen_graph_set_param: unknown parameter");
   cen_job probe;  // validates the value with the job rules
   apply_param(&probe, param, value);
   g->param[param] = value;

@@ -1,0 +1,541 @@
+// Balanced bidirectional sampler for set betweenness (Sec. 5 sampleHEs).
+//
+// One CTA handles one sample at a time; resident CTAs ("slots") take sample
+// ids from a counter.  For the pair (s, t) a forward ball grows from s over
+// out-arcs and a backward ball from t over in-arcs, one level at a time,
+// always on the side whose frontier has fewer arcs to scan (Sec. 5: the
+// balanced bidirectional BFS).  The first level that touches the other ball
+// fixes d(s, t) = ls + lb + 1, where ls and lb are the two frontier levels,
+// and every shortest path crosses exactly one arc from the forward frontier
+// into the backward frontier.
+//
+// The hyper-edge equals the one the forward sampler draws for the same
+// sample: the cone (nodes on some shortest s-t path) is cut from the crossing
+// arcs down both balls; the path counts sigma_s (shortest s -> v paths) are
+// taken over the cone in order of distance from s, through the crossing arcs
+// into the backward ball; and the backward walk from t draws the same Philox
+// numbers and scans in-neighbours in the same ascending order.  A node one
+// step closer to s than a cone node, with an arc into it, is itself a cone
+// node, so these counts equal a full BFS's wherever the walk reads them, and
+// which side grew when changes only the cost.
+//
+// Work the per-CTA resources cannot hold is left to the bit-parallel
+// sampler, which gives the identical hyper-edge: more than kBiMaxLevels
+// levels on one side or more than QC nodes in one ball ("search" deferral,
+// distance unknown); a cone side larger than QC, a path count reaching 2^64,
+// or a full member arena ("walk" deferral, distance known).
+#include <algorithm>
+
+#include "job.cuh"
+
+namespace cen {
+
+namespace {
+
+constexpr int kBiThreads = 256;
+constexpr int kBiWarps = kBiThreads / 32;
+constexpr int kBiMaxLevels = 1024;  // levels per side (0 .. kBiMaxLevels - 1)
+constexpr int kBiHeavy = 256;       // rows longer than this are scanned by the whole block
+constexpr uint32_t kBiEpochMax = (1u << 20) - 1;
+
+// State word of one (slot, node): epoch 20 | cone index 28 | cone 1 | side 1 | level 14.
+// A word whose epoch differs from the slot's current one is unvisited.
+constexpr uint64_t kConeBit = 1ull << 15;
+__device__ __forceinline__ uint32_t st_epoch(uint64_t s) { return (uint32_t)(s >> 44); }
+__device__ __forceinline__ int st_level(uint64_t s) { return (int)(s & 0x3FFFu); }
+__device__ __forceinline__ int st_side(uint64_t s) { return (int)((s >> 14) & 1u); }
+__device__ __forceinline__ bool st_cone(uint64_t s) { return (s & kConeBit) != 0; }
+__device__ __forceinline__ int64_t st_cidx(uint64_t s) { return (int64_t)((s >> 16) & 0xFFFFFFFull); }
+__device__ __forceinline__ uint64_t st_make(uint32_t epoch, int side, int level) {
+  return ((uint64_t)epoch << 44) | ((uint64_t)side << 14) | (uint64_t)level;
+}
+
+struct BiShared {
+  int lo[2][kBiMaxLevels + 1];  // ball queue of side x: level L is lo[x][L] .. lo[x][L+1]
+  int cs[2][kBiMaxLevels];      // cone list of side x: level L is cs[x][L] .. ce[x][L]
+  int ce[2][kBiMaxLevels];
+  unsigned long long cost[2];   // arcs out of each side's frontier (out-arcs forward, in-arcs backward)
+  unsigned long long addcost;
+  unsigned long long red[kBiWarps];
+  int redovf;
+  int added, nheavy, ccount[2];
+  int lvl[2];
+  int met, ovf;
+  int status, d;
+  int s, t;
+  uint32_t epoch;
+  int clear;
+  unsigned long long j;
+  long long abase;
+  unsigned long long arcs;
+};
+
+// Sets the cone bit of w and, the first time, appends w to the cone list of
+// side x and stores its cone index (x QC + position) in the state word.
+__device__ __forceinline__ void bi_mark(uint64_t *state, uint32_t *clist, int x, int64_t QC, BiShared &sh, int w) {
+  const unsigned long long old = atomicOr((unsigned long long *)&state[w], (unsigned long long)kConeBit);
+  if (old & kConeBit) return;
+  const int pos = atomicAdd(&sh.ccount[x], 1);
+  if (pos >= QC) {
+    sh.ovf = 1;
+    return;
+  }
+  clist[pos] = (uint32_t)w;
+  atomicOr((unsigned long long *)&state[w], (unsigned long long)((int64_t)x * QC + pos) << 16);
+}
+
+// Group size for a list of cnt rows with `arcs` arcs in all: the power of two
+// near the mean row length, 1 .. 32.
+__device__ __forceinline__ int bi_group(unsigned long long arcs, int cnt) {
+  const unsigned long long mean = cnt ? (arcs + cnt - 1) / (unsigned long long)cnt : 1;
+  int gs = 1;
+  while (gs < 32 && (unsigned long long)gs < mean) gs <<= 1;
+  return gs;
+}
+
+// For every node v of list[0, cnt) and every arc of v's row in (o, c), calls
+// f(v, w).  Rows of at most kBiHeavy arcs are scanned by a group of gs lanes;
+// longer rows are queued in `heavy` and scanned by the whole block.  With
+// use_stop, a raised sh.met ends the scan early.  Called by all threads.
+template <class F>
+__device__ void bi_scan_rows(const uint32_t *list, int cnt, const int64_t *__restrict__ o,
+                             const int32_t *__restrict__ c, int gs, uint32_t *heavy, BiShared &sh, bool use_stop,
+                             F &&f) {
+  const int tid = threadIdx.x;
+  if (tid == 0) sh.nheavy = 0;
+  __syncthreads();
+  const int gl = tid & (gs - 1), gi = tid / gs, ng = kBiThreads / gs;
+  unsigned long long arcs = 0;
+  for (int i = gi; i < cnt; i += ng) {
+    if (use_stop && *(volatile int *)&sh.met) break;
+    const int v = (int)list[i];
+    const int64_t e0 = o[v], e1 = o[v + 1];
+    if (e1 - e0 > kBiHeavy) {
+      if (gl == 0) heavy[atomicAdd(&sh.nheavy, 1)] = (uint32_t)v;
+      continue;
+    }
+    for (int64_t e = e0 + gl; e < e1; e += gs) f(v, c[e]);
+    if (gl == 0) arcs += (unsigned long long)(e1 - e0);
+  }
+  __syncthreads();
+  const int nh = sh.nheavy;
+  for (int h = 0; h < nh; ++h) {
+    if (use_stop && *(volatile int *)&sh.met) break;
+    const int v = (int)heavy[h];
+    const int64_t e0 = o[v], e1 = o[v + 1];
+    for (int64_t e = e0 + tid; e < e1; e += kBiThreads) f(v, c[e]);
+    if (tid == 0) arcs += (unsigned long long)(e1 - e0);
+  }
+  if (arcs) atomicAdd(&sh.arcs, arcs);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void add_carry(unsigned long long &acc, unsigned long long v, int &ovf) {
+  acc += v;
+  ovf |= acc < v;
+}
+
+// Path counts of the cone nodes list[0, cnt), all at distance D from s: each
+// is the sum of the counts of its in-neighbours that are cone nodes at D - 1
+// (D of a node: its level in the forward ball, d minus its level in the
+// backward ball).  A sum that wraps 2^64 raises sh.ovf.
+__device__ void bi_sigma_level(const uint32_t *list, int cnt, int D, int d, uint32_t epoch,
+                               const uint64_t *__restrict__ state, uint64_t *sg, const int64_t *__restrict__ roff,
+                               const int32_t *__restrict__ rcol, int gs, uint32_t *heavy, BiShared &sh) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) sh.nheavy = 0;
+  __syncthreads();
+  const int gl = tid & (gs - 1), gi = tid / gs, ng = kBiThreads / gs;
+  const unsigned gmask = gs == 32 ? 0xffffffffu : (((1u << gs) - 1u) << (lane & ~(gs - 1)));
+  int ovf = 0;
+  unsigned long long arcs = 0;
+  for (int i = gi; i < cnt; i += ng) {
+    const int v = (int)list[i];
+    const int64_t e0 = roff[v], e1 = roff[v + 1];
+    if (e1 - e0 > kBiHeavy) {
+      if (gl == 0) heavy[atomicAdd(&sh.nheavy, 1)] = (uint32_t)v;
+      continue;
+    }
+    unsigned long long acc = 0;
+    for (int64_t e = e0 + gl; e < e1; e += gs) {
+      const uint64_t su = state[rcol[e]];
+      if (st_epoch(su) == epoch && st_cone(su) && (st_side(su) ? d - st_level(su) : st_level(su)) == D - 1)
+        add_carry(acc, sg[st_cidx(su)], ovf);
+    }
+    for (int o2 = gs >> 1; o2; o2 >>= 1) add_carry(acc, __shfl_xor_sync(gmask, acc, o2, gs), ovf);
+    if (gl == 0) {
+      sg[st_cidx(state[v])] = acc;
+      arcs += (unsigned long long)(e1 - e0);
+    }
+  }
+  if (ovf) sh.ovf = 1;
+  __syncthreads();
+  const int nh = sh.nheavy;
+  for (int h = 0; h < nh; ++h) {
+    const int v = (int)heavy[h];
+    const int64_t e0 = roff[v], e1 = roff[v + 1];
+    unsigned long long acc = 0;
+    int hovf = 0;
+    for (int64_t e = e0 + tid; e < e1; e += kBiThreads) {
+      const uint64_t su = state[rcol[e]];
+      if (st_epoch(su) == epoch && st_cone(su) && (st_side(su) ? d - st_level(su) : st_level(su)) == D - 1)
+        add_carry(acc, sg[st_cidx(su)], hovf);
+    }
+    for (int o2 = 16; o2; o2 >>= 1) add_carry(acc, __shfl_xor_sync(0xffffffffu, acc, o2), hovf);
+    if (lane == 0) sh.red[tid >> 5] = acc;
+    if (hovf) sh.ovf = 1;
+    __syncthreads();
+    if (tid == 0) {
+      unsigned long long tot = 0;
+      int tovf = 0;
+      for (int w = 0; w < kBiWarps; ++w) add_carry(tot, sh.red[w], tovf);
+      if (tovf) sh.ovf = 1;
+      sg[st_cidx(state[v])] = tot;
+      arcs += (unsigned long long)(e1 - e0);
+    }
+    __syncthreads();
+  }
+  if (arcs) atomicAdd(&sh.arcs, arcs);
+  __syncthreads();
+}
+
+}  // namespace
+
+struct BiArgs {
+  int32_t n;
+  const int64_t *off, *roff;
+  const int32_t *col, *rcol;
+  uint64_t seed, j0, count;
+  uint64_t *state;    // [slots][n]
+  uint32_t *lists;    // [slots][5][QC]: ball queues (forward, backward), cone lists (same), heavy rows
+  uint64_t *sig;      // [slots][2 QC]: path counts by cone index
+  uint32_t *epochs;   // [slots]
+  int64_t QC;
+  int32_t *ps, *pt, *pd;
+  int *bmax;
+  int32_t *arena;
+  int64_t arena_cap;
+  int64_t *aoff;      // [count]: first member in the arena, or -1
+  uint64_t *dsearch;  // [count]: search-deferred sample ids
+  uint64_t *dwalk;    // [count]: walk-deferred sample ids
+  BiCtl *ctl;
+  unsigned long long *units;
+};
+
+__global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
+  __shared__ BiShared sh;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t QC = A.QC;
+  uint64_t *state = A.state + (size_t)blockIdx.x * (size_t)A.n;
+  uint32_t *q[2] = {A.lists + ((size_t)blockIdx.x * 5 + 0) * (size_t)QC,
+                    A.lists + ((size_t)blockIdx.x * 5 + 1) * (size_t)QC};
+  uint32_t *cl[2] = {A.lists + ((size_t)blockIdx.x * 5 + 2) * (size_t)QC,
+                     A.lists + ((size_t)blockIdx.x * 5 + 3) * (size_t)QC};
+  uint32_t *heavy = A.lists + ((size_t)blockIdx.x * 5 + 4) * (size_t)QC;
+  uint64_t *sg = A.sig + (size_t)blockIdx.x * 2 * (size_t)QC;
+  const int64_t *csr_o[2] = {A.off, A.roff};  // side 0 grows over out-arcs, side 1 over in-arcs
+  const int32_t *csr_c[2] = {A.col, A.rcol};
+  if (tid == 0) sh.arcs = 0;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      sh.j = atomicAdd(&A.ctl->next, 1ull);
+      uint32_t e = A.epochs[blockIdx.x] + 1;
+      sh.clear = e > kBiEpochMax;
+      if (sh.clear) e = 1;
+      A.epochs[blockIdx.x] = e;
+      sh.epoch = e;
+    }
+    __syncthreads();
+    if (sh.j >= A.count) break;
+    if (sh.clear) {  // the epoch field wrapped: this slot's words start over
+      for (int64_t v = tid; v < A.n; v += kBiThreads) state[v] = 0;
+      __syncthreads();
+    }
+    const uint64_t j = A.j0 + sh.j;
+    const uint32_t epoch = sh.epoch;
+    if (tid == 0) {
+      // Sec. 5: s uniform over V; t uniform over V \ {s} (Sec. 3.1 pairs u != v)
+      const int32_t s = (int32_t)uniform_below64(A.seed, j, kPurposeS, (uint64_t)A.n);
+      const int32_t tt = (int32_t)uniform_below64(A.seed, j, kPurposeT, (uint64_t)(A.n - 1));
+      const int32_t t = tt + (tt >= s);
+      A.ps[j] = s;
+      A.pt[j] = t;
+      sh.s = s;
+      sh.t = t;
+      state[s] = st_make(epoch, 0, 0);
+      state[t] = st_make(epoch, 1, 0);
+      q[0][0] = (uint32_t)s;
+      q[1][0] = (uint32_t)t;
+      sh.lo[0][0] = 0;
+      sh.lo[0][1] = 1;
+      sh.lo[1][0] = 0;
+      sh.lo[1][1] = 1;
+      sh.lvl[0] = sh.lvl[1] = 0;
+      sh.cost[0] = (unsigned long long)(A.off[s + 1] - A.off[s]);
+      sh.cost[1] = (unsigned long long)(A.roff[t + 1] - A.roff[t]);
+      sh.met = 0;
+      sh.ovf = 0;
+      sh.status = 0;
+      sh.d = -1;
+    }
+    __syncthreads();
+
+    // ---- discovery: grow the cheaper side until the balls touch
+    for (;;) {
+      const int x = sh.cost[0] <= sh.cost[1] ? 0 : 1;
+      const int L = sh.lvl[x];
+      if (L + 1 >= kBiMaxLevels) {
+        if (tid == 0) sh.status = 1;
+        break;
+      }
+      const int f0 = sh.lo[x][L], f1 = sh.lo[x][L + 1];
+      const unsigned long long fcost = sh.cost[x];
+      __syncthreads();
+      if (tid == 0) {
+        sh.added = 0;
+        sh.addcost = 0;
+      }
+      __syncthreads();
+      uint32_t *qx = q[x];
+      const int64_t *o = csr_o[x];
+      const int32_t *c = csr_c[x];
+      const uint64_t mine = st_make(epoch, x, L + 1);
+      bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, true, [&](int, int w) {
+        const uint64_t sw = *(volatile uint64_t *)&state[w];
+        if (st_epoch(sw) == epoch) {
+          if (st_side(sw) != x) sh.met = 1;
+          return;
+        }
+        const unsigned long long old =
+            atomicCAS((unsigned long long *)&state[w], (unsigned long long)sw, (unsigned long long)mine);
+        if (old == sw) {
+          const int pos = atomicAdd(&sh.added, 1);
+          if ((int64_t)f1 + pos < QC)
+            qx[f1 + pos] = (uint32_t)w;
+          else
+            sh.ovf = 1;
+          atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
+        } else if (st_epoch(old) == epoch && st_side(old) != x) {
+          sh.met = 1;
+        }
+      });
+      if (sh.met) {
+        if (tid == 0) sh.d = sh.lvl[0] + sh.lvl[1] + 1;
+        break;
+      }
+      if (sh.ovf) {
+        if (tid == 0) sh.status = 1;
+        break;
+      }
+      if (sh.added == 0) break;  // this side's ball is closed: t is unreachable
+      __syncthreads();
+      if (tid == 0) {
+        sh.lo[x][L + 2] = f1 + sh.added;
+        sh.lvl[x] = L + 1;
+        sh.cost[x] = sh.addcost;
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    const int d = sh.d;
+    const uint64_t jr = sh.j;
+    if (sh.status == 1) {  // distance unknown: the bit-parallel sampler takes the whole sample
+      if (tid == 0) {
+        A.pd[j] = -1;
+        A.aoff[jr] = -1;
+        A.dsearch[atomicAdd(&A.ctl->nsearch, 1ull)] = j;
+      }
+      continue;
+    }
+    if (tid == 0) {
+      A.pd[j] = d;
+      A.aoff[jr] = -1;
+      if (d >= 2) {
+        atomicMax(A.bmax, d - 1);
+        const unsigned long long base = atomicAdd(&A.ctl->cursor, (unsigned long long)(d - 1));
+        if ((long long)(base + (unsigned long long)(d - 1)) > A.arena_cap)
+          sh.status = 2;
+        else
+          sh.abase = (long long)base;
+      }
+      sh.ccount[0] = sh.ccount[1] = 0;
+      sh.ovf = 0;
+    }
+    __syncthreads();
+    if (d < 2) continue;  // adjacent or unreachable: the empty hyper-edge
+
+    const int ls = sh.lvl[0], lb = sh.lvl[1];
+    if (sh.status == 0) {
+      // ---- crossing arcs: forward frontier (level ls) -> backward frontier (level lb)
+      if (sh.cost[0] <= sh.cost[1]) {
+        const int f0 = sh.lo[0][ls], f1 = sh.lo[0][ls + 1];
+        bi_scan_rows(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.cost[0], f1 - f0), heavy, sh, false,
+                     [&](int v, int w) {
+                       const uint64_t sw = state[w];
+                       if (st_epoch(sw) == epoch && st_side(sw) == 1 && st_level(sw) == lb) {
+                         bi_mark(state, cl[0], 0, QC, sh, v);
+                         bi_mark(state, cl[1], 1, QC, sh, w);
+                       }
+                     });
+      } else {
+        const int f0 = sh.lo[1][lb], f1 = sh.lo[1][lb + 1];
+        bi_scan_rows(q[1] + f0, f1 - f0, A.roff, A.rcol, bi_group(sh.cost[1], f1 - f0), heavy, sh, false,
+                     [&](int x, int u) {
+                       const uint64_t su = state[u];
+                       if (st_epoch(su) == epoch && st_side(su) == 0 && st_level(su) == ls) {
+                         bi_mark(state, cl[0], 0, QC, sh, u);
+                         bi_mark(state, cl[1], 1, QC, sh, x);
+                       }
+                     });
+      }
+      if (tid == 0) {
+        sh.cs[0][ls] = 0;
+        sh.ce[0][ls] = min(sh.ccount[0], (int)QC);
+        sh.cs[1][lb] = 0;
+        sh.ce[1][lb] = min(sh.ccount[1], (int)QC);
+      }
+      __syncthreads();
+      // ---- cone, forward ball: in-neighbours one level down
+      for (int L = ls; L >= 1 && !sh.ovf; --L) {
+        const int a = sh.cs[0][L], b = sh.ce[0][L];
+        bi_scan_rows(cl[0] + a, b - a, A.roff, A.rcol, 8, heavy, sh, false, [&](int, int u) {
+          const uint64_t su = state[u];
+          if (st_epoch(su) == epoch && st_side(su) == 0 && st_level(su) == L - 1) bi_mark(state, cl[0], 0, QC, sh, u);
+        });
+        if (tid == 0) {
+          sh.cs[0][L - 1] = b;
+          sh.ce[0][L - 1] = min(sh.ccount[0], (int)QC);
+        }
+        __syncthreads();
+      }
+      // ---- cone, backward ball: out-neighbours one level down (towards t)
+      for (int L = lb; L >= 1 && !sh.ovf; --L) {
+        const int a = sh.cs[1][L], b = sh.ce[1][L];
+        bi_scan_rows(cl[1] + a, b - a, A.off, A.col, 8, heavy, sh, false, [&](int, int y) {
+          const uint64_t sy = state[y];
+          if (st_epoch(sy) == epoch && st_side(sy) == 1 && st_level(sy) == L - 1) bi_mark(state, cl[1], 1, QC, sh, y);
+        });
+        if (tid == 0) {
+          sh.cs[1][L - 1] = b;
+          sh.ce[1][L - 1] = min(sh.ccount[1], (int)QC);
+        }
+        __syncthreads();
+      }
+      if (sh.ovf) {
+        __syncthreads();
+        if (tid == 0) sh.status = 2;
+      }
+      __syncthreads();
+    }
+    if (sh.status == 0) {
+      // ---- path counts over the cone, by distance from s
+      if (tid == 0) sg[st_cidx(state[sh.s])] = 1;
+      __syncthreads();
+      for (int D = 1; D <= d && !sh.ovf; ++D) {
+        const int x = D <= ls ? 0 : 1;
+        const int L = x ? d - D : D;
+        const int a = sh.cs[x][L], b = sh.ce[x][L];
+        bi_sigma_level(cl[x] + a, b - a, D, d, epoch, state, sg, A.roff, A.rcol, 8, heavy, sh);
+      }
+      __syncthreads();
+      if (sh.ovf && tid == 0) sh.status = 2;
+      __syncthreads();
+    }
+    if (sh.status == 0) {
+      // ---- backward walk from t (warp 0), the forward sampler's rule
+      if (tid < 32) {
+        int32_t v = sh.t;
+        uint64_t sv = sg[st_cidx(state[v])];
+        int32_t *out = A.arena + sh.abase;
+        uint32_t step = 0;
+        unsigned long long scanned = 0;
+        for (int L = d; L >= 2; --L, ++step) {
+          const uint64_t r = uniform_below64(A.seed, j, kPurposeWalk0 + step, sv);
+          uint64_t cum = 0;
+          int32_t pick = -1;
+          uint64_t pick_sig = 0;
+          const int64_t e0 = A.roff[v], e1 = A.roff[v + 1];
+          for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
+            const int64_t i = base + lane;
+            const int32_t u = i < e1 ? A.rcol[i] : -1;
+            uint64_t val = 0;
+            if (u >= 0) {
+              const uint64_t su = state[u];
+              if (st_epoch(su) == epoch && st_cone(su) && (st_side(su) ? d - st_level(su) : st_level(su)) == L - 1)
+                val = sg[st_cidx(su)];
+            }
+            uint64_t pre = val;
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+              const uint64_t y = __shfl_up_sync(0xffffffffu, pre, o2);
+              if (lane >= o2) pre += y;
+            }
+            const unsigned hit = __ballot_sync(0xffffffffu, val != 0 && cum + pre > r);
+            if (hit) {
+              const int src = __ffs(hit) - 1;
+              pick = __shfl_sync(0xffffffffu, u, src);
+              pick_sig = __shfl_sync(0xffffffffu, val, src);
+            } else {
+              cum += __shfl_sync(0xffffffffu, pre, 31);
+            }
+            scanned += 32;
+          }
+          if (pick < 0) {  // cannot happen with consistent counts
+            if (lane == 0) atomicExch(&A.ctl->err, CEN_EINVAL);
+            break;
+          }
+          if (lane == 0) out[L - 2] = pick;
+          v = pick;
+          sv = pick_sig;
+        }
+        if (lane == 0) {
+          A.aoff[jr] = sh.abase;
+          if (scanned) atomicAdd(&sh.arcs, scanned);
+        }
+      }
+    } else if (tid == 0) {
+      A.dwalk[atomicAdd(&A.ctl->nwalk, 1ull)] = j;
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && sh.arcs) atomicAdd(A.units, sh.arcs * 12ull);
+}
+
+// ------------------------------------------------------------------ host
+int bidir_resident_slots() { return resident_grid((const void *)k_bidir, kBiThreads); }
+
+void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap) {
+  const cen_graph *g = job->g;
+  BiWS &w = *job->bws;
+  cudaStream_t st = job->st;
+  CEN_CK(cudaMemsetAsync(w.ctl.p, 0, sizeof(BiCtl), st));
+  BiArgs a;
+  a.n = g->n;
+  a.off = g->off.as<int64_t>();
+  a.col = g->col.as<int32_t>();
+  a.roff = g->in_off();
+  a.rcol = g->in_col();
+  a.seed = job->seed;
+  a.j0 = j0;
+  a.count = count;
+  a.state = w.state.as<uint64_t>();
+  a.lists = w.lists.as<uint32_t>();
+  a.sig = w.sig.as<uint64_t>();
+  a.epochs = w.epochs.as<uint32_t>();
+  a.QC = w.QC;
+  a.ps = job->ps.as<int32_t>();
+  a.pt = job->pt.as<int32_t>();
+  a.pd = job->pd.as<int32_t>();
+  a.bmax = job->bmax.as<int>();
+  a.arena = w.arena.as<int32_t>();
+  a.arena_cap = arena_cap;
+  a.aoff = w.aoff.as<int64_t>();
+  a.dsearch = w.dsearch.as<uint64_t>();
+  a.dwalk = w.dwalk.as<uint64_t>();
+  a.ctl = w.ctl.as<BiCtl>();
+  a.units = (unsigned long long *)(job->stats.d_units + K_BIDIR);
+  const int grid = (int)std::min<uint64_t>((uint64_t)w.nslots, count);
+  launch(&job->stats, K_BIDIR, st, [&] { k_bidir<<<grid, kBiThreads, 0, st>>>(a); });
+}
+
+}  // namespace cen

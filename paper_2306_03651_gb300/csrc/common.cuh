@@ -78,6 +78,15 @@ struct DevBuf {
     p = np;
     bytes = cap;
   }
+  // Capacity of exactly `need` bytes when it has to grow (large workspaces).
+  void ensure_exact(size_t need, cudaStream_t s) {
+    st = s;
+    if (need <= bytes && p) return;
+    release();
+    alloc_fault_tick();
+    CEN_CK(cudaMallocAsync(&p, need, s));
+    bytes = need;
+  }
   template <class T>
   T *as() const { return static_cast<T *>(p); }
   void swap(DevBuf &o) {
@@ -175,6 +184,7 @@ enum KClass : int {
   K_SELECT,      // top-k positive sums
   K_GRAPH,       // graph validation / in-CSR
   K_MISC,        // scans, fills
+  K_BIDIR,       // bidirectional sampler (search, cone, counts, walk)
   K_COUNT
 };
 static_assert(K_COUNT <= CEN_NKCLASS, "too many kernel classes");
@@ -258,7 +268,7 @@ struct cen_graph {
   cudaStream_t st = nullptr;
   cen::DevBuf off, col, roff, rcol;  // roff/rcol empty when undirected (alias off/col)
   cen::ChunkTable out_chunks, in_chunks_own;  // in_chunks_own used only when directed
-  double param[5] = {0, 0, 0, 0, 0};          // tuning defaults for jobs on this graph (0 = unset)
+  double param[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // tuning defaults for jobs on this graph (0 = unset)
   const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
   const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
   const cen::ChunkTable &in_chunks() const { return directed ? in_chunks_own : out_chunks; }

@@ -48,6 +48,25 @@ struct WaveWS {
   DevBuf arc_range;                           // per level: [first, end) of its logged arcs
 };
 
+// Workspace of the bidirectional sampler (bidir.cu): for each of `nslots`
+// resident CTAs, a state word per node ([nslots][n], zeroed once; words are
+// epoch-stamped so nothing is cleared between samples), five lists of QC
+// entries (two ball queues, two cone lists, heavy rows) and 2 QC path counts.
+struct BiCtl {
+  unsigned long long next;     // next sample, relative to the launch's first
+  unsigned long long cursor;   // arena entries reserved
+  unsigned long long nsearch;  // samples left whole to the bit-parallel sampler
+  unsigned long long nwalk;    // samples whose walk is left to it (distance known)
+  int err;
+  int pad;
+};
+struct BiWS {
+  DevBuf state, lists, sig, epochs, ctl, aoff, dsearch, dwalk, arena;
+  int nslots = 0;
+  int64_t QC = 0;
+  int32_t n = 0;
+};
+
 }  // namespace cen
 
 struct cen_job {
@@ -80,10 +99,19 @@ struct cen_job {
   cen::Stats stats;
   size_t level_budget = (size_t)1 << 30;   // bytes allowed for one [n][G] level array
   int max_wave_words = 32;                 // upper bound on G (wave width / 64)
+  // bidirectional sampler
+  std::unique_ptr<cen::BiWS> bws;
+  int sampler = 0;                          // 0 bidirectional (bit-parallel for what it defers), 1 bit-parallel
+  size_t bidir_budget = (size_t)4 << 30;    // bytes of per-slot workspace
+  int64_t bidir_queue = (int64_t)1 << 18;   // entries per ball / cone list
+  uint64_t bidir_deferred_search = 0;       // samples it left whole to the bit-parallel sampler
+  uint64_t bidir_deferred_walk = 0;         // samples whose walk it left (distance known)
 };
 
 namespace cen {
 void sample_append(cen_job *job, uint64_t m_new);
+void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap);
+int bidir_resident_slots();
 void build_incidence(cen_job *job);
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered);
 void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b);

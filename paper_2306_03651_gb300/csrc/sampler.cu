@@ -372,9 +372,10 @@ __global__ void __launch_bounds__(256) k_level_finalize(int32_t n, int G, int gs
 // One block: per-sample s, t, d of the wave, wave-local member offsets
 // woff[b] (exclusive prefix of max(d-1, 0)), the wave's member total and the
 // running max |h|.
-__global__ void __launch_bounds__(1024) k_wave_lengths(int count, uint64_t jbase, const int32_t *slot_s,
-                                                       const int32_t *slot_t, const int32_t *slot_d, int64_t *woff,
-                                                       int32_t *ps, int32_t *pt, int32_t *pd, int *bmax, Ctl *ctl) {
+__global__ void __launch_bounds__(1024) k_wave_lengths(int count, uint64_t jbase, const uint64_t *__restrict__ jlist,
+                                                       const int32_t *slot_s, const int32_t *slot_t,
+                                                       const int32_t *slot_d, int64_t *woff, int32_t *ps, int32_t *pt,
+                                                       int32_t *pd, int *bmax, Ctl *ctl) {
   __shared__ long long wsum[32];
   __shared__ long long carry;
   if (threadIdx.x == 0) carry = 0;
@@ -386,9 +387,10 @@ __global__ void __launch_bounds__(1024) k_wave_lengths(int count, uint64_t jbase
     if (b < count) {
       const int d = slot_d[b];
       len = d >= 2 ? d - 1 : 0;
-      ps[jbase + b] = slot_s[b];
-      pt[jbase + b] = slot_t[b];
-      pd[jbase + b] = d;
+      const uint64_t j = jlist ? jlist[b] : jbase + b;
+      ps[j] = slot_s[b];
+      pt[j] = slot_t[b];
+      pd[j] = d;
       mymax = max(mymax, len);
     }
     long long x = len;
@@ -433,6 +435,29 @@ __global__ void k_hoff_add(int64_t *hoff, uint64_t j0, uint64_t count, const int
   for (uint64_t i = 1 + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= count;
        i += (uint64_t)gridDim.x * blockDim.x)
     hoff[j0 + i] = base + ex[i];
+}
+
+// aoff[jlist[b] - j0] = base + woff[b] for the slots of a wave whose members
+// went to the arena at base (slots with d < 2 have none).
+__global__ void k_set_aoff(int count, const uint64_t *__restrict__ jlist, uint64_t j0, const int64_t *__restrict__ woff,
+                           const int32_t *__restrict__ slot_d, int64_t base, int64_t *aoff) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x)
+    aoff[jlist[b] - j0] = slot_d[b] >= 2 ? base + woff[b] : -1;
+}
+
+// Warp per new sample: its members move from the arena (at aoff) to the store.
+__global__ void k_gather_arena(uint64_t count, uint64_t j0, const int64_t *__restrict__ aoff,
+                               const int32_t *__restrict__ pd, const int64_t *__restrict__ hoff,
+                               const int32_t *__restrict__ arena, int32_t *hmem) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nwarps) {
+    const int64_t a = aoff[i];
+    const int d = pd[j0 + i];
+    if (a < 0 || d < 2) continue;
+    const int64_t h = hoff[j0 + i];
+    for (int q = lane; q < d - 1; q += 32) hmem[h + q] = arena[a + q];
+  }
 }
 
 // ------------------------------------------------------------------ cone
@@ -1063,7 +1088,7 @@ struct Sampler {
       const int Lmax = discover(count, jbase, jlist);
       if (wave_total) {
         launch(S, K_APPEND, st, [&] {
-          k_wave_lengths<<<1, 1024, 0, st>>>(count, jbase, slot_s, slot_t, slot_d, ws().woff.as<int64_t>(),
+          k_wave_lengths<<<1, 1024, 0, st>>>(count, jbase, jlist, slot_s, slot_t, slot_d, ws().woff.as<int64_t>(),
                                              job->ps.as<int32_t>(), job->pt.as<int32_t>(), job->pd.as<int32_t>(),
                                              job->bmax.as<int>(), ctl);
         });
@@ -1156,29 +1181,194 @@ struct WaveOut {
 
 }  // namespace
 
-// Alg. 1 "sampleHEs": the new samples are cut into waves; up to
+namespace {
+
+Sampler make_sampler(cen_job *job, WaveWS &w, cudaStream_t st) {
+  Sampler sp;
+  sp.job = job;
+  sp.wsp = &w;
+  sp.g = job->g;
+  sp.st = st;
+  sp.S = &job->stats;
+  sp.n = job->g->n;
+  return sp;
+}
+
+WaveWS &wave_ws0(cen_job *job) {
+  if (job->wws.empty()) job->wws.emplace_back(new WaveWS());
+  return *job->wws[0];
+}
+
+// Uploads ids to the workspace's jlist through its pinned staging.
+void upload_jlist(WaveWS &w, const uint64_t *ids, int count, cudaStream_t st) {
+  w.jlist.ensure(8 * (size_t)kMaxW, st);
+  uint64_t *h = (uint64_t *)ws_staging(w, 8 * (size_t)kMaxW + sizeof(Ctl));
+  memcpy(h, ids, 8 * (size_t)count);
+  CEN_CK(cudaMemcpyAsync(w.jlist.p, h, 8 * (size_t)count, cudaMemcpyHostToDevice, st));
+  CEN_CK(cudaStreamSynchronize(st));
+}
+
+// Members of the listed samples (offsets already in hoff) written in place
+// by the bit-parallel sampler: 64-bit counts first, then 128-bit counts for
+// the pairs whose count reached 2^64.
+void rerun_in_place(cen_job *job, std::vector<uint64_t> ids) {
+  if (ids.empty()) return;
+  std::sort(ids.begin(), ids.end());
+  cudaStream_t st = job->st;
+  WaveWS &w0 = wave_ws0(job);
+  Sampler sp = make_sampler(job, w0, st);
+  std::vector<uint64_t> wide;
+  for (size_t q0 = 0; q0 < ids.size();) {
+    const int G = pick_G(ids.size() - q0, job->g->n, job->level_budget, job->max_wave_words);
+    const int count = (int)std::min<size_t>((size_t)64 * G, ids.size() - q0);
+    upload_jlist(w0, ids.data() + q0, count, st);
+    sp.setup(G);
+    const int Lmax = sp.discover_and_cone(count, 0, w0.jlist.as<uint64_t>(), nullptr);
+    sp.sigma_and_walk<uint64_t>(count, Lmax, nullptr, job->hmem.as<int32_t>());
+    CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    CEN_CK(cudaStreamSynchronize(st));
+    CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent path counts in the backward walk");
+    for (int f = 0; f < sp.hctl->nflag; ++f) wide.push_back(ids[q0 + sp.hctl->flagged[f]]);
+    q0 += (size_t)count;
+  }
+  if (wide.empty()) return;
+  std::sort(wide.begin(), wide.end());
+  sp.setup(1);
+  for (size_t q0 = 0; q0 < wide.size(); q0 += 64) {
+    const int count = (int)std::min<size_t>(64, wide.size() - q0);
+    upload_jlist(w0, wide.data() + q0, count, st);
+    sp.hctl = (Ctl *)ws_staging(w0, sizeof(Ctl));
+    const int Lmax = sp.discover_and_cone(count, 0, w0.jlist.as<uint64_t>(), nullptr);
+    sp.sigma_and_walk<u128>(count, Lmax, nullptr, job->hmem.as<int32_t>());
+    CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, offsetof(Ctl, flagged), cudaMemcpyDeviceToHost, st));
+    CEN_CK(cudaStreamSynchronize(st));
+    CEN_REQUIRE(sp.hctl->err != CEN_EOVERFLOW, CEN_EOVERFLOW, "cen_sample: a sampled pair has >= 2^128 shortest paths");
+    CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent 128-bit path counts");
+  }
+}
+
+// hoff of the new samples from their distances; returns their member total.
+int64_t offsets_from_distances(cen_job *job, uint64_t m0, uint64_t m_new) {
+  cudaStream_t st = job->st;
+  Stats *S = &job->stats;
+  WaveWS &w0 = wave_ws0(job);
+  w0.lens.ensure(4 * (size_t)m_new, st);
+  w0.exoff.ensure(8 * ((size_t)m_new + 1), st);
+  launch(S, K_APPEND, st, [&] {
+    k_lengths_of<<<grid_for(m_new, 256), 256, 0, st>>>(job->pd.as<int32_t>(), m0, m_new, w0.lens.as<int32_t>());
+  });
+  counts_to_offsets(w0.lens.as<int32_t>(), w0.exoff.as<int64_t>(), (size_t)m_new, w0.scan_tmp, st, S);
+  launch(S, K_APPEND, st, [&] {
+    k_hoff_add<<<grid_for(m_new, 256), 256, 0, st>>>(job->hoff.as<int64_t>(), m0, m_new, w0.exoff.as<int64_t>());
+  });
+  int64_t *h = (int64_t *)host_staging(job, 8);
+  CEN_CK(cudaMemcpyAsync(h, w0.exoff.as<int64_t>() + m_new, 8, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  return *h;
+}
+
+// Workspace for as many resident CTAs as the byte budget allows (at least one).
+void bidir_setup(cen_job *job, uint64_t m_new) {
+  const int32_t n = job->g->n;
+  cudaStream_t st = job->st;
+  if (!job->bws) job->bws.reset(new BiWS());
+  BiWS &w = *job->bws;
+  const int64_t QC = std::max<int64_t>(16, std::min<int64_t>(n, job->bidir_queue));
+  const size_t per_slot = 8 * (size_t)n + 5 * 4 * (size_t)QC + 2 * 8 * (size_t)QC;
+  const size_t fit = std::max<size_t>(1, job->bidir_budget / per_slot);
+  const int slots = (int)std::min<size_t>((size_t)bidir_resident_slots(), fit);
+  if (w.n != n || w.QC != QC || w.nslots != slots) {
+    w.state.ensure_exact(8 * (size_t)n * slots, st);
+    w.lists.ensure_exact(4 * 5 * (size_t)QC * slots, st);
+    w.sig.ensure_exact(8 * 2 * (size_t)QC * slots, st);
+    w.epochs.ensure(4 * (size_t)slots, st);
+    CEN_CK(cudaMemsetAsync(w.state.p, 0, 8 * (size_t)n * slots, st));
+    CEN_CK(cudaMemsetAsync(w.epochs.p, 0, 4 * (size_t)slots, st));
+    w.n = n;
+    w.QC = QC;
+    w.nslots = slots;
+  }
+  w.ctl.ensure(sizeof(BiCtl), st);
+  w.aoff.ensure(8 * (size_t)m_new, st);
+  w.dsearch.ensure(8 * (size_t)m_new, st);
+  w.dwalk.ensure(8 * (size_t)m_new, st);
+}
+
+// Bidirectional form: one CTA per sample writes its members to an arena;
+// what it defers runs on the bit-parallel sampler (see bidir.cu).  Returns
+// the new members.
+int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
+  cudaStream_t st = job->st;
+  bidir_setup(job, m_new);
+  BiWS &bw = *job->bws;
+  const double mean = job->m ? (double)job->members / (double)job->m : 4.0;
+  const int64_t cap = (int64_t)((double)m_new * std::max(8.0, 2.0 * mean)) + ((int64_t)1 << 20);
+  bw.arena.ensure(4 * (size_t)cap, st);
+  bidir_launch(job, m0, m_new, cap);
+  BiCtl *hc = (BiCtl *)host_staging(job, sizeof(BiCtl));
+  CEN_CK(cudaMemcpyAsync(hc, bw.ctl.p, sizeof(BiCtl), cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  CEN_REQUIRE(hc->err == 0, hc->err, "cen_sample: inconsistent path counts in the bidirectional walk");
+  const BiCtl h = *hc;
+  std::vector<uint64_t> search(h.nsearch), walk(h.nwalk);
+  if (h.nsearch)
+    CEN_CK(cudaMemcpyAsync(search.data(), bw.dsearch.p, 8 * h.nsearch, cudaMemcpyDeviceToHost, st));
+  if (h.nwalk) CEN_CK(cudaMemcpyAsync(walk.data(), bw.dwalk.p, 8 * h.nwalk, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  std::sort(search.begin(), search.end());
+
+  // whole samples the CTAs could not search: bit-parallel, members into the arena
+  int64_t cursor = std::min<int64_t>((int64_t)h.cursor, cap);
+  if (!search.empty()) {
+    WaveWS &w0 = wave_ws0(job);
+    Sampler sp = make_sampler(job, w0, st);
+    for (size_t q0 = 0; q0 < search.size();) {
+      const int G = pick_G(search.size() - q0, job->g->n, job->level_budget, job->max_wave_words);
+      const int count = (int)std::min<size_t>((size_t)64 * G, search.size() - q0);
+      upload_jlist(w0, search.data() + q0, count, st);
+      sp.setup(G);
+      int64_t total = 0;
+      const int Lmax = sp.discover_and_cone(count, 0, w0.jlist.as<uint64_t>(), &total);
+      bw.arena.ensure(4 * (size_t)(cursor + total + 1), st, 4 * (size_t)cursor);
+      sp.sigma_and_walk<uint64_t>(count, Lmax, w0.woff.as<int64_t>(), bw.arena.as<int32_t>() + cursor);
+      launch(&job->stats, K_APPEND, st, [&] {
+        k_set_aoff<<<grid_for(count, 256), 256, 0, st>>>(count, w0.jlist.as<uint64_t>(), m0, w0.woff.as<int64_t>(),
+                                                          sp.slot_d, cursor, bw.aoff.as<int64_t>());
+      });
+      CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+      CEN_CK(cudaStreamSynchronize(st));
+      CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent path counts in the backward walk");
+      for (int f = 0; f < sp.hctl->nflag; ++f) walk.push_back(search[q0 + sp.hctl->flagged[f]]);
+      cursor += total;
+      q0 += (size_t)count;
+    }
+  }
+  const int64_t total = offsets_from_distances(job, m0, m_new);
+  job->hmem.ensure(4 * (size_t)(job->members + total + 1), st, 4 * (size_t)job->members);
+  launch(&job->stats, K_APPEND, st, [&] {
+    k_gather_arena<<<grid_for(m_new * 32, 256), 256, 0, st>>>(m_new, m0, bw.aoff.as<int64_t>(),
+                                                              job->pd.as<int32_t>(), job->hoff.as<int64_t>(),
+                                                              bw.arena.as<int32_t>(), job->hmem.as<int32_t>());
+  });
+  // walks the CTAs left (cone or counts too large, arena full) and the pairs
+  // whose count reached 2^64 in the waves above: written in place
+  rerun_in_place(job, walk);
+  job->bidir_deferred_search += h.nsearch;
+  job->bidir_deferred_walk += walk.size();
+  return total;
+}
+
+// Bit-parallel form: the new samples are cut into waves; up to
 // job->wave_streams waves run at once, each on its own stream and workspace,
 // writing members to a wave buffer.  Then the offsets of all new samples come
 // from one scan of their lengths and the wave buffers are copied in order, so
 // the store is the same whatever the concurrency.  Pairs whose path count
-// reached 2^64 are re-run with 128-bit counts at the end.
-void sample_append(cen_job *job, uint64_t m_new) {
-  if (m_new == 0) return;
-  Range range("cen_sample");
+// reached 2^64 are re-run with 128-bit counts at the end.  Returns the new
+// members.
+int64_t append_waves(cen_job *job, uint64_t m0, uint64_t m_new) {
   const cen_graph *g = job->g;
   cudaStream_t st = job->st;
-  const uint64_t m0 = job->m;
   const uint64_t m1 = m0 + m_new;
-  job->hoff.ensure(sizeof(int64_t) * (m1 + 1), st, sizeof(int64_t) * (m0 + 1));
-  if (m0 == 0) CEN_CK(cudaMemsetAsync(job->hoff.p, 0, sizeof(int64_t), st));
-  job->ps.ensure(4 * m1, st, 4 * m0);
-  job->pt.ensure(4 * m1, st, 4 * m0);
-  job->pd.ensure(4 * m1, st, 4 * m0);
-  job->sign.ensure(4 * (size_t)job->nw * m1, st, 4 * (size_t)job->nw * m0);
-  job->bmax.ensure(4, st, 4);
-  if (m0 == 0) CEN_CK(cudaMemsetAsync(job->bmax.p, 0, 4, st));
-
-  // waves
   std::vector<std::unique_ptr<WaveOut>> waves;
   for (uint64_t j0 = m0; j0 < m1;) {
     const int G = pick_G(m1 - j0, g->n, job->level_budget, job->max_wave_words);
@@ -1205,13 +1395,7 @@ void sample_append(cen_job *job, uint64_t m_new) {
   auto work = [&](int w) {
     try {
       WaveWS &wsw = *job->wws[w];
-      Sampler sp;
-      sp.job = job;
-      sp.wsp = &wsw;
-      sp.g = g;
-      sp.st = w == 0 ? st : wsw.own_stream;
-      sp.S = &job->stats;
-      sp.n = g->n;
+      Sampler sp = make_sampler(job, wsw, w == 0 ? st : wsw.own_stream);
       if (w > 0) CEN_CK(cudaStreamWaitEvent(sp.st, ready, 0));
       for (;;) {
         {
@@ -1229,13 +1413,7 @@ void sample_append(cen_job *job, uint64_t m_new) {
         CEN_CK(cudaMemcpyAsync(sp.hctl, sp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, sp.st));
         CEN_CK(cudaStreamSynchronize(sp.st));
         CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent path counts in the backward walk");
-        if (sp.hctl->nflag > 0) {
-          std::vector<int> fl(sp.hctl->flagged, sp.hctl->flagged + sp.hctl->nflag);
-          std::vector<uint64_t> slot_js(wo.count);
-          CEN_CK(cudaMemcpyAsync(slot_js.data(), sp.slot_j, 8 * (size_t)wo.count, cudaMemcpyDeviceToHost, sp.st));
-          CEN_CK(cudaStreamSynchronize(sp.st));
-          for (int b : fl) wo.flagged.push_back(slot_js[b]);
-        }
+        for (int f = 0; f < sp.hctl->nflag; ++f) wo.flagged.push_back(wo.j0 + (uint64_t)sp.hctl->flagged[f]);
       }
       CEN_CK(cudaStreamSynchronize(sp.st));
     } catch (const Error &e) {
@@ -1260,19 +1438,7 @@ void sample_append(cen_job *job, uint64_t m_new) {
   if (first_err.code != CEN_OK) throw first_err;
 
   // offsets of the new samples, then the wave buffers in order
-  Stats *S = &job->stats;
-  WaveWS &w0 = *job->wws[0];
-  w0.lens.ensure(4 * (size_t)m_new, st);
-  w0.exoff.ensure(8 * ((size_t)m_new + 1), st);
-  launch(S, K_APPEND, st, [&] {
-    k_lengths_of<<<grid_for(m_new, 256), 256, 0, st>>>(job->pd.as<int32_t>(), m0, m_new, w0.lens.as<int32_t>());
-  });
-  counts_to_offsets(w0.lens.as<int32_t>(), w0.exoff.as<int64_t>(), (size_t)m_new, w0.scan_tmp, st, S);
-  launch(S, K_APPEND, st, [&] {
-    k_hoff_add<<<grid_for(m_new, 256), 256, 0, st>>>(job->hoff.as<int64_t>(), m0, m_new, w0.exoff.as<int64_t>());
-  });
-  int64_t total = 0;
-  for (auto &wo : waves) total += wo->total;
+  const int64_t total = offsets_from_distances(job, m0, m_new);
   const int64_t members = job->members;
   job->hmem.ensure(4 * (size_t)(members + total + 1), st, 4 * (size_t)members);
   int64_t pos = members;
@@ -1284,25 +1450,15 @@ void sample_append(cen_job *job, uint64_t m_new) {
     pos += wo->total;
     flagged_js.insert(flagged_js.end(), wo->flagged.begin(), wo->flagged.end());
   }
-
   // 128-bit re-run of the slots whose path count reached 2^64 (offsets known)
   if (!flagged_js.empty()) {
     std::sort(flagged_js.begin(), flagged_js.end());
-    Sampler sp;
-    sp.job = job;
-    sp.wsp = &w0;
-    sp.g = g;
-    sp.st = st;
-    sp.S = S;
-    sp.n = g->n;
+    WaveWS &w0 = *job->wws[0];
+    Sampler sp = make_sampler(job, w0, st);
     sp.setup(1);
-    w0.jlist.ensure(8 * 64, st);
     for (size_t q0 = 0; q0 < flagged_js.size(); q0 += 64) {
       const int count = (int)std::min<size_t>(64, flagged_js.size() - q0);
-      uint64_t *h = (uint64_t *)ws_staging(w0, 8 * 64 + sizeof(Ctl));
-      memcpy(h, flagged_js.data() + q0, 8 * (size_t)count);
-      CEN_CK(cudaMemcpyAsync(w0.jlist.p, h, 8 * (size_t)count, cudaMemcpyHostToDevice, st));
-      CEN_CK(cudaStreamSynchronize(st));
+      upload_jlist(w0, flagged_js.data() + q0, count, st);
       sp.hctl = (Ctl *)ws_staging(w0, sizeof(Ctl));
       const int Lmax = sp.discover_and_cone(count, 0, w0.jlist.as<uint64_t>(), nullptr);
       sp.sigma_and_walk<u128>(count, Lmax, nullptr, job->hmem.as<int32_t>());
@@ -1313,18 +1469,40 @@ void sample_append(cen_job *job, uint64_t m_new) {
       CEN_REQUIRE(sp.hctl->err == 0, sp.hctl->err, "cen_sample: inconsistent 128-bit path counts");
     }
   }
+  for (auto &wo : waves) wo->mem.release();  // stream-ordered after the copies above
+  return total;
+}
+
+}  // namespace
+
+// Alg. 1 "sampleHEs": appends samples m .. m + m_new - 1 (pairs, distances,
+// hyper-edges, sign columns).
+void sample_append(cen_job *job, uint64_t m_new) {
+  if (m_new == 0) return;
+  Range range("cen_sample");
+  cudaStream_t st = job->st;
+  const uint64_t m0 = job->m;
+  const uint64_t m1 = m0 + m_new;
+  job->hoff.ensure(sizeof(int64_t) * (m1 + 1), st, sizeof(int64_t) * (m0 + 1));
+  if (m0 == 0) CEN_CK(cudaMemsetAsync(job->hoff.p, 0, sizeof(int64_t), st));
+  job->ps.ensure(4 * m1, st, 4 * m0);
+  job->pt.ensure(4 * m1, st, 4 * m0);
+  job->pd.ensure(4 * m1, st, 4 * m0);
+  job->sign.ensure(4 * (size_t)job->nw * m1, st, 4 * (size_t)job->nw * m0);
+  job->bmax.ensure(4, st, 4);
+  if (m0 == 0) CEN_CK(cudaMemsetAsync(job->bmax.p, 0, 4, st));
+  const int64_t total = job->sampler == 0 ? append_bidir(job, m0, m_new) : append_waves(job, m0, m_new);
   // sign columns of the new samples
   {
     const int nblk = (job->nw + 3) / 4;
-    launch(S, K_SIGN, st, [&] {
+    launch(&job->stats, K_SIGN, st, [&] {
       k_sign<<<grid_for(m_new * nblk, 256), 256, 0, st>>>(m0, m_new, job->t, job->nw, job->seed,
                                                           job->sign.as<uint32_t>());
     });
   }
-  for (auto &wo : waves) wo->mem.release();  // stream-ordered after the copies above
   CEN_CK(cudaStreamSynchronize(st));
   job->m = m1;
-  job->members = members + total;
+  job->members += total;
 }
 
 }  // namespace cen

@@ -67,6 +67,47 @@ def test_sample_parity(name):
     assert_same_samples(job.samples(), ref)
 
 
+@pytest.mark.parametrize("name", ["ba300", "rmat12_dir", "grid_rewired", "dpath"])
+def test_sample_parity_bit_parallel_only(name):
+    """The bit-parallel sampler alone (the bidirectional one's fallback) matches too."""
+    g = GRAPHS[name]
+    m = 2600 if g.n > 50 else 700
+    _, _, ref = oracle_samples(g, 11, m)
+    job = P.Job(P.Graph.of(g), 11, 10)
+    job.set_param(P.PARAM_SAMPLER, P.SAMPLER_WAVES)
+    job.sample(m)
+    assert_same_samples(job.samples(), ref)
+    assert job.sampler_info()["slots"] == 0
+
+
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_dir", "grid_rewired"])
+def test_bidirectional_search_deferral(name):
+    """Balls larger than a 16-node queue go whole to the bit-parallel sampler; the store
+    (members in the arena and in place) is still the oracle's."""
+    g = GRAPHS[name]
+    _, _, ref = oracle_samples(g, 17, 1500)
+    job = P.Job(P.Graph.of(g), 17, 10)
+    job.set_param(P.PARAM_BIDIR_QUEUE, 16)
+    job.sample(700)
+    job.sample(800)
+    assert_same_samples(job.samples(), ref)
+    info = job.sampler_info()
+    assert info["deferred_search"] > 0 and info["slots"] > 0
+
+
+def test_bidirectional_level_cap_deferral():
+    """A 5000-cycle: pairs more than 2046 apart need over 1023 levels on one side, past
+    the per-side level cap, and are searched by the bit-parallel sampler."""
+    n = 5000
+    g = I.from_edges(n, np.arange(n), (np.arange(n) + 1) % n, False)
+    _, _, ref = oracle_samples(g, 2, 300)
+    job = P.Job(P.Graph.of(g), 2, 10)
+    job.sample(300)
+    assert_same_samples(job.samples(), ref)
+    assert job.sampler_info()["deferred_search"] > 0
+    assert ref["d"].max() > 2 * 1023
+
+
 def test_sample_split_invariance():
     g = GRAPHS["ba300"]
     _, _, ref = oracle_samples(g, 5, 1000)
@@ -92,6 +133,7 @@ def test_path_counts_beyond_64_bits():
     job = P.Job(P.Graph.of(g), seed, 10)
     job.sample(m)
     assert_same_samples(job.samples(), ref)
+    assert job.sampler_info()["deferred_walk"] >= big  # their walks go to the 128-bit re-run
 
 
 def test_path_counts_beyond_128_bits_overflow():
