@@ -124,12 +124,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# kernel class -> (committed ncu summary, source file whose hash it records)
+DRAM_PROFILES = {"expand_pull": ("expand_pull_dram.md", "sampler.cu"), "bidir": ("bidir_dram.md", "bidir.cu")}
+
+
 def dram_traffic(kernel_class: str):
-    """DRAM bytes per launch of `kernel_class` from the committed ncu summary, or None when the
-    summary is for another class or the sampler source changed since the counters were taken."""
+    """DRAM bytes per launch of `kernel_class` from the committed ncu summary, or None when there
+    is none for the class or its source changed since the counters were taken."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "expand_pull_dram.md")
-    src = os.path.join(ROOT, "paper_2306_03651_gb300", "csrc", "sampler.cu")
+    if kernel_class not in DRAM_PROFILES:
+        return None
+    prof = os.path.join(ROOT, "profiles", DRAM_PROFILES[kernel_class][0])
+    src = os.path.join(ROOT, "paper_2306_03651_gb300", "csrc", DRAM_PROFILES[kernel_class][1])
     try:
         kv = {}
         for line in open(prof):
@@ -259,7 +265,7 @@ def run_gpu(args, rank, world):
         peak, peak_src = float(pk["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    byte_classes = ("expand_pull", "expand_push", "level_finalize", "cone", "cone_sigma", "walk")
+    byte_classes = ("bidir", "expand_pull", "expand_push", "level_finalize", "cone", "cone_sigma", "walk")
     dom = max(stats, key=lambda k: stats[k]["ms"])
     roof = None
     if stats[dom]["ms"] > 0:

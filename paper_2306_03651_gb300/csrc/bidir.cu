@@ -22,8 +22,9 @@
 // Work the per-CTA resources cannot hold is left to the bit-parallel
 // sampler, which gives the identical hyper-edge: more than kBiMaxLevels
 // levels on one side or more than QC nodes in one ball ("search" deferral,
-// distance unknown); a cone side larger than QC, a path count reaching 2^64,
-// or a full member arena ("walk" deferral, distance known).
+// distance unknown); a path count reaching 2^64 or a full member arena
+// ("walk" deferral, distance known).  A cone side is part of its ball, so it
+// always fits.
 #include <algorithm>
 
 #include "job.cuh"
@@ -51,23 +52,21 @@ __device__ __forceinline__ uint64_t st_make(uint32_t epoch, int side, int level)
 }
 
 struct BiShared {
-  int lo[2][kBiMaxLevels + 1];  // ball queue of side x: level L is lo[x][L] .. lo[x][L+1]
-  int cs[2][kBiMaxLevels];      // cone list of side x: level L is cs[x][L] .. ce[x][L]
+  int lo[2][kBiMaxLevels + 1];                  // ball queue of side x: level L is lo[x][L] .. lo[x][L+1]
+  unsigned long long hcost[2][kBiMaxLevels];    // arcs out of level L of side x (out-arcs forward, in-arcs backward)
+  int cs[2][kBiMaxLevels];                      // cone list of side x: level L is cs[x][L] .. ce[x][L]
   int ce[2][kBiMaxLevels];
-  unsigned long long cost[2];   // arcs out of each side's frontier (out-arcs forward, in-arcs backward)
-  unsigned long long addcost;
   unsigned long long red[kBiWarps];
-  int redovf;
-  int added, nheavy, ccount[2];
+  unsigned long long addcost, sum, arcs;
+  int added, nheavy, ccount[2], ncross;
   int lvl[2];
-  int met, ovf;
+  int met, ovf, xovf;
   int status, d;
   int s, t;
   uint32_t epoch;
   int clear;
   unsigned long long j;
   long long abase;
-  unsigned long long arcs;
 };
 
 // Sets the cone bit of w and, the first time, appends w to the cone list of
@@ -93,21 +92,41 @@ __device__ __forceinline__ int bi_group(unsigned long long arcs, int cnt) {
   return gs;
 }
 
+// sh.sum = sum over list[0, cnt) of the row lengths in o.  Called by all threads.
+__device__ unsigned long long bi_row_sum(const uint32_t *list, int cnt, const int64_t *__restrict__ o, BiShared &sh) {
+  const int tid = threadIdx.x;
+  unsigned long long a = 0;
+  for (int i = tid; i < cnt; i += kBiThreads) {
+    const int v = (int)list[i];
+    a += (unsigned long long)(o[v + 1] - o[v]);
+  }
+  a = warp_sum(a);
+  if ((tid & 31) == 0) sh.red[tid >> 5] = a;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < kBiWarps; ++w) tot += sh.red[w];
+    sh.sum = tot;
+  }
+  __syncthreads();
+  const unsigned long long r = sh.sum;
+  __syncthreads();
+  return r;
+}
+
 // For every node v of list[0, cnt) and every arc of v's row in (o, c), calls
 // f(v, w).  Rows of at most kBiHeavy arcs are scanned by a group of gs lanes;
-// longer rows are queued in `heavy` and scanned by the whole block.  With
-// use_stop, a raised sh.met ends the scan early.  Called by all threads.
+// longer rows are queued in `heavy` and scanned by the whole block.  Called
+// by all threads.
 template <class F>
 __device__ void bi_scan_rows(const uint32_t *list, int cnt, const int64_t *__restrict__ o,
-                             const int32_t *__restrict__ c, int gs, uint32_t *heavy, BiShared &sh, bool use_stop,
-                             F &&f) {
+                             const int32_t *__restrict__ c, int gs, uint32_t *heavy, BiShared &sh, F &&f) {
   const int tid = threadIdx.x;
   if (tid == 0) sh.nheavy = 0;
   __syncthreads();
   const int gl = tid & (gs - 1), gi = tid / gs, ng = kBiThreads / gs;
   unsigned long long arcs = 0;
   for (int i = gi; i < cnt; i += ng) {
-    if (use_stop && *(volatile int *)&sh.met) break;
     const int v = (int)list[i];
     const int64_t e0 = o[v], e1 = o[v + 1];
     if (e1 - e0 > kBiHeavy) {
@@ -120,7 +139,6 @@ __device__ void bi_scan_rows(const uint32_t *list, int cnt, const int64_t *__res
   __syncthreads();
   const int nh = sh.nheavy;
   for (int h = 0; h < nh; ++h) {
-    if (use_stop && *(volatile int *)&sh.met) break;
     const int v = (int)heavy[h];
     const int64_t e0 = o[v], e1 = o[v + 1];
     for (int64_t e = e0 + tid; e < e1; e += kBiThreads) f(v, c[e]);
@@ -135,13 +153,16 @@ __device__ __forceinline__ void add_carry(unsigned long long &acc, unsigned long
   ovf |= acc < v;
 }
 
-// Path counts of the cone nodes list[0, cnt), all at distance D from s: each
-// is the sum of the counts of its in-neighbours that are cone nodes at D - 1
-// (D of a node: its level in the forward ball, d minus its level in the
-// backward ball).  A sum that wraps 2^64 raises sh.ovf.
-__device__ void bi_sigma_level(const uint32_t *list, int cnt, int D, int d, uint32_t epoch,
-                               const uint64_t *__restrict__ state, uint64_t *sg, const int64_t *__restrict__ roff,
-                               const int32_t *__restrict__ rcol, int gs, uint32_t *heavy, BiShared &sh) {
+// Distance from s of a visited node: its level in the forward ball, d minus
+// its level in the backward ball.
+__device__ __forceinline__ int st_dist(uint64_t s, int d) { return st_side(s) ? d - st_level(s) : st_level(s); }
+
+// Pull form of one path-count level: each cone node of list[0, cnt) (all at
+// distance D from s) gets the sum of the counts of its in-neighbours that are
+// cone nodes at D - 1.  A sum that wraps 2^64 raises sh.ovf.
+__device__ void bi_sigma_pull(const uint32_t *list, int cnt, int D, int d, uint32_t epoch,
+                              const uint64_t *__restrict__ state, uint64_t *sg, const int64_t *__restrict__ roff,
+                              const int32_t *__restrict__ rcol, int gs, uint32_t *heavy, BiShared &sh) {
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) sh.nheavy = 0;
   __syncthreads();
@@ -159,8 +180,7 @@ __device__ void bi_sigma_level(const uint32_t *list, int cnt, int D, int d, uint
     unsigned long long acc = 0;
     for (int64_t e = e0 + gl; e < e1; e += gs) {
       const uint64_t su = state[rcol[e]];
-      if (st_epoch(su) == epoch && st_cone(su) && (st_side(su) ? d - st_level(su) : st_level(su)) == D - 1)
-        add_carry(acc, sg[st_cidx(su)], ovf);
+      if (st_epoch(su) == epoch && st_cone(su) && st_dist(su, d) == D - 1) add_carry(acc, sg[st_cidx(su)], ovf);
     }
     for (int o2 = gs >> 1; o2; o2 >>= 1) add_carry(acc, __shfl_xor_sync(gmask, acc, o2, gs), ovf);
     if (gl == 0) {
@@ -178,8 +198,7 @@ __device__ void bi_sigma_level(const uint32_t *list, int cnt, int D, int d, uint
     int hovf = 0;
     for (int64_t e = e0 + tid; e < e1; e += kBiThreads) {
       const uint64_t su = state[rcol[e]];
-      if (st_epoch(su) == epoch && st_cone(su) && (st_side(su) ? d - st_level(su) : st_level(su)) == D - 1)
-        add_carry(acc, sg[st_cidx(su)], hovf);
+      if (st_epoch(su) == epoch && st_cone(su) && st_dist(su, d) == D - 1) add_carry(acc, sg[st_cidx(su)], hovf);
     }
     for (int o2 = 16; o2; o2 >>= 1) add_carry(acc, __shfl_xor_sync(0xffffffffu, acc, o2), hovf);
     if (lane == 0) sh.red[tid >> 5] = acc;
@@ -199,6 +218,20 @@ __device__ void bi_sigma_level(const uint32_t *list, int cnt, int D, int d, uint
   __syncthreads();
 }
 
+// Whether the sorted row c[e0, e1) holds v (binary search).
+__device__ __forceinline__ bool row_has(const int32_t *__restrict__ c, int64_t e0, int64_t e1, int32_t v) {
+  while (e0 < e1) {
+    const int64_t mid = e0 + ((e1 - e0) >> 1);
+    const int32_t x = c[mid];
+    if (x == v) return true;
+    if (x < v)
+      e0 = mid + 1;
+    else
+      e1 = mid;
+  }
+  return false;
+}
+
 }  // namespace
 
 struct BiArgs {
@@ -207,7 +240,8 @@ struct BiArgs {
   const int32_t *col, *rcol;
   uint64_t seed, j0, count;
   uint64_t *state;    // [slots][n]
-  uint32_t *lists;    // [slots][5][QC]: ball queues (forward, backward), cone lists (same), heavy rows
+  uint32_t *lists;    // [slots][7][QC]: ball queues and cone lists (forward, backward), heavy rows,
+                      //                  crossing-arc tails and heads
   uint64_t *sig;      // [slots][2 QC]: path counts by cone index
   uint32_t *epochs;   // [slots]
   int64_t QC;
@@ -227,14 +261,12 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t QC = A.QC;
   uint64_t *state = A.state + (size_t)blockIdx.x * (size_t)A.n;
-  uint32_t *q[2] = {A.lists + ((size_t)blockIdx.x * 5 + 0) * (size_t)QC,
-                    A.lists + ((size_t)blockIdx.x * 5 + 1) * (size_t)QC};
-  uint32_t *cl[2] = {A.lists + ((size_t)blockIdx.x * 5 + 2) * (size_t)QC,
-                     A.lists + ((size_t)blockIdx.x * 5 + 3) * (size_t)QC};
-  uint32_t *heavy = A.lists + ((size_t)blockIdx.x * 5 + 4) * (size_t)QC;
+  uint32_t *lists = A.lists + (size_t)blockIdx.x * 7 * (size_t)QC;
+  uint32_t *q[2] = {lists, lists + QC};
+  uint32_t *cl[2] = {lists + 2 * QC, lists + 3 * QC};
+  uint32_t *heavy = lists + 4 * QC;
+  uint32_t *xt = lists + 5 * QC, *xh = lists + 6 * QC;
   uint64_t *sg = A.sig + (size_t)blockIdx.x * 2 * (size_t)QC;
-  const int64_t *csr_o[2] = {A.off, A.roff};  // side 0 grows over out-arcs, side 1 over in-arcs
-  const int32_t *csr_c[2] = {A.col, A.rcol};
   if (tid == 0) sh.arcs = 0;
   for (;;) {
     __syncthreads();
@@ -272,41 +304,53 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       sh.lo[1][0] = 0;
       sh.lo[1][1] = 1;
       sh.lvl[0] = sh.lvl[1] = 0;
-      sh.cost[0] = (unsigned long long)(A.off[s + 1] - A.off[s]);
-      sh.cost[1] = (unsigned long long)(A.roff[t + 1] - A.roff[t]);
+      sh.hcost[0][0] = (unsigned long long)(A.off[s + 1] - A.off[s]);
+      sh.hcost[1][0] = (unsigned long long)(A.roff[t + 1] - A.roff[t]);
       sh.met = 0;
       sh.ovf = 0;
+      sh.xovf = 0;
+      sh.ncross = 0;
       sh.status = 0;
       sh.d = -1;
     }
     __syncthreads();
 
-    // ---- discovery: grow the cheaper side until the balls touch
+    // ---- discovery: grow the cheaper side until the balls touch.  The level
+    // that touches is scanned to its end so that every crossing arc is logged.
     for (;;) {
-      const int x = sh.cost[0] <= sh.cost[1] ? 0 : 1;
+      const int x = sh.hcost[0][sh.lvl[0]] <= sh.hcost[1][sh.lvl[1]] ? 0 : 1;
       const int L = sh.lvl[x];
       if (L + 1 >= kBiMaxLevels) {
         if (tid == 0) sh.status = 1;
         break;
       }
       const int f0 = sh.lo[x][L], f1 = sh.lo[x][L + 1];
-      const unsigned long long fcost = sh.cost[x];
+      const unsigned long long fcost = sh.hcost[x][L];
       __syncthreads();
       if (tid == 0) {
         sh.added = 0;
         sh.addcost = 0;
       }
-      __syncthreads();
       uint32_t *qx = q[x];
-      const int64_t *o = csr_o[x];
-      const int32_t *c = csr_c[x];
+      const int64_t *o = x ? A.roff : A.off;
+      const int32_t *c = x ? A.rcol : A.col;
       const uint64_t mine = st_make(epoch, x, L + 1);
-      bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, true, [&](int, int w) {
+      bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
         const uint64_t sw = *(volatile uint64_t *)&state[w];
         if (st_epoch(sw) == epoch) {
-          if (st_side(sw) != x) sh.met = 1;
+          if (st_side(sw) != x) {  // an arc between the balls: (tail, head) in s -> t direction
+            sh.met = 1;
+            const int pos = atomicAdd(&sh.ncross, 1);
+            if (pos < QC) {
+              xt[pos] = (uint32_t)(x ? w : v);
+              xh[pos] = (uint32_t)(x ? v : w);
+            } else {
+              sh.xovf = 1;
+            }
+          }
           return;
         }
+        if (*(volatile int *)&sh.met) return;  // the distance is known: no more claims
         const unsigned long long old =
             atomicCAS((unsigned long long *)&state[w], (unsigned long long)sw, (unsigned long long)mine);
         if (old == sw) {
@@ -316,8 +360,6 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
           else
             sh.ovf = 1;
           atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
-        } else if (st_epoch(old) == epoch && st_side(old) != x) {
-          sh.met = 1;
         }
       });
       if (sh.met) {
@@ -332,8 +374,8 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       __syncthreads();
       if (tid == 0) {
         sh.lo[x][L + 2] = f1 + sh.added;
+        sh.hcost[x][L + 1] = sh.addcost;
         sh.lvl[x] = L + 1;
-        sh.cost[x] = sh.addcost;
       }
       __syncthreads();
     }
@@ -366,26 +408,23 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
     if (d < 2) continue;  // adjacent or unreachable: the empty hyper-edge
 
     const int ls = sh.lvl[0], lb = sh.lvl[1];
+    const int ncross = min(sh.ncross, (int)QC);
     if (sh.status == 0) {
-      // ---- crossing arcs: forward frontier (level ls) -> backward frontier (level lb)
-      if (sh.cost[0] <= sh.cost[1]) {
+      // ---- crossing arcs: forward level ls -> backward level lb
+      if (!sh.xovf) {
+        for (int i = tid; i < ncross; i += kBiThreads) {
+          bi_mark(state, cl[0], 0, QC, sh, (int)xt[i]);
+          bi_mark(state, cl[1], 1, QC, sh, (int)xh[i]);
+        }
+        __syncthreads();
+      } else {
         const int f0 = sh.lo[0][ls], f1 = sh.lo[0][ls + 1];
-        bi_scan_rows(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.cost[0], f1 - f0), heavy, sh, false,
+        bi_scan_rows(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][ls], f1 - f0), heavy, sh,
                      [&](int v, int w) {
                        const uint64_t sw = state[w];
                        if (st_epoch(sw) == epoch && st_side(sw) == 1 && st_level(sw) == lb) {
                          bi_mark(state, cl[0], 0, QC, sh, v);
                          bi_mark(state, cl[1], 1, QC, sh, w);
-                       }
-                     });
-      } else {
-        const int f0 = sh.lo[1][lb], f1 = sh.lo[1][lb + 1];
-        bi_scan_rows(q[1] + f0, f1 - f0, A.roff, A.rcol, bi_group(sh.cost[1], f1 - f0), heavy, sh, false,
-                     [&](int x, int u) {
-                       const uint64_t su = state[u];
-                       if (st_epoch(su) == epoch && st_side(su) == 0 && st_level(su) == ls) {
-                         bi_mark(state, cl[0], 0, QC, sh, u);
-                         bi_mark(state, cl[1], 1, QC, sh, x);
                        }
                      });
       }
@@ -396,26 +435,52 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
         sh.ce[1][lb] = min(sh.ccount[1], (int)QC);
       }
       __syncthreads();
-      // ---- cone, forward ball: in-neighbours one level down
+      // ---- cone, forward ball, level L -> L-1: scan the cone nodes' in-arcs,
+      // or the out-arcs of level L-1 of the ball, whichever is fewer
       for (int L = ls; L >= 1 && !sh.ovf; --L) {
         const int a = sh.cs[0][L], b = sh.ce[0][L];
-        bi_scan_rows(cl[0] + a, b - a, A.roff, A.rcol, 8, heavy, sh, false, [&](int, int u) {
-          const uint64_t su = state[u];
-          if (st_epoch(su) == epoch && st_side(su) == 0 && st_level(su) == L - 1) bi_mark(state, cl[0], 0, QC, sh, u);
-        });
+        const unsigned long long in_cone = bi_row_sum(cl[0] + a, b - a, A.roff, sh);
+        if (in_cone <= sh.hcost[0][L - 1]) {
+          bi_scan_rows(cl[0] + a, b - a, A.roff, A.rcol, 8, heavy, sh, [&](int, int u) {
+            const uint64_t su = state[u];
+            if (st_epoch(su) == epoch && st_side(su) == 0 && st_level(su) == L - 1)
+              bi_mark(state, cl[0], 0, QC, sh, u);
+          });
+        } else {
+          const int f0 = sh.lo[0][L - 1], f1 = sh.lo[0][L];
+          bi_scan_rows(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][L - 1], f1 - f0), heavy, sh,
+                       [&](int u, int w) {
+                         const uint64_t sw = state[w];
+                         if (st_epoch(sw) == epoch && st_cone(sw) && st_side(sw) == 0 && st_level(sw) == L)
+                           bi_mark(state, cl[0], 0, QC, sh, u);
+                       });
+        }
         if (tid == 0) {
           sh.cs[0][L - 1] = b;
           sh.ce[0][L - 1] = min(sh.ccount[0], (int)QC);
         }
         __syncthreads();
       }
-      // ---- cone, backward ball: out-neighbours one level down (towards t)
+      // ---- cone, backward ball, level L -> L-1 (towards t): the cone nodes'
+      // out-arcs, or the in-arcs of level L-1 of the ball
       for (int L = lb; L >= 1 && !sh.ovf; --L) {
         const int a = sh.cs[1][L], b = sh.ce[1][L];
-        bi_scan_rows(cl[1] + a, b - a, A.off, A.col, 8, heavy, sh, false, [&](int, int y) {
-          const uint64_t sy = state[y];
-          if (st_epoch(sy) == epoch && st_side(sy) == 1 && st_level(sy) == L - 1) bi_mark(state, cl[1], 1, QC, sh, y);
-        });
+        const unsigned long long out_cone = bi_row_sum(cl[1] + a, b - a, A.off, sh);
+        if (out_cone <= sh.hcost[1][L - 1]) {
+          bi_scan_rows(cl[1] + a, b - a, A.off, A.col, 8, heavy, sh, [&](int, int y) {
+            const uint64_t sy = state[y];
+            if (st_epoch(sy) == epoch && st_side(sy) == 1 && st_level(sy) == L - 1)
+              bi_mark(state, cl[1], 1, QC, sh, y);
+          });
+        } else {
+          const int f0 = sh.lo[1][L - 1], f1 = sh.lo[1][L];
+          bi_scan_rows(q[1] + f0, f1 - f0, A.roff, A.rcol, bi_group(sh.hcost[1][L - 1], f1 - f0), heavy, sh,
+                       [&](int y, int xv) {
+                         const uint64_t sx = state[xv];
+                         if (st_epoch(sx) == epoch && st_cone(sx) && st_side(sx) == 1 && st_level(sx) == L)
+                           bi_mark(state, cl[1], 1, QC, sh, y);
+                       });
+        }
         if (tid == 0) {
           sh.cs[1][L - 1] = b;
           sh.ce[1][L - 1] = min(sh.ccount[1], (int)QC);
@@ -429,21 +494,60 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       __syncthreads();
     }
     if (sh.status == 0) {
-      // ---- path counts over the cone, by distance from s
+      // ---- path counts over the cone, by distance D from s; each level is
+      // pulled over the cone nodes' in-arcs or pushed over the out-arcs of
+      // the level below, whichever is fewer; the crossing level adds along
+      // the logged crossing arcs
+      for (int i = tid; i < sh.ccount[0]; i += kBiThreads) sg[i] = 0;
+      for (int i = tid; i < sh.ccount[1]; i += kBiThreads) sg[QC + i] = 0;
+      __syncthreads();
       if (tid == 0) sg[st_cidx(state[sh.s])] = 1;
       __syncthreads();
       for (int D = 1; D <= d && !sh.ovf; ++D) {
         const int x = D <= ls ? 0 : 1;
         const int L = x ? d - D : D;
-        const int a = sh.cs[x][L], b = sh.ce[x][L];
-        bi_sigma_level(cl[x] + a, b - a, D, d, epoch, state, sg, A.roff, A.rcol, 8, heavy, sh);
+        const int xp = D - 1 <= ls ? 0 : 1;
+        const int Lp = xp ? d - (D - 1) : D - 1;
+        const uint32_t *cur = cl[x] + sh.cs[x][L];
+        const int ncur = sh.ce[x][L] - sh.cs[x][L];
+        const uint32_t *prev = cl[xp] + sh.cs[xp][Lp];
+        const int nprev = sh.ce[xp][Lp] - sh.cs[xp][Lp];
+        if (D == ls + 1 && !sh.xovf) {
+          int ovf = 0;
+          for (int i = tid; i < ncross; i += kBiThreads) {
+            const unsigned long long add = sg[st_cidx(state[xt[i]])];
+            const unsigned long long old = atomicAdd((unsigned long long *)&sg[st_cidx(state[xh[i]])], add);
+            ovf |= old + add < old;
+          }
+          if (ovf) sh.ovf = 1;
+          __syncthreads();
+          continue;
+        }
+        const unsigned long long pull = bi_row_sum(cur, ncur, A.roff, sh);
+        const unsigned long long push = bi_row_sum(prev, nprev, A.off, sh);
+        if (pull <= push) {
+          bi_sigma_pull(cur, ncur, D, d, epoch, state, sg, A.roff, A.rcol, 8, heavy, sh);
+        } else {
+          bi_scan_rows(prev, nprev, A.off, A.col, bi_group(push, nprev), heavy, sh, [&](int u, int w) {
+            const uint64_t sw = state[w];
+            if (st_epoch(sw) == epoch && st_cone(sw) && st_dist(sw, d) == D) {
+              const unsigned long long add = sg[st_cidx(state[u])];
+              const unsigned long long old = atomicAdd((unsigned long long *)&sg[st_cidx(sw)], add);
+              if (old + add < old) sh.ovf = 1;
+            }
+          });
+        }
       }
       __syncthreads();
       if (sh.ovf && tid == 0) sh.status = 2;
       __syncthreads();
     }
     if (sh.status == 0) {
-      // ---- backward walk from t (warp 0), the forward sampler's rule
+      // ---- backward walk from t (warp 0), the forward sampler's rule: at v
+      // on distance L draw r below sigma_v and take the in-neighbour on L - 1
+      // (ascending id) whose running count first exceeds r.  When the cone
+      // level L - 1 has at most 32 nodes and v's row is long, the candidates
+      // are those cone nodes with an arc into v, ranked by id.
       if (tid < 32) {
         int32_t v = sh.t;
         uint64_t sv = sg[st_cidx(state[v])];
@@ -452,33 +556,58 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
         unsigned long long scanned = 0;
         for (int L = d; L >= 2; --L, ++step) {
           const uint64_t r = uniform_below64(A.seed, j, kPurposeWalk0 + step, sv);
-          uint64_t cum = 0;
+          const int xp = L - 1 <= ls ? 0 : 1;
+          const int Lp = xp ? d - (L - 1) : L - 1;
+          const int npc = sh.ce[xp][Lp] - sh.cs[xp][Lp];
+          const int64_t e0 = A.roff[v], e1 = A.roff[v + 1];
           int32_t pick = -1;
           uint64_t pick_sig = 0;
-          const int64_t e0 = A.roff[v], e1 = A.roff[v + 1];
-          for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
-            const int64_t i = base + lane;
-            const int32_t u = i < e1 ? A.rcol[i] : -1;
+          if (npc <= 32 && e1 - e0 > 64) {
+            const uint32_t *pc = cl[xp] + sh.cs[xp][Lp];
+            int32_t u = -1;
             uint64_t val = 0;
-            if (u >= 0) {
-              const uint64_t su = state[u];
-              if (st_epoch(su) == epoch && st_cone(su) && (st_side(su) ? d - st_level(su) : st_level(su)) == L - 1)
-                val = sg[st_cidx(su)];
+            if (lane < npc) {
+              u = (int32_t)pc[lane];
+              if (row_has(A.col, A.off[u], A.off[u + 1], v)) val = sg[st_cidx(state[u])];
+              scanned += 16;
             }
-            uint64_t pre = val;
-            for (int o2 = 1; o2 < 32; o2 <<= 1) {
-              const uint64_t y = __shfl_up_sync(0xffffffffu, pre, o2);
-              if (lane >= o2) pre += y;
+            uint64_t pre = 0;  // counts of the candidates with smaller ids
+            for (int k = 0; k < 32; ++k) {
+              const int32_t uk = __shfl_sync(0xffffffffu, u, k);
+              const uint64_t vk = __shfl_sync(0xffffffffu, val, k);
+              if (vk != 0 && uk < u) pre += vk;
             }
-            const unsigned hit = __ballot_sync(0xffffffffu, val != 0 && cum + pre > r);
+            const unsigned hit = __ballot_sync(0xffffffffu, val != 0 && pre <= r && r - pre < val);
             if (hit) {
               const int src = __ffs(hit) - 1;
               pick = __shfl_sync(0xffffffffu, u, src);
               pick_sig = __shfl_sync(0xffffffffu, val, src);
-            } else {
-              cum += __shfl_sync(0xffffffffu, pre, 31);
             }
-            scanned += 32;
+          } else {
+            uint64_t cum = 0;
+            for (int64_t base = e0; base < e1 && pick < 0; base += 32) {
+              const int64_t i = base + lane;
+              const int32_t u = i < e1 ? A.rcol[i] : -1;
+              uint64_t val = 0;
+              if (u >= 0) {
+                const uint64_t su = state[u];
+                if (st_epoch(su) == epoch && st_cone(su) && st_dist(su, d) == L - 1) val = sg[st_cidx(su)];
+              }
+              uint64_t pre = val;
+              for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, pre, o2);
+                if (lane >= o2) pre += y;
+              }
+              const unsigned hit = __ballot_sync(0xffffffffu, val != 0 && cum + pre > r);
+              if (hit) {
+                const int src = __ffs(hit) - 1;
+                pick = __shfl_sync(0xffffffffu, u, src);
+                pick_sig = __shfl_sync(0xffffffffu, val, src);
+              } else {
+                cum += __shfl_sync(0xffffffffu, pre, 31);
+              }
+              scanned += 32;
+            }
           }
           if (pick < 0) {  // cannot happen with consistent counts
             if (lane == 0) atomicExch(&A.ctl->err, CEN_EINVAL);

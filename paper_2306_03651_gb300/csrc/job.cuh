@@ -50,8 +50,9 @@ struct WaveWS {
 
 // Workspace of the bidirectional sampler (bidir.cu): for each of `nslots`
 // resident CTAs, a state word per node ([nslots][n], zeroed once; words are
-// epoch-stamped so nothing is cleared between samples), five lists of QC
-// entries (two ball queues, two cone lists, heavy rows) and 2 QC path counts.
+// epoch-stamped so nothing is cleared between samples), seven lists of QC
+// entries (two ball queues, two cone lists, heavy rows, crossing-arc tails and
+// heads) and 2 QC path counts.
 struct BiCtl {
   unsigned long long next;     // next sample, relative to the launch's first
   unsigned long long cursor;   // arena entries reserved

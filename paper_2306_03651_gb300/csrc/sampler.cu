@@ -1274,12 +1274,12 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
   if (!job->bws) job->bws.reset(new BiWS());
   BiWS &w = *job->bws;
   const int64_t QC = std::max<int64_t>(16, std::min<int64_t>(n, job->bidir_queue));
-  const size_t per_slot = 8 * (size_t)n + 5 * 4 * (size_t)QC + 2 * 8 * (size_t)QC;
+  const size_t per_slot = 8 * (size_t)n + 7 * 4 * (size_t)QC + 2 * 8 * (size_t)QC;
   const size_t fit = std::max<size_t>(1, job->bidir_budget / per_slot);
   const int slots = (int)std::min<size_t>((size_t)bidir_resident_slots(), fit);
   if (w.n != n || w.QC != QC || w.nslots != slots) {
     w.state.ensure_exact(8 * (size_t)n * slots, st);
-    w.lists.ensure_exact(4 * 5 * (size_t)QC * slots, st);
+    w.lists.ensure_exact(4 * 7 * (size_t)QC * slots, st);
     w.sig.ensure_exact(8 * 2 * (size_t)QC * slots, st);
     w.epochs.ensure(4 * (size_t)slots, st);
     CEN_CK(cudaMemsetAsync(w.state.p, 0, 8 * (size_t)n * slots, st));

@@ -318,11 +318,19 @@ def test_stats_and_timing():
     job.greedy_cover(10)
     job.mcera(10)
     st = job.stats()
-    assert st["pairs"]["launches"] >= 1 and st["walk"]["launches"] >= 1
+    assert st["bidir"]["launches"] >= 1 and st["bidir"]["units"] > 0
+    assert st["bidir"]["ms"] > 0 and st["bidir"]["timed"] == st["bidir"]["launches"]
+    assert st["greedy"]["launches"] >= 1 and st["select"]["launches"] >= 1
+    job.reset_stats()
+    assert job.stats()["bidir"]["launches"] == 0
+    waves = P.Job(P.Graph.of(g), 1, 10)
+    waves.set_param(P.PARAM_SAMPLER, P.SAMPLER_WAVES)
+    waves.set_timing(True)
+    waves.sample(2048)
+    st = waves.stats()
+    assert st["pairs"]["launches"] >= 1 and st["walk"]["launches"] >= 1 and st["bidir"]["launches"] == 0
     assert st["expand_pull"]["launches"] + st["expand_push"]["launches"] >= 1
     assert st["walk"]["ms"] > 0 and st["walk"]["timed"] == st["walk"]["launches"]
-    job.reset_stats()
-    assert job.stats()["walk"]["launches"] == 0
 
 
 # ---------------------------------------------------------------- full size
