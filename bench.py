@@ -56,6 +56,9 @@ def parse():
                          "64-job BA workload, one job at a time vs batched; serve: Poisson request stream; "
                          "tsweep: fixed-m rounds over the number t of Rademacher vectors (SD bound and time); "
                          "schedule: time to certified eps with the doubling and the paper's sample schedule")
+    ap.add_argument("--sampler", type=int, default=0, help="0 bidirectional (default), 1 bit-parallel waves")
+    ap.add_argument("--bidir-budget", type=float, default=0, help="bytes of bidirectional workspace (0: default)")
+    ap.add_argument("--bidir-queue", type=int, default=0, help="nodes per ball / cone list (0: default)")
     ap.add_argument("--tsweep-m", type=int, default=500000)
     ap.add_argument("--tsweep-t", default="1,10,50,100,250,500")
     ap.add_argument("--tsweep-k", type=int, default=50)
@@ -185,6 +188,16 @@ def merge_stats(acc, st):
             a[f] += v[f]
 
 
+def apply_sampler_args(P, graph, args):
+    """Sampler choice and workspace limits as defaults for every job on the graph."""
+    if args.sampler:
+        graph.set_param(P.PARAM_SAMPLER, args.sampler)
+    if args.bidir_budget:
+        graph.set_param(P.PARAM_BIDIR_BUDGET, args.bidir_budget)
+    if args.bidir_queue:
+        graph.set_param(P.PARAM_BIDIR_QUEUE, args.bidir_queue)
+
+
 def run_gpu(args, rank, world):
     import torch
     import paper_2306_03651_gb300 as P
@@ -195,6 +208,7 @@ def run_gpu(args, rank, world):
     wl = make()
     g = wl.graph
     graph = P.Graph.of(g)
+    apply_sampler_args(P, graph, args)
     M = args.m
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
     seed0 = rank_seed(rank)
@@ -239,6 +253,7 @@ def run_gpu(args, rank, world):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             gg = P.Graph(g.n, off_h.numpy(), col_h.numpy(), g.directed)
+            apply_sampler_args(P, gg, args)
             job = P.Job(gg, seed0 + 2000 + s, wl.t)
             job.sample(M)
             S, cov = job.greedy_cover(wl.k)

@@ -233,10 +233,17 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
                                     bit-parallel sampler for what exceeds its per-CTA limits (default);
                                     1: bit-parallel waves only.  Hyper-edges are identical. */
 #define CEN_PARAM_BIDIR_BUDGET 6 /* device bytes for the bidirectional sampler's per-CTA workspace,
-                                    >= 2^20 (default 2^32); fewer CTAs run when it is small */
+                                    >= 2^20 (default 2^34); fewer CTAs run when it is small.  One CTA
+                                    needs 8 n + 60 min(n, queue) bytes */
 #define CEN_PARAM_BIDIR_QUEUE 7  /* nodes one CTA may hold per ball or cone side, 16 .. 2^27 (default
-                                    2^18, at most n); larger searches go to the bit-parallel sampler */
+                                    2^17, at most n); larger searches go to the bit-parallel sampler */
 int cen_job_set_param(cen_job *job, int32_t param, double value);
+/* Releases the device memory the library keeps for reuse once jobs end: idle
+ * bidirectional-sampler workspaces (up to four, each as large as
+ * CEN_PARAM_BIDIR_BUDGET allows) and the unused part of the current device's
+ * stream-ordered memory pool, which the library sets to keep freed memory.
+ * Synchronizes the device.  Later jobs allocate again. */
+int cen_release_cached(void);
 /* How the job's samples were drawn so far: samples the bidirectional search
  * left whole to the bit-parallel sampler (*deferred_search), samples whose walk
  * it left to it (*deferred_walk), and the CTAs (slots) the bidirectional search

@@ -92,6 +92,7 @@ def _load():
         "cen_job_set_timing": ([vp, ip], ip),
         "cen_job_stats": ([vp, vp, vp], ip),
         "cen_job_sampler_info": ([vp, vp, vp, vp], ip),
+        "cen_release_cached": ([], ip),
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
         "cen_run_batch": ([vp, i32, i32, vp], ip),
@@ -294,6 +295,11 @@ class Job:
         _check(_lib.cen_job_stats(self.h, arr, ctypes.byref(nc)), "cen_job_stats")
         return {arr[i].name.decode(): dict(launches=arr[i].launches, ms=arr[i].ms, timed=arr[i].timed,
                                            units=arr[i].units) for i in range(nc.value)}
+
+
+def release_cached():
+    """``cen_release_cached``: frees device memory kept for reuse after jobs end."""
+    _check(_lib.cen_release_cached(), "cen_release_cached")
 
 
 def bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i):

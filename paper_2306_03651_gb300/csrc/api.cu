@@ -310,6 +310,7 @@ int cen_job_free(cen_job *job) {
     cudaStream_t st = job->st;
     cudaStreamSynchronize(st);
     void *h = job->host;
+    cen::bidir_give(std::move(job->bws));  // idle, since the stream has drained
     delete job;
     CEN_CK(cudaStreamSynchronize(st));
     if (h) cudaFreeHost(h);
@@ -539,6 +540,18 @@ int cen_job_set_param(cen_job *job, int32_t param, double value) {
   CEN_API_BEGIN
   CEN_REQUIRE(job, CEN_EINVAL, "cen_job_set_param: null job");
   apply_param(job, param, value);
+  CEN_API_END
+}
+
+int cen_release_cached(void) {
+  CEN_API_BEGIN
+  cen::bidir_drop_cached();
+  int dev = 0;
+  CEN_CK(cudaGetDevice(&dev));
+  cudaMemPool_t pool;
+  CEN_CK(cudaDeviceGetDefaultMemPool(&pool, dev));
+  CEN_CK(cudaDeviceSynchronize());  // the dropped workspaces are freed in stream order
+  CEN_CK(cudaMemPoolTrimTo(pool, 0));
   CEN_API_END
 }
 

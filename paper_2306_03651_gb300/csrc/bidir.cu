@@ -26,6 +26,7 @@
 // ("walk" deferral, distance known).  A cone side is part of its ball, so it
 // always fits.
 #include <algorithm>
+#include <mutex>
 
 #include "job.cuh"
 
@@ -632,6 +633,50 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
 
 // ------------------------------------------------------------------ host
 int bidir_resident_slots() { return resident_grid((const void *)k_bidir, kBiThreads); }
+
+namespace {
+constexpr size_t kBiCacheMax = 4;
+struct BiCache {
+  std::mutex mu;
+  std::vector<std::unique_ptr<BiWS>> idle;  // oldest first
+};
+// Never destroyed: nothing is freed after the CUDA runtime has unloaded.
+BiCache &bi_cache() {
+  static BiCache *c = new BiCache();
+  return *c;
+}
+}  // namespace
+
+std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int slots) {
+  BiCache &c = bi_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  for (size_t i = c.idle.size(); i-- > 0;) {
+    BiWS &w = *c.idle[i];
+    if (w.dev == dev && w.n == n && w.QC == QC && w.nslots == slots) {
+      std::unique_ptr<BiWS> out = std::move(c.idle[i]);
+      c.idle.erase(c.idle.begin() + (ptrdiff_t)i);
+      return out;
+    }
+  }
+  return nullptr;
+}
+
+void bidir_give(std::unique_ptr<BiWS> w) {
+  if (!w) return;
+  // the job's stream may be gone before these buffers are: free them in order on the legacy stream
+  for (DevBuf *b : {&w->state, &w->lists, &w->sig, &w->epochs, &w->ctl, &w->aoff, &w->dsearch, &w->dwalk, &w->arena})
+    b->st = nullptr;
+  BiCache &c = bi_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  c.idle.push_back(std::move(w));
+  if (c.idle.size() > kBiCacheMax) c.idle.erase(c.idle.begin());
+}
+
+void bidir_drop_cached() {
+  BiCache &c = bi_cache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  c.idle.clear();
+}
 
 void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap) {
   const cen_graph *g = job->g;

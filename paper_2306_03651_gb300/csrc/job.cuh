@@ -66,7 +66,16 @@ struct BiWS {
   int nslots = 0;
   int64_t QC = 0;
   int32_t n = 0;
+  int dev = -1;
 };
+// A finished job's workspace is kept for the next job of the same shape on the
+// same device (its state words stay valid under the persisting epochs, so it
+// is not cleared again); at most a few are kept.
+std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int slots);
+void bidir_give(std::unique_ptr<BiWS> w);
+void bidir_drop_cached();
+// Lets the current device's stream-ordered pool keep freed memory for reuse.
+void keep_pool_memory();
 
 }  // namespace cen
 
@@ -103,8 +112,8 @@ struct cen_job {
   // bidirectional sampler
   std::unique_ptr<cen::BiWS> bws;
   int sampler = 0;                          // 0 bidirectional (bit-parallel for what it defers), 1 bit-parallel
-  size_t bidir_budget = (size_t)4 << 30;    // bytes of per-slot workspace
-  int64_t bidir_queue = (int64_t)1 << 18;   // entries per ball / cone list
+  size_t bidir_budget = (size_t)16 << 30;   // bytes of per-slot workspace
+  int64_t bidir_queue = (int64_t)1 << 17;   // entries per ball / cone list
   uint64_t bidir_deferred_search = 0;       // samples it left whole to the bit-parallel sampler
   uint64_t bidir_deferred_walk = 0;         // samples whose walk it left (distance known)
 };

@@ -315,3 +315,24 @@ extern "C" int cen_debug_fail_alloc(int64_t n) {
   cen::g_fail_alloc.store(n);
   return CEN_OK;
 }
+
+namespace cen {
+// Stream-ordered frees return memory to the device's default pool; with the
+// release threshold at its maximum the pool keeps it mapped for the next
+// allocation instead of handing it back at every synchronisation.  Once per
+// device; cen_release_cached trims the pool.
+void keep_pool_memory() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+}  // namespace cen

@@ -1277,21 +1277,32 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
   const size_t per_slot = 8 * (size_t)n + 7 * 4 * (size_t)QC + 2 * 8 * (size_t)QC;
   const size_t fit = std::max<size_t>(1, job->bidir_budget / per_slot);
   const int slots = (int)std::min<size_t>((size_t)bidir_resident_slots(), fit);
-  if (w.n != n || w.QC != QC || w.nslots != slots) {
-    w.state.ensure_exact(8 * (size_t)n * slots, st);
-    w.lists.ensure_exact(4 * 7 * (size_t)QC * slots, st);
-    w.sig.ensure_exact(8 * 2 * (size_t)QC * slots, st);
-    w.epochs.ensure(4 * (size_t)slots, st);
-    CEN_CK(cudaMemsetAsync(w.state.p, 0, 8 * (size_t)n * slots, st));
-    CEN_CK(cudaMemsetAsync(w.epochs.p, 0, 4 * (size_t)slots, st));
-    w.n = n;
-    w.QC = QC;
-    w.nslots = slots;
+  int dev = 0;
+  CEN_CK(cudaGetDevice(&dev));
+  if (!(w.n == n && w.QC == QC && w.nslots == slots && w.dev == dev)) {
+    if (w.nslots) bidir_give(std::move(job->bws));  // another shape: keep this one for later jobs
+    job->bws = bidir_take(dev, n, QC, slots);
+    if (!job->bws) job->bws.reset(new BiWS());
   }
-  w.ctl.ensure(sizeof(BiCtl), st);
-  w.aoff.ensure(8 * (size_t)m_new, st);
-  w.dsearch.ensure(8 * (size_t)m_new, st);
-  w.dwalk.ensure(8 * (size_t)m_new, st);
+  BiWS &wk = *job->bws;
+  if (wk.nslots == 0) {
+    keep_pool_memory();
+    wk.state.ensure_exact(8 * (size_t)n * slots, st);
+    wk.lists.ensure_exact(4 * 7 * (size_t)QC * slots, st);
+    wk.sig.ensure_exact(8 * 2 * (size_t)QC * slots, st);
+    wk.epochs.ensure(4 * (size_t)slots, st);
+    CEN_CK(cudaMemsetAsync(wk.state.p, 0, 8 * (size_t)n * slots, st));
+    CEN_CK(cudaMemsetAsync(wk.epochs.p, 0, 4 * (size_t)slots, st));
+    wk.n = n;
+    wk.QC = QC;
+    wk.nslots = slots;
+    wk.dev = dev;
+  }
+  for (DevBuf *b : {&wk.state, &wk.lists, &wk.sig, &wk.epochs}) b->st = st;
+  wk.ctl.ensure(sizeof(BiCtl), st);
+  wk.aoff.ensure(8 * (size_t)m_new, st);
+  wk.dsearch.ensure(8 * (size_t)m_new, st);
+  wk.dwalk.ensure(8 * (size_t)m_new, st);
 }
 
 // Bidirectional form: one CTA per sample writes its members to an arena;

@@ -58,23 +58,30 @@ class Result:
         return self.end_s - self.arrival_s
 
 
-def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: float = 8.0, levels: int = 16) -> int:
+def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: float = 8.0, levels: int = 16,
+                       bidir_budget: int = 16 << 30, bidir_queue: int = 1 << 17, resident_ctas: int = 608) -> int:
     """Upper estimate of one job's device memory (admission policy, not the method).
 
-    Wave workspace: `levels` + 6 arrays of n*G words (G = wave words, at most 32
-    and at most 1 GB per array) and the initial cone-arc log (2 n G records of
-    24 bytes); sample store for m_cap samples: offsets, endpoints, distance,
-    sign words and members (twice: samples and the incidence); AMCERA table
-    R[t][n] and greedy / incidence arrays."""
+    Bidirectional sampler: one workspace per resident CTA (a state word per node,
+    seven lists of `bidir_queue` entries, 2 `bidir_queue` path counts), as many
+    as fit in `bidir_budget`.  Wave workspace (the fallback): `levels` + 6 arrays
+    of n*G words (G = wave words, at most 32 and at most 1 GB per array) and the
+    initial cone-arc log (2 n G records of 24 bytes); sample store for m_cap
+    samples: offsets, endpoints, distance, sign words and members (twice: samples
+    and the incidence), plus the member arena; AMCERA table R[t][n] and greedy /
+    incidence arrays."""
+    qc = max(16, min(n, bidir_queue))
+    per_slot = 8 * n + 7 * 4 * qc + 2 * 8 * qc
+    bidir = min(resident_ctas, max(1, bidir_budget // per_slot)) * per_slot
     G = 32
     while G > 1 and n * G * 8 > (1 << 30):
         G //= 2
     words = n * G
     wave = 8 * words * (levels + 6) + 24 * 2 * words
     nw = (t + 31) // 32
-    store = m_cap * (8 + 12 + 4 * nw) + 2 * 4 * int(m_cap * avg_hyperedge)
+    store = m_cap * (8 + 12 + 4 * nw) + 3 * 4 * int(m_cap * avg_hyperedge)
     node = n * (4 * t + 4 * 4 + 8)
-    return int(wave + store + node)
+    return int(bidir + wave + store + node)
 
 
 class Server:

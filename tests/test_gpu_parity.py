@@ -108,6 +108,22 @@ def test_bidirectional_level_cap_deferral():
     assert ref["d"].max() > 2 * 1023
 
 
+def test_workspace_reuse_across_jobs():
+    """Jobs that take a finished job's cached workspace (stale state words under later
+    epochs), interleaved with jobs of another shape, and jobs after the cache is
+    released, all draw the oracle's samples."""
+    refs = {name: oracle_samples(GRAPHS[name], 23, 1200)[2] for name in ("ba300", "rmat12_lcc")}
+    graphs = {name: P.Graph.of(GRAPHS[name]) for name in refs}
+    for round_ in range(3):
+        for name in ("ba300", "rmat12_lcc", "ba300"):
+            job = P.Job(graphs[name], 23, 10)
+            job.sample(1200)
+            assert_same_samples(job.samples(), refs[name])
+            job.close()
+        if round_ == 1:
+            P.release_cached()
+
+
 def test_sample_split_invariance():
     g = GRAPHS["ba300"]
     _, _, ref = oracle_samples(g, 5, 1000)
