@@ -234,9 +234,14 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
                                     1: bit-parallel waves only.  Hyper-edges are identical. */
 #define CEN_PARAM_BIDIR_BUDGET 6 /* device bytes for the bidirectional sampler's per-CTA workspace,
                                     >= 2^20 (default 2^34); fewer CTAs run when it is small.  One CTA
-                                    needs 8 n + 60 min(n, queue) bytes */
+                                    needs 8 n + 28 q + 8 h + 8 max(2 q, h) bytes (q = min(n, queue),
+                                    h = table entries) */
 #define CEN_PARAM_BIDIR_QUEUE 7  /* nodes one CTA may hold per ball or cone side, 16 .. 2^27 (default
                                     2^17, at most n); larger searches go to the bit-parallel sampler */
+#define CEN_PARAM_BIDIR_TABLE 8  /* entries of each CTA's node table: a power of two in 2^10 .. 2^24,
+                                    0 for none (one word per node only), or -1 (default) to size all
+                                    CTAs' tables to about 80 MiB so that they stay in L2; a search
+                                    that fills half its table moves to one word per node */
 int cen_job_set_param(cen_job *job, int32_t param, double value);
 /* Releases the device memory the library keeps for reuse once jobs end: idle
  * bidirectional-sampler workspaces (up to four, each as large as

@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 PARAM_WAVE_WORDS, PARAM_WAVE_STREAMS, PARAM_PUSH_RATIO, PARAM_LEVEL_BUDGET = 1, 2, 3, 4
-PARAM_SAMPLER, PARAM_BIDIR_BUDGET, PARAM_BIDIR_QUEUE = 5, 6, 7
+PARAM_SAMPLER, PARAM_BIDIR_BUDGET, PARAM_BIDIR_QUEUE, PARAM_BIDIR_TABLE = 5, 6, 7, 8
 SAMPLER_BIDIR, SAMPLER_WAVES = 0, 1
 SCHEDULE_DOUBLING, SCHEDULE_PAPER, SCHEDULE_EXTRAPOLATE = 0, 1, 2
 RULE_CENTRA, RULE_HEDGE_P = 0, 1

@@ -199,6 +199,13 @@ static void apply_param(cen_job *job, int32_t param, double value) {
       CEN_REQUIRE(value >= (1 << 20), CEN_EINVAL, "cen_job_set_param: bidirectional budget must be >= 1 MiB");
       job->bidir_budget = (size_t)value;
       break;
+    case CEN_PARAM_BIDIR_TABLE: {
+      const int64_t h = (int64_t)value;
+      CEN_REQUIRE(value == -1 || value == 0 || (h >= 1024 && h <= ((int64_t)1 << 24) && (h & (h - 1)) == 0),
+                  CEN_EINVAL, "cen_job_set_param: table entries must be -1, 0 or a power of two in [2^10, 2^24]");
+      job->bidir_table = h;
+      break;
+    }
     case CEN_PARAM_BIDIR_QUEUE:
       CEN_REQUIRE(value >= 16 && value <= (double)(1 << 27), CEN_EINVAL,
                   "cen_job_set_param: bidirectional queue must be in [16, 2^27]");
@@ -292,8 +299,8 @@ int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, c
     const int w = atoi(e);
     if (w >= 1 && w <= 8) job->wave_streams = w;
   }
-  for (int p = 1; p <= 7; ++p)  // the graph's tuned defaults override the environment
-    if (g->param[p] != 0) apply_param(job, p, g->param[p]);
+  for (int p = 1; p <= 8; ++p)  // the graph's tuned defaults override the environment
+    if (g->param_set[p]) apply_param(job, p, g->param[p]);
   try {
     job->stats.init(job->st);
   } catch (...) {
@@ -567,10 +574,11 @@ int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t
 int cen_graph_set_param(cen_graph *g, int32_t param, double value) {
   CEN_API_BEGIN
   CEN_REQUIRE(g, CEN_EINVAL, "cen_graph_set_param: null graph");
-  CEN_REQUIRE(param >= 1 && param <= 7, CEN_EINVAL, "cen_graph_set_param: unknown parameter");
+  CEN_REQUIRE(param >= 1 && param <= 8, CEN_EINVAL, "cen_graph_set_param: unknown parameter");
   cen_job probe;  // validates the value with the job rules
   apply_param(&probe, param, value);
   g->param[param] = value;
+  g->param_set[param] = true;
   CEN_API_END
 }
 

@@ -19,6 +19,12 @@
 // node, so these counts equal a full BFS's wherever the walk reads them, and
 // which side grew when changes only the cost.
 //
+// Node state lives in a small per-CTA hash table while the search is small
+// (open addressing, linear probing, entries stamped with a per-CTA epoch so
+// nothing is cleared between samples), sized so that all CTAs' tables stay in
+// L2; a search that fills half of it moves to a direct array of one word per
+// node and redoes the level it was building.
+//
 // Work the per-CTA resources cannot hold is left to the bit-parallel
 // sampler, which gives the identical hyper-edge: more than kBiMaxLevels
 // levels on one side or more than QC nodes in one ball ("search" deferral,
@@ -38,18 +44,105 @@ constexpr int kBiThreads = 256;
 constexpr int kBiWarps = kBiThreads / 32;
 constexpr int kBiMaxLevels = 1024;  // levels per side (0 .. kBiMaxLevels - 1)
 constexpr int kBiHeavy = 256;       // rows longer than this are scanned by the whole block
-constexpr uint32_t kBiEpochMax = (1u << 20) - 1;
+constexpr uint32_t kDirectEpochMax = (1u << 20) - 1;
+constexpr uint32_t kHashEpochMax = (1u << 16) - 1;
 
-// State word of one (slot, node): epoch 20 | cone index 28 | cone 1 | side 1 | level 14.
-// A word whose epoch differs from the slot's current one is unvisited.
+// Both word formats keep level (14 bits), side and cone in the low 16 bits.
+//   direct word of node v: epoch 20 | cone index 28 | cone 1 | side 1 | level 14
+//   table entry:           node 31 | epoch 16 | cone 1 | side 1 | level 14
 constexpr uint64_t kConeBit = 1ull << 15;
-__device__ __forceinline__ uint32_t st_epoch(uint64_t s) { return (uint32_t)(s >> 44); }
 __device__ __forceinline__ int st_level(uint64_t s) { return (int)(s & 0x3FFFu); }
 __device__ __forceinline__ int st_side(uint64_t s) { return (int)((s >> 14) & 1u); }
 __device__ __forceinline__ bool st_cone(uint64_t s) { return (s & kConeBit) != 0; }
-__device__ __forceinline__ int64_t st_cidx(uint64_t s) { return (int64_t)((s >> 16) & 0xFFFFFFFull); }
-__device__ __forceinline__ uint64_t st_make(uint32_t epoch, int side, int level) {
+__device__ __forceinline__ uint32_t d_epoch(uint64_t s) { return (uint32_t)(s >> 44); }
+__device__ __forceinline__ int64_t d_cidx(uint64_t s) { return (int64_t)((s >> 16) & 0xFFFFFFFull); }
+__device__ __forceinline__ uint64_t d_make(uint32_t epoch, int side, int level) {
   return ((uint64_t)epoch << 44) | ((uint64_t)side << 14) | (uint64_t)level;
+}
+__device__ __forceinline__ uint32_t h_epoch(uint64_t s) { return (uint32_t)((s >> 16) & 0xFFFFu); }
+__device__ __forceinline__ uint32_t h_node(uint64_t s) { return (uint32_t)(s >> 32); }
+__device__ __forceinline__ uint64_t h_make(uint32_t v, uint32_t epoch, int side, int level) {
+  return ((uint64_t)v << 32) | ((uint64_t)epoch << 16) | ((uint64_t)side << 14) | (uint64_t)level;
+}
+__device__ __forceinline__ uint32_t h_slot(uint32_t v, uint32_t mask) {
+  uint32_t h = v * 0x9E3779B1u;
+  return (h ^ (h >> 15)) & mask;
+}
+__device__ __forceinline__ uint64_t ld_vol(const uint64_t *p) { return *(const volatile uint64_t *)p; }
+
+// Where the current search keeps node state: the table (hash = 1) or the
+// direct words.  Copied into every thread; changed only between barriers.
+struct BiMap {
+  uint64_t *direct;
+  uint64_t *tab;
+  uint32_t hmask;
+  uint32_t dep, hep;  // current direct and table epochs
+  int hash;
+};
+
+// State of v in the current search (0 if unvisited); idx receives the index
+// of its path count (table position, or the cone index of a direct word).
+__device__ __forceinline__ uint64_t bi_find(const BiMap &M, int v, int64_t &idx) {
+  if (!M.hash) {
+    const uint64_t e = ld_vol(&M.direct[v]);
+    if (d_epoch(e) != M.dep) return 0;
+    idx = d_cidx(e);
+    return e;
+  }
+  uint32_t p = h_slot((uint32_t)v, M.hmask);
+  for (uint32_t k = 0; k <= M.hmask; ++k) {
+    const uint64_t e = ld_vol(&M.tab[p]);
+    if (h_epoch(e) != M.hep) return 0;  // a free position ends the probe: v was never inserted
+    if (h_node(e) == (uint32_t)v) {
+      idx = p;
+      return e;
+    }
+    p = (p + 1) & M.hmask;
+  }
+  return 0;
+}
+
+__device__ __forceinline__ uint64_t bi_find(const BiMap &M, int v) {
+  int64_t idx;
+  return bi_find(M, v, idx);
+}
+
+// Claims v for side x on `level`.  Returns 0 when this call claimed it, 1 when
+// it was already in the search (its state in *found).
+__device__ __forceinline__ int bi_claim(const BiMap &M, int v, int x, int level, uint64_t &found) {
+  if (!M.hash) {
+    const uint64_t e = ld_vol(&M.direct[v]);
+    if (d_epoch(e) == M.dep) {
+      found = e;
+      return 1;
+    }
+    const unsigned long long old = atomicCAS((unsigned long long *)&M.direct[v], (unsigned long long)e,
+                                             (unsigned long long)d_make(M.dep, x, level));
+    if (old == e) return 0;
+    found = old;
+    return 1;
+  }
+  const uint64_t mine = h_make((uint32_t)v, M.hep, x, level);
+  uint32_t p = h_slot((uint32_t)v, M.hmask);
+  for (uint32_t k = 0; k <= M.hmask; ++k) {
+    uint64_t e = ld_vol(&M.tab[p]);
+    for (;;) {
+      if (h_epoch(e) == M.hep) {
+        if (h_node(e) == (uint32_t)v) {
+          found = e;
+          return 1;
+        }
+        break;  // another node's entry: next position
+      }
+      const unsigned long long old =
+          atomicCAS((unsigned long long *)&M.tab[p], (unsigned long long)e, (unsigned long long)mine);
+      if (old == e) return 0;
+      e = old;  // taken meanwhile: look at it again
+    }
+    p = (p + 1) & M.hmask;
+  }
+  found = 0;
+  return 1;  // unreachable while the table is at most half full
 }
 
 struct BiShared {
@@ -60,28 +153,41 @@ struct BiShared {
   unsigned long long red[kBiWarps];
   unsigned long long addcost, sum, arcs;
   int added, nheavy, ccount[2], ncross;
+  int hcount, hfull;  // table entries of this search; set once it is half full
   int lvl[2];
   int met, ovf, xovf;
   int status, d;
   int s, t;
-  uint32_t epoch;
-  int clear;
+  uint32_t hep, dep;
+  int hash;
+  int clear_tab, clear_direct;
   unsigned long long j;
   long long abase;
 };
 
-// Sets the cone bit of w and, the first time, appends w to the cone list of
-// side x and stores its cone index (x QC + position) in the state word.
-__device__ __forceinline__ void bi_mark(uint64_t *state, uint32_t *clist, int x, int64_t QC, BiShared &sh, int w) {
-  const unsigned long long old = atomicOr((unsigned long long *)&state[w], (unsigned long long)kConeBit);
+// Sets the cone bit of v and, the first time, appends v to the cone list of
+// side x (a direct word also records its cone index, x QC + position).
+__device__ __forceinline__ void bi_mark(const BiMap &M, uint32_t *clist, int x, int64_t QC, BiShared &sh, int v) {
+  unsigned long long *w;
+  if (M.hash) {
+    int64_t p = -1;
+    if (!bi_find(M, v, p)) {  // cannot happen: every cone node is in its ball
+      sh.ovf = 1;
+      return;
+    }
+    w = (unsigned long long *)&M.tab[p];
+  } else {
+    w = (unsigned long long *)&M.direct[v];
+  }
+  const unsigned long long old = atomicOr(w, (unsigned long long)kConeBit);
   if (old & kConeBit) return;
   const int pos = atomicAdd(&sh.ccount[x], 1);
   if (pos >= QC) {
     sh.ovf = 1;
     return;
   }
-  clist[pos] = (uint32_t)w;
-  atomicOr((unsigned long long *)&state[w], (unsigned long long)((int64_t)x * QC + pos) << 16);
+  clist[pos] = (uint32_t)v;
+  if (!M.hash) atomicOr(w, (unsigned long long)((int64_t)x * QC + pos) << 16);
 }
 
 // Group size for a list of cnt rows with `arcs` arcs in all: the power of two
@@ -93,7 +199,7 @@ __device__ __forceinline__ int bi_group(unsigned long long arcs, int cnt) {
   return gs;
 }
 
-// sh.sum = sum over list[0, cnt) of the row lengths in o.  Called by all threads.
+// Sum over list[0, cnt) of the row lengths in o.  Called by all threads.
 __device__ unsigned long long bi_row_sum(const uint32_t *list, int cnt, const int64_t *__restrict__ o, BiShared &sh) {
   const int tid = threadIdx.x;
   unsigned long long a = 0;
@@ -161,9 +267,9 @@ __device__ __forceinline__ int st_dist(uint64_t s, int d) { return st_side(s) ? 
 // Pull form of one path-count level: each cone node of list[0, cnt) (all at
 // distance D from s) gets the sum of the counts of its in-neighbours that are
 // cone nodes at D - 1.  A sum that wraps 2^64 raises sh.ovf.
-__device__ void bi_sigma_pull(const uint32_t *list, int cnt, int D, int d, uint32_t epoch,
-                              const uint64_t *__restrict__ state, uint64_t *sg, const int64_t *__restrict__ roff,
-                              const int32_t *__restrict__ rcol, int gs, uint32_t *heavy, BiShared &sh) {
+__device__ void bi_sigma_pull(const uint32_t *list, int cnt, int D, int d, const BiMap &M, uint64_t *sg,
+                              const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol, int gs,
+                              uint32_t *heavy, BiShared &sh) {
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) sh.nheavy = 0;
   __syncthreads();
@@ -180,12 +286,15 @@ __device__ void bi_sigma_pull(const uint32_t *list, int cnt, int D, int d, uint3
     }
     unsigned long long acc = 0;
     for (int64_t e = e0 + gl; e < e1; e += gs) {
-      const uint64_t su = state[rcol[e]];
-      if (st_epoch(su) == epoch && st_cone(su) && st_dist(su, d) == D - 1) add_carry(acc, sg[st_cidx(su)], ovf);
+      int64_t iu = 0;
+      const uint64_t su = bi_find(M, rcol[e], iu);
+      if (su && st_cone(su) && st_dist(su, d) == D - 1) add_carry(acc, sg[iu], ovf);
     }
     for (int o2 = gs >> 1; o2; o2 >>= 1) add_carry(acc, __shfl_xor_sync(gmask, acc, o2, gs), ovf);
     if (gl == 0) {
-      sg[st_cidx(state[v])] = acc;
+      int64_t iv = 0;
+      bi_find(M, v, iv);
+      sg[iv] = acc;
       arcs += (unsigned long long)(e1 - e0);
     }
   }
@@ -198,8 +307,9 @@ __device__ void bi_sigma_pull(const uint32_t *list, int cnt, int D, int d, uint3
     unsigned long long acc = 0;
     int hovf = 0;
     for (int64_t e = e0 + tid; e < e1; e += kBiThreads) {
-      const uint64_t su = state[rcol[e]];
-      if (st_epoch(su) == epoch && st_cone(su) && st_dist(su, d) == D - 1) add_carry(acc, sg[st_cidx(su)], hovf);
+      int64_t iu = 0;
+      const uint64_t su = bi_find(M, rcol[e], iu);
+      if (su && st_cone(su) && st_dist(su, d) == D - 1) add_carry(acc, sg[iu], hovf);
     }
     for (int o2 = 16; o2; o2 >>= 1) add_carry(acc, __shfl_xor_sync(0xffffffffu, acc, o2), hovf);
     if (lane == 0) sh.red[tid >> 5] = acc;
@@ -210,7 +320,9 @@ __device__ void bi_sigma_pull(const uint32_t *list, int cnt, int D, int d, uint3
       int tovf = 0;
       for (int w = 0; w < kBiWarps; ++w) add_carry(tot, sh.red[w], tovf);
       if (tovf) sh.ovf = 1;
-      sg[st_cidx(state[v])] = tot;
+      int64_t iv = 0;
+      bi_find(M, v, iv);
+      sg[iv] = tot;
       arcs += (unsigned long long)(e1 - e0);
     }
     __syncthreads();
@@ -240,11 +352,14 @@ struct BiArgs {
   const int64_t *off, *roff;
   const int32_t *col, *rcol;
   uint64_t seed, j0, count;
-  uint64_t *state;    // [slots][n]
+  uint64_t *state;    // [slots][n] direct words
+  uint64_t *tab;      // [slots][H] table entries (H = hmask + 1; unused when hmask = 0)
+  uint32_t hmask;
   uint32_t *lists;    // [slots][7][QC]: ball queues and cone lists (forward, backward), heavy rows,
                       //                  crossing-arc tails and heads
-  uint64_t *sig;      // [slots][2 QC]: path counts by cone index
-  uint32_t *epochs;   // [slots]
+  uint64_t *sig;      // [slots][SG]: path counts by table position or cone index
+  int64_t SG;
+  uint32_t *epochs;   // [slots][2]: direct epoch, table epoch
   int64_t QC;
   int32_t *ps, *pt, *pd;
   int *bmax;
@@ -261,32 +376,56 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
   __shared__ BiShared sh;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t QC = A.QC;
-  uint64_t *state = A.state + (size_t)blockIdx.x * (size_t)A.n;
   uint32_t *lists = A.lists + (size_t)blockIdx.x * 7 * (size_t)QC;
   uint32_t *q[2] = {lists, lists + QC};
   uint32_t *cl[2] = {lists + 2 * QC, lists + 3 * QC};
   uint32_t *heavy = lists + 4 * QC;
   uint32_t *xt = lists + 5 * QC, *xh = lists + 6 * QC;
-  uint64_t *sg = A.sig + (size_t)blockIdx.x * 2 * (size_t)QC;
+  uint64_t *sg = A.sig + (size_t)blockIdx.x * (size_t)A.SG;
+  uint64_t *direct = A.state + (size_t)blockIdx.x * (size_t)A.n;
+  uint64_t *tab = A.hmask ? A.tab + (size_t)blockIdx.x * ((size_t)A.hmask + 1) : nullptr;
+  const uint32_t H = A.hmask ? A.hmask + 1 : 0;
+  uint32_t *epochs = A.epochs + 2 * (size_t)blockIdx.x;
   if (tid == 0) sh.arcs = 0;
   for (;;) {
     __syncthreads();
     if (tid == 0) {
       sh.j = atomicAdd(&A.ctl->next, 1ull);
-      uint32_t e = A.epochs[blockIdx.x] + 1;
-      sh.clear = e > kBiEpochMax;
-      if (sh.clear) e = 1;
-      A.epochs[blockIdx.x] = e;
-      sh.epoch = e;
+      sh.clear_tab = sh.clear_direct = 0;
+      if (H) {  // a table epoch per sample; the direct epoch only when a search moves there
+        uint32_t e = epochs[1] + 1;
+        if (e > kHashEpochMax) {
+          e = 1;
+          sh.clear_tab = 1;
+        }
+        epochs[1] = e;
+        sh.hep = e;
+        sh.dep = epochs[0];
+        sh.hash = 1;
+      } else {
+        uint32_t e = epochs[0] + 1;
+        if (e > kDirectEpochMax) {
+          e = 1;
+          sh.clear_direct = 1;
+        }
+        epochs[0] = e;
+        sh.dep = e;
+        sh.hep = 0;
+        sh.hash = 0;
+      }
     }
     __syncthreads();
     if (sh.j >= A.count) break;
-    if (sh.clear) {  // the epoch field wrapped: this slot's words start over
-      for (int64_t v = tid; v < A.n; v += kBiThreads) state[v] = 0;
+    if (sh.clear_tab) {  // the epoch field wrapped: the table starts over
+      for (uint32_t p = tid; p < H; p += kBiThreads) tab[p] = 0;
       __syncthreads();
     }
+    if (sh.clear_direct) {
+      for (int64_t v = tid; v < A.n; v += kBiThreads) direct[v] = 0;
+      __syncthreads();
+    }
+    BiMap M{direct, tab, A.hmask, sh.dep, sh.hep, sh.hash};
     const uint64_t j = A.j0 + sh.j;
-    const uint32_t epoch = sh.epoch;
     if (tid == 0) {
       // Sec. 5: s uniform over V; t uniform over V \ {s} (Sec. 3.1 pairs u != v)
       const int32_t s = (int32_t)uniform_below64(A.seed, j, kPurposeS, (uint64_t)A.n);
@@ -296,8 +435,9 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       A.pt[j] = t;
       sh.s = s;
       sh.t = t;
-      state[s] = st_make(epoch, 0, 0);
-      state[t] = st_make(epoch, 1, 0);
+      uint64_t f;
+      bi_claim(M, s, 0, 0, f);
+      bi_claim(M, t, 1, 0, f);
       q[0][0] = (uint32_t)s;
       q[1][0] = (uint32_t)t;
       sh.lo[0][0] = 0;
@@ -307,6 +447,8 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       sh.lvl[0] = sh.lvl[1] = 0;
       sh.hcost[0][0] = (unsigned long long)(A.off[s + 1] - A.off[s]);
       sh.hcost[1][0] = (unsigned long long)(A.roff[t + 1] - A.roff[t]);
+      sh.hcount = 2;
+      sh.hfull = 0;
       sh.met = 0;
       sh.ovf = 0;
       sh.xovf = 0;
@@ -331,41 +473,75 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       if (tid == 0) {
         sh.added = 0;
         sh.addcost = 0;
+        sh.ncross = 0;
+        sh.xovf = 0;
       }
       uint32_t *qx = q[x];
       const int64_t *o = x ? A.roff : A.off;
       const int32_t *c = x ? A.rcol : A.col;
-      const uint64_t mine = st_make(epoch, x, L + 1);
+      const int hlimit = (int)(H >> 1);
       bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
-        const uint64_t sw = *(volatile uint64_t *)&state[w];
-        if (st_epoch(sw) == epoch) {
-          if (st_side(sw) != x) {  // an arc between the balls: (tail, head) in s -> t direction
-            sh.met = 1;
-            const int pos = atomicAdd(&sh.ncross, 1);
-            if (pos < QC) {
-              xt[pos] = (uint32_t)(x ? w : v);
-              xh[pos] = (uint32_t)(x ? v : w);
-            } else {
-              sh.xovf = 1;
-            }
+        uint64_t sw = bi_find(M, w);
+        if (!sw) {
+          if (*(volatile int *)&sh.met || *(volatile int *)&sh.hfull) return;  // no more claims needed / possible
+          if (bi_claim(M, w, x, L + 1, sw) == 0) {
+            const int pos = atomicAdd(&sh.added, 1);
+            if ((int64_t)f1 + pos < QC)
+              qx[f1 + pos] = (uint32_t)w;
+            else
+              sh.ovf = 1;
+            atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
+            if (M.hash && atomicAdd(&sh.hcount, 1) + 1 >= hlimit) sh.hfull = 1;
+            return;
           }
-          return;
+          if (!sw) return;
         }
-        if (*(volatile int *)&sh.met) return;  // the distance is known: no more claims
-        const unsigned long long old =
-            atomicCAS((unsigned long long *)&state[w], (unsigned long long)sw, (unsigned long long)mine);
-        if (old == sw) {
-          const int pos = atomicAdd(&sh.added, 1);
-          if ((int64_t)f1 + pos < QC)
-            qx[f1 + pos] = (uint32_t)w;
-          else
-            sh.ovf = 1;
-          atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
+        if (st_side(sw) != x) {  // an arc between the balls: (tail, head) in s -> t direction
+          sh.met = 1;
+          const int pos = atomicAdd(&sh.ncross, 1);
+          if (pos < QC) {
+            xt[pos] = (uint32_t)(x ? w : v);
+            xh[pos] = (uint32_t)(x ? v : w);
+          } else {
+            sh.xovf = 1;
+          }
         }
       });
       if (sh.met) {
         if (tid == 0) sh.d = sh.lvl[0] + sh.lvl[1] + 1;
         break;
+      }
+      if (sh.hfull) {
+        // the table is half full: the search so far moves to direct words
+        // of a new epoch, without the half-built level, which is redone
+        if (tid == 0) {
+          uint32_t e = epochs[0] + 1;
+          sh.clear_direct = e > kDirectEpochMax;
+          if (sh.clear_direct) e = 1;
+          epochs[0] = e;
+          sh.dep = e;
+        }
+        __syncthreads();
+        if (sh.clear_direct) {
+          for (int64_t v = tid; v < A.n; v += kBiThreads) direct[v] = 0;
+          __syncthreads();
+        }
+        const uint32_t dep = sh.dep;
+        for (uint32_t p = tid; p < H; p += kBiThreads) {
+          const uint64_t e = tab[p];
+          if (h_epoch(e) == M.hep && !(st_side(e) == x && st_level(e) == L + 1))
+            direct[h_node(e)] = d_make(dep, st_side(e), st_level(e));
+        }
+        M.hash = 0;
+        M.dep = dep;
+        __syncthreads();
+        if (tid == 0) {
+          sh.hash = 0;
+          sh.hfull = 0;
+          sh.ovf = 0;
+        }
+        __syncthreads();
+        continue;
       }
       if (sh.ovf) {
         if (tid == 0) sh.status = 1;
@@ -414,18 +590,18 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       // ---- crossing arcs: forward level ls -> backward level lb
       if (!sh.xovf) {
         for (int i = tid; i < ncross; i += kBiThreads) {
-          bi_mark(state, cl[0], 0, QC, sh, (int)xt[i]);
-          bi_mark(state, cl[1], 1, QC, sh, (int)xh[i]);
+          bi_mark(M, cl[0], 0, QC, sh, (int)xt[i]);
+          bi_mark(M, cl[1], 1, QC, sh, (int)xh[i]);
         }
         __syncthreads();
       } else {
         const int f0 = sh.lo[0][ls], f1 = sh.lo[0][ls + 1];
         bi_scan_rows(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][ls], f1 - f0), heavy, sh,
                      [&](int v, int w) {
-                       const uint64_t sw = state[w];
-                       if (st_epoch(sw) == epoch && st_side(sw) == 1 && st_level(sw) == lb) {
-                         bi_mark(state, cl[0], 0, QC, sh, v);
-                         bi_mark(state, cl[1], 1, QC, sh, w);
+                       const uint64_t sw = bi_find(M, w);
+                       if (sw && st_side(sw) == 1 && st_level(sw) == lb) {
+                         bi_mark(M, cl[0], 0, QC, sh, v);
+                         bi_mark(M, cl[1], 1, QC, sh, w);
                        }
                      });
       }
@@ -443,17 +619,15 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
         const unsigned long long in_cone = bi_row_sum(cl[0] + a, b - a, A.roff, sh);
         if (in_cone <= sh.hcost[0][L - 1]) {
           bi_scan_rows(cl[0] + a, b - a, A.roff, A.rcol, 8, heavy, sh, [&](int, int u) {
-            const uint64_t su = state[u];
-            if (st_epoch(su) == epoch && st_side(su) == 0 && st_level(su) == L - 1)
-              bi_mark(state, cl[0], 0, QC, sh, u);
+            const uint64_t su = bi_find(M, u);
+            if (su && st_side(su) == 0 && st_level(su) == L - 1) bi_mark(M, cl[0], 0, QC, sh, u);
           });
         } else {
           const int f0 = sh.lo[0][L - 1], f1 = sh.lo[0][L];
           bi_scan_rows(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][L - 1], f1 - f0), heavy, sh,
                        [&](int u, int w) {
-                         const uint64_t sw = state[w];
-                         if (st_epoch(sw) == epoch && st_cone(sw) && st_side(sw) == 0 && st_level(sw) == L)
-                           bi_mark(state, cl[0], 0, QC, sh, u);
+                         const uint64_t sw = bi_find(M, w);
+                         if (sw && st_cone(sw) && st_side(sw) == 0 && st_level(sw) == L) bi_mark(M, cl[0], 0, QC, sh, u);
                        });
         }
         if (tid == 0) {
@@ -469,17 +643,15 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
         const unsigned long long out_cone = bi_row_sum(cl[1] + a, b - a, A.off, sh);
         if (out_cone <= sh.hcost[1][L - 1]) {
           bi_scan_rows(cl[1] + a, b - a, A.off, A.col, 8, heavy, sh, [&](int, int y) {
-            const uint64_t sy = state[y];
-            if (st_epoch(sy) == epoch && st_side(sy) == 1 && st_level(sy) == L - 1)
-              bi_mark(state, cl[1], 1, QC, sh, y);
+            const uint64_t sy = bi_find(M, y);
+            if (sy && st_side(sy) == 1 && st_level(sy) == L - 1) bi_mark(M, cl[1], 1, QC, sh, y);
           });
         } else {
           const int f0 = sh.lo[1][L - 1], f1 = sh.lo[1][L];
           bi_scan_rows(q[1] + f0, f1 - f0, A.roff, A.rcol, bi_group(sh.hcost[1][L - 1], f1 - f0), heavy, sh,
                        [&](int y, int xv) {
-                         const uint64_t sx = state[xv];
-                         if (st_epoch(sx) == epoch && st_cone(sx) && st_side(sx) == 1 && st_level(sx) == L)
-                           bi_mark(state, cl[1], 1, QC, sh, y);
+                         const uint64_t sx = bi_find(M, xv);
+                         if (sx && st_cone(sx) && st_side(sx) == 1 && st_level(sx) == L) bi_mark(M, cl[1], 1, QC, sh, y);
                        });
         }
         if (tid == 0) {
@@ -499,10 +671,18 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       // pulled over the cone nodes' in-arcs or pushed over the out-arcs of
       // the level below, whichever is fewer; the crossing level adds along
       // the logged crossing arcs
-      for (int i = tid; i < sh.ccount[0]; i += kBiThreads) sg[i] = 0;
-      for (int i = tid; i < sh.ccount[1]; i += kBiThreads) sg[QC + i] = 0;
+      for (int x = 0; x < 2; ++x)
+        for (int i = tid; i < sh.ccount[x]; i += kBiThreads) {
+          int64_t iv = 0;
+          bi_find(M, (int)cl[x][i], iv);
+          sg[iv] = 0;
+        }
       __syncthreads();
-      if (tid == 0) sg[st_cidx(state[sh.s])] = 1;
+      if (tid == 0) {
+        int64_t is = 0;
+        bi_find(M, sh.s, is);
+        sg[is] = 1;
+      }
       __syncthreads();
       for (int D = 1; D <= d && !sh.ovf; ++D) {
         const int x = D <= ls ? 0 : 1;
@@ -516,8 +696,11 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
         if (D == ls + 1 && !sh.xovf) {
           int ovf = 0;
           for (int i = tid; i < ncross; i += kBiThreads) {
-            const unsigned long long add = sg[st_cidx(state[xt[i]])];
-            const unsigned long long old = atomicAdd((unsigned long long *)&sg[st_cidx(state[xh[i]])], add);
+            int64_t it = 0, ih = 0;
+            bi_find(M, (int)xt[i], it);
+            bi_find(M, (int)xh[i], ih);
+            const unsigned long long add = sg[it];
+            const unsigned long long old = atomicAdd((unsigned long long *)&sg[ih], add);
             ovf |= old + add < old;
           }
           if (ovf) sh.ovf = 1;
@@ -527,13 +710,16 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
         const unsigned long long pull = bi_row_sum(cur, ncur, A.roff, sh);
         const unsigned long long push = bi_row_sum(prev, nprev, A.off, sh);
         if (pull <= push) {
-          bi_sigma_pull(cur, ncur, D, d, epoch, state, sg, A.roff, A.rcol, 8, heavy, sh);
+          bi_sigma_pull(cur, ncur, D, d, M, sg, A.roff, A.rcol, 8, heavy, sh);
         } else {
           bi_scan_rows(prev, nprev, A.off, A.col, bi_group(push, nprev), heavy, sh, [&](int u, int w) {
-            const uint64_t sw = state[w];
-            if (st_epoch(sw) == epoch && st_cone(sw) && st_dist(sw, d) == D) {
-              const unsigned long long add = sg[st_cidx(state[u])];
-              const unsigned long long old = atomicAdd((unsigned long long *)&sg[st_cidx(sw)], add);
+            int64_t iw = 0;
+            const uint64_t sw = bi_find(M, w, iw);
+            if (sw && st_cone(sw) && st_dist(sw, d) == D) {
+              int64_t iu = 0;
+              bi_find(M, u, iu);
+              const unsigned long long add = sg[iu];
+              const unsigned long long old = atomicAdd((unsigned long long *)&sg[iw], add);
               if (old + add < old) sh.ovf = 1;
             }
           });
@@ -551,7 +737,9 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       // are those cone nodes with an arc into v, ranked by id.
       if (tid < 32) {
         int32_t v = sh.t;
-        uint64_t sv = sg[st_cidx(state[v])];
+        int64_t it = 0;
+        bi_find(M, v, it);
+        uint64_t sv = sg[it];
         int32_t *out = A.arena + sh.abase;
         uint32_t step = 0;
         unsigned long long scanned = 0;
@@ -569,7 +757,11 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
             uint64_t val = 0;
             if (lane < npc) {
               u = (int32_t)pc[lane];
-              if (row_has(A.col, A.off[u], A.off[u + 1], v)) val = sg[st_cidx(state[u])];
+              if (row_has(A.col, A.off[u], A.off[u + 1], v)) {
+                int64_t iu = 0;
+                bi_find(M, u, iu);
+                val = sg[iu];
+              }
               scanned += 16;
             }
             uint64_t pre = 0;  // counts of the candidates with smaller ids
@@ -591,8 +783,9 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
               const int32_t u = i < e1 ? A.rcol[i] : -1;
               uint64_t val = 0;
               if (u >= 0) {
-                const uint64_t su = state[u];
-                if (st_epoch(su) == epoch && st_cone(su) && st_dist(su, d) == L - 1) val = sg[st_cidx(su)];
+                int64_t iu = 0;
+                const uint64_t su = bi_find(M, u, iu);
+                if (su && st_cone(su) && st_dist(su, d) == L - 1) val = sg[iu];
               }
               uint64_t pre = val;
               for (int o2 = 1; o2 < 32; o2 <<= 1) {
@@ -647,12 +840,12 @@ BiCache &bi_cache() {
 }
 }  // namespace
 
-std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int slots) {
+std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int64_t H, int slots) {
   BiCache &c = bi_cache();
   std::lock_guard<std::mutex> lk(c.mu);
   for (size_t i = c.idle.size(); i-- > 0;) {
     BiWS &w = *c.idle[i];
-    if (w.dev == dev && w.n == n && w.QC == QC && w.nslots == slots) {
+    if (w.dev == dev && w.n == n && w.QC == QC && w.H == H && w.nslots == slots) {
       std::unique_ptr<BiWS> out = std::move(c.idle[i]);
       c.idle.erase(c.idle.begin() + (ptrdiff_t)i);
       return out;
@@ -664,7 +857,8 @@ std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int slots) {
 void bidir_give(std::unique_ptr<BiWS> w) {
   if (!w) return;
   // the job's stream may be gone before these buffers are: free them in order on the legacy stream
-  for (DevBuf *b : {&w->state, &w->lists, &w->sig, &w->epochs, &w->ctl, &w->aoff, &w->dsearch, &w->dwalk, &w->arena})
+  for (DevBuf *b : {&w->state, &w->tab, &w->lists, &w->sig, &w->epochs, &w->ctl, &w->aoff, &w->dsearch, &w->dwalk,
+                    &w->arena})
     b->st = nullptr;
   BiCache &c = bi_cache();
   std::lock_guard<std::mutex> lk(c.mu);
@@ -693,8 +887,11 @@ void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap) 
   a.j0 = j0;
   a.count = count;
   a.state = w.state.as<uint64_t>();
+  a.tab = w.H ? w.tab.as<uint64_t>() : nullptr;
+  a.hmask = w.H ? (uint32_t)(w.H - 1) : 0u;
   a.lists = w.lists.as<uint32_t>();
   a.sig = w.sig.as<uint64_t>();
+  a.SG = w.SG;
   a.epochs = w.epochs.as<uint32_t>();
   a.QC = w.QC;
   a.ps = job->ps.as<int32_t>();

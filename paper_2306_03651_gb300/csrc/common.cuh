@@ -268,7 +268,8 @@ struct cen_graph {
   cudaStream_t st = nullptr;
   cen::DevBuf off, col, roff, rcol;  // roff/rcol empty when undirected (alias off/col)
   cen::ChunkTable out_chunks, in_chunks_own;  // in_chunks_own used only when directed
-  double param[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // tuning defaults for jobs on this graph (0 = unset)
+  double param[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // tuning defaults for jobs on this graph
+  bool param_set[9] = {};                           // which of them were set
   const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
   const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
   const cen::ChunkTable &in_chunks() const { return directed ? in_chunks_own : out_chunks; }

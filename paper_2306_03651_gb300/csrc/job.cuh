@@ -49,10 +49,11 @@ struct WaveWS {
 };
 
 // Workspace of the bidirectional sampler (bidir.cu): for each of `nslots`
-// resident CTAs, a state word per node ([nslots][n], zeroed once; words are
-// epoch-stamped so nothing is cleared between samples), seven lists of QC
-// entries (two ball queues, two cone lists, heavy rows, crossing-arc tails and
-// heads) and 2 QC path counts.
+// resident CTAs, a table of H entries and a state word per node ([nslots][n]),
+// both zeroed once (entries and words are epoch-stamped, so nothing is
+// cleared between samples), seven lists of QC entries (two ball queues, two
+// cone lists, heavy rows, crossing-arc tails and heads) and max(2 QC, H) path
+// counts.
 struct BiCtl {
   unsigned long long next;     // next sample, relative to the launch's first
   unsigned long long cursor;   // arena entries reserved
@@ -62,16 +63,18 @@ struct BiCtl {
   int pad;
 };
 struct BiWS {
-  DevBuf state, lists, sig, epochs, ctl, aoff, dsearch, dwalk, arena;
+  DevBuf state, tab, lists, sig, epochs, ctl, aoff, dsearch, dwalk, arena;
   int nslots = 0;
   int64_t QC = 0;
+  int64_t H = 0;   // table entries per slot (0: direct words only)
+  int64_t SG = 0;  // path counts per slot
   int32_t n = 0;
   int dev = -1;
 };
 // A finished job's workspace is kept for the next job of the same shape on the
 // same device (its state words stay valid under the persisting epochs, so it
 // is not cleared again); at most a few are kept.
-std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int slots);
+std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int64_t H, int slots);
 void bidir_give(std::unique_ptr<BiWS> w);
 void bidir_drop_cached();
 // Lets the current device's stream-ordered pool keep freed memory for reuse.
@@ -114,6 +117,7 @@ struct cen_job {
   int sampler = 0;                          // 0 bidirectional (bit-parallel for what it defers), 1 bit-parallel
   size_t bidir_budget = (size_t)16 << 30;   // bytes of per-slot workspace
   int64_t bidir_queue = (int64_t)1 << 17;   // entries per ball / cone list
+  int64_t bidir_table = -1;                 // table entries per CTA (-1: sized for L2, 0: none)
   uint64_t bidir_deferred_search = 0;       // samples it left whole to the bit-parallel sampler
   uint64_t bidir_deferred_walk = 0;         // samples whose walk it left (distance known)
 };

@@ -1267,38 +1267,56 @@ int64_t offsets_from_distances(cen_job *job, uint64_t m0, uint64_t m_new) {
   return *h;
 }
 
-// Workspace for as many resident CTAs as the byte budget allows (at least one).
+// Workspace for as many resident CTAs as the byte budget allows (at least
+// one).  The table is sized so that all CTAs' tables take about kTableL2
+// bytes (they stay in L2), unless a size was set.
+constexpr size_t kTableL2 = (size_t)80 << 20;
+
 void bidir_setup(cen_job *job, uint64_t m_new) {
   const int32_t n = job->g->n;
   cudaStream_t st = job->st;
-  if (!job->bws) job->bws.reset(new BiWS());
-  BiWS &w = *job->bws;
   const int64_t QC = std::max<int64_t>(16, std::min<int64_t>(n, job->bidir_queue));
-  const size_t per_slot = 8 * (size_t)n + 7 * 4 * (size_t)QC + 2 * 8 * (size_t)QC;
-  const size_t fit = std::max<size_t>(1, job->bidir_budget / per_slot);
-  const int slots = (int)std::min<size_t>((size_t)bidir_resident_slots(), fit);
+  int64_t H = 0;
+  auto per_slot = [&](int64_t h) {
+    return 8 * (size_t)n + 7 * 4 * (size_t)QC + 8 * (size_t)h + 8 * (size_t)std::max<int64_t>(2 * QC, h);
+  };
+  const size_t res = (size_t)bidir_resident_slots();
+  int slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(0)));
+  if (job->bidir_table < 0) {
+    H = 1024;
+    while ((size_t)(2 * H) * 8 * (size_t)slots <= kTableL2 && 2 * H <= 2 * QC) H *= 2;
+  } else {
+    H = job->bidir_table;
+  }
+  if (H) slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(H)));
+  const int64_t SG = std::max<int64_t>(2 * QC, H);
   int dev = 0;
   CEN_CK(cudaGetDevice(&dev));
-  if (!(w.n == n && w.QC == QC && w.nslots == slots && w.dev == dev)) {
-    if (w.nslots) bidir_give(std::move(job->bws));  // another shape: keep this one for later jobs
-    job->bws = bidir_take(dev, n, QC, slots);
+  BiWS *cur = job->bws.get();
+  if (!(cur && cur->n == n && cur->QC == QC && cur->H == H && cur->nslots == slots && cur->dev == dev)) {
+    if (cur && cur->nslots) bidir_give(std::move(job->bws));  // another shape: keep this one for later jobs
+    job->bws = bidir_take(dev, n, QC, H, slots);
     if (!job->bws) job->bws.reset(new BiWS());
   }
   BiWS &wk = *job->bws;
   if (wk.nslots == 0) {
     keep_pool_memory();
     wk.state.ensure_exact(8 * (size_t)n * slots, st);
+    if (H) wk.tab.ensure_exact(8 * (size_t)H * slots, st);
     wk.lists.ensure_exact(4 * 7 * (size_t)QC * slots, st);
-    wk.sig.ensure_exact(8 * 2 * (size_t)QC * slots, st);
-    wk.epochs.ensure(4 * (size_t)slots, st);
+    wk.sig.ensure_exact(8 * (size_t)SG * slots, st);
+    wk.epochs.ensure(8 * (size_t)slots, st);
     CEN_CK(cudaMemsetAsync(wk.state.p, 0, 8 * (size_t)n * slots, st));
-    CEN_CK(cudaMemsetAsync(wk.epochs.p, 0, 4 * (size_t)slots, st));
+    if (H) CEN_CK(cudaMemsetAsync(wk.tab.p, 0, 8 * (size_t)H * slots, st));
+    CEN_CK(cudaMemsetAsync(wk.epochs.p, 0, 8 * (size_t)slots, st));
     wk.n = n;
     wk.QC = QC;
+    wk.H = H;
+    wk.SG = SG;
     wk.nslots = slots;
     wk.dev = dev;
   }
-  for (DevBuf *b : {&wk.state, &wk.lists, &wk.sig, &wk.epochs}) b->st = st;
+  for (DevBuf *b : {&wk.state, &wk.tab, &wk.lists, &wk.sig, &wk.epochs}) b->st = st;
   wk.ctl.ensure(sizeof(BiCtl), st);
   wk.aoff.ensure(8 * (size_t)m_new, st);
   wk.dsearch.ensure(8 * (size_t)m_new, st);

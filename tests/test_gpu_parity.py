@@ -95,6 +95,19 @@ def test_bidirectional_search_deferral(name):
     assert info["deferred_search"] > 0 and info["slots"] > 0
 
 
+@pytest.mark.parametrize("table", [0, 1024])
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_dir", "grid_rewired", "rmat12_lcc"])
+def test_bidirectional_node_table_and_direct_words(name, table):
+    """Node state in direct words only (table 0), or in a 1,024-entry table that most
+    searches outgrow, moving to direct words mid-search: the oracle's samples either way."""
+    g = GRAPHS[name]
+    _, _, ref = oracle_samples(g, 29, 2000)
+    job = P.Job(P.Graph.of(g), 29, 10)
+    job.set_param(P.PARAM_BIDIR_TABLE, table)
+    job.sample(2000)
+    assert_same_samples(job.samples(), ref)
+
+
 def test_bidirectional_level_cap_deferral():
     """A 5000-cycle: pairs more than 2046 apart need over 1023 levels on one side, past
     the per-side level cap, and are searched by the bit-parallel sampler."""
