@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--sampler", type=int, default=0, help="0 bidirectional (default), 1 bit-parallel waves")
     ap.add_argument("--bidir-budget", type=float, default=0, help="bytes of bidirectional workspace (0: default)")
     ap.add_argument("--bidir-queue", type=int, default=0, help="nodes per ball / cone list (0: default)")
+    ap.add_argument("--bidir-table", type=int, default=-2,
+                    help="node-table entries per CTA (-1: sized for L2, 0: none; -2: library default)")
     ap.add_argument("--tsweep-m", type=int, default=500000)
     ap.add_argument("--tsweep-t", default="1,10,50,100,250,500")
     ap.add_argument("--tsweep-k", type=int, default=50)
@@ -196,6 +198,8 @@ def apply_sampler_args(P, graph, args):
         graph.set_param(P.PARAM_BIDIR_BUDGET, args.bidir_budget)
     if args.bidir_queue:
         graph.set_param(P.PARAM_BIDIR_QUEUE, args.bidir_queue)
+    if args.bidir_table != -2:
+        graph.set_param(P.PARAM_BIDIR_TABLE, args.bidir_table)
 
 
 def run_gpu(args, rank, world):
