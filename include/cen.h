@@ -241,7 +241,9 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
 #define CEN_PARAM_BIDIR_TABLE 8  /* entries of each CTA's node table: a power of two in 2^10 .. 2^24,
                                     0 for none (one word per node only), or -1 (default) to size all
                                     CTAs' tables to about 80 MiB so that they stay in L2; a search
-                                    that fills half its table moves to one word per node */
+                                    that fills half its table moves to one word per node.  With -1,
+                                    once a call of 1,024 or more samples sees most searches move,
+                                    later jobs on the graph use no table */
 int cen_job_set_param(cen_job *job, int32_t param, double value);
 /* Releases the device memory the library keeps for reuse once jobs end: idle
  * bidirectional-sampler workspaces (up to four, each as large as

@@ -40,9 +40,9 @@ namespace cen {
 
 namespace {
 
-constexpr int kBiThreads = 256;
+constexpr int kBiThreads = 128;
 constexpr int kBiWarps = kBiThreads / 32;
-constexpr int kBiMaxLevels = 1024;  // levels per side (0 .. kBiMaxLevels - 1)
+constexpr int kBiMaxLevels = 256;   // levels per side (0 .. kBiMaxLevels - 1)
 constexpr int kBiHeavy = 256;       // rows longer than this are scanned by the whole block
 constexpr uint32_t kDirectEpochMax = (1u << 20) - 1;
 constexpr uint32_t kHashEpochMax = (1u << 16) - 1;
@@ -539,6 +539,7 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
           sh.hash = 0;
           sh.hfull = 0;
           sh.ovf = 0;
+          atomicAdd(&A.ctl->nmigrate, 1ull);
         }
         __syncthreads();
         continue;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -270,6 +271,9 @@ struct cen_graph {
   cen::ChunkTable out_chunks, in_chunks_own;  // in_chunks_own used only when directed
   double param[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // tuning defaults for jobs on this graph
   bool param_set[9] = {};                           // which of them were set
+  // Set once most bidirectional searches on this graph outgrew their node
+  // table: later jobs (without an explicit table size) use direct words only.
+  mutable std::atomic<bool> bidir_table_off{false};
   const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
   const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
   const cen::ChunkTable &in_chunks() const { return directed ? in_chunks_own : out_chunks; }

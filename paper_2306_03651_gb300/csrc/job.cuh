@@ -59,6 +59,7 @@ struct BiCtl {
   unsigned long long cursor;   // arena entries reserved
   unsigned long long nsearch;  // samples left whole to the bit-parallel sampler
   unsigned long long nwalk;    // samples whose walk is left to it (distance known)
+  unsigned long long nmigrate; // searches that outgrew their table
   int err;
   int pad;
 };

@@ -1282,7 +1282,9 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
   };
   const size_t res = (size_t)bidir_resident_slots();
   int slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(0)));
-  if (job->bidir_table < 0) {
+  if (job->bidir_table < 0 && job->g->bidir_table_off.load()) {
+    H = 0;
+  } else if (job->bidir_table < 0) {
     H = 1024;
     while ((size_t)(2 * H) * 8 * (size_t)slots <= kTableL2 && 2 * H <= 2 * QC) H *= 2;
   } else {
@@ -1339,6 +1341,7 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   CEN_CK(cudaStreamSynchronize(st));
   CEN_REQUIRE(hc->err == 0, hc->err, "cen_sample: inconsistent path counts in the bidirectional walk");
   const BiCtl h = *hc;
+  if (job->bidir_table < 0 && m_new >= 1024 && 2 * h.nmigrate > m_new) job->g->bidir_table_off.store(true);
   std::vector<uint64_t> search(h.nsearch), walk(h.nwalk);
   if (h.nsearch)
     CEN_CK(cudaMemcpyAsync(search.data(), bw.dsearch.p, 8 * h.nsearch, cudaMemcpyDeviceToHost, st));

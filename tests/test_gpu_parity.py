@@ -109,8 +109,8 @@ def test_bidirectional_node_table_and_direct_words(name, table):
 
 
 def test_bidirectional_level_cap_deferral():
-    """A 5000-cycle: pairs more than 2046 apart need over 1023 levels on one side, past
-    the per-side level cap, and are searched by the bit-parallel sampler."""
+    """A 5000-cycle: pairs far apart need more levels on one side than the per-side level
+    cap (255) and are searched by the bit-parallel sampler."""
     n = 5000
     g = I.from_edges(n, np.arange(n), (np.arange(n) + 1) % n, False)
     _, _, ref = oracle_samples(g, 2, 300)
@@ -118,7 +118,7 @@ def test_bidirectional_level_cap_deferral():
     job.sample(300)
     assert_same_samples(job.samples(), ref)
     assert job.sampler_info()["deferred_search"] > 0
-    assert ref["d"].max() > 2 * 1023
+    assert ref["d"].max() > 2 * 255
 
 
 def test_workspace_reuse_across_jobs():
