@@ -175,12 +175,16 @@ def gpu_step(P, graph, wl, M, seed):
     job = P.Job(graph, seed, wl.t)
     job.set_timing(True)
     job.sample(M)
+    SAMPLER_INFO.append(job.sampler_info())
     S, cov = job.greedy_cover(wl.k)
     Rnum, Wnum, b = job.mcera(wl.k)
     stop, bd = P.bounds(cov, M, int(Rnum.sum()), wl.t, Wnum, b, wl.eps, wl.delta, 1)
     st = job.stats()
     job.close()
     return st, (S, cov, Rnum, Wnum, b, stop, bd)
+
+
+SAMPLER_INFO = []  # per step: how the bidirectional sampler handled the pairs
 
 
 def merge_stats(acc, st):
@@ -309,6 +313,7 @@ def run_gpu(args, rank, world):
                    "n": g.n, "arcs": g.nnz, "pairs_per_step": M, "l2": "flushed (256 MB write) between steps",
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+        "sampler": SAMPLER_INFO[-1] if SAMPLER_INFO else None,
         "wall_s": wall,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "units": v["units"]}
                     for k, v in sorted(stats.items(), key=lambda kv: -kv[1]["ms"]) if v["launches"]},

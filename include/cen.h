@@ -234,16 +234,17 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
                                     1: bit-parallel waves only.  Hyper-edges are identical. */
 #define CEN_PARAM_BIDIR_BUDGET 6 /* device bytes for the bidirectional sampler's per-CTA workspace,
                                     >= 2^20 (default 2^34); fewer CTAs run when it is small.  One CTA
-                                    needs 8 n + 28 q + 8 h + 8 max(2 q, h) bytes (q = min(n, queue),
-                                    h = table entries) */
+                                    needs 8 h + 16 H + 28 q bytes (q = min(n, queue), H = the power of
+                                    two >= 4 q, h = small-table entries), whatever the graph */
 #define CEN_PARAM_BIDIR_QUEUE 7  /* nodes one CTA may hold per ball or cone side, 16 .. 2^27 (default
-                                    2^17, at most n); larger searches go to the bit-parallel sampler */
-#define CEN_PARAM_BIDIR_TABLE 8  /* entries of each CTA's node table: a power of two in 2^10 .. 2^24,
-                                    0 for none (one word per node only), or -1 (default) to size all
-                                    CTAs' tables to about 80 MiB so that they stay in L2; a search
-                                    that fills half its table moves to one word per node.  With -1,
-                                    once a call of 1,024 or more samples sees most searches move,
-                                    later jobs on the graph use no table */
+                                    2^16, at most n); larger searches go to the bit-parallel sampler */
+#define CEN_PARAM_BIDIR_TABLE 8  /* entries of each CTA's small node table: a power of two in
+                                    2^10 .. 2^24 (at most H / 2), 0 for none (searches use the large
+                                    table of H entries only), or -1 (default) to size all CTAs' small
+                                    tables to about 80 MiB so that they stay in L2; a search that
+                                    fills half of it moves to the large table.  With -1, once a call
+                                    of 1,024 or more samples sees most searches move, later jobs on
+                                    the graph use no small table */
 int cen_job_set_param(cen_job *job, int32_t param, double value);
 /* Releases the device memory the library keeps for reuse once jobs end: idle
  * bidirectional-sampler workspaces (up to four, each as large as
@@ -253,9 +254,11 @@ int cen_job_set_param(cen_job *job, int32_t param, double value);
 int cen_release_cached(void);
 /* How the job's samples were drawn so far: samples the bidirectional search
  * left whole to the bit-parallel sampler (*deferred_search), samples whose walk
- * it left to it (*deferred_walk), and the CTAs (slots) the bidirectional search
- * runs on (0 before its first use).  Any pointer may be NULL. */
-int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, int32_t *slots);
+ * it left to it (*deferred_walk), searches that outgrew the small node table
+ * (*migrated), and the CTAs (slots) the bidirectional search runs on (0 before
+ * its first use).  Any pointer may be NULL. */
+int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, uint64_t *migrated,
+                         int32_t *slots);
 /* Defaults for jobs created later on this graph (cen_job_create, cen_run, cen_run_batch);
  * they take precedence over the environment (CEN_WAVE_WORDS, CEN_WAVE_STREAMS). */
 int cen_graph_set_param(cen_graph *g, int32_t param, double value);

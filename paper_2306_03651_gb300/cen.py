@@ -91,7 +91,7 @@ def _load():
         "cen_job_copy_signs": ([vp, vp], ip),
         "cen_job_set_timing": ([vp, ip], ip),
         "cen_job_stats": ([vp, vp, vp], ip),
-        "cen_job_sampler_info": ([vp, vp, vp, vp], ip),
+        "cen_job_sampler_info": ([vp, vp, vp, vp, vp], ip),
         "cen_release_cached": ([], ip),
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
@@ -283,11 +283,11 @@ class Job:
         _check(_lib.cen_job_reset_stats(self.h), "cen_job_reset_stats")
 
     def sampler_info(self) -> dict:
-        """``cen_job_sampler_info``: deferred_search, deferred_walk, slots."""
-        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32()
-        _check(_lib.cen_job_sampler_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+        """``cen_job_sampler_info``: deferred_search, deferred_walk, migrated, slots."""
+        a, b, m, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32()
+        _check(_lib.cen_job_sampler_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m), ctypes.byref(c)),
                "cen_job_sampler_info")
-        return dict(deferred_search=a.value, deferred_walk=b.value, slots=c.value)
+        return dict(deferred_search=a.value, deferred_walk=b.value, migrated=m.value, slots=c.value)
 
     def stats(self) -> dict:
         arr = (cen_kstat * NKCLASS)()

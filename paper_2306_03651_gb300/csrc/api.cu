@@ -562,11 +562,13 @@ int cen_release_cached(void) {
   CEN_API_END
 }
 
-int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, int32_t *slots) {
+int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, uint64_t *migrated,
+                         int32_t *slots) {
   CEN_API_BEGIN
   CEN_REQUIRE(job, CEN_EINVAL, "cen_job_sampler_info: null job");
   if (deferred_search) *deferred_search = job->bidir_deferred_search;
   if (deferred_walk) *deferred_walk = job->bidir_deferred_walk;
+  if (migrated) *migrated = job->bidir_migrated;
   if (slots) *slots = job->bws ? job->bws->nslots : 0;
   CEN_API_END
 }

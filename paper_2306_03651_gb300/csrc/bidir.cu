@@ -19,11 +19,13 @@
 // node, so these counts equal a full BFS's wherever the walk reads them, and
 // which side grew when changes only the cost.
 //
-// Node state lives in a small per-CTA hash table while the search is small
-// (open addressing, linear probing, entries stamped with a per-CTA epoch so
-// nothing is cleared between samples), sized so that all CTAs' tables stay in
-// L2; a search that fills half of it moves to a direct array of one word per
-// node and redoes the level it was building.
+// Node state lives in per-CTA hash tables (open addressing, linear probing,
+// entries stamped with a per-CTA epoch so nothing is cleared between
+// samples): a small table sized so that all CTAs' tables stay in L2, and a
+// large one of 4 QC entries that always has room for both balls.  A search
+// starts in the small table; one that fills half of it moves to the large
+// table and redoes the level it was building.  Path counts are indexed by
+// table position.
 //
 // Work the per-CTA resources cannot hold is left to the bit-parallel
 // sampler, which gives the identical hyper-edge: more than kBiMaxLevels
@@ -44,21 +46,13 @@ constexpr int kBiThreads = 128;
 constexpr int kBiWarps = kBiThreads / 32;
 constexpr int kBiMaxLevels = 256;   // levels per side (0 .. kBiMaxLevels - 1)
 constexpr int kBiHeavy = 256;       // rows longer than this are scanned by the whole block
-constexpr uint32_t kDirectEpochMax = (1u << 20) - 1;
-constexpr uint32_t kHashEpochMax = (1u << 16) - 1;
+constexpr uint32_t kEpochMax = (1u << 16) - 1;
 
-// Both word formats keep level (14 bits), side and cone in the low 16 bits.
-//   direct word of node v: epoch 20 | cone index 28 | cone 1 | side 1 | level 14
-//   table entry:           node 31 | epoch 16 | cone 1 | side 1 | level 14
+// Table entry: node 31 | epoch 16 | cone 1 | side 1 | level 14.
 constexpr uint64_t kConeBit = 1ull << 15;
 __device__ __forceinline__ int st_level(uint64_t s) { return (int)(s & 0x3FFFu); }
 __device__ __forceinline__ int st_side(uint64_t s) { return (int)((s >> 14) & 1u); }
 __device__ __forceinline__ bool st_cone(uint64_t s) { return (s & kConeBit) != 0; }
-__device__ __forceinline__ uint32_t d_epoch(uint64_t s) { return (uint32_t)(s >> 44); }
-__device__ __forceinline__ int64_t d_cidx(uint64_t s) { return (int64_t)((s >> 16) & 0xFFFFFFFull); }
-__device__ __forceinline__ uint64_t d_make(uint32_t epoch, int side, int level) {
-  return ((uint64_t)epoch << 44) | ((uint64_t)side << 14) | (uint64_t)level;
-}
 __device__ __forceinline__ uint32_t h_epoch(uint64_t s) { return (uint32_t)((s >> 16) & 0xFFFFu); }
 __device__ __forceinline__ uint32_t h_node(uint64_t s) { return (uint32_t)(s >> 32); }
 __device__ __forceinline__ uint64_t h_make(uint32_t v, uint32_t epoch, int side, int level) {
@@ -70,34 +64,26 @@ __device__ __forceinline__ uint32_t h_slot(uint32_t v, uint32_t mask) {
 }
 __device__ __forceinline__ uint64_t ld_vol(const uint64_t *p) { return *(const volatile uint64_t *)p; }
 
-// Where the current search keeps node state: the table (hash = 1) or the
-// direct words.  Copied into every thread; changed only between barriers.
+// The table the current search uses.  Copied into every thread; changed only
+// between barriers.
 struct BiMap {
-  uint64_t *direct;
   uint64_t *tab;
-  uint32_t hmask;
-  uint32_t dep, hep;  // current direct and table epochs
-  int hash;
+  uint32_t mask;  // entries - 1
+  uint32_t ep;    // current epoch
 };
 
-// State of v in the current search (0 if unvisited); idx receives the index
-// of its path count (table position, or the cone index of a direct word).
+// State of v in the current search (0 if unvisited); idx receives its table
+// position, which also indexes its path count.
 __device__ __forceinline__ uint64_t bi_find(const BiMap &M, int v, int64_t &idx) {
-  if (!M.hash) {
-    const uint64_t e = ld_vol(&M.direct[v]);
-    if (d_epoch(e) != M.dep) return 0;
-    idx = d_cidx(e);
-    return e;
-  }
-  uint32_t p = h_slot((uint32_t)v, M.hmask);
-  for (uint32_t k = 0; k <= M.hmask; ++k) {
+  uint32_t p = h_slot((uint32_t)v, M.mask);
+  for (uint32_t k = 0; k <= M.mask; ++k) {
     const uint64_t e = ld_vol(&M.tab[p]);
-    if (h_epoch(e) != M.hep) return 0;  // a free position ends the probe: v was never inserted
+    if (h_epoch(e) != M.ep) return 0;  // a free position ends the probe: v was never inserted
     if (h_node(e) == (uint32_t)v) {
       idx = p;
       return e;
     }
-    p = (p + 1) & M.hmask;
+    p = (p + 1) & M.mask;
   }
   return 0;
 }
@@ -108,26 +94,14 @@ __device__ __forceinline__ uint64_t bi_find(const BiMap &M, int v) {
 }
 
 // Claims v for side x on `level`.  Returns 0 when this call claimed it, 1 when
-// it was already in the search (its state in *found).
+// it was already in the search (its state in *found, 0 if the table is full).
 __device__ __forceinline__ int bi_claim(const BiMap &M, int v, int x, int level, uint64_t &found) {
-  if (!M.hash) {
-    const uint64_t e = ld_vol(&M.direct[v]);
-    if (d_epoch(e) == M.dep) {
-      found = e;
-      return 1;
-    }
-    const unsigned long long old = atomicCAS((unsigned long long *)&M.direct[v], (unsigned long long)e,
-                                             (unsigned long long)d_make(M.dep, x, level));
-    if (old == e) return 0;
-    found = old;
-    return 1;
-  }
-  const uint64_t mine = h_make((uint32_t)v, M.hep, x, level);
-  uint32_t p = h_slot((uint32_t)v, M.hmask);
-  for (uint32_t k = 0; k <= M.hmask; ++k) {
+  const uint64_t mine = h_make((uint32_t)v, M.ep, x, level);
+  uint32_t p = h_slot((uint32_t)v, M.mask);
+  for (uint32_t k = 0; k <= M.mask; ++k) {
     uint64_t e = ld_vol(&M.tab[p]);
     for (;;) {
-      if (h_epoch(e) == M.hep) {
+      if (h_epoch(e) == M.ep) {
         if (h_node(e) == (uint32_t)v) {
           found = e;
           return 1;
@@ -139,10 +113,10 @@ __device__ __forceinline__ int bi_claim(const BiMap &M, int v, int x, int level,
       if (old == e) return 0;
       e = old;  // taken meanwhile: look at it again
     }
-    p = (p + 1) & M.hmask;
+    p = (p + 1) & M.mask;
   }
   found = 0;
-  return 1;  // unreachable while the table is at most half full
+  return 1;
 }
 
 struct BiShared {
@@ -153,33 +127,27 @@ struct BiShared {
   unsigned long long red[kBiWarps];
   unsigned long long addcost, sum, arcs;
   int added, nheavy, ccount[2], ncross;
-  int hcount, hfull;  // table entries of this search; set once it is half full
+  int hcount, hfull;  // small-table entries of this search; set once it is half full
   int lvl[2];
   int met, ovf, xovf;
   int status, d;
   int s, t;
-  uint32_t hep, dep;
-  int hash;
-  int clear_tab, clear_direct;
+  uint32_t ep;        // epoch of the table in use
+  int tier;           // 1: small table, 2: large table
+  int clear;          // the table in use must be cleared first
   unsigned long long j;
   long long abase;
 };
 
 // Sets the cone bit of v and, the first time, appends v to the cone list of
-// side x (a direct word also records its cone index, x QC + position).
+// side x.
 __device__ __forceinline__ void bi_mark(const BiMap &M, uint32_t *clist, int x, int64_t QC, BiShared &sh, int v) {
-  unsigned long long *w;
-  if (M.hash) {
-    int64_t p = -1;
-    if (!bi_find(M, v, p)) {  // cannot happen: every cone node is in its ball
-      sh.ovf = 1;
-      return;
-    }
-    w = (unsigned long long *)&M.tab[p];
-  } else {
-    w = (unsigned long long *)&M.direct[v];
+  int64_t p = -1;
+  if (!bi_find(M, v, p)) {  // cannot happen: every cone node is in its ball
+    sh.ovf = 1;
+    return;
   }
-  const unsigned long long old = atomicOr(w, (unsigned long long)kConeBit);
+  const unsigned long long old = atomicOr((unsigned long long *)&M.tab[p], (unsigned long long)kConeBit);
   if (old & kConeBit) return;
   const int pos = atomicAdd(&sh.ccount[x], 1);
   if (pos >= QC) {
@@ -187,7 +155,6 @@ __device__ __forceinline__ void bi_mark(const BiMap &M, uint32_t *clist, int x, 
     return;
   }
   clist[pos] = (uint32_t)v;
-  if (!M.hash) atomicOr(w, (unsigned long long)((int64_t)x * QC + pos) << 16);
 }
 
 // Group size for a list of cnt rows with `arcs` arcs in all: the power of two
@@ -352,14 +319,14 @@ struct BiArgs {
   const int64_t *off, *roff;
   const int32_t *col, *rcol;
   uint64_t seed, j0, count;
-  uint64_t *state;    // [slots][n] direct words
-  uint64_t *tab;      // [slots][H] table entries (H = hmask + 1; unused when hmask = 0)
-  uint32_t hmask;
+  uint64_t *tab1;     // [slots][H1] small tables (H1 = mask1 + 1; none when mask1 = 0)
+  uint32_t mask1;
+  uint64_t *tab2;     // [slots][H2] large tables
+  uint32_t mask2;
   uint32_t *lists;    // [slots][7][QC]: ball queues and cone lists (forward, backward), heavy rows,
                       //                  crossing-arc tails and heads
-  uint64_t *sig;      // [slots][SG]: path counts by table position or cone index
-  int64_t SG;
-  uint32_t *epochs;   // [slots][2]: direct epoch, table epoch
+  uint64_t *sig;      // [slots][H2]: path counts by table position
+  uint32_t *epochs;   // [slots][2]: epochs of the small and the large table
   int64_t QC;
   int32_t *ps, *pt, *pd;
   int *bmax;
@@ -381,50 +348,33 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
   uint32_t *cl[2] = {lists + 2 * QC, lists + 3 * QC};
   uint32_t *heavy = lists + 4 * QC;
   uint32_t *xt = lists + 5 * QC, *xh = lists + 6 * QC;
-  uint64_t *sg = A.sig + (size_t)blockIdx.x * (size_t)A.SG;
-  uint64_t *direct = A.state + (size_t)blockIdx.x * (size_t)A.n;
-  uint64_t *tab = A.hmask ? A.tab + (size_t)blockIdx.x * ((size_t)A.hmask + 1) : nullptr;
-  const uint32_t H = A.hmask ? A.hmask + 1 : 0;
+  const uint32_t H1 = A.mask1 ? A.mask1 + 1 : 0, H2 = A.mask2 + 1;
+  uint64_t *sg = A.sig + (size_t)blockIdx.x * (size_t)H2;
+  uint64_t *tab1 = H1 ? A.tab1 + (size_t)blockIdx.x * (size_t)H1 : nullptr;
+  uint64_t *tab2 = A.tab2 + (size_t)blockIdx.x * (size_t)H2;
   uint32_t *epochs = A.epochs + 2 * (size_t)blockIdx.x;
   if (tid == 0) sh.arcs = 0;
   for (;;) {
     __syncthreads();
     if (tid == 0) {
       sh.j = atomicAdd(&A.ctl->next, 1ull);
-      sh.clear_tab = sh.clear_direct = 0;
-      if (H) {  // a table epoch per sample; the direct epoch only when a search moves there
-        uint32_t e = epochs[1] + 1;
-        if (e > kHashEpochMax) {
-          e = 1;
-          sh.clear_tab = 1;
-        }
-        epochs[1] = e;
-        sh.hep = e;
-        sh.dep = epochs[0];
-        sh.hash = 1;
-      } else {
-        uint32_t e = epochs[0] + 1;
-        if (e > kDirectEpochMax) {
-          e = 1;
-          sh.clear_direct = 1;
-        }
-        epochs[0] = e;
-        sh.dep = e;
-        sh.hep = 0;
-        sh.hash = 0;
-      }
+      sh.tier = H1 ? 1 : 2;  // a new epoch of the table the search starts in
+      uint32_t e = epochs[sh.tier - 1] + 1;
+      sh.clear = e > kEpochMax;
+      if (sh.clear) e = 1;
+      epochs[sh.tier - 1] = e;
+      sh.ep = e;
     }
     __syncthreads();
     if (sh.j >= A.count) break;
-    if (sh.clear_tab) {  // the epoch field wrapped: the table starts over
-      for (uint32_t p = tid; p < H; p += kBiThreads) tab[p] = 0;
+    if (sh.clear) {  // the epoch field wrapped: the table starts over
+      uint64_t *t0 = sh.tier == 1 ? tab1 : tab2;
+      const uint32_t h0 = sh.tier == 1 ? H1 : H2;
+      for (uint32_t p = tid; p < h0; p += kBiThreads) t0[p] = 0;
       __syncthreads();
     }
-    if (sh.clear_direct) {
-      for (int64_t v = tid; v < A.n; v += kBiThreads) direct[v] = 0;
-      __syncthreads();
-    }
-    BiMap M{direct, tab, A.hmask, sh.dep, sh.hep, sh.hash};
+    BiMap M{sh.tier == 1 ? tab1 : tab2, sh.tier == 1 ? A.mask1 : A.mask2, sh.ep};
+    int tier = sh.tier;
     const uint64_t j = A.j0 + sh.j;
     if (tid == 0) {
       // Sec. 5: s uniform over V; t uniform over V \ {s} (Sec. 3.1 pairs u != v)
@@ -479,7 +429,7 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
       uint32_t *qx = q[x];
       const int64_t *o = x ? A.roff : A.off;
       const int32_t *c = x ? A.rcol : A.col;
-      const int hlimit = (int)(H >> 1);
+      const int hlimit = (int)(H1 >> 1);
       bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
         uint64_t sw = bi_find(M, w);
         if (!sw) {
@@ -491,7 +441,7 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
             else
               sh.ovf = 1;
             atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
-            if (M.hash && atomicAdd(&sh.hcount, 1) + 1 >= hlimit) sh.hfull = 1;
+            if (tier == 1 && atomicAdd(&sh.hcount, 1) + 1 >= hlimit) sh.hfull = 1;
             return;
           }
           if (!sw) return;
@@ -512,31 +462,33 @@ __global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
         break;
       }
       if (sh.hfull) {
-        // the table is half full: the search so far moves to direct words
-        // of a new epoch, without the half-built level, which is redone
+        // the small table is half full: the search so far moves to the large
+        // table (a new epoch of it), without the half-built level, which is redone
         if (tid == 0) {
-          uint32_t e = epochs[0] + 1;
-          sh.clear_direct = e > kDirectEpochMax;
-          if (sh.clear_direct) e = 1;
-          epochs[0] = e;
-          sh.dep = e;
+          uint32_t e = epochs[1] + 1;
+          sh.clear = e > kEpochMax;
+          if (sh.clear) e = 1;
+          epochs[1] = e;
+          sh.ep = e;
         }
         __syncthreads();
-        if (sh.clear_direct) {
-          for (int64_t v = tid; v < A.n; v += kBiThreads) direct[v] = 0;
+        if (sh.clear) {
+          for (uint32_t p = tid; p < H2; p += kBiThreads) tab2[p] = 0;
           __syncthreads();
         }
-        const uint32_t dep = sh.dep;
-        for (uint32_t p = tid; p < H; p += kBiThreads) {
-          const uint64_t e = tab[p];
-          if (h_epoch(e) == M.hep && !(st_side(e) == x && st_level(e) == L + 1))
-            direct[h_node(e)] = d_make(dep, st_side(e), st_level(e));
+        const BiMap M2{tab2, A.mask2, sh.ep};
+        for (uint32_t p = tid; p < H1; p += kBiThreads) {
+          const uint64_t e = tab1[p];
+          if (h_epoch(e) == M.ep && !(st_side(e) == x && st_level(e) == L + 1)) {
+            uint64_t f;
+            bi_claim(M2, (int)h_node(e), st_side(e), st_level(e), f);
+          }
         }
-        M.hash = 0;
-        M.dep = dep;
+        M = M2;
+        tier = 2;
         __syncthreads();
         if (tid == 0) {
-          sh.hash = 0;
+          sh.tier = 2;
           sh.hfull = 0;
           sh.ovf = 0;
           atomicAdd(&A.ctl->nmigrate, 1ull);
@@ -841,12 +793,12 @@ BiCache &bi_cache() {
 }
 }  // namespace
 
-std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int64_t H, int slots) {
+std::unique_ptr<BiWS> bidir_take(int dev, int64_t QC, int64_t H1, int slots) {
   BiCache &c = bi_cache();
   std::lock_guard<std::mutex> lk(c.mu);
   for (size_t i = c.idle.size(); i-- > 0;) {
     BiWS &w = *c.idle[i];
-    if (w.dev == dev && w.n == n && w.QC == QC && w.H == H && w.nslots == slots) {
+    if (w.dev == dev && w.QC == QC && w.H1 == H1 && w.nslots == slots) {
       std::unique_ptr<BiWS> out = std::move(c.idle[i]);
       c.idle.erase(c.idle.begin() + (ptrdiff_t)i);
       return out;
@@ -858,7 +810,7 @@ std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int64_t H, int 
 void bidir_give(std::unique_ptr<BiWS> w) {
   if (!w) return;
   // the job's stream may be gone before these buffers are: free them in order on the legacy stream
-  for (DevBuf *b : {&w->state, &w->tab, &w->lists, &w->sig, &w->epochs, &w->ctl, &w->aoff, &w->dsearch, &w->dwalk,
+  for (DevBuf *b : {&w->tab1, &w->tab2, &w->lists, &w->sig, &w->epochs, &w->ctl, &w->aoff, &w->dsearch, &w->dwalk,
                     &w->arena})
     b->st = nullptr;
   BiCache &c = bi_cache();
@@ -887,12 +839,12 @@ void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap) 
   a.seed = job->seed;
   a.j0 = j0;
   a.count = count;
-  a.state = w.state.as<uint64_t>();
-  a.tab = w.H ? w.tab.as<uint64_t>() : nullptr;
-  a.hmask = w.H ? (uint32_t)(w.H - 1) : 0u;
+  a.tab1 = w.H1 ? w.tab1.as<uint64_t>() : nullptr;
+  a.mask1 = w.H1 ? (uint32_t)(w.H1 - 1) : 0u;
+  a.tab2 = w.tab2.as<uint64_t>();
+  a.mask2 = (uint32_t)(w.H2 - 1);
   a.lists = w.lists.as<uint32_t>();
   a.sig = w.sig.as<uint64_t>();
-  a.SG = w.SG;
   a.epochs = w.epochs.as<uint32_t>();
   a.QC = w.QC;
   a.ps = job->ps.as<int32_t>();

@@ -49,33 +49,32 @@ struct WaveWS {
 };
 
 // Workspace of the bidirectional sampler (bidir.cu): for each of `nslots`
-// resident CTAs, a table of H entries and a state word per node ([nslots][n]),
-// both zeroed once (entries and words are epoch-stamped, so nothing is
+// resident CTAs, a small table of H1 entries (0: none) and a large one of H2
+// = 4 QC entries, zeroed once (entries are epoch-stamped, so nothing is
 // cleared between samples), seven lists of QC entries (two ball queues, two
-// cone lists, heavy rows, crossing-arc tails and heads) and max(2 QC, H) path
-// counts.
+// cone lists, heavy rows, crossing-arc tails and heads) and H2 path counts.
+// Nothing in it grows with the graph.
 struct BiCtl {
   unsigned long long next;     // next sample, relative to the launch's first
   unsigned long long cursor;   // arena entries reserved
   unsigned long long nsearch;  // samples left whole to the bit-parallel sampler
   unsigned long long nwalk;    // samples whose walk is left to it (distance known)
-  unsigned long long nmigrate; // searches that outgrew their table
+  unsigned long long nmigrate; // searches that outgrew the small table
   int err;
   int pad;
 };
 struct BiWS {
-  DevBuf state, tab, lists, sig, epochs, ctl, aoff, dsearch, dwalk, arena;
+  DevBuf tab1, tab2, lists, sig, epochs, ctl, aoff, dsearch, dwalk, arena;
   int nslots = 0;
   int64_t QC = 0;
-  int64_t H = 0;   // table entries per slot (0: direct words only)
-  int64_t SG = 0;  // path counts per slot
-  int32_t n = 0;
+  int64_t H1 = 0;
+  int64_t H2 = 0;
   int dev = -1;
 };
 // A finished job's workspace is kept for the next job of the same shape on the
 // same device (its state words stay valid under the persisting epochs, so it
 // is not cleared again); at most a few are kept.
-std::unique_ptr<BiWS> bidir_take(int dev, int32_t n, int64_t QC, int64_t H, int slots);
+std::unique_ptr<BiWS> bidir_take(int dev, int64_t QC, int64_t H1, int slots);
 void bidir_give(std::unique_ptr<BiWS> w);
 void bidir_drop_cached();
 // Lets the current device's stream-ordered pool keep freed memory for reuse.
@@ -117,10 +116,11 @@ struct cen_job {
   std::unique_ptr<cen::BiWS> bws;
   int sampler = 0;                          // 0 bidirectional (bit-parallel for what it defers), 1 bit-parallel
   size_t bidir_budget = (size_t)16 << 30;   // bytes of per-slot workspace
-  int64_t bidir_queue = (int64_t)1 << 17;   // entries per ball / cone list
-  int64_t bidir_table = -1;                 // table entries per CTA (-1: sized for L2, 0: none)
+  int64_t bidir_queue = (int64_t)1 << 16;   // entries per ball / cone list
+  int64_t bidir_table = -1;                 // small-table entries per CTA (-1: sized for L2, 0: none)
   uint64_t bidir_deferred_search = 0;       // samples it left whole to the bit-parallel sampler
   uint64_t bidir_deferred_walk = 0;         // samples whose walk it left (distance known)
+  uint64_t bidir_migrated = 0;              // searches that outgrew the small table
 };
 
 namespace cen {

@@ -1268,7 +1268,7 @@ int64_t offsets_from_distances(cen_job *job, uint64_t m0, uint64_t m_new) {
 }
 
 // Workspace for as many resident CTAs as the byte budget allows (at least
-// one).  The table is sized so that all CTAs' tables take about kTableL2
+// one).  The small tables are sized so that all of them take about kTableL2
 // bytes (they stay in L2), unless a size was set.
 constexpr size_t kTableL2 = (size_t)80 << 20;
 
@@ -1276,49 +1276,45 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
   const int32_t n = job->g->n;
   cudaStream_t st = job->st;
   const int64_t QC = std::max<int64_t>(16, std::min<int64_t>(n, job->bidir_queue));
-  int64_t H = 0;
-  auto per_slot = [&](int64_t h) {
-    return 8 * (size_t)n + 7 * 4 * (size_t)QC + 8 * (size_t)h + 8 * (size_t)std::max<int64_t>(2 * QC, h);
-  };
+  int64_t H2 = 1024;
+  while (H2 < 4 * QC) H2 *= 2;
+  auto per_slot = [&](int64_t h1) { return 8 * (size_t)h1 + 16 * (size_t)H2 + 7 * 4 * (size_t)QC; };
   const size_t res = (size_t)bidir_resident_slots();
   int slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(0)));
-  if (job->bidir_table < 0 && job->g->bidir_table_off.load()) {
-    H = 0;
-  } else if (job->bidir_table < 0) {
-    H = 1024;
-    while ((size_t)(2 * H) * 8 * (size_t)slots <= kTableL2 && 2 * H <= 2 * QC) H *= 2;
-  } else {
-    H = job->bidir_table;
+  int64_t H1 = 0;
+  if (job->bidir_table < 0 && !job->g->bidir_table_off.load()) {
+    H1 = 1024;
+    while ((size_t)(2 * H1) * 8 * (size_t)slots <= kTableL2 && 2 * H1 < H2) H1 *= 2;
+  } else if (job->bidir_table > 0) {
+    H1 = std::min<int64_t>(job->bidir_table, H2 / 2);
   }
-  if (H) slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(H)));
-  const int64_t SG = std::max<int64_t>(2 * QC, H);
+  if (H1) slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(H1)));
   int dev = 0;
   CEN_CK(cudaGetDevice(&dev));
   BiWS *cur = job->bws.get();
-  if (!(cur && cur->n == n && cur->QC == QC && cur->H == H && cur->nslots == slots && cur->dev == dev)) {
+  if (!(cur && cur->QC == QC && cur->H1 == H1 && cur->nslots == slots && cur->dev == dev)) {
     if (cur && cur->nslots) bidir_give(std::move(job->bws));  // another shape: keep this one for later jobs
-    job->bws = bidir_take(dev, n, QC, H, slots);
+    job->bws = bidir_take(dev, QC, H1, slots);
     if (!job->bws) job->bws.reset(new BiWS());
   }
   BiWS &wk = *job->bws;
   if (wk.nslots == 0) {
     keep_pool_memory();
-    wk.state.ensure_exact(8 * (size_t)n * slots, st);
-    if (H) wk.tab.ensure_exact(8 * (size_t)H * slots, st);
+    if (H1) wk.tab1.ensure_exact(8 * (size_t)H1 * slots, st);
+    wk.tab2.ensure_exact(8 * (size_t)H2 * slots, st);
     wk.lists.ensure_exact(4 * 7 * (size_t)QC * slots, st);
-    wk.sig.ensure_exact(8 * (size_t)SG * slots, st);
+    wk.sig.ensure_exact(8 * (size_t)H2 * slots, st);
     wk.epochs.ensure(8 * (size_t)slots, st);
-    CEN_CK(cudaMemsetAsync(wk.state.p, 0, 8 * (size_t)n * slots, st));
-    if (H) CEN_CK(cudaMemsetAsync(wk.tab.p, 0, 8 * (size_t)H * slots, st));
+    if (H1) CEN_CK(cudaMemsetAsync(wk.tab1.p, 0, 8 * (size_t)H1 * slots, st));
+    CEN_CK(cudaMemsetAsync(wk.tab2.p, 0, 8 * (size_t)H2 * slots, st));
     CEN_CK(cudaMemsetAsync(wk.epochs.p, 0, 8 * (size_t)slots, st));
-    wk.n = n;
     wk.QC = QC;
-    wk.H = H;
-    wk.SG = SG;
+    wk.H1 = H1;
+    wk.H2 = H2;
     wk.nslots = slots;
     wk.dev = dev;
   }
-  for (DevBuf *b : {&wk.state, &wk.tab, &wk.lists, &wk.sig, &wk.epochs}) b->st = st;
+  for (DevBuf *b : {&wk.tab1, &wk.tab2, &wk.lists, &wk.sig, &wk.epochs}) b->st = st;
   wk.ctl.ensure(sizeof(BiCtl), st);
   wk.aoff.ensure(8 * (size_t)m_new, st);
   wk.dsearch.ensure(8 * (size_t)m_new, st);
@@ -1387,6 +1383,7 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   rerun_in_place(job, walk);
   job->bidir_deferred_search += h.nsearch;
   job->bidir_deferred_walk += walk.size();
+  job->bidir_migrated += h.nmigrate;
   return total;
 }
 

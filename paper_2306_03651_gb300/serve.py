@@ -59,20 +59,24 @@ class Result:
 
 
 def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: float = 8.0, levels: int = 16,
-                       bidir_budget: int = 16 << 30, bidir_queue: int = 1 << 17, resident_ctas: int = 608) -> int:
+                       bidir_budget: int = 16 << 30, bidir_queue: int = 1 << 16, resident_ctas: int = 1216) -> int:
     """Upper estimate of one job's device memory (admission policy, not the method).
 
-    Bidirectional sampler: one workspace per resident CTA (a state word per node,
-    seven lists of `bidir_queue` entries, 2 `bidir_queue` path counts), as many
-    as fit in `bidir_budget`.  Wave workspace (the fallback): `levels` + 6 arrays
+    Bidirectional sampler: one workspace per resident CTA (a large node table
+    and as many path counts, H = 4 `bidir_queue` entries each, seven lists of
+    `bidir_queue` entries, and a small table of at most 80 MiB over all CTAs),
+    as many as fit in `bidir_budget`.  Wave workspace (the fallback): `levels` + 6 arrays
     of n*G words (G = wave words, at most 32 and at most 1 GB per array) and the
     initial cone-arc log (2 n G records of 24 bytes); sample store for m_cap
     samples: offsets, endpoints, distance, sign words and members (twice: samples
     and the incidence), plus the member arena; AMCERA table R[t][n] and greedy /
     incidence arrays."""
     qc = max(16, min(n, bidir_queue))
-    per_slot = 8 * n + 7 * 4 * qc + 2 * 8 * qc
-    bidir = min(resident_ctas, max(1, bidir_budget // per_slot)) * per_slot
+    h2 = 1024
+    while h2 < 4 * qc:
+        h2 *= 2
+    per_slot = 16 * h2 + 7 * 4 * qc
+    bidir = min(resident_ctas, max(1, bidir_budget // per_slot)) * per_slot + (80 << 20)
     G = 32
     while G > 1 and n * G * 8 > (1 << 30):
         G //= 2

@@ -98,14 +98,17 @@ def test_bidirectional_search_deferral(name):
 @pytest.mark.parametrize("table", [0, 1024])
 @pytest.mark.parametrize("name", ["ba2000", "rmat12_dir", "grid_rewired", "rmat12_lcc"])
 def test_bidirectional_node_table_and_direct_words(name, table):
-    """Node state in direct words only (table 0), or in a 1,024-entry table that most
-    searches outgrow, moving to direct words mid-search: the oracle's samples either way."""
+    """Node state in the large table only (small table 0), or in a 1,024-entry small table
+    that many searches outgrow, moving to the large table mid-search: the oracle's samples
+    either way."""
     g = GRAPHS[name]
     _, _, ref = oracle_samples(g, 29, 2000)
     job = P.Job(P.Graph.of(g), 29, 10)
     job.set_param(P.PARAM_BIDIR_TABLE, table)
     job.sample(2000)
     assert_same_samples(job.samples(), ref)
+    info = job.sampler_info()
+    assert info["migrated"] == 0 if table == 0 else (name != "grid_rewired" or info["migrated"] > 0)
 
 
 def test_bidirectional_level_cap_deferral():
