@@ -339,7 +339,10 @@ struct BiArgs {
   unsigned long long *units;
 };
 
-__global__ void __launch_bounds__(kBiThreads) k_bidir(BiArgs A) {
+// 16 CTAs of 128 threads per SM (32 registers): the kernel is bound by the
+// latency of dependent L2 accesses, so samples in flight matter more than the
+// few registers spilled.
+__global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
   __shared__ BiShared sh;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t QC = A.QC;
