@@ -63,8 +63,11 @@ def _load():
         "orc_rade_matrix": ([vp, vp, vp], ctypes.c_int),
         "orc_bounds": ([u64, u64, i64, i32, i64, i32, dbl, dbl, i32, vp], ctypes.c_int),
         "orc_run": ([vp, i32, dbl, dbl, i32, u64, u64, u64, vp, vp, vp, vp, vp, vp, i32], ctypes.c_int),
-        "orc_run_ex": ([vp, i32, dbl, dbl, i32, u64, u64, u64, i32, dbl, i32, vp, vp, vp, vp, vp, vp, i32],
-                       ctypes.c_int),
+        "orc_run_ex": ([vp, i32, dbl, dbl, i32, u64, u64, u64, i32, dbl, i32, i32, i32, vp, vp, vp, vp, vp, vp,
+                        i32], ctypes.c_int),
+        "orc_job_new_space": ([vp, u64, i32, i32, i32, ctypes.POINTER(vp)], ctypes.c_int),
+        "orc_triangle_count": ([vp], i64),
+        "orc_triangle_unrank": ([vp, i64, vp, vp, vp], ctypes.c_int),
         "orc_bounds_hedge": ([u64, u64, i32, i32, dbl, dbl, i32, vp], ctypes.c_int),
         "orc_schedule_guess": ([dbl, dbl, dbl, i32], dbl),
         "orc_schedule_next": ([i32, dbl, u64, u64, dbl, u64, dbl, dbl, i32], u64),
@@ -157,14 +160,25 @@ class Graph:
                                    ctypes.byref(ln), _p(path))
         return rc, s.value, t.value, d.value, path[: ln.value].tolist() if rc == 0 else []
 
-    def run(self, k, eps, delta, t, seed, m0=1000, m_cap=1 << 26, max_rounds=64, schedule=0, alpha=1.2, rule=0):
+    def triangle_count(self) -> int:
+        return int(_load().orc_triangle_count(self.h))
+
+    def triangle(self, r: int):
+        u, v, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        rc = _load().orc_triangle_unrank(self.h, r, ctypes.byref(u), ctypes.byref(v), ctypes.byref(w))
+        if rc:
+            raise OracleError(rc, "triangle_unrank")
+        return u.value, v.value, w.value
+
+    def run(self, k, eps, delta, t, seed, m0=1000, m_cap=1 << 26, max_rounds=64, schedule=0, alpha=1.2, rule=0,
+            space=0, kappa=0):
         """Algorithm 1.  schedule 0 doubling / 1 the paper's / 2 the paper's plus a predicted size;
         rule 0 CentRA / 1 HEDGE-P."""
         S = np.empty(k, np.int32)
         size, rounds = ctypes.c_int32(), ctypes.c_int32()
         cov, mf = ctypes.c_uint64(), ctypes.c_uint64()
         log = np.zeros((max_rounds, 16), np.float64)
-        rc = _load().orc_run_ex(self.h, k, eps, delta, t, seed, m0, m_cap, schedule, alpha, rule, _p(S),
+        rc = _load().orc_run_ex(self.h, k, eps, delta, t, seed, m0, m_cap, schedule, alpha, rule, space, kappa, _p(S),
                                 ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds),
                                 _p(log), max_rounds)
         if rc not in (OK, ENOTCERTIFIED):
@@ -173,13 +187,16 @@ class Graph:
                     log=log[: rounds.value].copy())
 
 
+SPACE_BETWEENNESS, SPACE_KPATH, SPACE_TRIANGLE = 0, 1, 2
+
+
 class Job:
-    def __init__(self, graph: Graph, seed: int, t: int):
+    def __init__(self, graph: Graph, seed: int, t: int, space: int = 0, kappa: int = 0):
         self.graph = graph
         self.seed = seed
         self.t = t
         h = ctypes.c_void_p()
-        rc = _load().orc_job_new(graph.h, seed, t, ctypes.byref(h))
+        rc = _load().orc_job_new_space(graph.h, seed, t, space, kappa, ctypes.byref(h))
         if rc:
             raise OracleError(rc, "job_new")
         self.h = h

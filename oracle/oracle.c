@@ -345,6 +345,122 @@ int orc_hyperedge(const orc_graph *g, uint64_t seed, uint64_t j, int32_t *s, int
 }
 
 /* ------------------------------------------------------------------ job */
+/* ------------------------------------------------- other hyper-edge spaces */
+/* kappa-path centrality (Sec. 2: "sets of nodes traversed by simple paths of
+ * length at most kappa").  Reading: s uniform over V (purpose 0), a length
+ * l uniform in 1..kappa (purpose 1), then a random simple walk from s of up
+ * to l steps: at step i the walk moves to the r-th (ascending id) out-neighbour
+ * of the current node not yet on the walk, r uniform below their number
+ * (purpose 2 + i), and stops early when there is none.  The hyper-edge is the
+ * nodes after s, in walk order (at most kappa of them, the paper's b <= kappa).
+ * Writes s, l, the steps taken and the path; returns the path length. */
+static int32_t kpath_walk(const orc_graph *g, uint64_t seed, uint64_t j, int32_t kappa, int32_t *s_out,
+                          int32_t *l_out, int32_t *path, uint64_t *arcs) {
+  const int32_t s = (int32_t)uniform_below(seed, j, PURPOSE_S, (u128)(uint32_t)g->n, NULL);
+  const int32_t l = 1 + (int32_t)uniform_below(seed, j, PURPOSE_T, (u128)(uint32_t)kappa, NULL);
+  int32_t len = 0, cur = s;
+  for (int32_t i = 0; i < l; ++i) {
+    int64_t free_nb = 0;
+    for (int64_t e = g->off[cur]; e < g->off[cur + 1]; ++e) {
+      int32_t w = g->col[e], seen = (w == s);
+      for (int32_t q = 0; q < len && !seen; ++q) seen = (path[q] == w);
+      free_nb += !seen;
+    }
+    *arcs += (uint64_t)(g->off[cur + 1] - g->off[cur]);
+    if (free_nb == 0) break;
+    int64_t r = (int64_t)uniform_below(seed, j, PURPOSE_WALK0 + (uint32_t)i, (u128)(uint64_t)free_nb, NULL);
+    int32_t next = -1;
+    for (int64_t e = g->off[cur]; e < g->off[cur + 1] && next < 0; ++e) {
+      int32_t w = g->col[e], seen = (w == s);
+      for (int32_t q = 0; q < len && !seen; ++q) seen = (path[q] == w);
+      if (!seen && r-- == 0) next = w;
+    }
+    path[len++] = next;
+    cur = next;
+  }
+  *s_out = s;
+  *l_out = l;
+  return len;
+}
+
+/* Triangle centrality (Sec. 2: "sets of nodes incident to triangles of G").
+ * Reading: a triangle {u, v, w} of the undirected graph drawn uniformly; its
+ * three nodes are the hyper-edge, in ascending order.  Triangles are ranked
+ * by (u, v, w) with u < v < w: off[e] (the exclusive prefix over arcs e = (u,v)
+ * in CSR order of the number of common neighbours w > v when v > u, else 0)
+ * ranks the first triangle on arc e, and within the arc the common
+ * neighbours ascend.  r uniform below the total (purpose 0) is unranked. */
+static int64_t common_above(const orc_graph *g, int32_t u, int32_t v, int32_t *w_out, int64_t rank) {
+  int64_t a = g->off[u], ae = g->off[u + 1], b = g->off[v], be = g->off[v + 1], c = 0;
+  while (a < ae && b < be) {
+    if (g->col[a] < g->col[b]) ++a;
+    else if (g->col[a] > g->col[b]) ++b;
+    else {
+      if (g->col[a] > v) {
+        if (w_out && c == rank) {
+          *w_out = g->col[a];
+          return c;
+        }
+        ++c;
+      }
+      ++a;
+      ++b;
+    }
+  }
+  return c;
+}
+
+static int64_t *triangle_offsets(const orc_graph *g) {
+  int64_t *off = (int64_t *)malloc(sizeof(int64_t) * ((size_t)g->nnz + 1));
+  if (!off) return NULL;
+  int64_t acc = 0;
+  for (int32_t u = 0; u < g->n; ++u)
+    for (int64_t e = g->off[u]; e < g->off[u + 1]; ++e) {
+      off[e] = acc;
+      if (g->col[e] > u) acc += common_above(g, u, g->col[e], NULL, -1);
+    }
+  off[g->nnz] = acc;
+  return off;
+}
+
+/* the triangle of rank r (0 <= r < off[nnz]) */
+static void triangle_unrank(const orc_graph *g, const int64_t *off, int64_t r, int32_t *u, int32_t *v, int32_t *w) {
+  int64_t lo = 0, hi = g->nnz; /* last arc e with off[e] <= r and a triangle on it */
+  while (hi - lo > 1) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (off[mid] <= r) lo = mid; else hi = mid;
+  }
+  while (off[lo + 1] == off[lo]) ++lo; /* arcs without triangles share the prefix */
+  int32_t a = 0, b = g->n; /* the row holding arc lo */
+  while (b - a > 1) {
+    int32_t mid = a + (b - a) / 2;
+    if (g->off[mid] <= lo) a = mid; else b = mid;
+  }
+  *u = a;
+  *v = g->col[lo];
+  common_above(g, a, *v, w, r - off[lo]);
+}
+
+int64_t orc_triangle_count(const orc_graph *g) {
+  if (!g || g->directed) return -1;
+  int64_t *off = triangle_offsets(g);
+  if (!off) return -1;
+  int64_t T = off[g->nnz];
+  free(off);
+  return T;
+}
+
+int orc_triangle_unrank(const orc_graph *g, int64_t r, int32_t *u, int32_t *v, int32_t *w) {
+  if (!g || g->directed) return ORC_EINVAL;
+  int64_t *off = triangle_offsets(g);
+  if (!off) return ORC_ENOMEM;
+  int rc = ORC_OK;
+  if (r < 0 || r >= off[g->nnz]) rc = ORC_EINVAL;
+  else triangle_unrank(g, off, r, u, v, w);
+  free(off);
+  return rc;
+}
+
 struct orc_job {
   const orc_graph *g;
   uint64_t seed;
@@ -358,14 +474,35 @@ struct orc_job {
   int64_t cap_mem;
   int32_t *ps, *pt, *pd;
   uint64_t work[4];
+  int32_t space, kappa; /* hyper-edge space (ORC_SPACE_*) and the path bound of the kappa-path space */
+  int64_t *tri_off;     /* triangle space: exclusive prefix of per-arc triangle counts ([nnz+1]) */
 };
 
 int orc_job_new(const orc_graph *g, uint64_t seed, int32_t t, orc_job **out) {
+  return orc_job_new_space(g, seed, t, ORC_SPACE_BETWEENNESS, 0, out);
+}
+
+int orc_job_new_space(const orc_graph *g, uint64_t seed, int32_t t, int32_t space, int32_t kappa, orc_job **out) {
   if (!g || t < 1) return ORC_EINVAL;
+  if (space != ORC_SPACE_BETWEENNESS && space != ORC_SPACE_KPATH && space != ORC_SPACE_TRIANGLE) return ORC_EINVAL;
+  if (space == ORC_SPACE_KPATH && (kappa < 1 || kappa > 1024)) return ORC_EINVAL;
+  int64_t *tri_off = NULL;
+  if (space == ORC_SPACE_TRIANGLE) {
+    if (g->directed) return ORC_EINVAL;
+    tri_off = triangle_offsets(g);
+    if (!tri_off) return ORC_ENOMEM;
+    if (tri_off[g->nnz] == 0) { /* no triangle to draw */
+      free(tri_off);
+      return ORC_EINVAL;
+    }
+  }
   orc_job *job = (orc_job *)calloc(1, sizeof(orc_job));
   job->g = g;
   job->seed = seed;
   job->t = t;
+  job->space = space;
+  job->kappa = kappa;
+  job->tri_off = tri_off;
   job->cap_m = 1024;
   job->hoff = (int64_t *)calloc(job->cap_m + 1, sizeof(int64_t));
   job->ps = (int32_t *)malloc(sizeof(int32_t) * job->cap_m);
@@ -381,6 +518,7 @@ int orc_job_new(const orc_graph *g, uint64_t seed, int32_t t, orc_job **out) {
 void orc_job_free(orc_job *job) {
   if (!job) return;
   free(job->hoff); free(job->hmem); free(job->ps); free(job->pt); free(job->pd); free(job->ids);
+  free(job->tri_off);
   free(job);
 }
 
@@ -430,8 +568,22 @@ int orc_job_sample(orc_job *job, uint64_t m_new) {
     const uint64_t jid = job->next_id;
     w.reached_lt_d = 0;
     w.arcs_expanded = 0;
-    rc = hyperedge_ws(g, job->seed, jid, &w, &s, &t, &d, &len, path, &walk_arcs);
-    if (rc != ORC_OK) break;
+    if (job->space == ORC_SPACE_KPATH) {
+      /* s: start, t: drawn length l, d: steps taken */
+      len = kpath_walk(g, job->seed, jid, job->kappa, &s, &t, path, &walk_arcs);
+      d = len;
+    } else if (job->space == ORC_SPACE_TRIANGLE) {
+      /* s, t, d: the triangle's nodes, ascending */
+      const int64_t r = (int64_t)uniform_below(job->seed, jid, PURPOSE_S, (u128)(uint64_t)job->tri_off[g->nnz], NULL);
+      triangle_unrank(g, job->tri_off, r, &s, &t, &d);
+      path[0] = s;
+      path[1] = t;
+      path[2] = d;
+      len = 3;
+    } else {
+      rc = hyperedge_ws(g, job->seed, jid, &w, &s, &t, &d, &len, path, &walk_arcs);
+      if (rc != ORC_OK) break;
+    }
     int64_t base = job->hoff[j];
     if (base + len > job->cap_mem) {
       while (base + len > job->cap_mem) job->cap_mem *= 2;
@@ -715,19 +867,20 @@ uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t
 int orc_run(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
             uint64_t m_cap, int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final, int32_t *rounds,
             double *log, int32_t max_rounds) {
-  return orc_run_ex(g, k, eps, delta, t, seed, m0, m_cap, 0, 2.0, 0, S_out, S_size, covered, m_final, rounds, log,
-                    max_rounds);
+  return orc_run_ex(g, k, eps, delta, t, seed, m0, m_cap, 0, 2.0, 0, 0, 0, S_out, S_size, covered, m_final, rounds,
+                    log, max_rounds);
 }
 
 int orc_run_ex(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
-               uint64_t m_cap, int32_t schedule, double alpha, int32_t rule, int32_t *S_out, int32_t *S_size,
-               uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds) {
+               uint64_t m_cap, int32_t schedule, double alpha, int32_t rule, int32_t space, int32_t kappa,
+               int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log,
+               int32_t max_rounds) {
   double a = 1.0 - exp(-1.0);
   if (!g || k < 1 || t < 1 || !(eps > 0.0 && eps < a) || !(delta > 0.0 && delta < 1.0) || m0 < 1 || m_cap < m0 ||
       schedule < 0 || schedule > 2 || (schedule != 0 && !(alpha > 1.0)) || (rule != 0 && rule != 1))
     return ORC_EINVAL;
   orc_job *job;
-  int rc = orc_job_new(g, seed, t, &job);
+  int rc = orc_job_new_space(g, seed, t, space, kappa, &job);
   if (rc) return rc;
   int64_t *Rnum = (int64_t *)malloc(sizeof(int64_t) * (size_t)t);
   uint64_t m_prev = 0;

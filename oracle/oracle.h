@@ -17,6 +17,7 @@
  *     sigma_sw / sigma_sv, scanning in-neighbours in ascending id order;
  *   - greedyCover: ties to the lowest node id; stops early at zero gain;
  *   - sign matrix: extended (never redrawn) across rounds, keyed by sample;
+ *   - other spaces (kappa-path, triangle): see orc_job_new_space;
  *   - schedule: m_i = m0 * 2^(i-1) (doubling), or Sec. 4.2's growth by alpha
  *     with the optimistic guess (R = 0, nu = 1, target eta = eps C_{i-1} /
  *     (1 - 1/e), C_0 = 1); delta_i = delta / 2^i.
@@ -75,6 +76,20 @@ int orc_hyperedge(const orc_graph *g, uint64_t seed, uint64_t j, int32_t *s, int
 
 /* Job: the growing sample H = (h_0, ..., h_{m-1}) of one CentRA run. */
 int orc_job_new(const orc_graph *g, uint64_t seed, int32_t t, orc_job **out);
+/* Hyper-edge spaces (Sec. 2): set betweenness (interior nodes of a uniform
+ * shortest path between a uniform pair), kappa-path (the nodes after s of a
+ * random simple walk of up to l steps, l uniform in 1..kappa), triangle (the
+ * three nodes of a uniform triangle; undirected graphs with a triangle only).
+ * The copied s, t, d of a sample are (s, t, d(s,t)), (s, l, steps taken) and
+ * the triangle's nodes in ascending order.  See oracle.c for the draws. */
+#define ORC_SPACE_BETWEENNESS 0
+#define ORC_SPACE_KPATH 1
+#define ORC_SPACE_TRIANGLE 2
+int orc_job_new_space(const orc_graph *g, uint64_t seed, int32_t t, int32_t space, int32_t kappa, orc_job **out);
+/* Triangles of an undirected graph: their number, and the one of rank r in
+ * (u, v, w) order with u < v < w. */
+int64_t orc_triangle_count(const orc_graph *g);
+int orc_triangle_unrank(const orc_graph *g, int64_t r, int32_t *u, int32_t *v, int32_t *w);
 void orc_job_free(orc_job *job);
 int orc_job_sample(orc_job *job, uint64_t m_new);      /* append samples [m, m+m_new) */
 /* append the samples with ids j_first .. j_first+count-1 (shards by sample index) */
@@ -127,8 +142,9 @@ int orc_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double 
  * Thm. "bound_dev"), rule 1 = HEDGE-P (orc_bounds_hedge; no AMCERA; the log's
  * C, nu and eta columns hold C, nu_U, eta_U and the AMCERA columns are 0). */
 int orc_run_ex(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
-               uint64_t m_cap, int32_t schedule, double alpha, int32_t rule, int32_t *S_out, int32_t *S_size,
-               uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log, int32_t max_rounds);
+               uint64_t m_cap, int32_t schedule, double alpha, int32_t rule, int32_t space, int32_t kappa,
+               int32_t *S_out, int32_t *S_size, uint64_t *covered, uint64_t *m_final, int32_t *rounds, double *log,
+               int32_t max_rounds);
 
 #ifdef __cplusplus
 }
