@@ -67,6 +67,27 @@ int cen_graph_info(const cen_graph *g, int32_t *n, int64_t *nnz, int *directed);
 /* A job holds the growing sample H (Alg. 1 "H_i") for one (graph, seed, t).
  * t >= 1 is the number of Rademacher vectors (rows of sigma, Sec. 3.2). */
 int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, cen_job **out);
+
+/* Hyper-edge spaces (Sec. 2; CentRA is oblivious to the sampler, Sec. 4.2):
+ *   BETWEENNESS  set betweenness: the interior nodes of a uniform shortest
+ *                s -> t path, s uniform, t uniform over V \ {s} (the default);
+ *   KPATH        kappa-path centrality: s uniform, a length l uniform in
+ *                1..kappa, then a random simple walk of up to l steps, each to
+ *                a uniform out-neighbour not yet on the walk (stopping early
+ *                when there is none); the hyper-edge is the nodes after s;
+ *   TRIANGLE     triangle centrality: the three nodes of a uniform triangle of
+ *                an undirected graph.
+ * The per-sample s, t, d of cen_job_copy_samples are (s, t, d(s,t)),
+ * (s, l, steps taken) and the triangle's nodes in ascending order. */
+#define CEN_SPACE_BETWEENNESS 0
+#define CEN_SPACE_KPATH 1
+#define CEN_SPACE_TRIANGLE 2
+/* cen_job_create with a space.  kappa (KPATH only) in 1 .. 1024.  TRIANGLE
+ * needs an undirected graph with at least one triangle (else CEN_EINVAL); the
+ * first such job on a graph ranks its triangles on the GPU and keeps the ranks
+ * on the graph. */
+int cen_job_create_space(const cen_graph *g, uint64_t seed, int32_t t, int32_t space, int32_t kappa, void *stream,
+                         cen_job **out);
 int cen_job_free(cen_job *job);
 /* m = samples drawn so far; members = sum of |h| over them. */
 int cen_job_size(const cen_job *job, uint64_t *m, int64_t *members);
@@ -150,6 +171,8 @@ typedef struct cen_run_opts {
   int32_t schedule; /* CEN_SCHEDULE_* */
   int32_t rule;     /* CEN_RULE_* */
   double alpha;     /* growth factor of PAPER and EXTRAPOLATE (> 1) */
+  int32_t space;    /* CEN_SPACE_* (zeroed: set betweenness) */
+  int32_t kappa;    /* path bound of CEN_SPACE_KPATH */
 } cen_run_opts;
 
 /* cen_run with options (NULL = defaults).  Same outputs and status codes. */

@@ -26,6 +26,7 @@ PARAM_SAMPLER, PARAM_BIDIR_BUDGET, PARAM_BIDIR_QUEUE, PARAM_BIDIR_TABLE = 5, 6, 
 SAMPLER_BIDIR, SAMPLER_WAVES = 0, 1
 SCHEDULE_DOUBLING, SCHEDULE_PAPER, SCHEDULE_EXTRAPOLATE = 0, 1, 2
 RULE_CENTRA, RULE_HEDGE_P = 0, 1
+SPACE_BETWEENNESS, SPACE_KPATH, SPACE_TRIANGLE = 0, 1, 2
 LOG_COLS = ("i", "m", "covered", "Rsum", "Wnum", "b", "C", "A", "w", "nu", "xi", "Rt", "R", "eta", "stop", "S_size")
 NKCLASS = 24
 
@@ -37,7 +38,8 @@ class CenError(RuntimeError):
 
 
 class cen_run_opts(ctypes.Structure):
-    _fields_ = [("schedule", ctypes.c_int32), ("rule", ctypes.c_int32), ("alpha", ctypes.c_double)]
+    _fields_ = [("schedule", ctypes.c_int32), ("rule", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("space", ctypes.c_int32), ("kappa", ctypes.c_int32)]
 
 
 class cen_job_spec(ctypes.Structure):
@@ -92,6 +94,7 @@ def _load():
         "cen_job_set_timing": ([vp, ip], ip),
         "cen_job_stats": ([vp, vp, vp], ip),
         "cen_job_sampler_info": ([vp, vp, vp, vp, vp], ip),
+        "cen_job_create_space": ([vp, u64, i32, i32, i32, vp, ctypes.POINTER(vp)], ip),
         "cen_release_cached": ([], ip),
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
@@ -195,14 +198,15 @@ class Graph:
 class Job:
     """The growing sample of one CentRA run (``cen_job_*``)."""
 
-    def __init__(self, graph: Graph, seed: int, t: int, stream=None):
+    def __init__(self, graph: Graph, seed: int, t: int, stream=None, space: int = 0, kappa: int = 0):
         self.graph = graph
         self.seed = int(seed)
         self.t = int(t)
         self.nw = (self.t + 31) // 32
         self.stream = stream if stream is not None else graph.stream
         h = ctypes.c_void_p()
-        _check(_lib.cen_job_create(graph.h, self.seed, self.t, self.stream, ctypes.byref(h)), "cen_job_create")
+        _check(_lib.cen_job_create_space(graph.h, self.seed, self.t, int(space), int(kappa), self.stream,
+                                         ctypes.byref(h)), "cen_job_create")
         self.h = h
 
     def close(self):
@@ -319,17 +323,18 @@ def bounds_hedge(covered, m, n, k, eps, delta, i):
 
 
 def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: int = 1000, m_cap: int = 1 << 30,
-        stream=None, max_rounds: int = 64, schedule: int = 0, alpha: float = 1.2, rule: int = 0) -> dict:
+        stream=None, max_rounds: int = 64, schedule: int = 0, alpha: float = 1.2, rule: int = 0, space: int = 0,
+        kappa: int = 0) -> dict:
     """``cen_run_ex`` (Algorithm 1): certified top-k set; status OK or ENOTCERTIFIED.
     schedule: SCHEDULE_DOUBLING (m0 2^(i-1)), SCHEDULE_PAPER (growth by alpha plus the optimistic guess) or
     SCHEDULE_EXTRAPOLATE (PAPER plus the last SD bound scaled to the stopping threshold);
-    rule: RULE_CENTRA (AMCERA bounds) or RULE_HEDGE_P (union bound)."""
+    rule: RULE_CENTRA (AMCERA bounds) or RULE_HEDGE_P (union bound); space: SPACE_* (kappa for SPACE_KPATH)."""
     S = np.empty(k, np.int32)
     size, rounds = ctypes.c_int32(), ctypes.c_int32()
     cov, mf = ctypes.c_uint64(), ctypes.c_uint64()
     log = np.zeros((max_rounds, 16), np.float64)
     st = stream if stream is not None else graph.stream
-    opts = cen_run_opts(schedule, rule, alpha)
+    opts = cen_run_opts(schedule, rule, alpha, space, kappa)
     rc = _lib.cen_run_ex(graph.h, k, eps, delta, t, seed, m0, m_cap, ctypes.byref(opts), st, _p(S),
                          ctypes.byref(size), ctypes.byref(cov), ctypes.byref(mf), ctypes.byref(rounds), _p(log),
                          max_rounds)
@@ -341,7 +346,7 @@ def run(graph: Graph, k: int, eps: float, delta: float, t: int, seed: int, m0: i
 
 def run_batch(jobs, nworkers: int = 8, max_rounds: int = 64) -> list[dict]:
     """``cen_run_batch``: `jobs` is a list of dicts with graph (Graph), k, eps, delta, t, seed and optional
-    m0 (1000) / m_cap (2^30) / schedule (0) / rule (0) / alpha (1.2).  Returns one dict per job, like ``run`` plus start_s / end_s."""
+    m0 (1000) / m_cap (2^30) / schedule (0) / rule (0) / alpha (1.2) / space (0) / kappa (0).  Returns one dict per job, like ``run`` plus start_s / end_s."""
     n = len(jobs)
     specs = (cen_job_spec * max(n, 1))()
     res = (cen_job_result * max(n, 1))()
@@ -349,7 +354,8 @@ def run_batch(jobs, nworkers: int = 8, max_rounds: int = 64) -> list[dict]:
     for i, j in enumerate(jobs):
         specs[i] = cen_job_spec(j["graph"].h, j["k"], j["t"], j["eps"], j["delta"], j["seed"], j.get("m0", 1000),
                                 j.get("m_cap", 1 << 30),
-                                cen_run_opts(j.get("schedule", 0), j.get("rule", 0), j.get("alpha", 1.2)))
+                                cen_run_opts(j.get("schedule", 0), j.get("rule", 0), j.get("alpha", 1.2),
+                                             j.get("space", 0), j.get("kappa", 0)))
         S = np.empty(j["k"], np.int32)
         log = np.zeros((max_rounds, 16), np.float64)
         keep.append((S, log))

@@ -281,14 +281,27 @@ int cen_graph_info(const cen_graph *g, int32_t *n, int64_t *nnz, int *directed) 
 }
 
 int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, cen_job **out) {
+  return cen_job_create_space(g, seed, t, CEN_SPACE_BETWEENNESS, 0, stream, out);
+}
+
+int cen_job_create_space(const cen_graph *g, uint64_t seed, int32_t t, int32_t space, int32_t kappa, void *stream,
+                         cen_job **out) {
   CEN_API_BEGIN
   CEN_REQUIRE(g && out, CEN_EINVAL, "cen_job_create: null argument");
   CEN_REQUIRE(t >= 1 && t <= 4096, CEN_EINVAL, "cen_job_create: need 1 <= t <= 4096");
+  CEN_REQUIRE(space == CEN_SPACE_BETWEENNESS || space == CEN_SPACE_KPATH || space == CEN_SPACE_TRIANGLE, CEN_EINVAL,
+              "cen_job_create: unknown hyper-edge space");
+  CEN_REQUIRE(space != CEN_SPACE_KPATH || (kappa >= 1 && kappa <= cen::max_kappa()), CEN_EINVAL,
+              "cen_job_create: kappa must be in [1, 1024]");
+  CEN_REQUIRE(space != CEN_SPACE_TRIANGLE || !g->directed, CEN_EINVAL,
+              "cen_job_create: the triangle space needs an undirected graph");
   *out = nullptr;
   cen_job *job = new cen_job();
   job->g = g;
   job->seed = seed;
   job->t = t;
+  job->space = space;
+  job->kappa = space == CEN_SPACE_KPATH ? kappa : 0;
   job->nw = (t + 31) / 32;
   job->st = (cudaStream_t)stream;
   if (const char *e = getenv("CEN_WAVE_WORDS")) {  // wave width in 64-slot words (1..32), a tuning knob
@@ -303,7 +316,10 @@ int cen_job_create(const cen_graph *g, uint64_t seed, int32_t t, void *stream, c
     if (g->param_set[p]) apply_param(job, p, g->param[p]);
   try {
     job->stats.init(job->st);
+    if (space == CEN_SPACE_TRIANGLE)
+      CEN_REQUIRE(cen::triangle_index(job) > 0, CEN_EINVAL, "cen_job_create: the graph has no triangle");
   } catch (...) {
+    CEN_CK(cudaStreamSynchronize(job->st));
     delete job;
     throw;
   }
@@ -390,7 +406,7 @@ int cen_run_ex(const cen_graph *g, int32_t k, double eps, double delta, int32_t 
   int rc = CEN_OK;
   try {
     const double a = 1.0 - exp(-1.0);
-    const cen_run_opts o = opts ? *opts : cen_run_opts{CEN_SCHEDULE_DOUBLING, CEN_RULE_CENTRA, 0.0};
+    const cen_run_opts o = opts ? *opts : cen_run_opts{CEN_SCHEDULE_DOUBLING, CEN_RULE_CENTRA, 0.0, 0, 0};
     CEN_REQUIRE(g && S_out && S_size && covered && m_final && rounds, CEN_EINVAL, "cen_run: null argument");
     CEN_REQUIRE(k >= 1 && t >= 1 && eps > 0.0 && eps < a && delta > 0.0 && delta < 1.0 && m0 >= 1 && m_cap >= m0,
                 CEN_EINVAL, "cen_run: need k >= 1, t >= 1, 0 < eps < 1-1/e, 0 < delta < 1, 1 <= m0 <= m_cap");
@@ -398,7 +414,7 @@ int cen_run_ex(const cen_graph *g, int32_t k, double eps, double delta, int32_t 
                     (o.schedule == CEN_SCHEDULE_DOUBLING || o.alpha > 1.0),
                 CEN_EINVAL, "cen_run: unknown schedule, or alpha <= 1 for a growing schedule");
     CEN_REQUIRE(o.rule == CEN_RULE_CENTRA || o.rule == CEN_RULE_HEDGE_P, CEN_EINVAL, "cen_run: unknown rule");
-    int crc = cen_job_create(g, seed, t, stream, &job);
+    int crc = cen_job_create_space(g, seed, t, o.space, o.kappa, stream, &job);
     if (crc) return crc;
     std::vector<int64_t> Rnum(t);
     uint64_t m_prev = 0;

@@ -186,6 +186,7 @@ enum KClass : int {
   K_GRAPH,       // graph validation / in-CSR
   K_MISC,        // scans, fills
   K_BIDIR,       // bidirectional sampler (search, cone, counts, walk)
+  K_SPACE,       // samplers of the kappa-path and triangle spaces
   K_COUNT
 };
 static_assert(K_COUNT <= CEN_NKCLASS, "too many kernel classes");
@@ -274,6 +275,10 @@ struct cen_graph {
   // Set once most bidirectional searches on this graph outgrew their node
   // table: later jobs (without an explicit table size) use direct words only.
   mutable std::atomic<bool> bidir_table_off{false};
+  // Triangle ranks (triangle space): exclusive prefix of per-arc counts, built once.
+  std::mutex tri_mu;
+  cen::DevBuf tri_off;
+  int64_t tri_total = -1;
   const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
   const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
   const cen::ChunkTable &in_chunks() const { return directed ? in_chunks_own : out_chunks; }

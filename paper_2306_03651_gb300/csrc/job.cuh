@@ -121,11 +121,19 @@ struct cen_job {
   uint64_t bidir_deferred_search = 0;       // samples it left whole to the bit-parallel sampler
   uint64_t bidir_deferred_walk = 0;         // samples whose walk it left (distance known)
   uint64_t bidir_migrated = 0;              // searches that outgrew the small table
+  // hyper-edge space (CEN_SPACE_*) and the kappa of the kappa-path space
+  int32_t space = 0;
+  int32_t kappa = 0;
+  cen::DevBuf space_buf;                    // kappa-path walks before they are packed
 };
 
 namespace cen {
 void sample_append(cen_job *job, uint64_t m_new);
 void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap);
+void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out);
+int64_t triangle_index(cen_job *job);
+void triangle_sample(cen_job *job, uint64_t j0, uint64_t count);
+int max_kappa();
 int bidir_resident_slots();
 void build_incidence(cen_job *job);
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered);

@@ -20,7 +20,7 @@ const std::string &last_error() { return g_last_error; }
 // --------------------------------------------------------- accounting
 const char *const kClassNames[K_COUNT] = {"pairs", "target_check", "expand_push", "expand_pull", "level_finalize",
                                           "cone", "cone_sigma", "walk", "append", "sign", "transpose", "greedy",
-                                          "rade", "select", "graph", "misc", "bidir"};
+                                          "rade", "select", "graph", "misc", "bidir", "space"};
 
 Stats::Stats() {
   memset(k, 0, sizeof(k));

@@ -421,11 +421,24 @@ __global__ void __launch_bounds__(1024) k_wave_lengths(int count, uint64_t jbase
   if (threadIdx.x == 0) ctl->total = carry;
 }
 
-// lens[i] = max(d[j0+i] - 1, 0): member counts of samples j0 .. j0+count-1.
-__global__ void k_lengths_of(const int32_t *__restrict__ pd, uint64_t j0, uint64_t count, int32_t *lens) {
+// Member counts of samples j0 .. j0+count-1 from their third field: set
+// betweenness max(d - 1, 0) (the interior of a d-arc path), kappa-path the
+// steps taken, triangle 3.
+__global__ void k_lengths_of(const int32_t *__restrict__ pd, uint64_t j0, uint64_t count, int space, int32_t *lens) {
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
     const int d = pd[j0 + i];
-    lens[i] = d >= 2 ? d - 1 : 0;
+    lens[i] = space == CEN_SPACE_KPATH ? d : space == CEN_SPACE_TRIANGLE ? 3 : (d >= 2 ? d - 1 : 0);
+  }
+}
+
+// Warp per new sample: lens[i] members from src[i * stride] to the store.
+__global__ void k_gather_strided(uint64_t count, uint64_t j0, int stride, const int32_t *__restrict__ lens,
+                                 const int64_t *__restrict__ hoff, const int32_t *__restrict__ src, int32_t *hmem) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += nwarps) {
+    const int64_t h = hoff[j0 + i];
+    for (int q = lane; q < lens[i]; q += 32) hmem[h + q] = src[i * (uint64_t)stride + q];
   }
 }
 
@@ -1255,7 +1268,8 @@ int64_t offsets_from_distances(cen_job *job, uint64_t m0, uint64_t m_new) {
   w0.lens.ensure(4 * (size_t)m_new, st);
   w0.exoff.ensure(8 * ((size_t)m_new + 1), st);
   launch(S, K_APPEND, st, [&] {
-    k_lengths_of<<<grid_for(m_new, 256), 256, 0, st>>>(job->pd.as<int32_t>(), m0, m_new, w0.lens.as<int32_t>());
+    k_lengths_of<<<grid_for(m_new, 256), 256, 0, st>>>(job->pd.as<int32_t>(), m0, m_new, job->space,
+                                                        w0.lens.as<int32_t>());
   });
   counts_to_offsets(w0.lens.as<int32_t>(), w0.exoff.as<int64_t>(), (size_t)m_new, w0.scan_tmp, st, S);
   launch(S, K_APPEND, st, [&] {
@@ -1384,6 +1398,35 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   job->bidir_deferred_search += h.nsearch;
   job->bidir_deferred_walk += walk.size();
   job->bidir_migrated += h.nmigrate;
+  return total;
+}
+
+// kappa-path space: a warp per walk into a strided buffer, then packed.
+int64_t append_kpath(cen_job *job, uint64_t m0, uint64_t m_new) {
+  cudaStream_t st = job->st;
+  job->space_buf.ensure(4 * (size_t)m_new * (size_t)job->kappa, st);
+  kpath_sample(job, m0, m_new, job->space_buf.as<int32_t>());
+  const int64_t total = offsets_from_distances(job, m0, m_new);
+  job->hmem.ensure(4 * (size_t)(job->members + total + 1), st, 4 * (size_t)job->members);
+  WaveWS &w0 = wave_ws0(job);
+  launch(&job->stats, K_APPEND, st, [&] {
+    k_gather_strided<<<grid_for(m_new * 32, 256), 256, 0, st>>>(m_new, m0, job->kappa, w0.lens.as<int32_t>(),
+                                                                job->hoff.as<int64_t>(), job->space_buf.as<int32_t>(),
+                                                                job->hmem.as<int32_t>());
+  });
+  return total;
+}
+
+// Triangle space: three members each, written in place.
+int64_t append_triangle(cen_job *job, uint64_t m0, uint64_t m_new) {
+  cudaStream_t st = job->st;
+  const int64_t total = offsets_from_distances(job, m0, m_new);
+  job->hmem.ensure(4 * (size_t)(job->members + total + 1), st, 4 * (size_t)job->members);
+  triangle_sample(job, m0, m_new);
+  int *h = (int *)host_staging(job, 4);  // |h| = 3 for every sample
+  *h = 3;
+  CEN_CK(cudaMemcpyAsync(job->bmax.p, h, 4, cudaMemcpyHostToDevice, st));
+  CEN_CK(cudaStreamSynchronize(st));
   return total;
 }
 
@@ -1520,7 +1563,13 @@ void sample_append(cen_job *job, uint64_t m_new) {
   job->sign.ensure(4 * (size_t)job->nw * m1, st, 4 * (size_t)job->nw * m0);
   job->bmax.ensure(4, st, 4);
   if (m0 == 0) CEN_CK(cudaMemsetAsync(job->bmax.p, 0, 4, st));
-  const int64_t total = job->sampler == 0 ? append_bidir(job, m0, m_new) : append_waves(job, m0, m_new);
+  int64_t total;
+  if (job->space == CEN_SPACE_KPATH)
+    total = append_kpath(job, m0, m_new);
+  else if (job->space == CEN_SPACE_TRIANGLE)
+    total = append_triangle(job, m0, m_new);
+  else
+    total = job->sampler == 0 ? append_bidir(job, m0, m_new) : append_waves(job, m0, m_new);
   // sign columns of the new samples
   {
     const int nblk = (job->nw + 3) / 4;
