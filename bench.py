@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--bidir-queue", type=int, default=0, help="nodes per ball / cone list (0: default)")
     ap.add_argument("--bidir-table", type=int, default=-2,
                     help="node-table entries per CTA (-1: sized for L2, 0: none; -2: library default)")
+    ap.add_argument("--space", type=int, default=0, help="hyper-edge space: 0 set betweenness, 1 kappa-path, 2 triangle")
+    ap.add_argument("--kappa", type=int, default=8, help="path bound of the kappa-path space")
     ap.add_argument("--tsweep-m", type=int, default=500000)
     ap.add_argument("--tsweep-t", default="1,10,50,100,250,500")
     ap.add_argument("--tsweep-k", type=int, default=50)
@@ -171,8 +173,11 @@ def reduce_max(value: float, device) -> float:
 
 
 # ----------------------------------------------------------------- gpu arm
+SPACE = {"space": 0, "kappa": 0}  # hyper-edge space of the round mode (set from the arguments)
+
+
 def gpu_step(P, graph, wl, M, seed):
-    job = P.Job(graph, seed, wl.t)
+    job = P.Job(graph, seed, wl.t, space=SPACE["space"], kappa=SPACE["kappa"])
     job.set_timing(True)
     job.sample(M)
     SAMPLER_INFO.append(job.sampler_info())
@@ -217,6 +222,7 @@ def run_gpu(args, rank, world):
     g = wl.graph
     graph = P.Graph.of(g)
     apply_sampler_args(P, graph, args)
+    SPACE.update(space=args.space, kappa=args.kappa if args.space == 1 else 0)
     M = args.m
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2 (129 MB)
     seed0 = rank_seed(rank)
@@ -262,7 +268,7 @@ def run_gpu(args, rank, world):
             t1 = time.perf_counter()
             gg = P.Graph(g.n, off_h.numpy(), col_h.numpy(), g.directed)
             apply_sampler_args(P, gg, args)
-            job = P.Job(gg, seed0 + 2000 + s, wl.t)
+            job = P.Job(gg, seed0 + 2000 + s, wl.t, space=SPACE["space"], kappa=SPACE["kappa"])
             job.sample(M)
             S, cov = job.greedy_cover(wl.k)
             Rnum, Wnum, b = job.mcera(wl.k)
@@ -305,7 +311,8 @@ def run_gpu(args, rank, world):
                 "aggregate_counted_GBps": counted / (total_ms / 1e3) / 1e9}
     launches = int(sum(v["launches"] for v in stats.values()))
     out = {
-        "metric": "sampled paths/s", "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+        "metric": "sampled paths/s" if args.space == 0 else "sampled hyper-edges/s", "value": value,
+        "unit": "paths/s" if args.space == 0 else "hyper-edges/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}; one Algorithm-1 round per step at m={M} pairs, "
