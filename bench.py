@@ -318,6 +318,7 @@ def run_gpu(args, rank, world):
         "config": {"workload": f"{args.workload}: {desc}; one Algorithm-1 round per step at m={M} pairs, "
                                f"k={wl.k}, t={wl.t}, eps={wl.eps}, delta={wl.delta}",
                    "n": g.n, "arcs": g.nnz, "pairs_per_step": M, "l2": "flushed (256 MB write) between steps",
+                   "space": ["set betweenness", f"kappa-path (kappa={args.kappa})", "triangle"][args.space],
                    "parallelism": f"replicas x{world}"},
         "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
         "sampler": SAMPLER_INFO[-1] if SAMPLER_INFO else None,
