@@ -119,13 +119,41 @@ __device__ __forceinline__ int bi_claim(const BiMap &M, int v, int x, int level,
   return 1;
 }
 
+// One probe for discovery: returns 0 when this call claimed v for side x on
+// `level`, 1 when v was already in the search (its state in *found), 2 when
+// it was not and `claim` was false (nothing written).
+__device__ __forceinline__ int bi_visit(const BiMap &M, int v, int x, int level, bool claim, uint64_t &found) {
+  const uint64_t mine = h_make((uint32_t)v, M.ep, x, level);
+  uint32_t p = h_slot((uint32_t)v, M.mask);
+  for (uint32_t k = 0; k <= M.mask; ++k) {
+    uint64_t e = ld_vol(&M.tab[p]);
+    for (;;) {
+      if (h_epoch(e) == M.ep) {
+        if (h_node(e) == (uint32_t)v) {
+          found = e;
+          return 1;
+        }
+        break;  // another node's entry: next position
+      }
+      if (!claim) return 2;
+      const unsigned long long old =
+          atomicCAS((unsigned long long *)&M.tab[p], (unsigned long long)e, (unsigned long long)mine);
+      if (old == e) return 0;
+      e = old;  // taken meanwhile: look at it again
+    }
+    p = (p + 1) & M.mask;
+  }
+  return 2;
+}
+
 struct BiShared {
   int lo[2][kBiMaxLevels + 1];                  // ball queue of side x: level L is lo[x][L] .. lo[x][L+1]
   unsigned long long hcost[2][kBiMaxLevels];    // arcs out of level L of side x (out-arcs forward, in-arcs backward)
   int cs[2][kBiMaxLevels];                      // cone list of side x: level L is cs[x][L] .. ce[x][L]
   int ce[2][kBiMaxLevels];
   unsigned long long red[kBiWarps];
-  unsigned long long addcost, sum, arcs;
+  unsigned long long addcost, sum, sum2, arcs;
+  unsigned long long red2[kBiWarps];
   int added, nheavy, ccount[2], ncross;
   int hcount, hfull;  // small-table entries of this search; set once it is half full
   int lvl[2];
@@ -186,6 +214,43 @@ __device__ unsigned long long bi_row_sum(const uint32_t *list, int cnt, const in
   const unsigned long long r = sh.sum;
   __syncthreads();
   return r;
+}
+
+// Row-length sums of two lists at once (list1 in o1, list2 in o2), into
+// *s1, *s2.  Called by all threads.
+__device__ void bi_row_sum2(const uint32_t *list1, int cnt1, const int64_t *__restrict__ o1, const uint32_t *list2,
+                            int cnt2, const int64_t *__restrict__ o2, BiShared &sh, unsigned long long *s1,
+                            unsigned long long *s2) {
+  const int tid = threadIdx.x;
+  unsigned long long a = 0, b = 0;
+  for (int i = tid; i < cnt1; i += kBiThreads) {
+    const int v = (int)list1[i];
+    a += (unsigned long long)(o1[v + 1] - o1[v]);
+  }
+  for (int i = tid; i < cnt2; i += kBiThreads) {
+    const int v = (int)list2[i];
+    b += (unsigned long long)(o2[v + 1] - o2[v]);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if ((tid & 31) == 0) {
+    sh.red[tid >> 5] = a;
+    sh.red2[tid >> 5] = b;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long ta = 0, tb = 0;
+    for (int w = 0; w < kBiWarps; ++w) {
+      ta += sh.red[w];
+      tb += sh.red2[w];
+    }
+    sh.sum = ta;
+    sh.sum2 = tb;
+  }
+  __syncthreads();
+  *s1 = sh.sum;
+  *s2 = sh.sum2;
+  __syncthreads();
 }
 
 // For every node v of list[0, cnt) and every arc of v's row in (o, c), calls
@@ -434,21 +499,21 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       const int32_t *c = x ? A.rcol : A.col;
       const int hlimit = (int)(H1 >> 1);
       bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
-        uint64_t sw = bi_find(M, w);
-        if (!sw) {
-          if (*(volatile int *)&sh.met || *(volatile int *)&sh.hfull) return;  // no more claims needed / possible
-          if (bi_claim(M, w, x, L + 1, sw) == 0) {
-            const int pos = atomicAdd(&sh.added, 1);
-            if ((int64_t)f1 + pos < QC)
-              qx[f1 + pos] = (uint32_t)w;
-            else
-              sh.ovf = 1;
-            atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
-            if (tier == 1 && atomicAdd(&sh.hcount, 1) + 1 >= hlimit) sh.hfull = 1;
-            return;
-          }
-          if (!sw) return;
+        uint64_t sw = 0;
+        // once the distance is known, or the small table is half full, nothing more is claimed
+        const bool claim = !(*(volatile int *)&sh.met || *(volatile int *)&sh.hfull);
+        const int r = bi_visit(M, w, x, L + 1, claim, sw);
+        if (r == 0) {
+          const int pos = atomicAdd(&sh.added, 1);
+          if ((int64_t)f1 + pos < QC)
+            qx[f1 + pos] = (uint32_t)w;
+          else
+            sh.ovf = 1;
+          atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
+          if (tier == 1 && atomicAdd(&sh.hcount, 1) + 1 >= hlimit) sh.hfull = 1;
+          return;
         }
+        if (r == 2 || !sw) return;
         if (st_side(sw) != x) {  // an arc between the balls: (tail, head) in s -> t direction
           sh.met = 1;
           const int pos = atomicAdd(&sh.ncross, 1);
@@ -663,8 +728,8 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
           __syncthreads();
           continue;
         }
-        const unsigned long long pull = bi_row_sum(cur, ncur, A.roff, sh);
-        const unsigned long long push = bi_row_sum(prev, nprev, A.off, sh);
+        unsigned long long pull = 0, push = 0;
+        bi_row_sum2(cur, ncur, A.roff, prev, nprev, A.off, sh, &pull, &push);
         if (pull <= push) {
           bi_sigma_pull(cur, ncur, D, d, M, sg, A.roff, A.rcol, 8, heavy, sh);
         } else {
