@@ -227,6 +227,9 @@ inline void launch(Stats *S, int cls, cudaStream_t st, F &&f) {
 // Blocks of `block` threads that are resident at once on the current device
 // (SM count x blocks per SM for this kernel), cached per kernel.
 int resident_grid(const void *kernel, int block);
+// Blocks for a cooperative launch of `kernel` (all resident at once: one per
+// SM up to what fits), or 0 when the device cannot launch cooperatively.
+int cooperative_grid(const void *kernel, int block);
 
 inline int grid_for(size_t items, int per_block, int cap = 152 * 32) {
   size_t g = (items + per_block - 1) / per_block;

@@ -1,5 +1,9 @@
 // Node -> sample incidence and greedyCover(k, H) (Sec. 3.1; Alg. 1 line "greedyCover").
+#include <cooperative_groups.h>
+
 #include "job.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace cen {
 
@@ -118,6 +122,59 @@ __global__ void __launch_bounds__(256) k_greedy_update(const int64_t *__restrict
   }
 }
 
+// All k iterations in one cooperative launch: each iteration is the argmax
+// (block maxima, one atomicMax per block), a grid barrier, the update of the
+// picked node's samples, and another barrier.  The picks, ties and counts
+// are those of k_greedy_argmax / k_greedy_update.  A cooperative launch runs
+// only when every block is resident at once, so the barriers always complete.
+__global__ void __launch_bounds__(256) k_greedy_all(const int64_t *__restrict__ noff, const int32_t *__restrict__ nsamp,
+                                                    const int64_t *__restrict__ hoff, const int32_t *__restrict__ hmem,
+                                                    int32_t *gain, int32_t n, uint32_t *covered, GreedyCtl *ctl,
+                                                    int k) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ unsigned long long wb[8];
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int it = 0; it < k; ++it) {
+    const int slot = it & 1;
+    unsigned long long best = 0;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+      const unsigned long long key = ((unsigned long long)(uint32_t)gain[u] << 32) | (0xFFFFFFFFu - (uint32_t)u);
+      best = key > best ? key : best;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+      best = y > best ? y : best;
+    }
+    if (lane == 0) wb[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = wb[w] > best ? wb[w] : best;
+      if (best) atomicMax(&ctl->key[slot], best);
+    }
+    grid.sync();
+    const unsigned long long key = ((volatile unsigned long long *)ctl->key)[slot];
+    const uint32_t g = (uint32_t)(key >> 32);
+    if (g == 0) break;  // every block sees the same key: all leave together
+    const int32_t u = (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      ctl->S[it] = u;
+      ctl->size = it + 1;
+      ctl->covered += g;
+      ctl->key[slot ^ 1] = 0;
+    }
+    const int64_t r0 = noff[u], r1 = noff[u + 1];
+    for (int64_t q = r0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); q < r1; q += nwarps) {
+      const int32_t j = nsamp[q];
+      const uint32_t mask = 1u << (j & 31);
+      if (covered[j >> 5] & mask) continue;
+      if (lane == 0) atomicOr(&covered[j >> 5], mask);
+      for (int64_t e = hoff[j] + lane; e < hoff[j + 1]; e += 32) atomicSub(&gain[hmem[e]], 1);
+    }
+    grid.sync();
+  }
+}
+
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered) {
   CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_greedy_cover: k must be >= 1");
   Range range("cen_greedy_cover");
@@ -134,16 +191,33 @@ void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t
   GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
   launch(St, K_GREEDY, st,
          [&] { k_gain_init<<<grid_for(n, 256), 256, 0, st>>>(job->c.as<int32_t>(), job->gain.as<int32_t>(), n); });
-  const int gblocks = grid_for((size_t)n, 256, 152 * 4);
-  for (int it = 0; it < k; ++it) {
-    const int slot = it & 1;
-    launch(St, K_GREEDY, st,
-           [&] { k_greedy_argmax<<<gblocks, 256, 0, st>>>(job->gain.as<int32_t>(), n, ctl, slot); });
+  const int coop = cooperative_grid((const void *)k_greedy_all, 256);
+  if (coop > 0) {
+    const int64_t *a_noff = job->noff.as<int64_t>();
+    const int32_t *a_nsamp = job->nsamp.as<int32_t>();
+    const int64_t *a_hoff = job->hoff.as<int64_t>();
+    const int32_t *a_hmem = job->hmem.as<int32_t>();
+    int32_t *a_gain = job->gain.as<int32_t>();
+    int32_t a_n = n;
+    uint32_t *a_cov = job->covered.as<uint32_t>();
+    int a_k = k;
+    void *args[] = {&a_noff, &a_nsamp, &a_hoff, &a_hmem, &a_gain, &a_n, &a_cov, &ctl, &a_k};
     launch(St, K_GREEDY, st, [&] {
-      k_greedy_update<<<152 * 4, 256, 0, st>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
-                                                job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
-                                                job->gain.as<int32_t>(), job->covered.as<uint32_t>(), ctl, slot, it);
+      CEN_CK(cudaLaunchCooperativeKernel((const void *)k_greedy_all, dim3(coop), dim3(256), args, 0, st));
     });
+  } else {
+    const int gblocks = grid_for((size_t)n, 256, 152 * 4);
+    for (int it = 0; it < k; ++it) {
+      const int slot = it & 1;
+      launch(St, K_GREEDY, st,
+             [&] { k_greedy_argmax<<<gblocks, 256, 0, st>>>(job->gain.as<int32_t>(), n, ctl, slot); });
+      launch(St, K_GREEDY, st, [&] {
+        k_greedy_update<<<152 * 4, 256, 0, st>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
+                                                  job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
+                                                  job->gain.as<int32_t>(), job->covered.as<uint32_t>(), ctl, slot,
+                                                  it);
+      });
+    }
   }
   char *h = (char *)host_staging(job, cbytes);
   CEN_CK(cudaMemcpyAsync(h, ctl, cbytes, cudaMemcpyDeviceToHost, st));

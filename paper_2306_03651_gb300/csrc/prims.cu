@@ -5,6 +5,7 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -334,5 +335,16 @@ void keep_pool_memory() {
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
   }
   done[dev] = true;
+}
+}  // namespace cen
+
+namespace cen {
+int cooperative_grid(const void *kernel, int block) {
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) return 0;
+  return sms * std::min(per_sm, 2);
 }
 }  // namespace cen
