@@ -39,9 +39,9 @@ def test_kpath_parity(name, kappa):
     assert np.array_equal(Rn, Rn2) and Wn == Wn2 and b == b2 <= kappa
 
 
-@pytest.mark.parametrize("name", ["ba300", "rmat12_lcc", "grid_rewired"])
+@pytest.mark.parametrize("name", ["ba300", "rmat12_lcc", "ba2000"])
 def test_triangle_parity(name):
-    g = GRAPHS[name]
+    g = GRAPHS[name] if name in GRAPHS else I.ba(2000, 4, 1)
     og = O.Graph.of(g)
     job = P.Job(P.Graph.of(g), 17, 8, space=P.SPACE_TRIANGLE)
     ojob = O.Job(og, 17, 8, space=O.SPACE_TRIANGLE)
@@ -72,5 +72,7 @@ def test_spaces_reject_bad_arguments():
     with pytest.raises(P.CenError):
         P.Job(P.Graph.of(GRAPHS["rmat12_dir"]), 1, 4, space=P.SPACE_TRIANGLE)
     tree = I.from_edges(5, [0, 0, 1, 1], [1, 2, 3, 4], False)
-    with pytest.raises(P.CenError):
-        P.Job(P.Graph.of(tree), 1, 4, space=P.SPACE_TRIANGLE)
+    for g in (tree, GRAPHS["grid_rewired"]):  # no triangle: both sides reject the space
+        assert O.Graph.of(g).triangle_count() == 0
+        with pytest.raises(P.CenError):
+            P.Job(P.Graph.of(g), 1, 4, space=P.SPACE_TRIANGLE)
