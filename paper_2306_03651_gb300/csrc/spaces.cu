@@ -100,23 +100,35 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_kpath(uint64_t j0, uint64_t
   }
 }
 
-// Number of common neighbours w > v of u and v: binary search of the shorter
-// row's entries above v in the longer row.  With want >= 0, the common
-// neighbour of that rank is returned in *w_out instead.
+// Common neighbours w > v of u and v, ascending: the shorter row's entries
+// above v are looked up in the longer row by binary search (both rows are
+// sorted, so either order of the two rows gives the same ascending w).
+// Returns how many there are; with want >= 0, stops at the one of that rank
+// and returns it in *w_out.
 __device__ int64_t common_above(const int64_t *__restrict__ off, const int32_t *__restrict__ col, int32_t u, int32_t v,
                                 int64_t want, int32_t *w_out) {
   int64_t a0 = off[u], a1 = off[u + 1], b0 = off[v], b1 = off[v + 1];
-  if (want < 0 && a1 - a0 > b1 - b0) {  // counting: search the shorter row's entries in the longer
-    int64_t t0 = a0, t1 = a1;
+  if (a1 - a0 > b1 - b0) {
+    const int64_t t0 = a0, t1 = a1;
     a0 = b0;
     a1 = b1;
     b0 = t0;
     b1 = t1;
   }
+  {  // first entry of the shorter row above v
+    int64_t lo = a0, hi = a1;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (col[mid] <= v)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    a0 = lo;
+  }
   int64_t c = 0;
   for (int64_t a = a0; a < a1; ++a) {
     const int32_t w = col[a];
-    if (w <= v) continue;
     int64_t lo = b0, hi = b1;
     while (lo < hi) {
       const int64_t mid = lo + ((hi - lo) >> 1);
@@ -125,6 +137,7 @@ __device__ int64_t common_above(const int64_t *__restrict__ off, const int32_t *
       else
         hi = mid;
     }
+    b0 = lo;  // w ascends, so the search range only shrinks
     if (lo < b1 && col[lo] == w) {
       if (c == want) {
         *w_out = w;
