@@ -307,7 +307,10 @@ def run_gpu(args, rank, world):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                 "avg_launch_ms": avg_ms, "launches": stats[dom]["launches"],
                 "algorithmic_bytes_per_launch": per_launch_bytes,
-                "note": "per-launch event times of concurrent wave pipelines include sharing the GPU",
+                "note": ("one launch samples the whole step; the kernel is bound by the latency of dependent L2 "
+                         "accesses (DRAM traffic about 0.9x the counted bytes, profiles/bidir_dram.md)"
+                         if dom == "bidir" else
+                         "per-launch event times of concurrent wave pipelines include sharing the GPU"),
                 "aggregate_counted_GBps": counted / (total_ms / 1e3) / 1e9}
     launches = int(sum(v["launches"] for v in stats.values()))
     out = {
