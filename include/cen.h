@@ -257,11 +257,10 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
                                     1: bit-parallel waves only.  Hyper-edges are identical. */
 #define CEN_PARAM_BIDIR_BUDGET 6 /* device bytes for the bidirectional sampler's per-CTA workspace,
                                     >= 2^20 (default 2^34); fewer CTAs run when it is small.  One CTA
-                                    needs 8 h + 16 H + 36 q bytes (q = min(n, queue), H = the power of
+                                    needs 8 h + 16 H + 28 q bytes (q = min(n, queue), H = the power of
                                     two >= 4 q, h = small-table entries), whatever the graph */
 #define CEN_PARAM_BIDIR_QUEUE 7  /* nodes one CTA may hold per ball or cone side, 16 .. 2^27 (default
-                                    2^16; used: at most n and 2^24 - 1024); larger searches go to the
-                                    bit-parallel sampler */
+                                    2^16, at most n); larger searches go to the bit-parallel sampler */
 #define CEN_PARAM_BIDIR_TABLE 8  /* entries of each CTA's small node table: a power of two in
                                     2^10 .. 2^24 (at most H / 2), 0 for none (searches use the large
                                     table of H entries only), or -1 (default) to size all CTAs' small

@@ -152,10 +152,9 @@ struct BiShared {
   int cs[2][kBiMaxLevels];                      // cone list of side x: level L is cs[x][L] .. ce[x][L]
   int ce[2][kBiMaxLevels];
   unsigned long long red[kBiWarps];
-  unsigned long long addpack;  // claims of the level being built: count << 40 | arcs of their rows
-  unsigned long long sum, sum2, arcs;
+  unsigned long long addcost, sum, sum2, arcs;
   unsigned long long red2[kBiWarps];
-  int nheavy, ccount[2], ncross;
+  int added, nheavy, ccount[2], ncross;
   int hcount, hfull;  // small-table entries of this search; set once it is half full
   int lvl[2];
   int met, ovf, xovf;
@@ -389,8 +388,8 @@ struct BiArgs {
   uint32_t mask1;
   uint64_t *tab2;     // [slots][H2] large tables
   uint32_t mask2;
-  uint32_t *lists;    // [slots][9][QC]: ball queues and cone lists (forward, backward), heavy rows,
-                      //                  crossing-arc tails and heads, ball row starts (forward, backward)
+  uint32_t *lists;    // [slots][7][QC]: ball queues and cone lists (forward, backward), heavy rows,
+                      //                  crossing-arc tails and heads
   uint64_t *sig;      // [slots][H2]: path counts by table position
   uint32_t *epochs;   // [slots][2]: epochs of the small and the large table
   int64_t QC;
@@ -412,14 +411,11 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
   __shared__ BiShared sh;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t QC = A.QC;
-  uint32_t *lists = A.lists + (size_t)blockIdx.x * 9 * (size_t)QC;
+  uint32_t *lists = A.lists + (size_t)blockIdx.x * 7 * (size_t)QC;
   uint32_t *q[2] = {lists, lists + QC};
   uint32_t *cl[2] = {lists + 2 * QC, lists + 3 * QC};
   uint32_t *heavy = lists + 4 * QC;
   uint32_t *xt = lists + 5 * QC, *xh = lists + 6 * QC;
-  // qb[x][i]: where the row of ball entry i starts in its level's arc space
-  // (the rows of one level, in queue order, laid end to end from 0)
-  uint32_t *qb[2] = {lists + 7 * QC, lists + 8 * QC};
   const uint32_t H1 = A.mask1 ? A.mask1 + 1 : 0, H2 = A.mask2 + 1;
   uint64_t *sg = A.sig + (size_t)blockIdx.x * (size_t)H2;
   uint64_t *tab1 = H1 ? A.tab1 + (size_t)blockIdx.x * (size_t)H1 : nullptr;
@@ -462,7 +458,6 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       bi_claim(M, t, 1, 0, f);
       q[0][0] = (uint32_t)s;
       q[1][0] = (uint32_t)t;
-      qb[0][0] = qb[1][0] = 0;
       sh.lo[0][0] = 0;
       sh.lo[0][1] = 1;
       sh.lo[1][0] = 0;
@@ -494,32 +489,27 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       const unsigned long long fcost = sh.hcost[x][L];
       __syncthreads();
       if (tid == 0) {
-        sh.addpack = 0;
+        sh.added = 0;
+        sh.addcost = 0;
         sh.ncross = 0;
         sh.xovf = 0;
       }
-      __syncthreads();
-      uint32_t *qx = q[x], *qbx = qb[x];
+      uint32_t *qx = q[x];
       const int64_t *o = x ? A.roff : A.off;
       const int32_t *c = x ? A.rcol : A.col;
       const int hlimit = (int)(H1 >> 1);
-      auto visit = [&](int v, int w) {
+      bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
         uint64_t sw = 0;
-        // once the distance is known, the small table is half full or the
-        // queue is full, nothing more is claimed
-        const bool claim = !(*(volatile int *)&sh.met || *(volatile int *)&sh.hfull || *(volatile int *)&sh.ovf);
+        // once the distance is known, or the small table is half full, nothing more is claimed
+        const bool claim = !(*(volatile int *)&sh.met || *(volatile int *)&sh.hfull);
         const int r = bi_visit(M, w, x, L + 1, claim, sw);
         if (r == 0) {
-          const unsigned long long deg = (unsigned long long)(o[w + 1] - o[w]);
-          const unsigned long long old = atomicAdd(&sh.addpack, (1ull << 40) | deg);
-          const int64_t pos = (int64_t)(old >> 40);
-          const unsigned long long base = old & ((1ull << 40) - 1);
-          if (f1 + pos < QC && base + deg <= 0xFFFFFFFFull) {
+          const int pos = atomicAdd(&sh.added, 1);
+          if ((int64_t)f1 + pos < QC)
             qx[f1 + pos] = (uint32_t)w;
-            qbx[f1 + pos] = (uint32_t)base;
-          } else {
+          else
             sh.ovf = 1;
-          }
+          atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
           if (tier == 1 && atomicAdd(&sh.hcount, 1) + 1 >= hlimit) sh.hfull = 1;
           return;
         }
@@ -534,40 +524,7 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
             sh.xovf = 1;
           }
         }
-      };
-      {
-        // every thread takes an equal contiguous range of the frontier's arcs
-        // (its rows laid end to end), found by one binary search over the
-        // row starts, then walks it row by row
-        const unsigned long long a0 = fcost * (unsigned long long)tid / kBiThreads;
-        const unsigned long long a1 = fcost * (unsigned long long)(tid + 1) / kBiThreads;
-        if (a0 < a1) {
-          int lo = f0, hi = f1;  // last entry whose row starts at or before a0
-          while (hi - lo > 1) {
-            const int mid = lo + ((hi - lo) >> 1);
-            if ((unsigned long long)qbx[mid] <= a0)
-              lo = mid;
-            else
-              hi = mid;
-          }
-          int i = lo;
-          unsigned long long base = qbx[i], next = i + 1 < f1 ? qbx[i + 1] : fcost;
-          int v = (int)qx[i];
-          int64_t e0 = o[v];
-          for (unsigned long long a = a0; a < a1; ++a) {
-            while (a >= next) {  // rows of length zero are stepped over
-              ++i;
-              base = next;
-              next = i + 1 < f1 ? qbx[i + 1] : fcost;
-              v = (int)qx[i];
-              e0 = o[v];
-            }
-            visit(v, c[e0 + (int64_t)(a - base)]);
-          }
-          atomicAdd(&sh.arcs, a1 - a0);
-        }
-      }
-      __syncthreads();
+      });
       if (sh.met) {
         if (tid == 0) sh.d = sh.lvl[0] + sh.lvl[1] + 1;
         break;
@@ -611,12 +568,11 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
         if (tid == 0) sh.status = 1;
         break;
       }
-      const int added = (int)(sh.addpack >> 40);
-      if (added == 0) break;  // this side's ball is closed: t is unreachable
+      if (sh.added == 0) break;  // this side's ball is closed: t is unreachable
       __syncthreads();
       if (tid == 0) {
-        sh.lo[x][L + 2] = f1 + added;
-        sh.hcost[x][L + 1] = sh.addpack & ((1ull << 40) - 1);
+        sh.lo[x][L + 2] = f1 + sh.added;
+        sh.hcost[x][L + 1] = sh.addcost;
         sh.lvl[x] = L + 1;
       }
       __syncthreads();

@@ -51,9 +51,8 @@ struct WaveWS {
 // Workspace of the bidirectional sampler (bidir.cu): for each of `nslots`
 // resident CTAs, a small table of H1 entries (0: none) and a large one of H2
 // = 4 QC entries, zeroed once (entries are epoch-stamped, so nothing is
-// cleared between samples), nine lists of QC entries (two ball queues, two
-// cone lists, heavy rows, crossing-arc tails and heads, the balls' row
-// starts) and H2 path counts.
+// cleared between samples), seven lists of QC entries (two ball queues, two
+// cone lists, heavy rows, crossing-arc tails and heads) and H2 path counts.
 // Nothing in it grows with the graph.
 struct BiCtl {
   unsigned long long next;     // next sample, relative to the launch's first

@@ -1289,11 +1289,10 @@ constexpr size_t kTableL2 = (size_t)80 << 20;
 void bidir_setup(cen_job *job, uint64_t m_new) {
   const int32_t n = job->g->n;
   cudaStream_t st = job->st;
-  // a level's claims are counted in 24 bits (see k_bidir): at most 2^24 - 2^10 per ball
-  const int64_t QC = std::max<int64_t>(16, std::min<int64_t>({(int64_t)n, job->bidir_queue, ((int64_t)1 << 24) - 1024}));
+  const int64_t QC = std::max<int64_t>(16, std::min<int64_t>(n, job->bidir_queue));
   int64_t H2 = 1024;
   while (H2 < 4 * QC) H2 *= 2;
-  auto per_slot = [&](int64_t h1) { return 8 * (size_t)h1 + 16 * (size_t)H2 + 9 * 4 * (size_t)QC; };
+  auto per_slot = [&](int64_t h1) { return 8 * (size_t)h1 + 16 * (size_t)H2 + 7 * 4 * (size_t)QC; };
   const size_t res = (size_t)bidir_resident_slots();
   int slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(0)));
   int64_t H1 = 0;
@@ -1317,7 +1316,7 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
     keep_pool_memory();
     if (H1) wk.tab1.ensure_exact(8 * (size_t)H1 * slots, st);
     wk.tab2.ensure_exact(8 * (size_t)H2 * slots, st);
-    wk.lists.ensure_exact(4 * 9 * (size_t)QC * slots, st);
+    wk.lists.ensure_exact(4 * 7 * (size_t)QC * slots, st);
     wk.sig.ensure_exact(8 * (size_t)H2 * slots, st);
     wk.epochs.ensure(8 * (size_t)slots, st);
     if (H1) CEN_CK(cudaMemsetAsync(wk.tab1.p, 0, 8 * (size_t)H1 * slots, st));

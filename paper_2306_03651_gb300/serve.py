@@ -63,7 +63,7 @@ def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: floa
     """Upper estimate of one job's device memory (admission policy, not the method).
 
     Bidirectional sampler: one workspace per resident CTA (a large node table
-    and as many path counts, H = 4 `bidir_queue` entries each, nine lists of
+    and as many path counts, H = 4 `bidir_queue` entries each, seven lists of
     `bidir_queue` entries, and a small table of at most 80 MiB over all CTAs),
     as many as fit in `bidir_budget`.  Wave workspace (the fallback): `levels` + 6 arrays
     of n*G words (G = wave words, at most 32 and at most 1 GB per array) and the
@@ -75,7 +75,7 @@ def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: floa
     h2 = 1024
     while h2 < 4 * qc:
         h2 *= 2
-    per_slot = 16 * h2 + 9 * 4 * qc
+    per_slot = 16 * h2 + 7 * 4 * qc
     bidir = min(resident_ctas, max(1, bidir_budget // per_slot)) * per_slot + (80 << 20)
     G = 32
     while G > 1 and n * G * 8 > (1 << 30):
