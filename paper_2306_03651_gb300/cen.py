@@ -274,9 +274,13 @@ class Job:
     def set_param(self, param: int, value: float):
         _check(_lib.cen_job_set_param(self.h, int(param), float(value)), "cen_job_set_param")
 
-    def tune(self, wave_words=None, wave_streams=None, push_ratio=None, level_budget=None):
+    def tune(self, wave_words=None, wave_streams=None, push_ratio=None, level_budget=None, sampler=None,
+             bidir_budget=None, bidir_queue=None, bidir_table=None):
+        """Speed and memory parameters (the samples do not depend on them)."""
         for p, v in ((PARAM_WAVE_WORDS, wave_words), (PARAM_WAVE_STREAMS, wave_streams),
-                     (PARAM_PUSH_RATIO, push_ratio), (PARAM_LEVEL_BUDGET, level_budget)):
+                     (PARAM_PUSH_RATIO, push_ratio), (PARAM_LEVEL_BUDGET, level_budget), (PARAM_SAMPLER, sampler),
+                     (PARAM_BIDIR_BUDGET, bidir_budget), (PARAM_BIDIR_QUEUE, bidir_queue),
+                     (PARAM_BIDIR_TABLE, bidir_table)):
             if v is not None:
                 self.set_param(p, v)
 

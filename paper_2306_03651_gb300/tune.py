@@ -1,8 +1,10 @@
 """Autotuner for the sampler's launch parameters.
 
-The wave width (slots per bit-parallel wave), the number of wave pipelines in
-flight and the top-down/bottom-up switch only change speed and memory: every
-configuration yields the same samples.  ``autotune`` times one probe round per
+The sampler choice (bidirectional with the bit-parallel fallback, or
+bit-parallel waves only), the bidirectional sampler's node-table size, and
+the wave parameters (wave width, wave pipelines in flight, top-down/bottom-up
+switch) only change speed and memory: every configuration yields the same
+samples.  ``autotune`` times one probe round per
 configuration on the caller's graph, checks that all configurations produced
 identical hyper-edges, and stores the fastest as the graph's default
 (``cen_graph_set_param``) so that later jobs, ``run``, ``run_batch`` and the
@@ -18,7 +20,10 @@ import numpy as np
 
 from . import cen as P
 
-DEFAULT_GRID = dict(wave_words=(8, 16, 32), wave_streams=(1, 2, 4), push_ratio=(2.0, 4.0, 16.0))
+DEFAULT_GRID = dict(sampler=(0, 1), bidir_table=(-1, 0, 8192), wave_streams=(1, 4))
+PARAM_IDS = {"wave_words": P.PARAM_WAVE_WORDS, "wave_streams": P.PARAM_WAVE_STREAMS, "push_ratio": P.PARAM_PUSH_RATIO,
+             "level_budget": P.PARAM_LEVEL_BUDGET, "sampler": P.PARAM_SAMPLER, "bidir_budget": P.PARAM_BIDIR_BUDGET,
+             "bidir_queue": P.PARAM_BIDIR_QUEUE, "bidir_table": P.PARAM_BIDIR_TABLE}
 
 
 def _digest(h: dict) -> str:
@@ -50,8 +55,6 @@ def autotune(graph: "P.Graph", t: int = 10, probe_pairs: int = 8192, seed: int =
         raise RuntimeError("autotune: configurations disagree on the samples")
     best, secs = min(table, key=lambda x: x[1])
     if apply:
-        for name, pid in (("wave_words", P.PARAM_WAVE_WORDS), ("wave_streams", P.PARAM_WAVE_STREAMS),
-                          ("push_ratio", P.PARAM_PUSH_RATIO)):
-            if name in best:
-                graph.set_param(pid, best[name])
+        for name, value in best.items():
+            graph.set_param(PARAM_IDS[name], value)
     return dict(best=best, seconds=secs, table=table, digest=digests.pop())

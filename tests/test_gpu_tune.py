@@ -47,6 +47,8 @@ def test_autotune_sets_graph_defaults_without_changing_results():
     res = tune.autotune(gg, t=8, probe_pairs=2048, grid=dict(wave_words=(4, 32), wave_streams=(1, 2),
                                                               push_ratio=(4.0,)))
     assert res["best"]["wave_words"] in (4, 32) and len(res["table"]) == 4
+    res = tune.autotune(gg, t=8, probe_pairs=2048, grid=dict(sampler=(0, 1), bidir_table=(-1, 0, 1024)))
+    assert res["best"]["sampler"] in (0, 1) and len(res["table"]) == 6
     after = P.run(gg, 8, 0.15, 0.1, 8, 3, m0=500)
     assert after["S"].tolist() == before["S"].tolist() and np.array_equal(after["log"], before["log"])
     with pytest.raises(P.CenError):
