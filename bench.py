@@ -285,7 +285,7 @@ def run_gpu(args, rank, world):
                "d2h_bytes_per_step": int(4 * wl.k + 8 * wl.t + 8 + 4 + 8 + 4)}
 
     # roofline: the kernel class with the most device time; its algorithmic
-    # bytes are counted by the kernels themselves
+    # bytes are counted by the kernels themselves, per unit of their class
     import json as _json
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(peaks_path):

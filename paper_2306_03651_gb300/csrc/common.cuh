@@ -276,7 +276,7 @@ struct cen_graph {
   double param[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // tuning defaults for jobs on this graph
   bool param_set[9] = {};                           // which of them were set
   // Set once most bidirectional searches on this graph outgrew their node
-  // table: later jobs (without an explicit table size) use direct words only.
+  // table: later jobs (without an explicit table size) use the large table only.
   mutable std::atomic<bool> bidir_table_off{false};
   // Triangle ranks (triangle space): exclusive prefix of per-arc counts, built once.
   std::mutex tri_mu;
