@@ -257,15 +257,12 @@ __device__ void bi_row_sum2(const uint32_t *list1, int cnt1, const int64_t *__re
 // f(v, w).  Rows of at most kBiHeavy arcs are scanned by a group of gs lanes;
 // longer rows are queued in `heavy` and scanned by the whole block.  Called
 // by all threads.
-// With kFresh the caller has already zeroed sh.nheavy before a barrier.
-template <bool kFresh = false, class F>
+template <class F>
 __device__ void bi_scan_rows(const uint32_t *list, int cnt, const int64_t *__restrict__ o,
                              const int32_t *__restrict__ c, int gs, uint32_t *heavy, BiShared &sh, F &&f) {
   const int tid = threadIdx.x;
-  if (!kFresh) {
-    if (tid == 0) sh.nheavy = 0;
-    __syncthreads();
-  }
+  if (tid == 0) sh.nheavy = 0;
+  __syncthreads();
   const int gl = tid & (gs - 1), gi = tid / gs, ng = kBiThreads / gs;
   unsigned long long arcs = 0;
   for (int i = gi; i < cnt; i += ng) {
@@ -470,11 +467,6 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       sh.hcost[1][0] = (unsigned long long)(A.roff[t + 1] - A.roff[t]);
       sh.hcount = 2;
       sh.hfull = 0;
-      sh.added = 0;
-      sh.addcost = 0;
-      sh.ncross = 0;
-      sh.xovf = 0;
-      sh.nheavy = 0;
       sh.met = 0;
       sh.ovf = 0;
       sh.xovf = 0;
@@ -495,13 +487,18 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       }
       const int f0 = sh.lo[x][L], f1 = sh.lo[x][L + 1];
       const unsigned long long fcost = sh.hcost[x][L];
-      // the level counters (added, addcost, ncross, xovf, nheavy) were zeroed
-      // by thread 0 before the barrier that ended the previous step
+      __syncthreads();
+      if (tid == 0) {
+        sh.added = 0;
+        sh.addcost = 0;
+        sh.ncross = 0;
+        sh.xovf = 0;
+      }
       uint32_t *qx = q[x];
       const int64_t *o = x ? A.roff : A.off;
       const int32_t *c = x ? A.rcol : A.col;
       const int hlimit = (int)(H1 >> 1);
-      bi_scan_rows<true>(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
+      bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
         uint64_t sw = 0;
         // once the distance is known, or the small table is half full, nothing more is claimed
         const bool claim = !(*(volatile int *)&sh.met || *(volatile int *)&sh.hfull);
@@ -562,11 +559,6 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
           sh.tier = 2;
           sh.hfull = 0;
           sh.ovf = 0;
-          sh.added = 0;
-          sh.addcost = 0;
-          sh.ncross = 0;
-          sh.xovf = 0;
-          sh.nheavy = 0;
           atomicAdd(&A.ctl->nmigrate, 1ull);
         }
         __syncthreads();
@@ -582,11 +574,6 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
         sh.lo[x][L + 2] = f1 + sh.added;
         sh.hcost[x][L + 1] = sh.addcost;
         sh.lvl[x] = L + 1;
-        sh.added = 0;
-        sh.addcost = 0;
-        sh.ncross = 0;
-        sh.xovf = 0;
-        sh.nheavy = 0;
       }
       __syncthreads();
     }
@@ -791,10 +778,7 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
             uint64_t val = 0;
             if (lane < npc) {
               u = (int32_t)pc[lane];
-              // u -> v: search the shorter of u's out-row and v's in-row
-              const int64_t u0 = A.off[u], u1 = A.off[u + 1];
-              const bool adj = (u1 - u0 <= e1 - e0) ? row_has(A.col, u0, u1, v) : row_has(A.rcol, e0, e1, u);
-              if (adj) {
+              if (row_has(A.col, A.off[u], A.off[u + 1], v)) {
                 int64_t iu = 0;
                 bi_find(M, u, iu);
                 val = sg[iu];
