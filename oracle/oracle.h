@@ -115,6 +115,10 @@ int orc_rade_matrix(const orc_job *job, int32_t *R, int32_t *c);
 
 /* Host FP64 bounds of Theorem "bound_dev" and the stopping test of
  * Algorithm 1 for iteration i >= 1 (delta_i = delta / 2^i).
+ * Parity unpinned at generic inputs: the paper prints no worked numeric
+ * example, so the values are pinned only by closed forms at C = 0, w = 0 and
+ * R~ = 0, the inequality chain of Prop. "main", monotonicity and the large-m
+ * limit.
  * out[0..7] = C, A (AMCERA), w (wimpy), nu, xi, Rtilde, R, eta; returns stop (0/1). */
 int orc_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
                double delta, int32_t i, double *out);
