@@ -157,7 +157,8 @@ void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
   Stats *S = &job->stats;
   const int32_t n = job->g->n;
   const int t = job->t;
-  job->R.ensure(4 * (size_t)n * t, st);
+  // rows 0 .. t-1: R_q^u; row t: c_u (so one selection gives every Rnum and Wnum)
+  job->R.ensure(4 * (size_t)n * (t + 1), st);
   CEN_CK(cudaMemsetAsync(job->R.p, 0, 4 * (size_t)n * t, st));
   launch(S, K_RADE, st, [&] {
     k_rade<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(n, t, job->nw, job->noff.as<int64_t>(),
@@ -165,12 +166,12 @@ void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
                                                                       job->sign.as<uint32_t>(), job->R.as<int32_t>(),
                                                                       (unsigned long long *)(job->stats.d_units + K_RADE));
   });
-  std::vector<long long> rn(t);
-  topk_positive_sum(job, job->R.as<int32_t>(), n, t, k, rn.data());
+  CEN_CK(cudaMemcpyAsync(job->R.as<int32_t>() + (size_t)n * t, job->c.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice,
+                         st));
+  std::vector<long long> rn(t + 1);
+  topk_positive_sum(job, job->R.as<int32_t>(), n, t + 1, k, rn.data());
   for (int q = 0; q < t; ++q) Rnum[q] = rn[q];
-  long long w = 0;
-  topk_positive_sum(job, job->c.as<int32_t>(), n, 1, k, &w);
-  *Wnum = w;
+  *Wnum = rn[t];  // the c_u are positive, so this is the sum of the k largest
   int hb = 0;
   CEN_CK(cudaMemcpyAsync(host_staging(job, 4), job->bmax.p, 4, cudaMemcpyDeviceToHost, st));
   CEN_CK(cudaStreamSynchronize(st));

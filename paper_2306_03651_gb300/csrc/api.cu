@@ -14,12 +14,14 @@ const std::string &last_error();
 
 void *host_staging(cen_job *job, size_t bytes) {
   if (bytes > job->host_bytes) {
-    if (job->host) cudaFreeHost(job->host);
+    if (job->host) {
+      CEN_CK(cudaStreamSynchronize(job->st));  // no copy may still use the old buffer
+      pinned_give(job->host, job->host_bytes);
+    }
     job->host = nullptr;
     job->host_bytes = 0;
-    size_t cap = 4096;
-    while (cap < bytes) cap *= 2;
-    CEN_CK(cudaMallocHost(&job->host, cap));
+    size_t cap = 0;
+    job->host = pinned_take(bytes, &cap);
     job->host_bytes = cap;
   }
   return job->host;
@@ -333,10 +335,11 @@ int cen_job_free(cen_job *job) {
     cudaStream_t st = job->st;
     cudaStreamSynchronize(st);
     void *h = job->host;
+    const size_t hb = job->host_bytes;
     cen::bidir_give(std::move(job->bws));  // idle, since the stream has drained
     delete job;
     CEN_CK(cudaStreamSynchronize(st));
-    if (h) cudaFreeHost(h);
+    cen::pinned_give(h, hb);
   }
   CEN_API_END
 }
@@ -569,6 +572,7 @@ int cen_job_set_param(cen_job *job, int32_t param, double value) {
 int cen_release_cached(void) {
   CEN_API_BEGIN
   cen::bidir_drop_cached();
+  cen::pinned_drop_cached();
   int dev = 0;
   CEN_CK(cudaGetDevice(&dev));
   cudaMemPool_t pool;

@@ -227,6 +227,11 @@ inline void launch(Stats *S, int cls, cudaStream_t st, F &&f) {
 // Blocks of `block` threads that are resident at once on the current device
 // (SM count x blocks per SM for this kernel), cached per kernel.
 int resident_grid(const void *kernel, int block);
+// Page-locked host buffers, reused across jobs (capacity in *cap, >= bytes).
+// A buffer is given back only once no copy into or out of it is in flight.
+void *pinned_take(size_t bytes, size_t *cap);
+void pinned_give(void *p, size_t cap);
+void pinned_drop_cached();
 // Blocks for a cooperative launch of `kernel` (all resident at once: one per
 // SM up to what fits), or 0 when the device cannot launch cooperatively.
 int cooperative_grid(const void *kernel, int block);

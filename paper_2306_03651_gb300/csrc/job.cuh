@@ -40,7 +40,7 @@ struct WaveWS {
         b->st = nullptr;
       for (auto &l : lev) l->st = nullptr;
     }
-    if (host) cudaFreeHost(host);
+    if (host) pinned_give(host, host_bytes);  // its stream has drained (the job's stream is synced at free)
     if (own_stream) cudaStreamDestroy(own_stream);
   }
   DevBuf arcs;                                // cone arc log of the current wave

@@ -7,6 +7,7 @@
 #include <map>
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 
@@ -346,5 +347,61 @@ int cooperative_grid(const void *kernel, int block) {
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1) return 0;
   return sms * std::min(per_sm, 2);
+}
+}  // namespace cen
+
+namespace cen {
+// Pinned host buffers of finished jobs, kept for the next ones: allocating and
+// freeing page-locked memory costs far more than a round's small copies.
+namespace {
+constexpr size_t kPinnedKeep = 16;
+struct PinnedPool {
+  std::mutex mu;
+  std::vector<std::pair<void *, size_t>> idle;
+};
+PinnedPool &pinned_pool() {
+  static PinnedPool *p = new PinnedPool();  // never destroyed: nothing is freed after the runtime unloads
+  return *p;
+}
+}  // namespace
+
+void *pinned_take(size_t bytes, size_t *cap) {
+  {
+    PinnedPool &pp = pinned_pool();
+    std::lock_guard<std::mutex> lk(pp.mu);
+    size_t best = pp.idle.size();
+    for (size_t i = 0; i < pp.idle.size(); ++i)
+      if (pp.idle[i].second >= bytes && (best == pp.idle.size() || pp.idle[i].second < pp.idle[best].second)) best = i;
+    if (best < pp.idle.size()) {
+      void *p = pp.idle[best].first;
+      *cap = pp.idle[best].second;
+      pp.idle.erase(pp.idle.begin() + (ptrdiff_t)best);
+      return p;
+    }
+  }
+  size_t c = 4096;
+  while (c < bytes) c *= 2;
+  void *p = nullptr;
+  CEN_CK(cudaMallocHost(&p, c));
+  *cap = c;
+  return p;
+}
+
+void pinned_give(void *p, size_t cap) {
+  if (!p) return;
+  PinnedPool &pp = pinned_pool();
+  std::lock_guard<std::mutex> lk(pp.mu);
+  pp.idle.emplace_back(p, cap);
+  if (pp.idle.size() > kPinnedKeep) {
+    cudaFreeHost(pp.idle.front().first);
+    pp.idle.erase(pp.idle.begin());
+  }
+}
+
+void pinned_drop_cached() {
+  PinnedPool &pp = pinned_pool();
+  std::lock_guard<std::mutex> lk(pp.mu);
+  for (auto &e : pp.idle) cudaFreeHost(e.first);
+  pp.idle.clear();
 }
 }  // namespace cen

@@ -889,12 +889,11 @@ namespace {
 
 void *ws_staging(WaveWS &ws, size_t bytes) {
   if (bytes > ws.host_bytes) {
-    if (ws.host) cudaFreeHost(ws.host);
+    if (ws.host) cudaFreeHost(ws.host);  // synchronizes: no copy may still use it
     ws.host = nullptr;
     ws.host_bytes = 0;
-    size_t cap = 4096;
-    while (cap < bytes) cap *= 2;
-    CEN_CK(cudaMallocHost(&ws.host, cap));
+    size_t cap = 0;
+    ws.host = pinned_take(bytes, &cap);
     ws.host_bytes = cap;
   }
   return ws.host;
