@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--tsweep-t", default="1,10,50,100,250,500")
     ap.add_argument("--tsweep-k", type=int, default=50)
     ap.add_argument("--schedule-eps", default="0.1,0.05")
+    ap.add_argument("--schedule-k", default="", help="values of k for the schedule mode (default: the workload's)")
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -458,14 +459,15 @@ def run_schedule_mode(args):
              ("predict", P.SCHEDULE_EXTRAPOLATE, "centra", P.RULE_CENTRA),
              ("doubling", P.SCHEDULE_DOUBLING, "hedge_p", P.RULE_HEDGE_P),
              ("predict", P.SCHEDULE_EXTRAPOLATE, "hedge_p", P.RULE_HEDGE_P))
-    for eps in (float(x) for x in args.schedule_eps.split(",")):
+    ks = [int(x) for x in args.schedule_k.split(",")] if args.schedule_k else [wl.k]
+    for k, eps in ((k, float(e)) for k in ks for e in args.schedule_eps.split(",")):
         for name, sched, rname, rule in plans:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = P.run(graph, wl.k, eps, wl.delta, wl.t, wl.seed, m0=1000, m_cap=1 << 30, schedule=sched,
+            r = P.run(graph, k, eps, wl.delta, wl.t, wl.seed, m0=1000, m_cap=1 << 30, schedule=sched,
                       alpha=1.2, rule=rule)
             el = time.perf_counter() - t0
-            rows.append({"eps": eps, "schedule": name, "rule": rname, "status": r["status"], "seconds": el,
+            rows.append({"k": k, "eps": eps, "schedule": name, "rule": rname, "status": r["status"], "seconds": el,
                          "rounds": r["rounds"], "m_final": r["m_final"],
                          "C": float(r["log"][-1][6]) if r["rounds"] else None,
                          "eta": float(r["log"][-1][13]) if r["rounds"] else None})
@@ -474,7 +476,7 @@ def run_schedule_mode(args):
         "metric": "time to certified eps (s)", "value": rows[-1]["seconds"], "unit": "s", "n_gpus": 1,
         "steps": 1, "warmup": 1, "higher_is_better": False, "scaling": "strong", "vs_baseline": None,
         "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {desc}", "k": wl.k, "t": wl.t, "delta": wl.delta},
+        "config": {"workload": f"{args.workload}: {desc}", "k": ks, "t": wl.t, "delta": wl.delta},
         "rows": rows, "clocks": clk,
     }))
 
