@@ -130,7 +130,7 @@ struct cen_job {
 namespace cen {
 void sample_append(cen_job *job, uint64_t m_new);
 void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap);
-void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out);
+void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out, const int64_t *hoff);
 int64_t triangle_index(cen_job *job);
 void triangle_sample(cen_job *job, uint64_t j0, uint64_t count);
 int max_kappa();

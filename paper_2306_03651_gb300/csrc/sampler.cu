@@ -1400,13 +1400,27 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   return total;
 }
 
-// kappa-path space: a warp per walk into a strided buffer, then packed.
+// kappa-path space: a warp per walk into a strided buffer, then packed.  When
+// that buffer would exceed kKpathBuffer bytes, the walks run twice instead
+// (they are functions of the sample ids): once for their lengths, then again
+// writing members straight into the store.
+constexpr size_t kKpathBuffer = (size_t)1 << 30;
+
 int64_t append_kpath(cen_job *job, uint64_t m0, uint64_t m_new) {
   cudaStream_t st = job->st;
-  job->space_buf.ensure(4 * (size_t)m_new * (size_t)job->kappa, st);
-  kpath_sample(job, m0, m_new, job->space_buf.as<int32_t>());
+  const bool staged = 4 * (size_t)m_new * (size_t)job->kappa <= kKpathBuffer;
+  if (staged) {
+    job->space_buf.ensure(4 * (size_t)m_new * (size_t)job->kappa, st);
+    kpath_sample(job, m0, m_new, job->space_buf.as<int32_t>(), nullptr);
+  } else {
+    kpath_sample(job, m0, m_new, nullptr, nullptr);
+  }
   const int64_t total = offsets_from_distances(job, m0, m_new);
   job->hmem.ensure(4 * (size_t)(job->members + total + 1), st, 4 * (size_t)job->members);
+  if (!staged) {
+    kpath_sample(job, m0, m_new, job->hmem.as<int32_t>(), job->hoff.as<int64_t>());
+    return total;
+  }
   WaveWS &w0 = wave_ws0(job);
   launch(&job->stats, K_APPEND, st, [&] {
     k_gather_strided<<<grid_for(m_new * 32, 256), 256, 0, st>>>(m_new, m0, job->kappa, w0.lens.as<int32_t>(),

@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_kpath(uint64_t j0, uint64_t
                                                            const int64_t *__restrict__ off,
                                                            const int32_t *__restrict__ col, uint64_t seed,
                                                            int32_t *ps, int32_t *pt, int32_t *pd, int32_t *out,
-                                                           int *bmax, unsigned long long *units) {
+                                                           const int64_t *__restrict__ hoff, int *bmax,
+                                                           unsigned long long *units) {
   extern __shared__ int32_t walk_sh[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t *walk = walk_sh + (size_t)wib * kappa;
@@ -85,7 +86,10 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_kpath(uint64_t j0, uint64_t
       ++len;
       cur = next;
     }
-    for (int q = lane; q < len; q += 32) out[(size_t)i * kappa + q] = walk[q];
+    if (out) {  // members at stride kappa, or at their place in the store when hoff is given
+      int32_t *dst = hoff ? out + hoff[j] : out + (size_t)i * kappa;
+      for (int q = lane; q < len; q += 32) dst[q] = walk[q];
+    }
     if (lane == 0) {
       ps[j] = s;
       pt[j] = l;
@@ -200,15 +204,16 @@ __global__ void k_tri_sample(uint64_t j0, uint64_t count, int32_t n, int64_t nnz
 
 }  // namespace
 
-// Writes the new samples' members to `out` at stride kappa, and ps/pt/pd.
-void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out) {
+// Writes ps/pt/pd of the new samples and their members: to `out` at stride
+// kappa, or, with hoff, into the store at hoff[j]; none when out is null.
+void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out, const int64_t *hoff) {
   const cen_graph *g = job->g;
   cudaStream_t st = job->st;
   const size_t smem = sizeof(int32_t) * (size_t)job->kappa * kWalkWarps;
   launch(&job->stats, K_SPACE, st, [&] {
     k_kpath<<<grid_for(count, kWalkWarps, 152 * 16), 32 * kWalkWarps, smem, st>>>(
         j0, count, g->n, job->kappa, g->off.as<int64_t>(), g->col.as<int32_t>(), job->seed, job->ps.as<int32_t>(),
-        job->pt.as<int32_t>(), job->pd.as<int32_t>(), out, job->bmax.as<int>(),
+        job->pt.as<int32_t>(), job->pd.as<int32_t>(), out, hoff, job->bmax.as<int>(),
         (unsigned long long *)(job->stats.d_units + K_SPACE));
   });
 }

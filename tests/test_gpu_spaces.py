@@ -39,6 +39,19 @@ def test_kpath_parity(name, kappa):
     assert np.array_equal(Rn, Rn2) and Wn == Wn2 and b == b2 <= kappa
 
 
+def test_kpath_two_pass_when_the_walk_buffer_would_be_large():
+    """300,000 walks of kappa = 1024 would stage 1.2 GB: the walks then run twice (lengths,
+    then members in place).  A star keeps them short; the samples are still the oracle's."""
+    n = 1001
+    star = I.from_edges(n, [0] * (n - 1), list(range(1, n)), False)
+    m = 300000
+    job = P.Job(P.Graph.of(star), 7, 4, space=P.SPACE_KPATH, kappa=1024)
+    job.sample(m)
+    ojob = O.Job(O.Graph.of(star), 7, 4, space=O.SPACE_KPATH, kappa=1024)
+    ojob.sample(m)
+    same(job, ojob)
+
+
 @pytest.mark.parametrize("name", ["ba300", "rmat12_lcc", "ba2000"])
 def test_triangle_parity(name):
     g = GRAPHS[name] if name in GRAPHS else I.ba(2000, 4, 1)
