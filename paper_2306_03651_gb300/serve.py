@@ -59,7 +59,7 @@ class Result:
 
 
 def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: float = 8.0, levels: int = 16,
-                       bidir_budget: int = 16 << 30, bidir_queue: int = 1 << 16, resident_ctas: int = 1216) -> int:
+                       bidir_budget: int = 16 << 30, bidir_queue: int = 1 << 16, resident_ctas: int = 2432) -> int:
     """Upper estimate of one job's device memory (admission policy, not the method).
 
     Bidirectional sampler: one workspace per resident CTA (a large node table
@@ -69,8 +69,9 @@ def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: floa
     of n*G words (G = wave words, at most 32 and at most 1 GB per array) and the
     initial cone-arc log (2 n G records of 24 bytes); sample store for m_cap
     samples: offsets, endpoints, distance, sign words and members (twice: samples
-    and the incidence), plus the member arena; AMCERA table R[t][n] and greedy /
-    incidence arrays."""
+    and the incidence), plus the member arena; AMCERA table R[t+1][n] and greedy /
+    incidence arrays.  `resident_ctas` is the sampler's CTAs in flight (16 per SM
+    on a 152-SM GB300)."""
     qc = max(16, min(n, bidir_queue))
     h2 = 1024
     while h2 < 4 * qc:
@@ -84,7 +85,7 @@ def estimate_job_bytes(n: int, nnz: int, t: int, m_cap: int, avg_hyperedge: floa
     wave = 8 * words * (levels + 6) + 24 * 2 * words
     nw = (t + 31) // 32
     store = m_cap * (8 + 12 + 4 * nw) + 3 * 4 * int(m_cap * avg_hyperedge)
-    node = n * (4 * t + 4 * 4 + 8)
+    node = n * (4 * (t + 1) + 4 * 4 + 8)
     return int(bidir + wave + store + node)
 
 
