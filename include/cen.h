@@ -61,6 +61,22 @@ const char *cen_last_error(void);
  * CEN_EINVAL.  n >= 2.  For directed graphs the in-arc CSR is built on the GPU. */
 int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
                    void *stream, cen_graph **out);
+/* cen_graph_load from any CSR with ids in [0, n) and offsets rising from 0 to
+ * nnz (else CEN_EINVAL).  flags:
+ *   CEN_GRAPH_CANONICALIZE  sort each row, drop repeated arcs and self-loops;
+ *   CEN_GRAPH_SYMMETRIZE    (undirected only) add the reverse of every arc
+ *                           first, then canonicalize.
+ * Done on the GPU (two stable radix sorts of the arc list and a compaction);
+ * the graph's nnz is the arcs kept (cen_graph_info).  flags = 0 is
+ * cen_graph_load.  At most 2^32 - 1 arcs after symmetrizing. */
+#define CEN_GRAPH_CANONICALIZE 1
+#define CEN_GRAPH_SYMMETRIZE 2
+int cen_graph_load_ex(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
+                      int flags, void *stream, cen_graph **out);
+/* The graph's canonical out-CSR: off[n+1] and col[nnz] (nnz of
+ * cen_graph_info), host or device pointers, caller-owned; either may be null.
+ * Synchronous on the graph's stream. */
+int cen_graph_copy(const cen_graph *g, int64_t *off, int32_t *col);
 int cen_graph_free(cen_graph *g);
 int cen_graph_info(const cen_graph *g, int32_t *n, int64_t *nnz, int *directed);
 

@@ -27,6 +27,7 @@ SAMPLER_BIDIR, SAMPLER_WAVES = 0, 1
 SCHEDULE_DOUBLING, SCHEDULE_PAPER, SCHEDULE_EXTRAPOLATE = 0, 1, 2
 RULE_CENTRA, RULE_HEDGE_P = 0, 1
 SPACE_BETWEENNESS, SPACE_KPATH, SPACE_TRIANGLE = 0, 1, 2
+GRAPH_CANONICALIZE, GRAPH_SYMMETRIZE = 1, 2
 LOG_COLS = ("i", "m", "covered", "Rsum", "Wnum", "b", "C", "A", "w", "nu", "xi", "Rt", "R", "eta", "stop", "S_size")
 NKCLASS = 24
 
@@ -75,6 +76,8 @@ def _load():
         "cen_version": ([], ip),
         "cen_last_error": ([], ctypes.c_char_p),
         "cen_graph_load": ([vp, vp, i32, i64, ip, ip, vp, pvp], ip),
+        "cen_graph_load_ex": ([vp, vp, i32, i64, ip, ip, ip, vp, pvp], ip),
+        "cen_graph_copy": ([vp, vp, vp], ip),
         "cen_graph_free": ([vp], ip),
         "cen_graph_info": ([vp, vp, vp, vp], ip),
         "cen_job_create": ([vp, u64, i32, vp, pvp], ip),
@@ -153,7 +156,8 @@ def _is_torch_cuda(x) -> bool:
 class Graph:
     """Device-resident canonical CSR graph (``cen_graph_load``)."""
 
-    def __init__(self, n: int, off, col, directed: bool = False, stream=None):
+    def __init__(self, n: int, off, col, directed: bool = False, stream=None, flags: int = 0):
+        """flags: GRAPH_CANONICALIZE / GRAPH_SYMMETRIZE (``cen_graph_load_ex``); 0 takes a canonical CSR as is."""
         self.n = int(n)
         self.directed = bool(directed)
         self.stream = stream if stream is not None else current_stream()
@@ -167,12 +171,21 @@ class Graph:
             on_dev, poff, pcol = 0, _p(off), _p(col)
             nnz = int(off[-1])
             self._keep = (off, col)
-        self.nnz = nnz
         h = ctypes.c_void_p()
-        _check(_lib.cen_graph_load(poff, pcol, self.n, nnz, int(directed), on_dev, self.stream, ctypes.byref(h)),
-               "cen_graph_load")
+        _check(_lib.cen_graph_load_ex(poff, pcol, self.n, nnz, int(directed), on_dev, int(flags), self.stream,
+                                      ctypes.byref(h)), "cen_graph_load")
         self.h = h
         self._keep = None
+        kept = ctypes.c_int64()
+        _check(_lib.cen_graph_info(self.h, None, ctypes.byref(kept), None), "cen_graph_info")
+        self.nnz = int(kept.value)
+
+    def csr(self):
+        """The device graph's CSR (off int64[n+1], col int32[nnz]) as host arrays (``cen_graph_copy``)."""
+        off = np.zeros(self.n + 1, np.int64)
+        col = np.zeros(max(self.nnz, 1), np.int32)
+        _check(_lib.cen_graph_copy(self.h, _p(off), _p(col)), "cen_graph_copy")
+        return off, col[:self.nnz]
 
     @classmethod
     def of(cls, g, stream=None):

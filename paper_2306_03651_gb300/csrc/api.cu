@@ -263,6 +263,42 @@ int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nn
   CEN_API_END
 }
 
+int cen_graph_load_ex(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
+                      int flags, void *stream, cen_graph **out) {
+  if (!(flags & (CEN_GRAPH_CANONICALIZE | CEN_GRAPH_SYMMETRIZE)))
+    return cen_graph_load(off, col, n, nnz, directed, on_device, stream, out);
+  CEN_API_BEGIN
+  CEN_REQUIRE(out && off && (col || nnz == 0), CEN_EINVAL, "cen_graph_load: null argument");
+  CEN_REQUIRE(n >= 2 && nnz >= 0, CEN_EINVAL, "cen_graph_load: need n >= 2 and nnz >= 0");
+  CEN_REQUIRE(!(flags & ~(CEN_GRAPH_CANONICALIZE | CEN_GRAPH_SYMMETRIZE)), CEN_EINVAL, "cen_graph_load: unknown flag");
+  CEN_REQUIRE(!(directed && (flags & CEN_GRAPH_SYMMETRIZE)), CEN_EINVAL,
+              "cen_graph_load: SYMMETRIZE is for undirected graphs");
+  *out = nullptr;
+  cen_graph *g = new cen_graph();
+  g->n = n;
+  g->directed = directed ? 1 : 0;
+  g->st = (cudaStream_t)stream;
+  try {
+    cen::graph_canonicalize(g, off, col, nnz, on_device != 0, (flags & CEN_GRAPH_SYMMETRIZE) != 0, nullptr);
+    cen::graph_build(g, nullptr, nullptr, true, nullptr);
+  } catch (...) {
+    delete g;
+    throw;
+  }
+  *out = g;
+  CEN_API_END
+}
+
+int cen_graph_copy(const cen_graph *g, int64_t *off, int32_t *col) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(g, CEN_EINVAL, "cen_graph_copy: null graph");
+  cudaStream_t st = g->st;
+  if (off) CEN_CK(cudaMemcpyAsync(off, g->off.p, sizeof(int64_t) * ((size_t)g->n + 1), cudaMemcpyDefault, st));
+  if (col && g->nnz) CEN_CK(cudaMemcpyAsync(col, g->col.p, sizeof(int32_t) * (size_t)g->nnz, cudaMemcpyDefault, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  CEN_API_END
+}
+
 int cen_graph_free(cen_graph *g) {
   CEN_API_BEGIN
   if (g) {

@@ -1,5 +1,7 @@
 // Graph upload: canonical-CSR validation on the GPU and, for directed graphs,
 // the in-arc CSR (a stable sort of arcs by head keeps each row ascending).
+#include <algorithm>
+
 #include "job.cuh"
 
 namespace cen {
@@ -78,15 +80,124 @@ static void build_chunks(const int64_t *off, int32_t n, ChunkTable &T, cudaStrea
   CEN_CK(cudaStreamSynchronize(st));
 }
 
+// ------------------------------------------------------- canonical form
+// Offsets non-decreasing from 0 to nnz and every id in [0, n): else *bad = 1.
+__global__ void k_check_ids(const int64_t *__restrict__ off, const int32_t *__restrict__ col, int32_t n, int64_t nnz,
+                            int *bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= (int64_t)n; i += (int64_t)gridDim.x * blockDim.x)
+    if ((i == 0 && off[0] != 0) || (i == n && off[n] != nnz) || (i > 0 && off[i] < off[i - 1])) *bad = 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    if (col[e] < 0 || col[e] >= n) *bad = 1;
+}
+
+// Arc list of the input rows (u, v), and with `both` also (v, u).
+__global__ void k_arc_list(const int64_t *__restrict__ off, const int32_t *__restrict__ col, int32_t n, int64_t nnz,
+                           bool both, uint32_t *tail, uint32_t *head) {
+  for (int32_t u = blockIdx.x * blockDim.y + threadIdx.y; u < n; u += gridDim.x * blockDim.y)
+    for (int64_t e = off[u] + threadIdx.x; e < off[u + 1]; e += blockDim.x) {
+      tail[e] = (uint32_t)u;
+      head[e] = (uint32_t)col[e];
+      if (both) {
+        tail[nnz + e] = (uint32_t)col[e];
+        head[nnz + e] = (uint32_t)u;
+      }
+    }
+}
+
+// keep[i] = arc i (of the list sorted by (tail, head)) is not a self-loop and
+// not a repeat of arc i - 1; cnt[tail] counts the kept arcs of each row.
+__global__ void k_keep_arcs(const uint32_t *__restrict__ tail, const uint32_t *__restrict__ head, int64_t A,
+                            int64_t *keep, int32_t *cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool k = tail[i] != head[i] && (i == 0 || tail[i] != tail[i - 1] || head[i] != head[i - 1]);
+    keep[i] = k;
+    if (k) atomicAdd(&cnt[tail[i]], 1);
+  }
+}
+
+__global__ void k_pack_arcs(const uint32_t *__restrict__ head, const int64_t *__restrict__ keep,
+                            const int64_t *__restrict__ pos, int64_t A, int32_t *col) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < A; i += (int64_t)gridDim.x * blockDim.x)
+    if (keep[i]) col[pos[i]] = (int32_t)head[i];
+}
+
+// Canonical CSR of the input rows on the device: rows sorted, repeated arcs and
+// self-loops dropped, and with `symmetrize` the reverse of every arc added
+// first.  Sets g->off, g->col and g->nnz.  Ids out of [0, n) or malformed
+// offsets give CEN_EINVAL.
+void graph_canonicalize(cen_graph *g, const int64_t *off, const int32_t *col, int64_t nnz, bool on_device,
+                        bool symmetrize, Stats *S) {
+  cudaStream_t st = g->st;
+  const int32_t n = g->n;
+  DevBuf ioff, icol, bad;
+  ioff.ensure(8 * ((size_t)n + 1), st);
+  icol.ensure(4 * (size_t)(nnz > 0 ? nnz : 1), st);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CEN_CK(cudaMemcpyAsync(ioff.p, off, 8 * ((size_t)n + 1), kind, st));
+  if (nnz) CEN_CK(cudaMemcpyAsync(icol.p, col, 4 * (size_t)nnz, kind, st));
+  bad.ensure(4, st);
+  CEN_CK(cudaMemsetAsync(bad.p, 0, 4, st));
+  launch(S, K_GRAPH, st, [&] {
+    k_check_ids<<<grid_for((size_t)std::max<int64_t>(nnz, n + 1), 256), 256, 0, st>>>(
+        ioff.as<int64_t>(), icol.as<int32_t>(), n, nnz, bad.as<int>());
+  });
+  int hbad = 0;
+  CEN_CK(cudaMemcpyAsync(&hbad, bad.p, 4, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  CEN_REQUIRE(hbad == 0, CEN_EINVAL, "cen_graph_load: offsets must rise from 0 to nnz and ids lie in [0, n)");
+  const int64_t A = symmetrize ? 2 * nnz : nnz;
+  CEN_REQUIRE(A < ((int64_t)1 << 32), CEN_EINVAL, "cen_graph_load: too many arcs to canonicalize");
+  g->off.ensure(8 * ((size_t)n + 1), st);
+  g->col.ensure(4 * (size_t)(A > 0 ? A : 1), st);
+  if (A == 0) {
+    CEN_CK(cudaMemsetAsync(g->off.p, 0, 8 * ((size_t)n + 1), st));
+    g->nnz = 0;
+    return;
+  }
+  DevBuf tail, head, k2, v2, hist, tmp, keep, pos, cnt;
+  tail.ensure(4 * (size_t)A, st);
+  head.ensure(4 * (size_t)A, st);
+  launch(S, K_GRAPH, st, [&] {
+    k_arc_list<<<grid_for((size_t)n, 8, 152 * 64), dim3(32, 8), 0, st>>>(ioff.as<int64_t>(), icol.as<int32_t>(), n,
+                                                                        nnz, symmetrize, tail.as<uint32_t>(),
+                                                                        head.as<uint32_t>());
+  });
+  int bits = 1;
+  while (bits < 31 && (1u << bits) < (uint32_t)n) ++bits;
+  // by head, then (stably) by tail: the arcs end up sorted by (tail, head)
+  radix_sort_pairs(head.as<uint32_t>(), tail.as<uint32_t>(), (size_t)A, bits, k2, v2, hist, tmp, st, S);
+  radix_sort_pairs(tail.as<uint32_t>(), head.as<uint32_t>(), (size_t)A, bits, k2, v2, hist, tmp, st, S);
+  keep.ensure(8 * (size_t)A, st);
+  pos.ensure(8 * (size_t)(A + 1), st);
+  cnt.ensure(4 * (size_t)n, st);
+  CEN_CK(cudaMemsetAsync(cnt.p, 0, 4 * (size_t)n, st));
+  launch(S, K_GRAPH, st, [&] {
+    k_keep_arcs<<<grid_for((size_t)A, 256), 256, 0, st>>>(tail.as<uint32_t>(), head.as<uint32_t>(), A,
+                                                           keep.as<int64_t>(), cnt.as<int32_t>());
+  });
+  exclusive_scan_i64(keep.as<int64_t>(), pos.as<int64_t>(), (size_t)A, pos.as<int64_t>() + A, tmp, st, S);
+  launch(S, K_GRAPH, st, [&] {
+    k_pack_arcs<<<grid_for((size_t)A, 256), 256, 0, st>>>(head.as<uint32_t>(), keep.as<int64_t>(), pos.as<int64_t>(),
+                                                           A, g->col.as<int32_t>());
+  });
+  counts_to_offsets(cnt.as<int32_t>(), g->off.as<int64_t>(), (size_t)n, tmp, st, S);
+  int64_t kept = 0;
+  CEN_CK(cudaMemcpyAsync(&kept, pos.as<int64_t>() + A, 8, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  g->nnz = kept;
+}
+
 void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_device, Stats *S) {
   cudaStream_t st = g->st;
   const int32_t n = g->n;
   const int64_t nnz = g->nnz;
-  g->off.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
-  g->col.ensure(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), st);
-  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  CEN_CK(cudaMemcpyAsync(g->off.p, off, sizeof(int64_t) * ((size_t)n + 1), kind, st));
-  if (nnz) CEN_CK(cudaMemcpyAsync(g->col.p, col, sizeof(int32_t) * (size_t)nnz, kind, st));
+  if (off) {  // null: g->off / g->col already hold the graph (see graph_canonicalize)
+    g->off.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
+    g->col.ensure(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), st);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CEN_CK(cudaMemcpyAsync(g->off.p, off, sizeof(int64_t) * ((size_t)n + 1), kind, st));
+    if (nnz) CEN_CK(cudaMemcpyAsync(g->col.p, col, sizeof(int32_t) * (size_t)nnz, kind, st));
+  }
   DevBuf bad;
   bad.ensure(sizeof(int), st);
   CEN_CK(cudaMemsetAsync(bad.p, 0, sizeof(int), st));

@@ -139,5 +139,7 @@ void build_incidence(cen_job *job);
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered);
 void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b);
 void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_device, Stats *S);
+void graph_canonicalize(cen_graph *g, const int64_t *off, const int32_t *col, int64_t nnz, bool on_device,
+                        bool symmetrize, Stats *S);
 void *host_staging(cen_job *job, size_t bytes);
 }  // namespace cen
