@@ -46,6 +46,23 @@ extern "C" {
 typedef struct cen_graph cen_graph;
 typedef struct cen_job cen_job;
 
+/* Device memory.  The library owns every device buffer it allocates (graph
+ * copies, samples, workspaces); arrays the caller passes stay the caller's.
+ * By default buffers come from the device's stream-ordered pool
+ * (cudaMallocAsync on the call's stream).  cen_set_allocator installs another
+ * source for the allocations made after it: alloc(bytes, stream, ctx) returns
+ * device memory for use on `stream` (null: the call fails with CEN_ENOMEM),
+ * and free(ptr, bytes, stream, ctx) takes back a buffer that alloc made,
+ * called only once `stream` has drained, so the memory is idle and may be
+ * handed out again at once.  A buffer always goes back to the allocator that
+ * made it, so an installed pair (and ctx) must stay valid until every graph
+ * and job is freed and cen_release_cached has run.  alloc = free = null
+ * restores the pool.  Both must be null or both set (else CEN_EINVAL).  Do not
+ * call it while another thread is inside the library. */
+typedef void *(*cen_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*cen_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int cen_set_allocator(cen_alloc_fn alloc, cen_free_fn free_fn, void *ctx);
+
 /* Library version (major * 10000 + minor * 100 + patch). */
 int cen_version(void);
 

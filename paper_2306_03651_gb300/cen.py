@@ -99,6 +99,7 @@ def _load():
         "cen_job_sampler_info": ([vp, vp, vp, vp, vp], ip),
         "cen_job_create_space": ([vp, u64, i32, i32, i32, vp, ctypes.POINTER(vp)], ip),
         "cen_release_cached": ([], ip),
+        "cen_set_allocator": ([vp, vp, vp], ip),
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
         "cen_run_batch": ([vp, i32, i32, vp], ip),
@@ -321,6 +322,35 @@ class Job:
 def release_cached():
     """``cen_release_cached``: frees device memory kept for reuse after jobs end."""
     _check(_lib.cen_release_cached(), "cen_release_cached")
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_installed = []  # callbacks the library may still call back (buffers go back to the allocator that made them)
+
+
+def use_torch_allocator(enable: bool = True):
+    """``cen_set_allocator``: take the library's device buffers from PyTorch's caching allocator (so
+    ``torch.cuda.memory_allocated`` counts them and the two share one pool), or, with enable=False,
+    from the stream-ordered device pool again.  Install it before creating graphs and jobs."""
+    if not enable:
+        _check(_lib.cen_set_allocator(None, None, None), "cen_set_allocator")
+        return
+    import torch
+
+    def alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+        except Exception:  # out of memory: the library reports CEN_ENOMEM
+            return None
+
+    def free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    fns = (_ALLOC_FN(alloc), _FREE_FN(free))
+    _installed.append(fns)
+    _check(_lib.cen_set_allocator(ctypes.cast(fns[0], ctypes.c_void_p), ctypes.cast(fns[1], ctypes.c_void_p), None),
+           "cen_set_allocator")
 
 
 def bounds(covered, m, Rsum, t, Wnum, b, eps, delta, i):

@@ -242,6 +242,13 @@ int cen_version(void) { return 100; }
 
 const char *cen_last_error(void) { return cen::last_error().c_str(); }
 
+int cen_set_allocator(cen_alloc_fn alloc, cen_free_fn free_fn, void *ctx) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(!alloc == !free_fn, CEN_EINVAL, "cen_set_allocator: give both functions or neither");
+  cen::set_allocator(alloc, free_fn, ctx);
+  CEN_API_END
+}
+
 int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
                    void *stream, cen_graph **out) {
   CEN_API_BEGIN

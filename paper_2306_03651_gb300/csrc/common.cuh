@@ -50,20 +50,38 @@ void set_last_error(const std::string &msg);
 // CEN_ENOMEM as if the device were full (see cen_debug_fail_alloc).
 void alloc_fault_tick();
 
+// ------------------------------------------------ device memory source
+// An allocator installed by cen_set_allocator.  Installed ones are never
+// freed, so a buffer can always go back to the one that made it.
+struct Allocator {
+  cen_alloc_fn alloc;
+  cen_free_fn free;
+  void *ctx;
+};
+void set_allocator(cen_alloc_fn alloc, cen_free_fn free_fn, void *ctx);
+// Allocates `bytes` for use on stream s from the installed allocator (*al set
+// to it) or, with none, stream-ordered from the device pool (*al = null).
+void *dev_alloc(size_t bytes, cudaStream_t s, const Allocator **al);
+// Returns p to its allocator: stream-ordered on s for the pool; for an
+// installed allocator, once s has drained.  Never throws.
+void dev_free(void *p, size_t bytes, cudaStream_t s, const Allocator *al) noexcept;
+
 // ------------------------------------------------ stream-ordered buffers
 // Device memory owned by the library, allocated and freed in stream order.
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
   cudaStream_t st = nullptr;
+  const Allocator *al = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFreeAsync(p, st);
+    if (p) dev_free(p, bytes, st, al);
     p = nullptr;
     bytes = 0;
+    al = nullptr;
   }
   // Ensure capacity >= need bytes; keeps the first `keep` bytes of old content.
   void ensure(size_t need, cudaStream_t s, size_t keep = 0) {
@@ -71,21 +89,24 @@ struct DevBuf {
     if (need <= bytes && p) return;
     size_t cap = bytes ? bytes : 256;
     while (cap < need) cap = cap + cap / 2 + 256;
-    void *np = nullptr;
-    alloc_fault_tick();
-    CEN_CK(cudaMallocAsync(&np, cap, s));
-    if (p && keep) CEN_CK(cudaMemcpyAsync(np, p, keep < bytes ? keep : bytes, cudaMemcpyDeviceToDevice, s));
-    if (p) CEN_CK(cudaFreeAsync(p, s));
+    const Allocator *nal = nullptr;
+    void *np = dev_alloc(cap, s, &nal);
+    if (p && keep) {
+      cudaError_t e = cudaMemcpyAsync(np, p, keep < bytes ? keep : bytes, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) dev_free(np, cap, s, nal);
+      CEN_CK(e);
+    }
+    if (p) dev_free(p, bytes, s, al);
     p = np;
     bytes = cap;
+    al = nal;
   }
   // Capacity of exactly `need` bytes when it has to grow (large workspaces).
   void ensure_exact(size_t need, cudaStream_t s) {
     st = s;
     if (need <= bytes && p) return;
     release();
-    alloc_fault_tick();
-    CEN_CK(cudaMallocAsync(&p, need, s));
+    p = dev_alloc(need, s, &al);
     bytes = need;
   }
   template <class T>
@@ -94,6 +115,7 @@ struct DevBuf {
     std::swap(p, o.p);
     std::swap(bytes, o.bytes);
     std::swap(st, o.st);
+    std::swap(al, o.al);
   }
 };
 
@@ -203,6 +225,7 @@ struct Stats {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   uint64_t *d_units = nullptr;  // device counters [K_COUNT]
+  const Allocator *d_units_al = nullptr;
   Stats();
   ~Stats();
   void init(cudaStream_t st);

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <atomic>
 #include <map>
+#include <memory>
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -34,11 +35,11 @@ Stats::~Stats() {
     cudaEventDestroy(p.b);
   }
   for (auto e : pool) cudaEventDestroy(e);
-  if (d_units) cudaFree(d_units);
+  if (d_units) dev_free(d_units, sizeof(uint64_t) * K_COUNT, nullptr, d_units_al);
 }
 void Stats::init(cudaStream_t st) {
   if (!d_units) {
-    CEN_CK(cudaMalloc(&d_units, sizeof(uint64_t) * K_COUNT));
+    d_units = (uint64_t *)dev_alloc(sizeof(uint64_t) * K_COUNT, st, &d_units_al);
     CEN_CK(cudaMemsetAsync(d_units, 0, sizeof(uint64_t) * K_COUNT, st));
   }
 }
@@ -95,6 +96,45 @@ static std::atomic<long long> g_fail_alloc{0};
 void alloc_fault_tick() {
   if (g_fail_alloc.load(std::memory_order_relaxed) <= 0) return;
   if (g_fail_alloc.fetch_sub(1) == 1) fail(CEN_ENOMEM, "device allocation failed (injected by cen_debug_fail_alloc)");
+}
+
+// ------------------------------------------------------ memory source
+static std::atomic<const Allocator *> g_allocator{nullptr};
+
+void set_allocator(cen_alloc_fn alloc, cen_free_fn free_fn, void *ctx) {
+  static std::mutex mu;
+  static std::vector<std::unique_ptr<Allocator>> installed;  // kept for the buffers they made
+  std::lock_guard<std::mutex> lk(mu);
+  if (!alloc) {
+    g_allocator.store(nullptr);
+    return;
+  }
+  installed.emplace_back(new Allocator{alloc, free_fn, ctx});
+  g_allocator.store(installed.back().get());
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t s, const Allocator **al) {
+  alloc_fault_tick();
+  const Allocator *a = g_allocator.load();
+  void *p = nullptr;
+  if (a) {
+    p = a->alloc(bytes, (void *)s, a->ctx);
+    CEN_REQUIRE(p, CEN_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed (installed allocator)");
+  } else {
+    CEN_CK(cudaMallocAsync(&p, bytes, s));
+  }
+  *al = a;
+  return p;
+}
+
+void dev_free(void *p, size_t bytes, cudaStream_t s, const Allocator *al) noexcept {
+  if (!p) return;
+  if (al) {
+    cudaStreamSynchronize(s);  // the allocator may hand p out again at once
+    al->free(p, bytes, (void *)s, al->ctx);
+  } else {
+    cudaFreeAsync(p, s);
+  }
 }
 
 // ------------------------------------------------------ occupancy

@@ -1306,7 +1306,10 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
   CEN_CK(cudaGetDevice(&dev));
   BiWS *cur = job->bws.get();
   if (!(cur && cur->QC == QC && cur->H1 == H1 && cur->nslots == slots && cur->dev == dev)) {
-    if (cur && cur->nslots) bidir_give(std::move(job->bws));  // another shape: keep this one for later jobs
+    if (cur && cur->nslots) {  // another shape: keep this one for later jobs, once idle
+      CEN_CK(cudaStreamSynchronize(st));
+      bidir_give(std::move(job->bws));
+    }
     job->bws = bidir_take(dev, QC, H1, slots);
     if (!job->bws) job->bws.reset(new BiWS());
   }
