@@ -152,7 +152,7 @@ struct BiShared {
   int cs[2][kBiMaxLevels];                      // cone list of side x: level L is cs[x][L] .. ce[x][L]
   int ce[2][kBiMaxLevels];
   unsigned long long red[kBiWarps];
-  unsigned long long addcost, sum, sum2, arcs;
+  unsigned long long sum, sum2, arcs;
   unsigned long long red2[kBiWarps];
   int added, nheavy, ccount[2], ncross;
   int hcount, hfull;  // small-table entries of this search; set once it is half full
@@ -490,14 +490,13 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       __syncthreads();
       if (tid == 0) {
         sh.added = 0;
-        sh.addcost = 0;
         sh.ncross = 0;
         sh.xovf = 0;
       }
       uint32_t *qx = q[x];
       const int64_t *o = x ? A.roff : A.off;
       const int32_t *c = x ? A.rcol : A.col;
-      const int hlimit = (int)(H1 >> 1);
+      const int hlimit = (int)(H1 >> 1), hbase = sh.hcount;
       bi_scan_rows(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, [&](int v, int w) {
         uint64_t sw = 0;
         // once the distance is known, or the small table is half full, nothing more is claimed
@@ -509,8 +508,7 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
             qx[f1 + pos] = (uint32_t)w;
           else
             sh.ovf = 1;
-          atomicAdd(&sh.addcost, (unsigned long long)(o[w + 1] - o[w]));
-          if (tier == 1 && atomicAdd(&sh.hcount, 1) + 1 >= hlimit) sh.hfull = 1;
+          if (tier == 1 && hbase + pos + 1 >= hlimit) sh.hfull = 1;
           return;
         }
         if (r == 2 || !sw) return;
@@ -569,11 +567,14 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
         break;
       }
       if (sh.added == 0) break;  // this side's ball is closed: t is unreachable
-      __syncthreads();
+      // arcs out of the new level, summed once it is complete (all rows at once)
+      const int nadd = sh.added;
+      const unsigned long long cost = bi_row_sum(qx + f1, nadd, o, sh);
       if (tid == 0) {
-        sh.lo[x][L + 2] = f1 + sh.added;
-        sh.hcost[x][L + 1] = sh.addcost;
+        sh.lo[x][L + 2] = f1 + nadd;
+        sh.hcost[x][L + 1] = cost;
         sh.lvl[x] = L + 1;
+        sh.hcount += nadd;
       }
       __syncthreads();
     }
