@@ -90,21 +90,28 @@ class ClockSampler:
         self.lines = []
         self.t = None
 
-    def start(self):
+    def start(self, interval_ms: int = 50):
+        """Starts sampling and returns once the first sample is in (at most 3 s), so that the
+        timed region that follows is sampled from its start."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(interval_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.perf_counter() + 3.0
+            while not self.lines and time.perf_counter() < t_end and self.proc.poll() is None:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def stop(self, t_begin: float | None = None, t_end: float | None = None):
+        """Median SM clock and the throttle reasons seen; with t_begin/t_end (perf_counter), only
+        samples taken inside that window (plus one interval) count, if there are any."""
         if not self.proc:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -114,9 +121,13 @@ class ClockSampler:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
+        lines = self.lines
+        if t_begin is not None and t_end is not None:
+            inside = [x for x in lines if t_begin <= x[0] <= t_end + 0.06]
+            lines = inside or lines
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        for _, ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -246,8 +257,9 @@ def run_gpu(args, rank, world):
         times.append(a.elapsed_time(b))
         merge_stats(stats, st)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - t0
-    clk = clocks.stop()
+    t_done = time.perf_counter()
+    wall = t_done - t0
+    clk = clocks.stop(t0, t_done)
     total_ms = float(sum(times))
     if world > 1:
         total_ms = reduce_max(total_ms, "cuda")

@@ -45,3 +45,32 @@ def test_serving_estimate_counts_the_sampler_workspace():
     assert roomy - tight > (1 << 30)
     with pytest.raises(TypeError):
         serve.estimate_job_bytes(2000)
+
+
+def test_clock_sampler_reads_a_window_of_samples(tmp_path, monkeypatch):
+    # a stand-in nvidia-smi: 1,500 MHz for its first lines, then 2,070 MHz with power capping
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "for i in 1 2 3; do echo '0, 1500, 2070, 300, 0x0, Not Active, Not Active, Not Active, Not Active';"
+                    " sleep 0.02; done\n"
+                    "while true; do echo '0, 2070, 2070, 900, 0x4, Not Active, Not Active, Not Active, Active';"
+                    " sleep 0.02; done\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    import time
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.lines  # start() returns once sampling runs
+    time.sleep(0.15)
+    t0 = time.perf_counter()
+    time.sleep(0.15)
+    t1 = time.perf_counter()
+    time.sleep(0.05)
+    r = c.stop(t0, t1)
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"] and r["samples"] >= 3
+    c = bench.ClockSampler(0)
+    c.start()
+    time.sleep(0.05)
+    r = c.stop()  # no window: every sample counts, the early 1,500 MHz ones too
+    assert r["samples"] >= 2 and r["sm_max_mhz"] == 2070.0
