@@ -169,7 +169,8 @@ struct BiShared {
 
 // Sets the cone bit of v and, the first time, appends v to the cone list of
 // side x.
-__device__ __forceinline__ void bi_mark(const BiMap &M, uint32_t *clist, int x, int64_t QC, BiShared &sh, int v) {
+__device__ __forceinline__ void bi_mark(const BiMap &M, uint64_t *sg, uint32_t *clist, int x, int64_t QC,
+                                        BiShared &sh, int v) {
   int64_t p = -1;
   if (!bi_find(M, v, p)) {  // cannot happen: every cone node is in its ball
     sh.ovf = 1;
@@ -177,6 +178,7 @@ __device__ __forceinline__ void bi_mark(const BiMap &M, uint32_t *clist, int x, 
   }
   const unsigned long long old = atomicOr((unsigned long long *)&M.tab[p], (unsigned long long)kConeBit);
   if (old & kConeBit) return;
+  sg[p] = 0;  // its path count starts from zero
   const int pos = atomicAdd(&sh.ccount[x], 1);
   if (pos >= QC) {
     sh.ovf = 1;
@@ -612,8 +614,8 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       // ---- crossing arcs: forward level ls -> backward level lb
       if (!sh.xovf) {
         for (int i = tid; i < ncross; i += kBiThreads) {
-          bi_mark(M, cl[0], 0, QC, sh, (int)xt[i]);
-          bi_mark(M, cl[1], 1, QC, sh, (int)xh[i]);
+          bi_mark(M, sg, cl[0], 0, QC, sh, (int)xt[i]);
+          bi_mark(M, sg, cl[1], 1, QC, sh, (int)xh[i]);
         }
         __syncthreads();
       } else {
@@ -622,8 +624,8 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
                      [&](int v, int w) {
                        const uint64_t sw = bi_find(M, w);
                        if (sw && st_side(sw) == 1 && st_level(sw) == lb) {
-                         bi_mark(M, cl[0], 0, QC, sh, v);
-                         bi_mark(M, cl[1], 1, QC, sh, w);
+                         bi_mark(M, sg, cl[0], 0, QC, sh, v);
+                         bi_mark(M, sg, cl[1], 1, QC, sh, w);
                        }
                      });
       }
@@ -642,14 +644,14 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
         if (in_cone <= sh.hcost[0][L - 1]) {
           bi_scan_rows(cl[0] + a, b - a, A.roff, A.rcol, 8, heavy, sh, [&](int, int u) {
             const uint64_t su = bi_find(M, u);
-            if (su && st_side(su) == 0 && st_level(su) == L - 1) bi_mark(M, cl[0], 0, QC, sh, u);
+            if (su && st_side(su) == 0 && st_level(su) == L - 1) bi_mark(M, sg, cl[0], 0, QC, sh, u);
           });
         } else {
           const int f0 = sh.lo[0][L - 1], f1 = sh.lo[0][L];
           bi_scan_rows(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][L - 1], f1 - f0), heavy, sh,
                        [&](int u, int w) {
                          const uint64_t sw = bi_find(M, w);
-                         if (sw && st_cone(sw) && st_side(sw) == 0 && st_level(sw) == L) bi_mark(M, cl[0], 0, QC, sh, u);
+                         if (sw && st_cone(sw) && st_side(sw) == 0 && st_level(sw) == L) bi_mark(M, sg, cl[0], 0, QC, sh, u);
                        });
         }
         if (tid == 0) {
@@ -666,14 +668,14 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
         if (out_cone <= sh.hcost[1][L - 1]) {
           bi_scan_rows(cl[1] + a, b - a, A.off, A.col, 8, heavy, sh, [&](int, int y) {
             const uint64_t sy = bi_find(M, y);
-            if (sy && st_side(sy) == 1 && st_level(sy) == L - 1) bi_mark(M, cl[1], 1, QC, sh, y);
+            if (sy && st_side(sy) == 1 && st_level(sy) == L - 1) bi_mark(M, sg, cl[1], 1, QC, sh, y);
           });
         } else {
           const int f0 = sh.lo[1][L - 1], f1 = sh.lo[1][L];
           bi_scan_rows(q[1] + f0, f1 - f0, A.roff, A.rcol, bi_group(sh.hcost[1][L - 1], f1 - f0), heavy, sh,
                        [&](int y, int xv) {
                          const uint64_t sx = bi_find(M, xv);
-                         if (sx && st_cone(sx) && st_side(sx) == 1 && st_level(sx) == L) bi_mark(M, cl[1], 1, QC, sh, y);
+                         if (sx && st_cone(sx) && st_side(sx) == 1 && st_level(sx) == L) bi_mark(M, sg, cl[1], 1, QC, sh, y);
                        });
         }
         if (tid == 0) {
@@ -693,13 +695,6 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
       // pulled over the cone nodes' in-arcs or pushed over the out-arcs of
       // the level below, whichever is fewer; the crossing level adds along
       // the logged crossing arcs
-      for (int x = 0; x < 2; ++x)
-        for (int i = tid; i < sh.ccount[x]; i += kBiThreads) {
-          int64_t iv = 0;
-          bi_find(M, (int)cl[x][i], iv);
-          sg[iv] = 0;
-        }
-      __syncthreads();
       if (tid == 0) {
         int64_t is = 0;
         bi_find(M, sh.s, is);
