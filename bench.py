@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--tsweep-k", type=int, default=50)
     ap.add_argument("--schedule-eps", default="0.1,0.05")
     ap.add_argument("--schedule-k", default="", help="values of k for the schedule mode (default: the workload's)")
+    ap.add_argument("--schedule-plans", default="",
+                    help="schedule:rule pairs for the schedule mode, e.g. 'predict:centra,doubling:centra' "
+                         "(default: all five)")
     ap.add_argument("--batch-jobs", type=int, default=64)
     ap.add_argument("--batch-workers", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -471,6 +474,11 @@ def run_schedule_mode(args):
              ("predict", P.SCHEDULE_EXTRAPOLATE, "centra", P.RULE_CENTRA),
              ("doubling", P.SCHEDULE_DOUBLING, "hedge_p", P.RULE_HEDGE_P),
              ("predict", P.SCHEDULE_EXTRAPOLATE, "hedge_p", P.RULE_HEDGE_P))
+    if args.schedule_plans:
+        want = [tuple(x.split(":")) for x in args.schedule_plans.split(",")]
+        plans = tuple(p for w in want for p in plans if (p[0], p[2]) == w)
+        if len(plans) != len(want):
+            raise SystemExit(f"--schedule-plans: unknown plan in {args.schedule_plans!r}")
     ks = [int(x) for x in args.schedule_k.split(",")] if args.schedule_k else [wl.k]
     for k, eps in ((k, float(e)) for k in ks for e in args.schedule_eps.split(",")):
         for name, sched, rname, rule in plans:
