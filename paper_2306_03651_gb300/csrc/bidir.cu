@@ -481,7 +481,10 @@ __global__ void __launch_bounds__(kBiThreads, 16) k_bidir(BiArgs A) {
     // ---- discovery: grow the cheaper side until the balls touch.  The level
     // that touches is scanned to its end so that every crossing arc is logged.
     for (;;) {
-      const int x = sh.hcost[0][sh.lvl[0]] <= sh.hcost[1][sh.lvl[1]] ? 0 : 1;
+      // the side with fewer arcs to scan; on a tie the shallower side, so that
+      // graphs whose frontiers cost the same (cycles, grids) grow both balls
+      const unsigned long long c0 = sh.hcost[0][sh.lvl[0]], c1 = sh.hcost[1][sh.lvl[1]];
+      const int x = c0 < c1 || (c0 == c1 && sh.lvl[0] <= sh.lvl[1]) ? 0 : 1;
       const int L = sh.lvl[x];
       if (L + 1 >= kBiMaxLevels) {
         if (tid == 0) sh.status = 1;

@@ -1345,13 +1345,25 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   bidir_setup(job, m_new);
   BiWS &bw = *job->bws;
   const double mean = job->m ? (double)job->members / (double)job->m : 4.0;
-  const int64_t cap = (int64_t)((double)m_new * std::max(8.0, 2.0 * mean)) + ((int64_t)1 << 20);
+  int64_t cap = (int64_t)((double)m_new * std::max(8.0, 2.0 * mean)) + ((int64_t)1 << 20);
   bw.arena.ensure(4 * (size_t)cap, st);
   bidir_launch(job, m0, m_new, cap);
   BiCtl *hc = (BiCtl *)host_staging(job, sizeof(BiCtl));
   CEN_CK(cudaMemcpyAsync(hc, bw.ctl.p, sizeof(BiCtl), cudaMemcpyDeviceToHost, st));
   CEN_CK(cudaStreamSynchronize(st));
   CEN_REQUIRE(hc->err == 0, hc->err, "cen_sample: inconsistent path counts in the bidirectional walk");
+  if ((int64_t)hc->cursor > cap) {
+    // The arena was short (long paths in a job's first round, where no mean
+    // is known yet): the cursor has counted every walk's members, so size the
+    // arena to it and run the samples again (they are functions of their ids)
+    // instead of leaving those walks to the bit-parallel sampler.
+    cap = (int64_t)hc->cursor + ((int64_t)1 << 20);
+    bw.arena.ensure(4 * (size_t)cap, st);
+    bidir_launch(job, m0, m_new, cap);
+    CEN_CK(cudaMemcpyAsync(hc, bw.ctl.p, sizeof(BiCtl), cudaMemcpyDeviceToHost, st));
+    CEN_CK(cudaStreamSynchronize(st));
+    CEN_REQUIRE(hc->err == 0, hc->err, "cen_sample: inconsistent path counts in the bidirectional walk");
+  }
   const BiCtl h = *hc;
   if (job->bidir_table < 0 && m_new >= 1024 && 2 * h.nmigrate > m_new) job->g->bidir_table_off.store(true);
   std::vector<uint64_t> search(h.nsearch), walk(h.nwalk);

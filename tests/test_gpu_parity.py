@@ -150,6 +150,29 @@ def test_sample_split_invariance():
         assert_same_samples(job.samples(), ref)
 
 
+def test_long_paths_in_the_first_round_fill_the_arena_without_deferral():
+    """Cycle of 1,001 nodes: paths of about 250 interior nodes, while a job's first round sizes
+    the member arena for 8 per sample.  The arena is resized from the walks' own total and the
+    samples run again on the bidirectional sampler; none is left to the fallback, and the
+    samples are the oracle's, in this round and the next.  Both frontiers of a cycle always
+    cost the same, so the searches stay under the level cap only if ties grow the shallower
+    side."""
+    n = 1001
+    src = np.arange(n, dtype=np.int32)
+    g = I.from_edges(n, src, (src + 1) % n, False)
+    seed, m1, m2 = 9, 6000, 3000
+    _, _, ref = oracle_samples(g, seed, m1 + m2)
+    job = P.Job(P.Graph.of(g), seed, 10)
+    job.sample(m1)
+    info = job.sampler_info()
+    assert info["deferred_search"] == 0, info  # balanced on ties
+    assert info["deferred_walk"] == 0, info  # the arena was resized, not overflowed
+    assert job.size()[1] > 8 * m1 + (1 << 20)  # more members than the first round's arena held
+    job.sample(m2)
+    assert job.sampler_info()["deferred_walk"] == 0
+    assert_same_samples(job.samples(), ref)
+
+
 def test_path_counts_beyond_64_bits():
     """60x60 grid: pairs with C(dx+dy, dx) >= 2^64 shortest paths take the 128-bit re-run."""
     W = 60
