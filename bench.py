@@ -318,13 +318,16 @@ def run_gpu(args, rank, world):
         per_launch_bytes = stats[dom]["units"] / max(stats[dom]["launches"], 1)
         achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if dom in byte_classes else None
         counted = sum(stats[k]["units"] for k in byte_classes if k in stats)
+        traffic = dram_traffic(dom)
+        ratio = (f"DRAM traffic {traffic / per_launch_bytes:.2f}x the counted bytes, profiles/bidir_dram.md"
+                 if traffic and per_launch_bytes else "DRAM traffic not profiled for this source")
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": dram_traffic(dom),
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
                 "avg_launch_ms": avg_ms, "launches": stats[dom]["launches"],
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "note": ("one launch samples the whole step; the kernel is bound by the latency of dependent L2 "
-                         "accesses (DRAM traffic about 0.9x the counted bytes, profiles/bidir_dram.md)"
+                         f"accesses ({ratio})"
                          if dom == "bidir" else
                          "per-launch event times of concurrent wave pipelines include sharing the GPU"),
                 "aggregate_counted_GBps": counted / (total_ms / 1e3) / 1e9}
