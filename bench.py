@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serial-round", action="store_true",
+                    help="greedyCover and the AMCERA one after the other instead of side by side")
     ap.add_argument("--mode", default="round", choices=["round", "batch", "serve", "tsweep", "schedule"],
                     help="round: one Algorithm-1 round per step (default); batch: time to certified eps of the "
                          "64-job BA workload, one job at a time vs batched; serve: Poisson request stream; "
@@ -191,13 +193,25 @@ def reduce_max(value: float, device) -> float:
 SPACE = {"space": 0, "kappa": 0}  # hyper-edge space of the round mode (set from the arguments)
 
 
+SERIAL_ROUND = {"on": False}  # --serial-round: greedyCover, then the AMCERA, as two calls
+
+
+def cover_and_mcera(job, k):
+    """greedyCover and the AMCERA of the round: side by side on two streams (one call), or, with
+    --serial-round, one after the other (two calls); the outputs are the same."""
+    if SERIAL_ROUND["on"]:
+        S, cov = job.greedy_cover(k)
+        Rnum, Wnum, b = job.mcera(k)
+        return S, cov, Rnum, Wnum, b
+    return job.cover_and_mcera(k)
+
+
 def gpu_step(P, graph, wl, M, seed):
     job = P.Job(graph, seed, wl.t, space=SPACE["space"], kappa=SPACE["kappa"])
     job.set_timing(True)
     job.sample(M)
     SAMPLER_INFO.append(job.sampler_info())
-    S, cov = job.greedy_cover(wl.k)
-    Rnum, Wnum, b = job.mcera(wl.k)
+    S, cov, Rnum, Wnum, b = cover_and_mcera(job, wl.k)
     stop, bd = P.bounds(cov, M, int(Rnum.sum()), wl.t, Wnum, b, wl.eps, wl.delta, 1)
     st = job.stats()
     job.close()
@@ -286,8 +300,7 @@ def run_gpu(args, rank, world):
             apply_sampler_args(P, gg, args)
             job = P.Job(gg, seed0 + 2000 + s, wl.t, space=SPACE["space"], kappa=SPACE["kappa"])
             job.sample(M)
-            S, cov = job.greedy_cover(wl.k)
-            Rnum, Wnum, b = job.mcera(wl.k)
+            S, cov, Rnum, Wnum, b = cover_and_mcera(job, wl.k)
             P.bounds(cov, M, int(Rnum.sum()), wl.t, Wnum, b, wl.eps, wl.delta, 1)
             job.close()
             gg.close()
@@ -341,7 +354,9 @@ def run_gpu(args, rank, world):
                                f"k={wl.k}, t={wl.t}, eps={wl.eps}, delta={wl.delta}",
                    "n": g.n, "arcs": g.nnz, "pairs_per_step": M, "l2": "flushed (256 MB write) between steps",
                    "space": ["set betweenness", f"kappa-path (kappa={args.kappa})", "triangle"][args.space],
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "round": ("greedyCover then AMCERA (two calls)" if args.serial_round
+                             else "greedyCover and AMCERA side by side (cen_cover_and_mcera)")},
         "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
         "sampler": SAMPLER_INFO[-1] if SAMPLER_INFO else None,
         "wall_s": wall,
@@ -568,6 +583,7 @@ def oracle_sharded_rate(wl, count: int, procs: int, seed: int = 424243):
 
 def main():
     args = parse()
+    SERIAL_ROUND["on"] = args.serial_round
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.mode == "batch":

@@ -148,6 +148,14 @@ int cen_greedy_cover(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, u
  * Then AMCERA = sum_q Rnum_q / (t m) and the wimpy variance w = b Wnum / m. */
 int cen_mcera(cen_job *job, int32_t k, int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out);
 
+/* cen_greedy_cover and cen_mcera of one Alg. 1 round in one call, with the same
+ * outputs: the two read the same sample and write disjoint buffers, so the
+ * greedy runs on the job's stream while the AMCERA runs on a second stream
+ * of the job (made on first use).  Synchronous at return; host outputs as
+ * above.  cen_run uses it for every CentRA round. */
+int cen_cover_and_mcera(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered,
+                        int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out);
+
 /* Host FP64 bounds of Thm. "bound_dev" (eq. "epsrade", ln(5/delta_i)) and the
  * stopping test of Alg. 1 at iteration i >= 1 (delta_i = delta / 2^i).
  * out[8] = C, AMCERA, w, nu, xi, R~, R, eta.  *stop = 1 iff

@@ -77,6 +77,7 @@ def _load():
         "cen_last_error": ([], ctypes.c_char_p),
         "cen_graph_load": ([vp, vp, i32, i64, ip, ip, vp, pvp], ip),
         "cen_graph_load_ex": ([vp, vp, i32, i64, ip, ip, ip, vp, pvp], ip),
+        "cen_cover_and_mcera": ([vp, i32, vp, vp, vp, vp, vp, vp], ip),
         "cen_graph_copy": ([vp, vp, vp], ip),
         "cen_graph_free": ([vp], ip),
         "cen_graph_info": ([vp, vp, vp, vp], ip),
@@ -257,6 +258,17 @@ class Job:
         W, b = ctypes.c_int64(), ctypes.c_int32()
         _check(_lib.cen_mcera(self.h, k, _p(Rnum), ctypes.byref(W), ctypes.byref(b)), "cen_mcera")
         return Rnum, W.value, b.value
+
+    def cover_and_mcera(self, k: int):
+        """``cen_cover_and_mcera``: greedy_cover(k) and mcera(k) side by side on two streams;
+        returns (S, covered, Rnum, Wnum, b)."""
+        S = np.empty(k, np.int32)
+        size, cov = ctypes.c_int32(), ctypes.c_uint64()
+        Rnum = np.empty(self.t, np.int64)
+        W, b = ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.cen_cover_and_mcera(self.h, k, _p(S), ctypes.byref(size), ctypes.byref(cov), _p(Rnum),
+                                        ctypes.byref(W), ctypes.byref(b)), "cen_cover_and_mcera")
+        return S[: size.value].copy(), cov.value, Rnum, W.value, b.value
 
     def samples(self):
         m, mem = self.size()

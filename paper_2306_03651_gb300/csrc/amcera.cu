@@ -125,59 +125,113 @@ __global__ void k_sel_step(int nrows, int shift, SelRow *rows, unsigned int *hcn
   }
 }
 
-// Sum of the <= k largest positive entries of each of `nrows` rows of length n.
-static void topk_positive_sum(cen_job *job, const int32_t *vals, int64_t n, int nrows, int32_t k, long long *out_host) {
-  cudaStream_t st = job->st;
+// Enqueues on `run` the sums of the <= k largest positive entries of each of
+// `nrows` rows of length n (select state sized beforehand, see mcera_prepare);
+// the per-row results reach hdst (pinned, nrows SelRow) once `run` drains.
+static void topk_enqueue(cen_job *job, const int32_t *vals, int64_t n, int nrows, int32_t k, cudaStream_t run,
+                         SelRow *hdst) {
   Stats *S = &job->stats;
-  job->selst.ensure(sizeof(SelRow) * (size_t)nrows, st);
-  job->selh.ensure((size_t)nrows * 256 * (4 + 8), st);
   SelRow *rows = job->selst.as<SelRow>();
   unsigned int *hcnt = job->selh.as<unsigned int>();
   unsigned long long *hsum = (unsigned long long *)(hcnt + (size_t)nrows * 256);
-  CEN_CK(cudaMemsetAsync(job->selh.p, 0, (size_t)nrows * 256 * 12, st));
-  launch(S, K_SELECT, st, [&] { k_sel_init<<<grid_for(nrows, 128), 128, 0, st>>>(rows, nrows, k); });
+  CEN_CK(cudaMemsetAsync(job->selh.p, 0, (size_t)nrows * 256 * 12, run));
+  launch(S, K_SELECT, run, [&] { k_sel_init<<<grid_for(nrows, 128), 128, 0, run>>>(rows, nrows, k); });
   const int bx = grid_for((size_t)n, 256 * 8, 512);
   for (int shift = 24; shift >= 0; shift -= 8) {
-    launch(S, K_SELECT, st, [&] {
-      k_sel_hist<<<dim3(bx, nrows), 256, 0, st>>>(vals, n, nrows, shift, rows, hcnt, hsum);
+    launch(S, K_SELECT, run, [&] {
+      k_sel_hist<<<dim3(bx, nrows), 256, 0, run>>>(vals, n, nrows, shift, rows, hcnt, hsum);
     });
-    launch(S, K_SELECT, st, [&] { k_sel_step<<<grid_for(nrows, 64), 64, 0, st>>>(nrows, shift, rows, hcnt, hsum); });
+    launch(S, K_SELECT, run, [&] { k_sel_step<<<grid_for(nrows, 64), 64, 0, run>>>(nrows, shift, rows, hcnt, hsum); });
   }
-  SelRow *h = (SelRow *)host_staging(job, sizeof(SelRow) * (size_t)nrows);
-  CEN_CK(cudaMemcpyAsync(h, rows, sizeof(SelRow) * (size_t)nrows, cudaMemcpyDeviceToHost, st));
-  CEN_CK(cudaStreamSynchronize(st));
-  for (int r = 0; r < nrows; ++r) out_host[r] = h[r].sum;
+  CEN_CK(cudaMemcpyAsync(hdst, rows, sizeof(SelRow) * (size_t)nrows, cudaMemcpyDeviceToHost, run));
+}
+
+// Host bytes mcera_enqueue copies into: t + 1 select rows, then b_H.
+size_t mcera_result_bytes(const cen_job *job) { return sizeof(SelRow) * (size_t)(job->t + 1) + 8; }
+
+// Sizes the AMCERA workspace (allocations ordered on the job's stream).  The
+// incidence must be current.
+void mcera_prepare(cen_job *job, int32_t k) {
+  CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_mcera: k must be >= 1");
+  cudaStream_t st = job->st;
+  const int nrows = job->t + 1;
+  job->R.ensure(4 * (size_t)job->g->n * nrows, st);
+  job->selst.ensure(sizeof(SelRow) * (size_t)nrows, st);
+  job->selh.ensure((size_t)nrows * 256 * (4 + 8), st);
+}
+
+// Enqueues the AMCERA of Alg. 1 on stream `run` (after mcera_prepare): rows
+// 0 .. t-1 of R are R_q^u, row t is c_u, so one selection gives every Rnum and
+// Wnum.  Results reach hdst (pinned, mcera_result_bytes) once `run` drains.
+void mcera_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
+  Stats *S = &job->stats;
+  const int32_t n = job->g->n;
+  const int t = job->t;
+  CEN_CK(cudaMemsetAsync(job->R.p, 0, 4 * (size_t)n * t, run));
+  launch(S, K_RADE, run, [&] {
+    k_rade<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, run>>>(n, t, job->nw, job->noff.as<int64_t>(),
+                                                                       job->nsamp.as<int32_t>(),
+                                                                       job->sign.as<uint32_t>(), job->R.as<int32_t>(),
+                                                                       (unsigned long long *)(job->stats.d_units + K_RADE));
+  });
+  CEN_CK(cudaMemcpyAsync(job->R.as<int32_t>() + (size_t)n * t, job->c.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice,
+                         run));
+  SelRow *hrows = (SelRow *)hdst;
+  topk_enqueue(job, job->R.as<int32_t>(), n, t + 1, k, run, hrows);
+  CEN_CK(cudaMemcpyAsync(hrows + t + 1, job->bmax.p, 4, cudaMemcpyDeviceToHost, run));
+}
+
+// Rnum[t], Wnum and b_H from the copied result.
+void mcera_result(cen_job *job, int32_t k, const void *h, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
+  const SelRow *hrows = (const SelRow *)h;
+  const int t = job->t;
+  for (int q = 0; q < t; ++q) Rnum[q] = hrows[q].sum;
+  *Wnum = hrows[t].sum;  // the c_u are positive, so this is the sum of the k largest
+  int hb = 0;
+  memcpy(&hb, hrows + t + 1, 4);
+  *b = job->m ? hb : 0;
+  job->rade_valid_k = k;
+}
+
+// greedyCover on the job's stream and the AMCERA on its second stream at the
+// same time: the two read the same incidence and write disjoint buffers, so
+// the results are those of greedy_cover followed by mcera.
+void cover_and_mcera(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered, int64_t *Rnum,
+                     int64_t *Wnum, int32_t *b) {
+  CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_cover_and_mcera: k must be >= 1");
+  Range range("cen_cover_and_mcera");
+  build_incidence(job);
+  greedy_prepare(job, k);
+  mcera_prepare(job, k);
+  const size_t gb = (greedy_result_bytes(k) + 15) & ~(size_t)15;
+  char *h = (char *)host_staging(job, gb + mcera_result_bytes(job));
+  job->aux.ensure();
+  CEN_CK(cudaEventRecord(job->aux.fork, job->st));
+  CEN_CK(cudaStreamWaitEvent(job->aux.st, job->aux.fork, 0));
+  greedy_enqueue(job, k, job->st, h);
+  try {
+    mcera_enqueue(job, k, job->aux.st, h + gb);
+  } catch (...) {  // still join, so that nothing on the job's stream outruns the second stream
+    cudaEventRecord(job->aux.join, job->aux.st);
+    cudaStreamWaitEvent(job->st, job->aux.join, 0);
+    throw;
+  }
+  CEN_CK(cudaEventRecord(job->aux.join, job->aux.st));
+  CEN_CK(cudaStreamWaitEvent(job->st, job->aux.join, 0));
+  CEN_CK(cudaStreamSynchronize(job->st));
+  greedy_result(h, S, S_size, covered);
+  mcera_result(job, k, h + gb, Rnum, Wnum, b);
 }
 
 void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
   CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_mcera: k must be >= 1");
   Range range("cen_mcera");
   build_incidence(job);
-  cudaStream_t st = job->st;
-  Stats *S = &job->stats;
-  const int32_t n = job->g->n;
-  const int t = job->t;
-  // rows 0 .. t-1: R_q^u; row t: c_u (so one selection gives every Rnum and Wnum)
-  job->R.ensure(4 * (size_t)n * (t + 1), st);
-  CEN_CK(cudaMemsetAsync(job->R.p, 0, 4 * (size_t)n * t, st));
-  launch(S, K_RADE, st, [&] {
-    k_rade<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, st>>>(n, t, job->nw, job->noff.as<int64_t>(),
-                                                                      job->nsamp.as<int32_t>(),
-                                                                      job->sign.as<uint32_t>(), job->R.as<int32_t>(),
-                                                                      (unsigned long long *)(job->stats.d_units + K_RADE));
-  });
-  CEN_CK(cudaMemcpyAsync(job->R.as<int32_t>() + (size_t)n * t, job->c.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice,
-                         st));
-  std::vector<long long> rn(t + 1);
-  topk_positive_sum(job, job->R.as<int32_t>(), n, t + 1, k, rn.data());
-  for (int q = 0; q < t; ++q) Rnum[q] = rn[q];
-  *Wnum = rn[t];  // the c_u are positive, so this is the sum of the k largest
-  int hb = 0;
-  CEN_CK(cudaMemcpyAsync(host_staging(job, 4), job->bmax.p, 4, cudaMemcpyDeviceToHost, st));
-  CEN_CK(cudaStreamSynchronize(st));
-  memcpy(&hb, host_staging(job, 4), 4);
-  *b = job->m ? hb : 0;
-  job->rade_valid_k = k;
+  mcera_prepare(job, k);
+  void *h = host_staging(job, mcera_result_bytes(job));
+  mcera_enqueue(job, k, job->st, h);
+  CEN_CK(cudaStreamSynchronize(job->st));
+  mcera_result(job, k, h, Rnum, Wnum, b);
 }
 
 }  // namespace cen

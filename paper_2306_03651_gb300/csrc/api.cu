@@ -412,6 +412,15 @@ int cen_greedy_cover(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, u
   CEN_API_END
 }
 
+int cen_cover_and_mcera(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered,
+                        int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && S_out && S_size && covered && Rnum_out && Wnum_out && b_out, CEN_EINVAL,
+              "cen_cover_and_mcera: null argument");
+  cen::cover_and_mcera(job, k, S_out, S_size, covered, Rnum_out, Wnum_out, b_out);
+  CEN_API_END
+}
+
 int cen_mcera(cen_job *job, int32_t k, int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out) {
   CEN_API_BEGIN
   CEN_REQUIRE(job && Rnum_out && Wnum_out && b_out, CEN_EINVAL, "cen_mcera: null argument");
@@ -472,16 +481,16 @@ int cen_run_ex(const cen_graph *g, int32_t k, double eps, double delta, int32_t 
       CEN_REQUIRE(m_i < (1ull << 31), CEN_EINVAL, "cen_run: at most 2^31 - 1 samples per job");
       cen::sample_append(job, m_i - m_prev);
       uint64_t cov = 0;
-      cen::greedy_cover(job, k, S_out, S_size, &cov);
       int64_t Wnum = 0, Rsum = 0;
       int32_t b = 0;
       double bd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       int stop;
       if (o.rule == CEN_RULE_CENTRA) {
-        cen::mcera(job, k, Rnum.data(), &Wnum, &b);
+        cen::cover_and_mcera(job, k, S_out, S_size, &cov, Rnum.data(), &Wnum, &b);
         for (int q = 0; q < t; ++q) Rsum += Rnum[q];
         stop = cen::bounds_fp64(cov, m_i, Rsum, t, Wnum, b, eps, delta, i, bd);
       } else {  // HEDGE-P needs no AMCERA; its C, nu_U, eta_U go to the C, nu, eta columns
+        cen::greedy_cover(job, k, S_out, S_size, &cov);
         double hb[4];
         stop = cen::bounds_hedge_fp64(cov, m_i, g->n, k, eps, delta, i, hb);
         bd[0] = hb[0];

@@ -175,22 +175,29 @@ __global__ void __launch_bounds__(256) k_greedy_all(const int64_t *__restrict__ 
   }
 }
 
-void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered) {
+size_t greedy_result_bytes(int32_t k) { return sizeof(GreedyCtl) + 4 * (size_t)k; }
+
+// Sizes the greedy workspace for k picks (allocations ordered on the job's
+// stream).  The incidence must be current.
+void greedy_prepare(cen_job *job, int32_t k) {
   CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_greedy_cover: k must be >= 1");
-  Range range("cen_greedy_cover");
-  build_incidence(job);
   cudaStream_t st = job->st;
+  job->gain.ensure(4 * (size_t)job->g->n, st);
+  job->covered.ensure(4 * ((job->m + 31) / 32 + 1), st);
+  job->gctl.ensure(greedy_result_bytes(k), st);
+}
+
+// Enqueues greedyCover(k) on stream `run` (after greedy_prepare); the result
+// reaches hdst (pinned, greedy_result_bytes(k)) once `run` has drained.
+void greedy_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
   Stats *St = &job->stats;
   const int32_t n = job->g->n;
-  job->gain.ensure(4 * (size_t)n, st);
-  job->covered.ensure(4 * ((job->m + 31) / 32 + 1), st);
-  const size_t cbytes = sizeof(GreedyCtl) + 4 * (size_t)k;
-  job->gctl.ensure(cbytes, st);
-  CEN_CK(cudaMemsetAsync(job->covered.p, 0, 4 * ((job->m + 31) / 32 + 1), st));
-  CEN_CK(cudaMemsetAsync(job->gctl.p, 0, cbytes, st));
+  const size_t cbytes = greedy_result_bytes(k);
+  CEN_CK(cudaMemsetAsync(job->covered.p, 0, 4 * ((job->m + 31) / 32 + 1), run));
+  CEN_CK(cudaMemsetAsync(job->gctl.p, 0, cbytes, run));
   GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
-  launch(St, K_GREEDY, st,
-         [&] { k_gain_init<<<grid_for(n, 256), 256, 0, st>>>(job->c.as<int32_t>(), job->gain.as<int32_t>(), n); });
+  launch(St, K_GREEDY, run,
+         [&] { k_gain_init<<<grid_for(n, 256), 256, 0, run>>>(job->c.as<int32_t>(), job->gain.as<int32_t>(), n); });
   const int coop = cooperative_grid((const void *)k_greedy_all, 256);
   if (coop > 0) {
     const int64_t *a_noff = job->noff.as<int64_t>();
@@ -202,30 +209,43 @@ void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t
     uint32_t *a_cov = job->covered.as<uint32_t>();
     int a_k = k;
     void *args[] = {&a_noff, &a_nsamp, &a_hoff, &a_hmem, &a_gain, &a_n, &a_cov, &ctl, &a_k};
-    launch(St, K_GREEDY, st, [&] {
-      CEN_CK(cudaLaunchCooperativeKernel((const void *)k_greedy_all, dim3(coop), dim3(256), args, 0, st));
+    launch(St, K_GREEDY, run, [&] {
+      CEN_CK(cudaLaunchCooperativeKernel((const void *)k_greedy_all, dim3(coop), dim3(256), args, 0, run));
     });
   } else {
     const int gblocks = grid_for((size_t)n, 256, 152 * 4);
     for (int it = 0; it < k; ++it) {
       const int slot = it & 1;
-      launch(St, K_GREEDY, st,
-             [&] { k_greedy_argmax<<<gblocks, 256, 0, st>>>(job->gain.as<int32_t>(), n, ctl, slot); });
-      launch(St, K_GREEDY, st, [&] {
-        k_greedy_update<<<152 * 4, 256, 0, st>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
-                                                  job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
-                                                  job->gain.as<int32_t>(), job->covered.as<uint32_t>(), ctl, slot,
-                                                  it);
+      launch(St, K_GREEDY, run,
+             [&] { k_greedy_argmax<<<gblocks, 256, 0, run>>>(job->gain.as<int32_t>(), n, ctl, slot); });
+      launch(St, K_GREEDY, run, [&] {
+        k_greedy_update<<<152 * 4, 256, 0, run>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
+                                                   job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
+                                                   job->gain.as<int32_t>(), job->covered.as<uint32_t>(), ctl, slot,
+                                                   it);
       });
     }
   }
-  char *h = (char *)host_staging(job, cbytes);
-  CEN_CK(cudaMemcpyAsync(h, ctl, cbytes, cudaMemcpyDeviceToHost, st));
-  CEN_CK(cudaStreamSynchronize(st));
+  CEN_CK(cudaMemcpyAsync(hdst, ctl, cbytes, cudaMemcpyDeviceToHost, run));
+}
+
+// S, |S| and the covered count from the copied result.
+void greedy_result(const void *h, int32_t *S, int32_t *S_size, uint64_t *covered) {
   const GreedyCtl *hc = (const GreedyCtl *)h;
   *S_size = hc->size;
   *covered = hc->covered;
   for (int i = 0; i < hc->size; ++i) S[i] = hc->S[i];
+}
+
+void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered) {
+  CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_greedy_cover: k must be >= 1");
+  Range range("cen_greedy_cover");
+  build_incidence(job);
+  greedy_prepare(job, k);
+  void *h = host_staging(job, greedy_result_bytes(k));
+  greedy_enqueue(job, k, job->st, h);
+  CEN_CK(cudaStreamSynchronize(job->st));
+  greedy_result(h, S, S_size, covered);
 }
 
 }  // namespace cen

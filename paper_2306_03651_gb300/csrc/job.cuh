@@ -82,6 +82,29 @@ void keep_pool_memory();
 
 }  // namespace cen
 
+namespace cen {
+// A second stream of a job, with the events that fork work onto it and join
+// it back (cen_cover_and_mcera); created on first use.
+struct AuxStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  AuxStream() = default;
+  AuxStream(const AuxStream &) = delete;
+  AuxStream &operator=(const AuxStream &) = delete;
+  ~AuxStream() {
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (st) cudaStreamDestroy(st);
+  }
+  void ensure() {
+    if (st) return;
+    CEN_CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    CEN_CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    CEN_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  }
+};
+}  // namespace cen
+
 struct cen_job {
   const cen_graph *g = nullptr;
   uint64_t seed = 0;
@@ -100,6 +123,8 @@ struct cen_job {
   // AMCERA workspace
   cen::DevBuf R, selh, selst;
   int32_t rade_valid_k = -1;
+  // greedyCover and AMCERA side by side (cen_cover_and_mcera)
+  cen::AuxStream aux;
   // sampler pipelines (workspace 0 runs on the job's stream)
   std::vector<std::unique_ptr<cen::WaveWS>> wws;
   int wave_streams = 4;  // waves of one cen_sample call run at once
@@ -138,6 +163,16 @@ int bidir_resident_slots();
 void build_incidence(cen_job *job);
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered);
 void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b);
+size_t greedy_result_bytes(int32_t k);
+void greedy_prepare(cen_job *job, int32_t k);
+void greedy_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst);
+void greedy_result(const void *h, int32_t *S, int32_t *S_size, uint64_t *covered);
+size_t mcera_result_bytes(const cen_job *job);
+void mcera_prepare(cen_job *job, int32_t k);
+void mcera_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst);
+void mcera_result(cen_job *job, int32_t k, const void *h, int64_t *Rnum, int64_t *Wnum, int32_t *b);
+void cover_and_mcera(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered, int64_t *Rnum,
+                     int64_t *Wnum, int32_t *b);
 void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_device, Stats *S);
 void graph_canonicalize(cen_graph *g, const int64_t *off, const int32_t *col, int64_t nnz, bool on_device,
                         bool symmetrize, Stats *S);

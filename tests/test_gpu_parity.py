@@ -440,3 +440,21 @@ def test_rmat18_sampled_parity_and_properties(rmat18):
         chosen.append(u)
         if len(chosen) >= 5:
             break
+
+
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_lcc", "rmat12_dir"])
+def test_cover_and_mcera_equals_the_two_calls(name):
+    """greedyCover and the AMCERA side by side on two streams give what the two calls give, on a
+    job whose sample grows between rounds (the incidence is rebuilt each time)."""
+    g = GRAPHS[name]
+    gg = P.Graph.of(g)
+    a, b = P.Job(gg, 41, 12), P.Job(gg, 41, 12)
+    for m in (900, 1700):
+        a.sample(m)
+        b.sample(m)
+        for k in (1, 7, 25):
+            S, cov, Rnum, Wnum, bh = a.cover_and_mcera(k)
+            S2, cov2 = b.greedy_cover(k)
+            Rnum2, Wnum2, bh2 = b.mcera(k)
+            assert np.array_equal(S, S2) and cov == cov2
+            assert np.array_equal(Rnum, Rnum2) and Wnum == Wnum2 and bh == bh2
