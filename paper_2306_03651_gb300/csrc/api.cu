@@ -272,12 +272,11 @@ int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nn
 
 int cen_graph_load_ex(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
                       int flags, void *stream, cen_graph **out) {
-  if (!(flags & (CEN_GRAPH_CANONICALIZE | CEN_GRAPH_SYMMETRIZE)))
-    return cen_graph_load(off, col, n, nnz, directed, on_device, stream, out);
+  if (flags == 0) return cen_graph_load(off, col, n, nnz, directed, on_device, stream, out);
   CEN_API_BEGIN
+  CEN_REQUIRE(!(flags & ~(CEN_GRAPH_CANONICALIZE | CEN_GRAPH_SYMMETRIZE)), CEN_EINVAL, "cen_graph_load: unknown flag");
   CEN_REQUIRE(out && off && (col || nnz == 0), CEN_EINVAL, "cen_graph_load: null argument");
   CEN_REQUIRE(n >= 2 && nnz >= 0, CEN_EINVAL, "cen_graph_load: need n >= 2 and nnz >= 0");
-  CEN_REQUIRE(!(flags & ~(CEN_GRAPH_CANONICALIZE | CEN_GRAPH_SYMMETRIZE)), CEN_EINVAL, "cen_graph_load: unknown flag");
   CEN_REQUIRE(!(directed && (flags & CEN_GRAPH_SYMMETRIZE)), CEN_EINVAL,
               "cen_graph_load: SYMMETRIZE is for undirected graphs");
   *out = nullptr;

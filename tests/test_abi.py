@@ -80,3 +80,25 @@ def test_null_handles_rejected():
     off = np.array([0, 1], np.int64)
     col = np.array([0], np.int32)
     assert P.cen_graph_load(off.ctypes.data, col.ctypes.data, 1, 1, 0, 0, None, ctypes.byref(h)) == P.EINVAL
+
+
+def test_new_entry_points_check_arguments_before_any_device_work():
+    S = np.zeros(4, np.int32)
+    R = np.zeros(4, np.int64)
+    size, cov, W, b = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_int64(), ctypes.c_int32()
+    assert P.cen_cover_and_mcera(None, 4, S.ctypes.data, ctypes.byref(size), ctypes.byref(cov), R.ctypes.data,
+                                 ctypes.byref(W), ctypes.byref(b)) == P.EINVAL
+    off = np.array([0, 1, 1], np.int64)
+    col = np.array([1], np.int32)
+    h = ctypes.c_void_p()
+    # unknown flag; SYMMETRIZE on a directed graph; n < 2 -- all rejected on the host
+    assert P.cen_graph_load_ex(off.ctypes.data, col.ctypes.data, 2, 1, 0, 0, 8, None, ctypes.byref(h)) == P.EINVAL
+    assert P.cen_graph_load_ex(off.ctypes.data, col.ctypes.data, 2, 1, 1, 0, P.GRAPH_SYMMETRIZE, None,
+                               ctypes.byref(h)) == P.EINVAL
+    assert P.cen_graph_load_ex(off.ctypes.data, col.ctypes.data, 1, 1, 0, 0, P.GRAPH_CANONICALIZE, None,
+                               ctypes.byref(h)) == P.EINVAL
+    assert "SYMMETRIZE" in P.last_error() or "n >= 2" in P.last_error()
+    assert P.cen_graph_copy(None, off.ctypes.data, col.ctypes.data) == P.EINVAL
+    # an allocator needs both functions; restoring the default needs none
+    assert P.cen_set_allocator(ctypes.cast(P._ALLOC_FN(lambda n, s, c: None), ctypes.c_void_p), None, None) == P.EINVAL
+    assert P.cen_set_allocator(None, None, None) == P.OK
