@@ -1,6 +1,7 @@
-"""Host-side logic of bench.py and the serving estimate (no GPU): the DRAM-traffic lookup is
-reported only while the profiled source is unchanged, and the admission estimate counts the
-bidirectional workspace and grows with the sample cap."""
+"""Host-side logic of bench.py and of the serving loop (no GPU): the DRAM-traffic lookup is
+reported only while the profiled source is unchanged; the clock sampler reads a window of
+samples; the admission estimate counts the bidirectional workspace and grows with the sample
+cap; and admission is FIFO within the worker count and the byte budget."""
 import hashlib
 import os
 
@@ -74,3 +75,59 @@ def test_clock_sampler_reads_a_window_of_samples(tmp_path, monkeypatch):
     time.sleep(0.05)
     r = c.stop()  # no window: every sample counts, the early 1,500 MHz ones too
     assert r["samples"] >= 2 and r["sm_max_mhz"] == 2070.0
+
+
+class _FakeStream:
+    cuda_stream = 0
+
+
+class _FakeGraph:
+    def __init__(self, n, nnz):
+        self.n, self.nnz = n, nnz
+
+
+def test_server_admission_by_budget_and_fifo(monkeypatch):
+    """The serving loop's host logic with a stand-in for the GPU run: requests start in arrival
+    order, never more at once than the workers or the byte budget allow, and every request
+    finishes with its own result."""
+    import threading
+    import time
+    import numpy as np
+    import torch
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _FakeStream())
+    running, peak, started = [0], [0], []
+    lock = threading.Lock()
+
+    def fake_run(g, k, eps, delta, t, seed, **kw):
+        with lock:
+            running[0] += 1
+            peak[0] = max(peak[0], running[0])
+            started.append(seed)
+        time.sleep(0.03)
+        with lock:
+            running[0] -= 1
+        return {"status": serve.P.OK, "S": np.arange(k, dtype=np.int32), "covered": seed, "m_final": 1000,
+                "rounds": 1, "log": np.zeros((1, 16))}
+
+    monkeypatch.setattr(serve.P, "run", fake_run)
+    graphs = {"a": _FakeGraph(2000, 16000)}
+    per_job = serve.estimate_job_bytes(2000, 16000, 8, 1 << 20)
+    reqs = [serve.Request(rid=i, graph="a", k=5, eps=0.1, delta=0.1, t=8, seed=100 + i, arrival_s=0.002 * i,
+                          m_cap=1 << 20) for i in range(12)]
+    # budget for two jobs at a time, four workers
+    srv = serve.Server(graphs, workers=4, hbm_budget_bytes=2 * per_job)
+    res = srv.serve(reqs)
+    assert [r.rid for r in res] == list(range(12))
+    assert all(r.covered == 100 + r.rid and r.status == serve.P.OK for r in res)
+    st = [r.start_s for r in res]  # FIFO: admitted in arrival order (thread start may jitter by a few ms)
+    assert all(a <= b + 0.01 for a, b in zip(st, st[1:]))
+    assert peak[0] <= 2 and srv.peak_running <= 2 and srv.peak_bytes <= 2 * per_job
+    # budget for all, two workers: the workers bound it
+    running[0], peak[0] = 0, 0
+    started.clear()
+    srv = serve.Server(graphs, workers=2, hbm_budget_bytes=100 * per_job)
+    res2 = srv.serve(reqs)
+    st = [r.start_s for r in res2]
+    assert peak[0] <= 2 and all(a <= b + 0.01 for a, b in zip(st, st[1:]))
+    summ = serve.summarize(res)
+    assert summ["jobs"] == 12 and summ["certified"] == 12
