@@ -46,7 +46,7 @@ extern "C" {
 typedef struct cen_graph cen_graph;
 typedef struct cen_job cen_job;
 
-/* Device memory.  The library owns every device buffer it allocates (graph
+/* Device memory (no counterpart in the paper).  The library owns every device buffer it allocates (graph
  * copies, samples, workspaces); arrays the caller passes stay the caller's.
  * By default buffers come from the device's stream-ordered pool
  * (cudaMallocAsync on the call's stream).  cen_set_allocator installs another
@@ -79,7 +79,8 @@ const char *cen_last_error(void);
 int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
                    void *stream, cen_graph **out);
 /* cen_graph_load from any CSR with ids in [0, n) and offsets rising from 0 to
- * nnz (else CEN_EINVAL).  flags:
+ * nnz (else CEN_EINVAL).  The paper takes G as given (Sec. 3.1); this builds
+ * the canonical form above from raw input.  flags:
  *   CEN_GRAPH_CANONICALIZE  sort each row, drop repeated arcs and self-loops;
  *   CEN_GRAPH_SYMMETRIZE    (undirected only) add the reverse of every arc
  *                           first, then canonicalize.
@@ -90,9 +91,9 @@ int cen_graph_load(const int64_t *off, const int32_t *col, int32_t n, int64_t nn
 #define CEN_GRAPH_SYMMETRIZE 2
 int cen_graph_load_ex(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int directed, int on_device,
                       int flags, void *stream, cen_graph **out);
-/* The graph's canonical out-CSR: off[n+1] and col[nnz] (nnz of
- * cen_graph_info), host or device pointers, caller-owned; either may be null.
- * Synchronous on the graph's stream. */
+/* The graph's canonical out-CSR, read back (no counterpart in the paper):
+ * off[n+1] and col[nnz] (nnz of cen_graph_info), host or device pointers,
+ * caller-owned; either may be null.  Synchronous on the graph's stream. */
 int cen_graph_copy(const cen_graph *g, int64_t *off, int32_t *col);
 int cen_graph_free(cen_graph *g);
 int cen_graph_info(const cen_graph *g, int32_t *n, int64_t *nnz, int *directed);
