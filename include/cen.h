@@ -46,9 +46,10 @@ extern "C" {
 typedef struct cen_graph cen_graph;
 typedef struct cen_job cen_job;
 
-/* Device memory (no counterpart in the paper).  The library owns every device buffer it allocates (graph
- * copies, samples, workspaces); arrays the caller passes stay the caller's.
- * By default buffers come from the device's stream-ordered pool
+/* Device memory (no counterpart in the paper).  The library owns every
+ * device buffer it allocates (graph copies, samples, workspaces); arrays the
+ * caller passes stay the caller's.  By default buffers come from the device's
+ * stream-ordered pool
  * (cudaMallocAsync on the call's stream).  cen_set_allocator installs another
  * source for the allocations made after it: alloc(bytes, stream, ctx) returns
  * device memory for use on `stream` (null: the call fails with CEN_ENOMEM),
