@@ -49,9 +49,8 @@ typedef struct cen_job cen_job;
 /* Device memory (no counterpart in the paper).  The library owns every
  * device buffer it allocates (graph copies, samples, workspaces); arrays the
  * caller passes stay the caller's.  By default buffers come from the device's
- * stream-ordered pool
- * (cudaMallocAsync on the call's stream).  cen_set_allocator installs another
- * source for the allocations made after it: alloc(bytes, stream, ctx) returns
+ * stream-ordered pool (cudaMallocAsync on the call's stream).
+ * cen_set_allocator installs another source for the allocations made after it: alloc(bytes, stream, ctx) returns
  * device memory for use on `stream` (null: the call fails with CEN_ENOMEM),
  * and free(ptr, bytes, stream, ctx) takes back a buffer that alloc made,
  * called only once `stream` has drained, so the memory is idle and may be
