@@ -178,7 +178,7 @@ void mcera_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
                          run));
   SelRow *hrows = (SelRow *)hdst;
   topk_enqueue(job, job->R.as<int32_t>(), n, t + 1, k, run, hrows);
-  CEN_CK(cudaMemcpyAsync(hrows + t + 1, job->bmax.p, 4, cudaMemcpyDeviceToHost, run));
+  if (job->m) CEN_CK(cudaMemcpyAsync(hrows + t + 1, job->bmax.p, 4, cudaMemcpyDeviceToHost, run));  // b_H = 0 if m = 0
 }
 
 // Rnum[t], Wnum and b_H from the copied result.
