@@ -113,12 +113,12 @@ int orc_mcera(const orc_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32
 /* the raw R matrix, R[u * t + q], and c[u] (for element-wise parity) */
 int orc_rade_matrix(const orc_job *job, int32_t *R, int32_t *c);
 
-/* Host FP64 bounds of Theorem "bound_dev" and the stopping test of
+/* Host FP64 bounds of Theorem 4.4 and the stopping test of
  * Algorithm 1 for iteration i >= 1 (delta_i = delta / 2^i).
- * Parity unpinned at generic inputs: the paper prints no worked numeric
- * example, so the values are pinned only by closed forms at C = 0, w = 0 and
- * R~ = 0, the inequality chain of Prop. "main", monotonicity and the large-m
- * limit.
+ * Pinned at generic inputs against the proofs' own steps: nu and R are the
+ * largest fixed points of the self-bounding tail inversions, R~ inverts the
+ * hypercube tail at the flip-sum bound 4 t m w~ (reached on a tight sample),
+ * and eta is Bousquet's inequality at E[Z] = 2R with variance nu.
  * out[0..7] = C, A (AMCERA), w (wimpy), nu, xi, Rtilde, R, eta; returns stop (0/1). */
 int orc_bounds(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, int64_t Wnum, int32_t b, double eps,
                double delta, int32_t i, double *out);
@@ -143,7 +143,7 @@ uint64_t orc_schedule_next(int32_t schedule, double alpha, uint64_t m0, uint64_t
 int orc_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double eps, double delta, int32_t i,
                      double *out);
 /* Algorithm 1 with a schedule and a stopping rule: rule 0 = CentRA (AMCERA and
- * Thm. "bound_dev"), rule 1 = HEDGE-P (orc_bounds_hedge; no AMCERA; the log's
+ * Thm. 4.4), rule 1 = HEDGE-P (orc_bounds_hedge; no AMCERA; the log's
  * C, nu and eta columns hold C, nu_U, eta_U and the AMCERA columns are 0). */
 int orc_run_ex(const orc_graph *g, int32_t k, double eps, double delta, int32_t t, uint64_t seed, uint64_t m0,
                uint64_t m_cap, int32_t schedule, double alpha, int32_t rule, int32_t space, int32_t kappa,
