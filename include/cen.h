@@ -157,7 +157,7 @@ int cen_mcera(cen_job *job, int32_t k, int64_t *Rnum_out, int64_t *Wnum_out, int
 int cen_cover_and_mcera(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered,
                         int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out);
 
-/* Host FP64 bounds of Thm. "bound_dev" (eq. "epsrade", ln(5/delta_i)) and the
+/* Host FP64 bounds of Thm. 4.4 (Eq. 2, ln(5/delta_i)) and the
  * stopping test of Alg. 1 at iteration i >= 1 (delta_i = delta / 2^i).
  * out[8] = C, AMCERA, w, nu, xi, R~, R, eta.  *stop = 1 iff
  * (1-1/e)((1-1/e-eps) xi + eta) <= eps C.  Pure host code; no GPU work. */
@@ -198,7 +198,7 @@ int cen_run(const cen_graph *g, int32_t k, double eps, double delta, int32_t t, 
  * m_cap is clamped to m_cap.
  *
  * Stopping rules:
- *   CENTRA   Alg. 1: AMCERA, Thm. "bound_dev", stop iff
+ *   CENTRA   Alg. 1: AMCERA, Thm. 4.4, stop iff
  *            (1-1/e)((1-1/e-eps) xi + eta) <= eps C.
  *   HEDGE_P  Sec. 6's progressive HEDGE: no AMCERA; the SD bound eta_U of
  *            cen_bounds_hedge; stop iff eta_U <= eps (C - eta_U) / 2.  The

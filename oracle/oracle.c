@@ -714,20 +714,20 @@ int orc_mcera(const orc_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32
 }
 
 /* ---------------------------------------------------------------- bounds */
-/* Theorem "bound_dev" (eq. "epsrade") with ln(5/delta_i), and Alg. 1's xi and
+/* Theorem 4.4 (Eq. 2) with ln(5/delta_i), and Alg. 1's xi and
  * stopping test, in this evaluation order (a = 1 - 1/e, L = ln(5/delta_i),
  * Lm = L/m):
  *   C   = covered / m
  *   A   = Rsum / (t m)                 (AMCERA, Alg. 1 line "r_j" average)
  *   w   = (b Wnum) / m                 (approximate wimpy variance, Sec. 4.1)
  *   xi  = sqrt(Lm Lm + (2 C L) / (a m)) + Lm          (Alg. 1 line "xi")
- *   nu  = C / a + xi                                  (Thm. "bound_dev")
+ *   nu  = C / a + xi                                  (Thm. 4.4)
  *   Rt  = A + sqrt((4 w L) / (t m))
  *   R   = Rt + sqrt(Lm Lm + (2 L Rt) / m) + Lm
  *   eta = 2 R + sqrt((2 L (nu + 4 R)) / m) + L / (3 m)
  *   stop  <=>  a ((a - eps) xi + eta) <= eps C        (Alg. 1 stopping line)
  */
-/* Thm. "bound_dev" from the sample's fractions C, A, w at sample size md and
+/* Thm. 4.4 from the sample's fractions C, A, w at sample size md and
  * L = ln(5 / delta_i); out[3..7] = nu, xi, Rtilde, R, eta. */
 static void bounds_from_fractions(double C, double A, double w, int32_t t, double md, double L, double *out) {
   double a = 1.0 - exp(-1.0);
@@ -831,7 +831,7 @@ static uint64_t predict_m(int32_t rule, double C, double A, double w, int32_t t,
 }
 
 /* ------------------------------------------------------------- Alg. 1 */
-/* Sec. 4.2 "samplingSchedule", optimistic part: Thm. "bound_dev" with R = 0
+/* Sec. 4.2 "samplingSchedule", optimistic part: Thm. 4.4 with R = 0
  * and nu = 1 leaves eta(m) = sqrt(2 L / m) + L / (3 m); the smallest m with
  * eta(m) <= eps C / (1 - 1/e) (the stopping test when xi is negligible) solves
  * (L/3) y^2 + sqrt(2 L) y - target = 0 for y = 1/sqrt(m).  Returns 0 when C = 0

@@ -27,14 +27,14 @@ void *host_staging(cen_job *job, size_t bytes) {
   return job->host;
 }
 
-// Thm. "bound_dev" (eq. "epsrade") with ln(5/delta_i) and the xi / stopping
+// Thm. 4.4 (Eq. 2) with ln(5/delta_i) and the xi / stopping
 // lines of Alg. 1.  Evaluation order (a = 1 - 1/e, L = ln(5/delta_i), Lm = L/m):
 //   C = covered/m;  A = Rsum/(t m);  w = (b Wnum)/m
 //   xi = sqrt(Lm Lm + (2 C L)/(a m)) + Lm;   nu = C/a + xi
 //   Rt = A + sqrt((4 w L)/(t m));   R = Rt + sqrt(Lm Lm + (2 L Rt)/m) + Lm
 //   eta = 2 R + sqrt((2 L (nu + 4 R))/m) + L/(3 m)
 //   stop <=> a ((a - eps) xi + eta) <= eps C
-// Thm. "bound_dev" from the sample's fractions C, A (AMCERA), w at sample
+// Thm. 4.4 from the sample's fractions C, A (AMCERA), w at sample
 // size md with L = ln(5 / delta_i); writes out[3..7] = nu, xi, R~, R, eta.
 static void bounds_from_fractions(double C, double A, double w, int32_t t, double md, double L, double *out) {
   const double a = 1.0 - exp(-1.0);
@@ -66,7 +66,7 @@ static int bounds_fp64(uint64_t covered, uint64_t m, int64_t Rsum, int32_t t, in
 
 // Sample-size schedule of Sec. 4.2.  The optimistic guess is the smallest m
 // at which the stopping test could pass if the sample showed no deviation
-// (R = 0, nu = 1 in Thm. "bound_dev"): eta(m) = sqrt(2L/m) + L/(3m) must reach
+// (R = 0, nu = 1 in Thm. 4.4): eta(m) = sqrt(2L/m) + L/(3m) must reach
 // eps C / (1 - 1/e).  With y = 1/sqrt(m) that is the quadratic
 // (L/3) y^2 + sqrt(2L) y = target, solved for its positive root.
 static double schedule_guess(double C, double eps, double delta, int32_t i) {

@@ -1,4 +1,4 @@
-"""Seeded synthetic graphs shaped like the paper's workloads (Sec. 5, Table "tab:graphs").
+"""Seeded synthetic graphs shaped like the paper's workloads (Sec. 5, Table 1).
 
 This module is input plumbing only: it holds none of the sampling, covering or
 bounding arithmetic, imports nothing else from the package, and serves both the

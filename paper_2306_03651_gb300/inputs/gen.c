@@ -2,7 +2,7 @@
  * Seeded synthetic graph generators (inputs only; no part of the sampling,
  * covering or bounding arithmetic lives here).
  *
- * The paper evaluates on SNAP/KONECT graphs (Table "tab:graphs", Sec. 5) that
+ * The paper evaluates on SNAP/KONECT graphs (Table 1, Sec. 5) that
  * are not available offline; these generators produce stand-ins with the same
  * shape: Barabasi-Albert preferential attachment, R-MAT (Chakrabarti et al.),
  * and a 4-neighbour grid with a fraction of its edges rewired.

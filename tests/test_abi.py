@@ -1,6 +1,6 @@
 """CPU checks of the boundary: libcen.so loads, exports every function that
 include/cen.h declares, rejects bad arguments without touching a GPU, and its
-host FP64 bounds (Thm. "bound_dev", Alg. 1 stopping test) equal the oracle's
+host FP64 bounds (Thm. 4.4, Alg. 1 stopping test) equal the oracle's
 bit for bit."""
 import ctypes
 import math

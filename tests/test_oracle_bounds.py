@@ -1,8 +1,8 @@
-"""Pins of the oracle's FP64 bounds (Thm. "bound_dev", eq. "epsrade"), the stopping
+"""Pins of the oracle's FP64 bounds (Thm. 4.4, Eq. 2), the stopping
 test of Algorithm 1, and the progressive loop.
 
 Special cases with closed forms (C = 0, w = 0, R~ = 0), the equivalence of the
-stopping line with the inequality chain in the proof of Prop. "main", the
+stopping line with the inequality chain in the proof of Prop. 4.5, the
 monotonicity of eta, its large-m limit 2 A, and the schedule
 (delta_i = delta / 2^i, m_i = m0 2^(i-1)), and Sec. 4.2's schedule (its guess
 solves the no-deviation eta for m; growth by alpha).  End to end: on a graph small enough
@@ -57,7 +57,7 @@ def test_scaled_inputs():
 
 def test_stop_equals_prop_main_chain():
     """Alg. 1's test a((a-eps) xi + eta) <= eps C is the middle inequality of the proof of
-    Prop. "main": C/a + xi <= (C - eta)/(a - eps)."""
+    Prop. 4.5: C/a + xi <= (C - eta)/(a - eps)."""
     rng = np.random.default_rng(0)
     agree = 0
     for _ in range(3000):
@@ -131,7 +131,7 @@ def test_run_rejects_bad_arguments():
 
 
 def test_certified_set_is_within_guarantee_on_tiny_graph():
-    """Prop. "main": C(S) >= (1 - 1/e - eps) C(S*), checked with exact set betweenness."""
+    """Prop. 4.5: C(S) >= (1 - 1/e - eps) C(S*), checked with exact set betweenness."""
     nx = pytest.importorskip("networkx")
     g = I.ba(14, 2, 6)
     G = nx.Graph()

@@ -4,7 +4,7 @@ greedyCover: the (1-1/e) guarantee against brute force over all k-subsets,
 step-by-step agreement with a set-based brute force argmax, submodularity of
 coverage, early stop at zero gain.  AMCERA: the per-vector sup against
 brute-force enumeration of node subsets, the invariants of Lemma
-"expectappxratio" (exact expectation over all 2^m sign vectors on tiny
+4.2 (exact expectation over all 2^m sign vectors on tiny
 samples), parity / range / aggregation invariants of R.
 """
 import itertools

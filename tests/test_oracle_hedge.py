@@ -1,5 +1,5 @@
 """Pins of the oracle's HEDGE-P rule (Sec. 6 progressive HEDGE; union bound of Sec. 2,
-eq. "unionboundsamples").
+Eq. 1).
 
 The SD bound eta_U comes from a two-sided Bernstein tail per set and a union bound over
 the n^k sets of size <= k.  Checked here: both roots solve their defining equations, the
