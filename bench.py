@@ -332,7 +332,7 @@ def run_gpu(args, rank, world):
         achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if dom in byte_classes else None
         counted = sum(stats[k]["units"] for k in byte_classes if k in stats)
         traffic = dram_traffic(dom)
-        ratio = (f"DRAM traffic {traffic / per_launch_bytes:.2f}x the counted bytes, profiles/bidir_dram.md"
+        ratio = (f"DRAM traffic {traffic / per_launch_bytes:.2f}x the counted bytes, from an ncu DRAM capture"
                  if traffic and per_launch_bytes else "DRAM traffic not profiled for this source")
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,

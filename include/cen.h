@@ -39,7 +39,6 @@ extern "C" {
 #define CEN_ECUDA (-3)         /* a CUDA runtime call or kernel failed */
 #define CEN_EOVERFLOW (-4)     /* a sampled pair has >= 2^128 shortest paths */
 #define CEN_ENOTCERTIFIED (-5) /* cen_run: the next sample size would exceed m_cap */
-#define CEN_ETIMEOUT (-6)      /* a bounded device-side wait ran out */
 
 #define CEN_LOG_COLS 16 /* per-round log row, see cen_run */
 
@@ -239,7 +238,9 @@ int cen_bounds_hedge(uint64_t covered, uint64_t m, int32_t n, int32_t k, double 
  * Caller-owned buffers: results[i].S (capacity specs[i].k) and, optionally,
  * results[i].log (results[i].max_rounds rows of CEN_LOG_COLS doubles).
  * Returns CEN_OK once every job has finished (per-job status in results[i]),
- * or CEN_EINVAL for bad arguments.  start_s/end_s: seconds since the call. */
+ * CEN_EINVAL for bad arguments, or CEN_ECUDA (text in cen_last_error) when no
+ * worker could set up its device and stream, so that some job never ran.
+ * start_s/end_s: seconds since the call. */
 typedef struct cen_job_spec {
   const cen_graph *graph;
   int32_t k, t;
@@ -266,14 +267,15 @@ int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t nworkers, ce
  * (about 390 KB, held by every GPU that loads the library until exit) sized
  * for at most 128 rows.
  *   vals  device, int32 [nrows][n] row-major (only entries > 0 count);
- *   n >= 0, 1 <= nrows <= 128, k >= 1, otherwise CEN_EINVAL;
+ *   0 <= n <= 2^31 - 1, 1 <= nrows <= 128, k >= 1, otherwise CEN_EINVAL;
  *   out   host, int64 [nrows]: out[r] = sum of the min(k, #positive) largest
  *         positive entries of row r (0 for a row without positives).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  All calls share the array, which keeps the last call's contents
  * (each call clears what must start at zero): calls that overlap on the GPU,
- * from any stream or thread, race.  Returns after the work on `stream` is done. */
+ * from any stream or thread, race.  The sums are copied to `out` through host
+ * memory, so the call synchronizes `stream` before it returns. */
 int cen_topk_positive_sum_noalloc(const int32_t *vals, int64_t n, int32_t nrows, int32_t k, int64_t *out,
                                   void *stream);
 

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcen.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
 
-OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED = 0, -1, -2, -3, -4, -5
 PARAM_WAVE_WORDS, PARAM_WAVE_STREAMS, PARAM_PUSH_RATIO, PARAM_LEVEL_BUDGET = 1, 2, 3, 4
 PARAM_SAMPLER, PARAM_BIDIR_BUDGET, PARAM_BIDIR_QUEUE, PARAM_BIDIR_TABLE = 5, 6, 7, 8
 SAMPLER_BIDIR, SAMPLER_WAVES = 0, 1

@@ -169,7 +169,7 @@ void mcera_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
   const int t = job->t;
   CEN_CK(cudaMemsetAsync(job->R.p, 0, 4 * (size_t)n * t, run));
   launch(S, K_RADE, run, [&] {
-    k_rade<<<grid_for((size_t)n * 32, 256, 152 * 64), 256, 0, run>>>(n, t, job->nw, job->noff.as<int64_t>(),
+    k_rade<<<grid_for((size_t)n * 32, 256, sm_count() * 64), 256, 0, run>>>(n, t, job->nw, job->noff.as<int64_t>(),
                                                                        job->nsamp.as<int32_t>(),
                                                                        job->sign.as<uint32_t>(), job->R.as<int32_t>(),
                                                                        (unsigned long long *)(job->stats.d_units + K_RADE));
@@ -285,6 +285,8 @@ extern "C" int cen_topk_positive_sum_noalloc(const int32_t *vals, int64_t n, int
     CEN_REQUIRE(nrows >= 1 && nrows <= kNoAllocMaxRows, CEN_EINVAL,
                 "cen_topk_positive_sum_noalloc: nrows must be in [1, 128] (size of the static scratch)");
     CEN_REQUIRE(n >= 0 && k >= 1, CEN_EINVAL, "cen_topk_positive_sum_noalloc: need n >= 0 and k >= 1");
+    // the select's bucket counts are 32-bit
+    CEN_REQUIRE(n <= INT32_MAX, CEN_EINVAL, "cen_topk_positive_sum_noalloc: rows longer than 2^31 - 1 entries");
     cudaStream_t st = (cudaStream_t)stream;
     NoAllocScratch *sc = noalloc_scratch();
     // the histograms must start at zero; the row states are written by k_sel_init

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <mutex>
+#include <string>
 #include <numeric>
 #include <thread>
 #include <vector>
@@ -30,10 +32,18 @@ extern "C" int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t n
     auto secs = [&] {
       return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     };
+    std::vector<char> ran(njobs, 0);
+    std::mutex err_mu;
+    std::string setup_err;  // why a worker could not start, if one could not
     auto worker = [&] {
-      if (cudaSetDevice(dev) != cudaSuccess) return;
       cudaStream_t st = nullptr;
-      if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+      cudaError_t e = cudaSetDevice(dev);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {  // the other workers take the jobs; the call fails only if none could
+        std::lock_guard<std::mutex> lk(err_mu);
+        setup_err = std::string("cen_run_batch: worker setup failed: ") + cudaGetErrorString(e);
+        return;
+      }
       for (;;) {
         const int32_t q = next.fetch_add(1);
         if (q >= njobs) break;
@@ -44,14 +54,21 @@ extern "C" int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t n
         r.status = cen_run_ex(sp.graph, sp.k, sp.eps, sp.delta, sp.t, sp.seed, sp.m0, sp.m_cap, &sp.opts, st, r.S,
                               &r.S_size, &r.covered, &r.m_final, &r.rounds, r.log, r.log ? r.max_rounds : 0);
         r.end_s = secs();
+        ran[i] = 1;
       }
       cudaStreamDestroy(st);
     };
     for (int32_t i = 0; i < njobs; ++i) results[i].status = CEN_ECUDA;  // until a worker runs it
     std::vector<std::thread> pool;
     const int32_t nw = std::min<int32_t>(nworkers, std::max<int32_t>(njobs, 1));
-    for (int32_t w = 0; w < nw; ++w) pool.emplace_back(worker);
+    try {
+      for (int32_t w = 0; w < nw; ++w) pool.emplace_back(worker);
+    } catch (...) {  // a thread could not be started: the ones that were finish the jobs
+      if (pool.empty()) throw;
+    }
     for (auto &th : pool) th.join();
+    for (int32_t i = 0; i < njobs; ++i)
+      if (!ran[i]) cen::fail(CEN_ECUDA, setup_err.empty() ? "cen_run_batch: a job was not run" : setup_err);
     return CEN_OK;
   } catch (const cen::Error &e) {
     cen::set_last_error(e.msg);

@@ -259,7 +259,13 @@ void pinned_drop_cached();
 // SM up to what fits), or 0 when the device cannot launch cooperatively.
 int cooperative_grid(const void *kernel, int block);
 
-inline int grid_for(size_t items, int per_block, int cap = 152 * 32) {
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count();
+
+// Blocks for `items` work items at `per_block` each, at most `cap` (default:
+// 32 blocks per SM of the current device).
+inline int grid_for(size_t items, int per_block, int cap = 0) {
+  if (cap <= 0) cap = sm_count() * 32;
   size_t g = (items + per_block - 1) / per_block;
   if (g < 1) g = 1;
   if (g > (size_t)cap) g = cap;

@@ -213,13 +213,13 @@ void greedy_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
       CEN_CK(cudaLaunchCooperativeKernel((const void *)k_greedy_all, dim3(coop), dim3(256), args, 0, run));
     });
   } else {
-    const int gblocks = grid_for((size_t)n, 256, 152 * 4);
+    const int gblocks = grid_for((size_t)n, 256, sm_count() * 4);
     for (int it = 0; it < k; ++it) {
       const int slot = it & 1;
       launch(St, K_GREEDY, run,
              [&] { k_greedy_argmax<<<gblocks, 256, 0, run>>>(job->gain.as<int32_t>(), n, ctl, slot); });
       launch(St, K_GREEDY, run, [&] {
-        k_greedy_update<<<152 * 4, 256, 0, run>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
+        k_greedy_update<<<sm_count() * 4, 256, 0, run>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
                                                    job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
                                                    job->gain.as<int32_t>(), job->covered.as<uint32_t>(), ctl, slot,
                                                    it);

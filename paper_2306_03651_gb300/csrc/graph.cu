@@ -158,7 +158,7 @@ void graph_canonicalize(cen_graph *g, const int64_t *off, const int32_t *col, in
   tail.ensure(4 * (size_t)A, st);
   head.ensure(4 * (size_t)A, st);
   launch(S, K_GRAPH, st, [&] {
-    k_arc_list<<<grid_for((size_t)n, 8, 152 * 64), dim3(32, 8), 0, st>>>(ioff.as<int64_t>(), icol.as<int32_t>(), n,
+    k_arc_list<<<grid_for((size_t)n, 8, sm_count() * 64), dim3(32, 8), 0, st>>>(ioff.as<int64_t>(), icol.as<int32_t>(), n,
                                                                         nnz, symmetrize, tail.as<uint32_t>(),
                                                                         head.as<uint32_t>());
   });

@@ -138,6 +138,20 @@ void dev_free(void *p, size_t bytes, cudaStream_t s, const Allocator *al) noexce
 }
 
 // ------------------------------------------------------ occupancy
+int sm_count() {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  CEN_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  CEN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cache[dev] = sms > 0 ? sms : 1;
+  return cache[dev];
+}
+
 int resident_grid(const void *kernel, int block) {
   static std::mutex mu;
   static std::map<std::pair<int, const void *>, int> cache;

@@ -45,7 +45,7 @@ struct Ctl {
 };
 constexpr int kMaxG = 32;
 constexpr int kMaxW = 64 * kMaxG;
-constexpr int kLevelBlocks = 152 * 8;  // grid of the per-level node sweeps
+constexpr int kLevelBlocksPerSM = 8;  // grid of the per-level node sweeps, per SM
 constexpr int kWalkUnroll = 8;          // 32-arc chunks in flight per walk step
 constexpr size_t kArcLogCap = (size_t)1 << 24;  // cone arcs logged per wave (24 B each)
 
@@ -1016,7 +1016,7 @@ struct Sampler {
         const ChunkTable &oc = g->out_chunks;
         if (oc.count)
           launch(S, K_PUSH, st, [&] {
-            k_expand_push_heavy<<<grid_for((size_t)oc.count * 32, 256, 152 * 64), 256, 0, st>>>(
+            k_expand_push_heavy<<<grid_for((size_t)oc.count * 32, 256, sm_count() * 64), 256, 0, st>>>(
                 oc.count, oc.rows(), oc.begins(), off, col, G, gshift, cur, nxt, ctl, units(K_PUSH));
           });
         launch(S, K_LEVEL_FIN, st, [&] {
@@ -1124,7 +1124,7 @@ struct Sampler {
     const uint64_t *any = w.any.as<uint64_t>();
     int64_t *base = w.base.as<int64_t>();
     launch(S, K_SIGMA, st, [&] {
-      k_popc_words<<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, any, w.cnt.as<int32_t>());
+      k_popc_words<<<grid_for(words, 256, sm_count() * kLevelBlocksPerSM), 256, 0, st>>>((int64_t)words, any, w.cnt.as<int32_t>());
     });
     counts_to_offsets(w.cnt.as<int32_t>(), base, words, w.scan_tmp, st, S);
     int64_t *h = (int64_t *)ws_staging(w, sizeof(Ctl) + 8);
@@ -1137,7 +1137,7 @@ struct Sampler {
     const SigIdx ix{any, base};
     T *sig = w.sigc.as<T>();
     launch(S, K_SIGMA, st, [&] {
-      k_cone_level1<T><<<grid_for(words, 256, kLevelBlocks), 256, 0, st>>>((int64_t)words, level(1), ix, sig);
+      k_cone_level1<T><<<grid_for(words, 256, sm_count() * kLevelBlocksPerSM), 256, 0, st>>>((int64_t)words, level(1), ix, sig);
     });
     *sig_out = sig;
     return ix;

@@ -211,7 +211,7 @@ void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out, const
   cudaStream_t st = job->st;
   const size_t smem = sizeof(int32_t) * (size_t)job->kappa * kWalkWarps;
   launch(&job->stats, K_SPACE, st, [&] {
-    k_kpath<<<grid_for(count, kWalkWarps, 152 * 16), 32 * kWalkWarps, smem, st>>>(
+    k_kpath<<<grid_for(count, kWalkWarps, sm_count() * 16), 32 * kWalkWarps, smem, st>>>(
         j0, count, g->n, job->kappa, g->off.as<int64_t>(), g->col.as<int32_t>(), job->seed, job->ps.as<int32_t>(),
         job->pt.as<int32_t>(), job->pd.as<int32_t>(), out, hoff, job->bmax.as<int>(),
         (unsigned long long *)(job->stats.d_units + K_SPACE));
@@ -228,7 +228,7 @@ int64_t triangle_index(cen_job *job) {
     cnt.ensure(8 * (size_t)(g->nnz + 1), st);
     g->tri_off.ensure(8 * (size_t)(g->nnz + 1), st);
     launch(&job->stats, K_SPACE, st, [&] {
-      k_tri_count<<<grid_for((size_t)g->n, 8, 152 * 64), dim3(32, 8), 0, st>>>(g->n, g->off.as<int64_t>(),
+      k_tri_count<<<grid_for((size_t)g->n, 8, sm_count() * 64), dim3(32, 8), 0, st>>>(g->n, g->off.as<int64_t>(),
                                                                               g->col.as<int32_t>(), cnt.as<int64_t>());
     });
     exclusive_scan_i64(cnt.as<int64_t>(), g->tri_off.as<int64_t>(), (size_t)g->nnz, g->tri_off.as<int64_t>() + g->nnz,

@@ -52,6 +52,7 @@ class Result:
     start_s: float
     end_s: float
     est_bytes: int
+    error: str = ""  # the library's message when status is an error
 
     @property
     def latency_s(self) -> float:
@@ -120,16 +121,22 @@ class Server:
     def _run_one(self, w: int, r: Request, est: int, arrival: float):
         g = self.graphs[r.graph]
         start = self._now()
-        out = P.run(g, r.k, r.eps, r.delta, r.t, r.seed, m0=r.m0, m_cap=r.m_cap,
-                    stream=ctypes.c_void_p(self.streams[w].cuda_stream))
-        end = self._now()
-        res = Result(r.rid, out["status"], out["S"], out["covered"], out["m_final"], out["rounds"], out["log"],
-                     arrival, start, end, est)
-        with self._cv:
-            self._results.append(res)
-            self._in_use -= est
-            self._free_workers.append(w)
-            self._cv.notify_all()
+        res = None
+        try:
+            out = P.run(g, r.k, r.eps, r.delta, r.t, r.seed, m0=r.m0, m_cap=r.m_cap,
+                        stream=ctypes.c_void_p(self.streams[w].cuda_stream))
+            res = Result(r.rid, out["status"], out["S"], out["covered"], out["m_final"], out["rounds"], out["log"],
+                         arrival, start, self._now(), est)
+        except Exception as e:  # the request ends with its error status; its worker and bytes go back below
+            res = Result(r.rid, int(getattr(e, "rc", P.ECUDA)), np.zeros(0, np.int32), 0, 0, 0,
+                         np.zeros((0, len(P.LOG_COLS))), arrival, start, self._now(), est, error=str(e))
+        finally:
+            with self._cv:
+                if res is not None:
+                    self._results.append(res)
+                self._in_use -= est
+                self._free_workers.append(w)
+                self._cv.notify_all()
 
     def _dispatch(self, total: int):
         threads = []

@@ -131,3 +131,33 @@ def test_server_admission_by_budget_and_fifo(monkeypatch):
     assert peak[0] <= 2 and all(a <= b + 0.01 for a, b in zip(st, st[1:]))
     summ = serve.summarize(res)
     assert summ["jobs"] == 12 and summ["certified"] == 12
+
+
+def test_server_failed_request_gets_a_result_and_frees_its_slot(monkeypatch):
+    """A run that raises (e.g. ENOMEM when the byte estimate was too low) ends that request
+    with its error status and message, and gives its worker and its bytes back: with one
+    worker, the requests after it still run."""
+    import numpy as np
+    import torch
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _FakeStream())
+
+    def fake_run(g, k, eps, delta, t, seed, **kw):
+        if seed % 3 == 0:
+            raise serve.P.CenError(serve.P.ENOMEM, "out of device memory")
+        return {"status": serve.P.OK, "S": np.arange(k, dtype=np.int32), "covered": seed, "m_final": 1000,
+                "rounds": 1, "log": np.zeros((1, 16))}
+
+    monkeypatch.setattr(serve.P, "run", fake_run)
+    graphs = {"a": _FakeGraph(2000, 16000)}
+    per_job = serve.estimate_job_bytes(2000, 16000, 8, 1 << 20)
+    reqs = [serve.Request(rid=i, graph="a", k=5, eps=0.1, delta=0.1, t=8, seed=i, m_cap=1 << 20) for i in range(7)]
+    srv = serve.Server(graphs, workers=1, hbm_budget_bytes=per_job)
+    res = srv.serve(reqs)
+    assert [r.rid for r in res] == list(range(7))
+    for r in res:
+        if r.rid % 3 == 0:
+            assert r.status == serve.P.ENOMEM and "out of device memory" in r.error and len(r.S) == 0
+        else:
+            assert r.status == serve.P.OK and r.covered == r.rid and r.error == ""
+    assert srv._in_use == 0 and srv._free_workers == [0]
+    assert serve.summarize(res)["certified"] == 4
