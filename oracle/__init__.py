@@ -54,6 +54,7 @@ def _load():
         "orc_job_free": ([vp], None),
         "orc_job_sample": ([vp, u64], ctypes.c_int),
         "orc_job_sample_from": ([vp, u64, u64], ctypes.c_int),
+        "orc_job_append": ([vp, u64, u64, vp, vp, vp, vp, vp], ctypes.c_int),
         "orc_job_m": ([vp], u64),
         "orc_job_members": ([vp], i64),
         "orc_job_copy": ([vp, vp, vp, vp, vp, vp], None),
@@ -220,6 +221,18 @@ class Job:
         rc = _load().orc_job_sample_from(self.h, j_first, count)
         if rc:
             raise OracleError(rc, "sample_from")
+
+    def append(self, j_first: int, h: dict):
+        """Store samples j_first.. that another job of the same graph and seed drew
+        (dict(hoff, hmem, s, t, d), hoff starting at 0), e.g. in a worker process."""
+        hoff = np.ascontiguousarray(h["hoff"], np.int64)
+        count = len(hoff) - 1
+        hmem = np.ascontiguousarray(h["hmem"], np.int32)
+        arr = [np.ascontiguousarray(h[k][:count], np.int32) for k in ("s", "t", "d")]
+        rc = _load().orc_job_append(self.h, j_first, count, _p(hoff), _p(hmem) if len(hmem) else None,
+                                    *[_p(a) for a in arr])
+        if rc:
+            raise OracleError(rc, "append")
 
     def hypergraph(self):
         """Returns dict(hoff, hmem, s, t, d) as numpy arrays."""

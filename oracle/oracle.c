@@ -532,6 +532,42 @@ int orc_job_sample_from(orc_job *job, uint64_t j_first, uint64_t count) {
 }
 int64_t orc_job_members(const orc_job *job) { return job->hoff[job->m]; }
 
+/* Stores `count` samples with ids j_first .. j_first+count-1 that another job
+ * of the same graph, seed and space drew (plumbing for computing index ranges
+ * in several processes: a sample is a function of its id).  hoff[count+1] is
+ * relative to hmem[0]; the work tallies are not carried over. */
+int orc_job_append(orc_job *job, uint64_t j_first, uint64_t count, const int64_t *hoff, const int32_t *hmem,
+                   const int32_t *s, const int32_t *t, const int32_t *d) {
+  if (!hoff || (count && (!s || !t || !d)) || hoff[0] != 0) return ORC_EINVAL;
+  int64_t add = hoff[count];
+  if (job->m + count > job->cap_m) {
+    while (job->m + count > job->cap_m) job->cap_m *= 2;
+    job->hoff = (int64_t *)realloc(job->hoff, sizeof(int64_t) * (job->cap_m + 1));
+    job->ps = (int32_t *)realloc(job->ps, sizeof(int32_t) * job->cap_m);
+    job->pt = (int32_t *)realloc(job->pt, sizeof(int32_t) * job->cap_m);
+    job->pd = (int32_t *)realloc(job->pd, sizeof(int32_t) * job->cap_m);
+    job->ids = (uint64_t *)realloc(job->ids, sizeof(uint64_t) * job->cap_m);
+  }
+  int64_t base = job->hoff[job->m];
+  if (base + add > job->cap_mem) {
+    while (base + add > job->cap_mem) job->cap_mem *= 2;
+    job->hmem = (int32_t *)realloc(job->hmem, sizeof(int32_t) * (size_t)job->cap_mem);
+  }
+  if (!job->hoff || !job->ps || !job->pt || !job->pd || !job->ids || !job->hmem) return ORC_ENOMEM;
+  if (add) memcpy(job->hmem + base, hmem, sizeof(int32_t) * (size_t)add);
+  for (uint64_t q = 0; q < count; ++q) {
+    uint64_t j = job->m + q;
+    job->hoff[j + 1] = base + hoff[q + 1];
+    job->ps[j] = s[q];
+    job->pt[j] = t[q];
+    job->pd[j] = d[q];
+    job->ids[j] = j_first + q;
+  }
+  job->m += count;
+  job->next_id = j_first + count;
+  return ORC_OK;
+}
+
 void orc_job_copy(const orc_job *job, int64_t *hoff, int32_t *hmem, int32_t *s, int32_t *t, int32_t *d) {
   if (hoff) memcpy(hoff, job->hoff, sizeof(int64_t) * (size_t)(job->m + 1));
   if (hmem) memcpy(hmem, job->hmem, sizeof(int32_t) * (size_t)job->hoff[job->m]);

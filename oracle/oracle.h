@@ -98,6 +98,10 @@ uint64_t orc_job_m(const orc_job *job);
 int64_t orc_job_members(const orc_job *job);           /* sum of |h| */
 /* copy out hoff[m+1], hmem[members], and per-sample s, t, d (any may be NULL) */
 void orc_job_copy(const orc_job *job, int64_t *hoff, int32_t *hmem, int32_t *s, int32_t *t, int32_t *d);
+/* Store count samples (ids j_first ..) drawn by another job of the same graph,
+ * seed and space, e.g. in another process; hoff[count+1] starts at 0. */
+int orc_job_append(orc_job *job, uint64_t j_first, uint64_t count, const int64_t *hoff, const int32_t *hmem,
+                   const int32_t *s, const int32_t *t, const int32_t *d);
 /* algorithmic-work tallies of all samples drawn so far:
  * [0] nodes reached at levels < d(s,t), [1] arcs scanned out of levels < d(s,t)-1,
  * [2] in-arcs scanned by the backward walks, [3] path members written */

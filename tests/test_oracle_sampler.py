@@ -256,3 +256,29 @@ def test_shards_by_sample_index_concatenate_to_the_whole():
     assert np.concatenate([p["hmem"] for p in parts]).tolist() == ref["hmem"].tolist()
     lens = np.concatenate([np.diff(p["hoff"]) for p in parts])
     assert lens.tolist() == np.diff(ref["hoff"]).tolist()
+
+
+def test_index_shards_in_worker_processes_equal_one_job():
+    """Samples are functions of their index: ranges drawn in spawned worker processes and
+    stored in index order give the single job's samples, and so its greedy and AMCERA."""
+    from oracle import shards
+    g = I.rmat(9, 8, seed=5)
+    one = O.Job(O.Graph.of(g), 17, 12)
+    one.sample(700)
+    with shards.Pool(g, 2) as pool:
+        merged = pool.job(17, 12, 700, chunk=128)
+        picks = pool.hyperedges(17, [0, 5, 699])
+    a, b = one.hypergraph(), merged.hypergraph()
+    for key in ("hoff", "s", "t", "d"):
+        assert np.array_equal(a[key], b[key]), key
+    assert np.array_equal(a["hmem"][: a["hoff"][-1]], b["hmem"][: b["hoff"][-1]])
+    Sa, ca = one.greedy_cover(9)
+    Sb, cb = merged.greedy_cover(9)
+    assert Sa.tolist() == Sb.tolist() and ca == cb
+    Ra, Wa, ba = one.mcera(9)
+    Rb, Wb, bb = merged.mcera(9)
+    assert np.array_equal(Ra, Rb) and Wa == Wb and ba == bb
+    assert np.array_equal(one.rade_matrix()[0], merged.rade_matrix()[0])
+    og = O.Graph.of(g)
+    for j, r in picks.items():
+        assert r == og.hyperedge(17, j)
