@@ -87,7 +87,7 @@ class _FakeGraph:
 
 
 def test_server_admission_by_budget_and_fifo(monkeypatch):
-    """The serving loop's host logic with a stand-in for the GPU run: requests start in arrival
+    """The serving loop's host logic with a stand-in runner: requests start in arrival
     order, never more at once than the workers or the byte budget allow, and every request
     finishes with its own result."""
     import threading
@@ -98,24 +98,24 @@ def test_server_admission_by_budget_and_fifo(monkeypatch):
     running, peak, started = [0], [0], []
     lock = threading.Lock()
 
-    def fake_run(g, k, eps, delta, t, seed, **kw):
+    def fake_runner(g, req, stream, reserve):
+        reserve(req.m0)
         with lock:
             running[0] += 1
             peak[0] = max(peak[0], running[0])
-            started.append(seed)
+            started.append(req.seed)
         time.sleep(0.03)
         with lock:
             running[0] -= 1
-        return {"status": serve.P.OK, "S": np.arange(k, dtype=np.int32), "covered": seed, "m_final": 1000,
+        return {"status": serve.P.OK, "S": np.arange(req.k, dtype=np.int32), "covered": req.seed, "m_final": 1000,
                 "rounds": 1, "log": np.zeros((1, 16))}
 
-    monkeypatch.setattr(serve.P, "run", fake_run)
     graphs = {"a": _FakeGraph(2000, 16000)}
-    per_job = serve.estimate_job_bytes(2000, 16000, 8, 1 << 20)
+    per_job = serve.estimate_job_bytes(2000, 16000, 8, 1000)
     reqs = [serve.Request(rid=i, graph="a", k=5, eps=0.1, delta=0.1, t=8, seed=100 + i, arrival_s=0.002 * i,
                           m_cap=1 << 20) for i in range(12)]
     # budget for two jobs at a time, four workers
-    srv = serve.Server(graphs, workers=4, hbm_budget_bytes=2 * per_job)
+    srv = serve.Server(graphs, workers=4, hbm_budget_bytes=2 * per_job, runner=fake_runner)
     res = srv.serve(reqs)
     assert [r.rid for r in res] == list(range(12))
     assert all(r.covered == 100 + r.rid and r.status == serve.P.OK for r in res)
@@ -125,12 +125,42 @@ def test_server_admission_by_budget_and_fifo(monkeypatch):
     # budget for all, two workers: the workers bound it
     running[0], peak[0] = 0, 0
     started.clear()
-    srv = serve.Server(graphs, workers=2, hbm_budget_bytes=100 * per_job)
+    srv = serve.Server(graphs, workers=2, hbm_budget_bytes=100 * per_job, runner=fake_runner)
     res2 = srv.serve(reqs)
     st = [r.start_s for r in res2]
     assert peak[0] <= 2 and all(a <= b + 0.01 for a, b in zip(st, st[1:]))
     summ = serve.summarize(res)
     assert summ["jobs"] == 12 and summ["certified"] == 12
+
+
+def test_server_growth_reservations_wait_and_never_deadlock(monkeypatch):
+    """Requests reserve the memory of each grown round: with room for three first rounds
+    but not for all of their growth, rounds wait for older requests to finish, and every
+    request finishes.  Only the oldest running request grows without waiting, so the
+    total stays within the budget plus one request's growth."""
+    import time
+    import numpy as np
+    import torch
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _FakeStream())
+    graphs = {"a": _FakeGraph(20000, 160000)}
+    m0, rounds = 1 << 16, 4
+    est = [serve.estimate_job_bytes(20000, 160000, 8, m0 << r) for r in range(rounds)]
+    budget = est[rounds - 1] + 2 * est[0]  # one request at its largest round and two first rounds
+
+    def fake_runner(g, req, stream, reserve):
+        for r in range(rounds):
+            reserve(m0 << r)
+            time.sleep(0.01)
+        return {"status": serve.P.OK, "S": np.zeros(0, np.int32), "covered": 0, "m_final": m0 << (rounds - 1),
+                "rounds": rounds, "log": np.zeros((rounds, 16))}
+
+    reqs = [serve.Request(rid=i, graph="a", k=5, eps=0.1, delta=0.1, t=8, seed=i, m0=m0, m_cap=1 << 30)
+            for i in range(8)]
+    srv = serve.Server(graphs, workers=4, hbm_budget_bytes=budget, runner=fake_runner)
+    res = srv.serve(reqs)
+    assert [r.rid for r in res] == list(range(8)) and all(r.status == serve.P.OK for r in res)
+    assert srv.peak_bytes <= budget + est[rounds - 1] - est[0] and srv.peak_running >= 2 and srv.waits > 0
+    assert srv._in_use == 0
 
 
 def test_server_failed_request_gets_a_result_and_frees_its_slot(monkeypatch):
@@ -141,17 +171,17 @@ def test_server_failed_request_gets_a_result_and_frees_its_slot(monkeypatch):
     import torch
     monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _FakeStream())
 
-    def fake_run(g, k, eps, delta, t, seed, **kw):
-        if seed % 3 == 0:
+    def fake_runner(g, req, stream, reserve):
+        reserve(req.m0)
+        if req.seed % 3 == 0:
             raise serve.P.CenError(serve.P.ENOMEM, "out of device memory")
-        return {"status": serve.P.OK, "S": np.arange(k, dtype=np.int32), "covered": seed, "m_final": 1000,
+        return {"status": serve.P.OK, "S": np.arange(req.k, dtype=np.int32), "covered": req.seed, "m_final": 1000,
                 "rounds": 1, "log": np.zeros((1, 16))}
 
-    monkeypatch.setattr(serve.P, "run", fake_run)
     graphs = {"a": _FakeGraph(2000, 16000)}
-    per_job = serve.estimate_job_bytes(2000, 16000, 8, 1 << 20)
+    per_job = serve.estimate_job_bytes(2000, 16000, 8, 1000)
     reqs = [serve.Request(rid=i, graph="a", k=5, eps=0.1, delta=0.1, t=8, seed=i, m_cap=1 << 20) for i in range(7)]
-    srv = serve.Server(graphs, workers=1, hbm_budget_bytes=per_job)
+    srv = serve.Server(graphs, workers=1, hbm_budget_bytes=per_job, runner=fake_runner)
     res = srv.serve(reqs)
     assert [r.rid for r in res] == list(range(7))
     for r in res:
