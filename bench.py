@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-certified block of the round mode")
     ap.add_argument("--serial-round", action="store_true",
                     help="greedyCover and the AMCERA one after the other instead of side by side")
     ap.add_argument("--mode", default="round", choices=["round", "batch", "serve", "tsweep", "schedule"],
@@ -61,6 +62,9 @@ def parse():
     ap.add_argument("--sampler", type=int, default=0, help="0 bidirectional (default), 1 bit-parallel waves")
     ap.add_argument("--bidir-budget", type=float, default=0, help="bytes of bidirectional workspace (0: default)")
     ap.add_argument("--bidir-queue", type=int, default=0, help="nodes per ball / cone list (0: default)")
+    ap.add_argument("--bidir-warps", type=int, default=-1,
+                    help="1: warp searches handed to the CTA when they outgrow a warp; 0: whole-CTA searches; "
+                         "2: escalated searches in a second launch (-1: library default)")
     ap.add_argument("--bidir-table", type=int, default=-2,
                     help="node-table entries per CTA (-1: sized for L2, 0: none; -2: library default)")
     ap.add_argument("--space", type=int, default=0, help="hyper-edge space: 0 set betweenness, 1 kappa-path, 2 triangle")
@@ -238,6 +242,48 @@ def apply_sampler_args(P, graph, args):
         graph.set_param(P.PARAM_BIDIR_QUEUE, args.bidir_queue)
     if args.bidir_table != -2:
         graph.set_param(P.PARAM_BIDIR_TABLE, args.bidir_table)
+    if args.bidir_warps >= 0:
+        graph.set_param(P.PARAM_BIDIR_WARPS, args.bidir_warps)
+
+
+def time_to_certified(P, graph, g, wl, args):
+    """Algorithm 1 to certification on the resident graph (cen_run) under the doubling and the
+    predicting schedule, and the same through the public API with host buffers: the graph
+    uploaded from pinned host memory inside the timed region and the results read back."""
+    import torch
+    plans = (("doubling", P.SCHEDULE_DOUBLING), ("predicting", P.SCHEDULE_EXTRAPOLATE))
+    P.run(graph, wl.k, 0.1, wl.delta, wl.t, 999, m0=1000)  # warm-up (workspaces, pools)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    t_begin = time.perf_counter()
+    out = {"workload": args.workload, "k": wl.k, "eps": wl.eps, "delta": wl.delta, "t": wl.t, "m0": 1000,
+           "seed": wl.seed, "how": "host wall clock around cen_run (device synchronized on both sides)"}
+    for name, sched in plans:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = P.run(graph, wl.k, wl.eps, wl.delta, wl.t, wl.seed, m0=1000, schedule=sched, alpha=1.2)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        out[name] = {"seconds": el, "status": "certified" if r["status"] == P.OK else "not certified",
+                     "m_final": r["m_final"], "rounds": r["rounds"], "covered": r["covered"],
+                     "C": float(r["log"][-1][6]) if r["rounds"] else None}
+    off_h = torch.from_numpy(g.off).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    e2e = {"h2d_bytes": int(g.off.nbytes + g.col.nbytes)}
+    for name, sched in plans:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gg = P.Graph(g.n, off_h.numpy(), col_h.numpy(), g.directed)
+        apply_sampler_args(P, gg, args)
+        r = P.run(gg, wl.k, wl.eps, wl.delta, wl.t, wl.seed, m0=1000, schedule=sched, alpha=1.2)
+        gg.close()
+        torch.cuda.synchronize()
+        e2e[name] = {"seconds": time.perf_counter() - t0, "m_final": r["m_final"],
+                     "same_as_resident": r["m_final"] == out[name]["m_final"] and r["covered"] == out[name]["covered"]}
+    out["e2e_host_buffers"] = e2e
+    out["clocks"] = clocks.stop(t_begin, time.perf_counter())
+    return out
 
 
 def run_gpu(args, rank, world):
@@ -345,6 +391,9 @@ def run_gpu(args, rank, world):
                          "per-launch event times of concurrent wave pipelines include sharing the GPU"),
                 "aggregate_counted_GBps": counted / (total_ms / 1e3) / 1e9}
     launches = int(sum(v["launches"] for v in stats.values()))
+    ttc = None
+    if rank == 0 and not args.no_ttc and args.space == 0 and args.workload in ("rmat18", "ba2000"):
+        ttc = time_to_certified(P, graph, g, wl, args)
     out = {
         "metric": "sampled paths/s" if args.space == 0 else "sampled hyper-edges/s", "value": value,
         "unit": "paths/s" if args.space == 0 else "hyper-edges/s", "n_gpus": world, "steps": args.steps,
@@ -357,7 +406,7 @@ def run_gpu(args, rank, world):
                    "parallelism": f"replicas x{world}",
                    "round": ("greedyCover then AMCERA (two calls)" if args.serial_round
                              else "greedyCover and AMCERA side by side (cen_cover_and_mcera)")},
-        "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+        "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof, "time_to_certified": ttc,
         "sampler": SAMPLER_INFO[-1] if SAMPLER_INFO else None,
         "wall_s": wall,
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "units": v["units"]}
@@ -388,10 +437,14 @@ def oracle_rate(wl, seconds: float, seed: int = 424242):
 
 
 def run_batch_mode(args):
-    """Time to certified eps of the batched workload: every job to certification,
-    one job at a time (the plain form) and batched (cen_run_batch), same results."""
+    """Time to certified eps of the batched workload, every job to certification:
+    the plain form (one job at a time, each sample searched by a whole CTA), the same
+    sequence with the library's default sampler settings, and the batched form
+    (cen_run_batch: jobs concurrently on worker streams, sampler settings autotuned
+    per graph beforehand, tuning timed apart); all three give identical results."""
     import torch
     import paper_2306_03651_gb300 as P
+    from paper_2306_03651_gb300 import tune
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     params = I.ba_batch_params(args.batch_jobs)
@@ -401,15 +454,27 @@ def run_batch_mode(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
+    for g in graphs:
+        g.set_param(P.PARAM_BIDIR_WARPS, 0)
     t0 = time.perf_counter()
     plain = P.run_batch(jobs, nworkers=1)
     t_plain = time.perf_counter() - t0
+    for g in graphs:
+        g.set_param(P.PARAM_BIDIR_WARPS, -1)
+    t0 = time.perf_counter()
+    plain_default = P.run_batch(jobs, nworkers=1)
+    t_plain_default = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tuned = [tune.autotune(g, t=32, probe_pairs=8192, grid=tune.SAMPLER_GRID)["best"] for g in graphs]
+    t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     batched = P.run_batch(jobs, nworkers=args.batch_workers)
     t_batch = time.perf_counter() - t0
     clk = clocks.stop()
-    same = all(a["S"].tolist() == b["S"].tolist() and a["m_final"] == b["m_final"] and a["covered"] == b["covered"]
-               for a, b in zip(plain, batched))
+
+    def same(a, b):
+        return all(x["S"].tolist() == y["S"].tolist() and x["m_final"] == y["m_final"] and x["covered"] == y["covered"]
+                   and np.array_equal(x["log"], y["log"]) for x, y in zip(a, b))
     samples = sum(r["m_final"] for r in batched)
     print(json.dumps({
         "metric": "time to certified eps (s)", "value": t_batch, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -417,9 +482,12 @@ def run_batch_mode(args):
         "config": {"workload": f"{args.batch_jobs} BA jobs, n log-uniform in [1e4, 5e5], 2-8 edges per node, "
                                f"k in {{10,50,100}}, eps=0.01, delta=0.1, t=32, m0=1000 doubling",
                    "batched_workers": args.batch_workers},
-        "plain_s": t_plain, "batched_s": t_batch, "speedup": t_plain / t_batch, "identical_results": same,
+        "plain_s": t_plain, "plain_default_s": t_plain_default, "batched_s": t_batch, "tuning_s": t_tune,
+        "speedup": t_plain / t_batch, "speedup_vs_plain_default": t_plain_default / t_batch,
+        "identical_results": same(plain, batched) and same(plain_default, batched),
         "certified": sum(1 for r in batched if r["status"] == P.OK), "samples_total": samples,
-        "paths_per_s_batched": samples / t_batch, "clocks": clk,
+        "paths_per_s_batched": samples / t_batch, "paths_per_s_plain": samples / t_plain,
+        "tuned_warp_searches": sum(1 for c in tuned if c["bidir_warps"] == 1), "clocks": clk,
     }))
 
 

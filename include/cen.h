@@ -156,6 +156,46 @@ int cen_mcera(cen_job *job, int32_t k, int64_t *Rnum_out, int64_t *Wnum_out, int
 int cen_cover_and_mcera(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered,
                         int64_t *Rnum_out, int64_t *Wnum_out, int32_t *b_out);
 
+/* ---- one sample split over several GPUs (shards) ----
+ * Samples are functions of (seed, sample id) (Sec. 5 sampleHEs; Alg. 1
+ * sampleRadeVars), so a round's m_i samples can be drawn as disjoint id sets
+ * on several jobs, one per GPU, and the round's greedyCover and AMCERA
+ * assembled from per-shard counts that add up (Sec. 3.1 coverage gains,
+ * Sec. 4.1 R_q^u and c_u are sums over samples).  The exchange (summing the
+ * shards' device vectors) is the caller's: a collective library, or host code
+ * for shards in one process.  All calls are synchronous at return.
+ *
+ * cen_job_set_ids: store position p of the job holds sample id
+ * p * stride + offset (stride >= 1; before the first cen_sample, else
+ * CEN_EINVAL).  Rank r of N uses (N, r): together the N jobs hold ids 0 .. m-1
+ * when job r holds ceil((m - r) / N) samples.  (1, 0) is the default. */
+int cen_job_set_ids(cen_job *job, uint64_t stride, uint64_t offset);
+/* greedyCover one pick at a time (Sec. 3.1).  cen_shard_greedy_begin: after the
+ * round's cen_sample, sets this shard's gains to its c_u and clears its covered
+ * bits.  cen_shard_gains: copies the n gains (int32) into the caller's device
+ * buffer `gains`.  cen_shard_pick: the pick over a device gain vector [n] (the
+ * shards' sum): *u = the largest gain, lowest id on ties, *gain = that gain (0:
+ * nothing left to cover, *u = -1 when every gain is 0).  cen_shard_apply: covers
+ * this shard's still-uncovered samples holding u and lowers their members'
+ * gains; *newly_covered = how many (the shards' counts add up to the pick's
+ * summed gain).  Gains and apply before a begin that follows the last
+ * cen_sample give CEN_EINVAL. */
+int cen_shard_greedy_begin(cen_job *job);
+int cen_shard_gains(const cen_job *job, int32_t *gains);
+int cen_shard_pick(cen_job *job, const int32_t *gains, int32_t *u, int32_t *gain);
+int cen_shard_apply(cen_job *job, int32_t u, uint64_t *newly_covered);
+/* AMCERA of a split sample (Sec. 4.1, Alg. 1 r_j^u line): cen_shard_rade writes
+ * this shard's R_q^u over its own samples into rows 0 .. t-1 and c_u into row
+ * t of the caller's device matrix R [t+1][n] (int32, row-major), and its b_H
+ * (max |h| over its samples, 0 without samples) to *b.  Summed over the shards,
+ * R and c are the whole sample's; b_H is the maximum.  cen_shard_topk: out[r] =
+ * the sum of the <= k largest positive entries of row r of a device matrix
+ * vals [nrows][n] (n of the job's graph): over the summed matrix, rows 0 .. t-1
+ * give Rnum and row t gives Wnum, as cen_mcera does for one job.  nrows >= 1,
+ * k >= 1, else CEN_EINVAL. */
+int cen_shard_rade(cen_job *job, int32_t *R, int32_t *b);
+int cen_shard_topk(cen_job *job, const int32_t *vals, int32_t nrows, int32_t k, int64_t *out);
+
 /* Host FP64 bounds of Thm. 4.4 (Eq. 2, ln(5/delta_i)) and the
  * stopping test of Alg. 1 at iteration i >= 1 (delta_i = delta / 2^i).
  * out[8] = C, AMCERA, w, nu, xi, R~, R, eta.  *stop = 1 iff
@@ -301,8 +341,9 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
                                     1: bit-parallel waves only.  Hyper-edges are identical. */
 #define CEN_PARAM_BIDIR_BUDGET 6 /* device bytes for the bidirectional sampler's per-CTA workspace,
                                     >= 2^20 (default 2^34); fewer CTAs run when it is small.  One CTA
-                                    needs 8 h + 16 H + 28 q bytes (q = min(n, queue), H = the power of
-                                    two >= 4 q, h = small-table entries), whatever the graph */
+                                    needs 8 h + 16 H + 28 q bytes, plus 32,800 with warp searches
+                                    (q = min(n, queue), H = the power of two >= max(4 q, 1024),
+                                    h = small-table entries), whatever the graph */
 #define CEN_PARAM_BIDIR_QUEUE 7  /* nodes one CTA may hold per ball or cone side, 16 .. 2^27 (default
                                     2^16, at most n); larger searches go to the bit-parallel sampler */
 #define CEN_PARAM_BIDIR_TABLE 8  /* entries of each CTA's small node table: a power of two in
@@ -312,6 +353,13 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
                                     fills half of it moves to the large table.  With -1, once a call
                                     of 1,024 or more samples sees most searches move, later jobs on
                                     the graph use no small table */
+#define CEN_PARAM_BIDIR_WARPS 9  /* 1: each warp of a CTA searches samples alone with a 1,024-entry
+                                    node table, and a second launch searches with whole CTAs those it
+                                    hands on (a level of more than 2,048 arcs to expand, more than 512
+                                    nodes, or more than 64 levels a side); 0: every sample is searched
+                                    by a whole CTA; -1 (default): 1 until a call of 1,024 or more
+                                    samples hands more than 30% on, then 0 for later jobs on the
+                                    graph.  Queues of fewer than 1,024 nodes use CTA searches only */
 int cen_job_set_param(cen_job *job, int32_t param, double value);
 /* Releases the device memory the library keeps for reuse once jobs end: idle
  * bidirectional-sampler workspaces (up to four, each as large as
@@ -322,10 +370,12 @@ int cen_release_cached(void);
 /* How the job's samples were drawn so far: samples the bidirectional search
  * left whole to the bit-parallel sampler (*deferred_search), samples whose walk
  * it left to it (*deferred_walk), searches that outgrew the small node table
- * (*migrated), and the CTAs (slots) the bidirectional search runs on (0 before
- * its first use).  Any pointer may be NULL. */
+ * (*migrated), the CTAs (slots) the bidirectional search runs on (0 before
+ * its first use), and the warp searches handed on to whole CTAs because a
+ * level, the node count or the depth was too large for one warp (*escalated).
+ * Any pointer may be NULL. */
 int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, uint64_t *migrated,
-                         int32_t *slots);
+                         int32_t *slots, uint64_t *escalated);
 /* Defaults for jobs created later on this graph (cen_job_create, cen_run, cen_run_batch);
  * they take precedence over the environment (CEN_WAVE_WORDS, CEN_WAVE_STREAMS). */
 int cen_graph_set_param(cen_graph *g, int32_t param, double value);

@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "cen.h")
 
 OK, EINVAL, ENOMEM, ECUDA, EOVERFLOW, ENOTCERTIFIED = 0, -1, -2, -3, -4, -5
 PARAM_WAVE_WORDS, PARAM_WAVE_STREAMS, PARAM_PUSH_RATIO, PARAM_LEVEL_BUDGET = 1, 2, 3, 4
-PARAM_SAMPLER, PARAM_BIDIR_BUDGET, PARAM_BIDIR_QUEUE, PARAM_BIDIR_TABLE = 5, 6, 7, 8
+PARAM_SAMPLER, PARAM_BIDIR_BUDGET, PARAM_BIDIR_QUEUE, PARAM_BIDIR_TABLE, PARAM_BIDIR_WARPS = 5, 6, 7, 8, 9
 SAMPLER_BIDIR, SAMPLER_WAVES = 0, 1
 SCHEDULE_DOUBLING, SCHEDULE_PAPER, SCHEDULE_EXTRAPOLATE = 0, 1, 2
 RULE_CENTRA, RULE_HEDGE_P = 0, 1
@@ -97,7 +97,7 @@ def _load():
         "cen_job_copy_signs": ([vp, vp], ip),
         "cen_job_set_timing": ([vp, ip], ip),
         "cen_job_stats": ([vp, vp, vp], ip),
-        "cen_job_sampler_info": ([vp, vp, vp, vp, vp], ip),
+        "cen_job_sampler_info": ([vp, vp, vp, vp, vp, vp], ip),
         "cen_job_create_space": ([vp, u64, i32, i32, i32, vp, ctypes.POINTER(vp)], ip),
         "cen_release_cached": ([], ip),
         "cen_set_allocator": ([vp, vp, vp], ip),
@@ -107,6 +107,13 @@ def _load():
         "cen_job_set_param": ([vp, i32, dbl], ip),
         "cen_graph_set_param": ([vp, i32, dbl], ip),
         "cen_debug_fail_alloc": ([i64], ip),
+        "cen_job_set_ids": ([vp, u64, u64], ip),
+        "cen_shard_greedy_begin": ([vp], ip),
+        "cen_shard_gains": ([vp, vp], ip),
+        "cen_shard_pick": ([vp, vp, vp, vp], ip),
+        "cen_shard_apply": ([vp, i32, vp], ip),
+        "cen_shard_rade": ([vp, vp, vp], ip),
+        "cen_shard_topk": ([vp, vp, i32, i32, vp], ip),
     }
     for name, (args, res) in sigs.items():
         f = getattr(lib, name)
@@ -300,13 +307,49 @@ class Job:
     def set_param(self, param: int, value: float):
         _check(_lib.cen_job_set_param(self.h, int(param), float(value)), "cen_job_set_param")
 
+    # ---- one shard of a sample split over several GPUs (device buffers are torch CUDA tensors)
+    def set_ids(self, stride: int, offset: int):
+        """``cen_job_set_ids``: store position p holds sample id p * stride + offset."""
+        _check(_lib.cen_job_set_ids(self.h, int(stride), int(offset)), "cen_job_set_ids")
+
+    def shard_greedy_begin(self):
+        _check(_lib.cen_shard_greedy_begin(self.h), "cen_shard_greedy_begin")
+
+    def shard_gains(self, out):
+        """This shard's gains into the int32 device tensor `out` [n]."""
+        _check(_lib.cen_shard_gains(self.h, ctypes.c_void_p(out.data_ptr())), "cen_shard_gains")
+
+    def shard_pick(self, gains):
+        """(u, gain) of the summed gains `gains` (int32 device tensor [n]); u = -1 when all are 0."""
+        u, g = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.cen_shard_pick(self.h, ctypes.c_void_p(gains.data_ptr()), ctypes.byref(u), ctypes.byref(g)),
+               "cen_shard_pick")
+        return u.value, g.value
+
+    def shard_apply(self, u: int) -> int:
+        newly = ctypes.c_uint64()
+        _check(_lib.cen_shard_apply(self.h, int(u), ctypes.byref(newly)), "cen_shard_apply")
+        return newly.value
+
+    def shard_rade(self, out) -> int:
+        """R (rows 0 .. t-1) and c (row t) of this shard into the int32 device tensor `out` [t+1][n]; returns b_H."""
+        b = ctypes.c_int32()
+        _check(_lib.cen_shard_rade(self.h, ctypes.c_void_p(out.data_ptr()), ctypes.byref(b)), "cen_shard_rade")
+        return b.value
+
+    def shard_topk(self, vals, nrows: int, k: int) -> np.ndarray:
+        out = np.zeros(nrows, np.int64)
+        _check(_lib.cen_shard_topk(self.h, ctypes.c_void_p(vals.data_ptr()), int(nrows), int(k), _p(out)),
+               "cen_shard_topk")
+        return out
+
     def tune(self, wave_words=None, wave_streams=None, push_ratio=None, level_budget=None, sampler=None,
-             bidir_budget=None, bidir_queue=None, bidir_table=None):
+             bidir_budget=None, bidir_queue=None, bidir_table=None, bidir_warps=None):
         """Speed and memory parameters (the samples do not depend on them)."""
         for p, v in ((PARAM_WAVE_WORDS, wave_words), (PARAM_WAVE_STREAMS, wave_streams),
                      (PARAM_PUSH_RATIO, push_ratio), (PARAM_LEVEL_BUDGET, level_budget), (PARAM_SAMPLER, sampler),
                      (PARAM_BIDIR_BUDGET, bidir_budget), (PARAM_BIDIR_QUEUE, bidir_queue),
-                     (PARAM_BIDIR_TABLE, bidir_table)):
+                     (PARAM_BIDIR_TABLE, bidir_table), (PARAM_BIDIR_WARPS, bidir_warps)):
             if v is not None:
                 self.set_param(p, v)
 
@@ -317,11 +360,12 @@ class Job:
         _check(_lib.cen_job_reset_stats(self.h), "cen_job_reset_stats")
 
     def sampler_info(self) -> dict:
-        """``cen_job_sampler_info``: deferred_search, deferred_walk, migrated, slots."""
-        a, b, m, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32()
-        _check(_lib.cen_job_sampler_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m), ctypes.byref(c)),
-               "cen_job_sampler_info")
-        return dict(deferred_search=a.value, deferred_walk=b.value, migrated=m.value, slots=c.value)
+        """``cen_job_sampler_info``: deferred_search, deferred_walk, migrated, slots, escalated."""
+        a, b, m, c, e = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int32(), ctypes.c_uint64()
+        _check(_lib.cen_job_sampler_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m), ctypes.byref(c),
+                                         ctypes.byref(e)), "cen_job_sampler_info")
+        return dict(deferred_search=a.value, deferred_walk=b.value, migrated=m.value, slots=c.value,
+                    escalated=e.value)
 
     def stats(self) -> dict:
         arr = (cen_kstat * NKCLASS)()

@@ -223,6 +223,44 @@ void cover_and_mcera(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint6
   mcera_result(job, k, h + gb, Rnum, Wnum, b);
 }
 
+// ----------------------------------------------- AMCERA of a split sample
+// A shard's R (rows 0 .. t-1) and c (row t) over its own samples, into a
+// caller's device matrix, and its b_H; the caller sums the shards' matrices
+// (R and c are sums over samples) and takes shard_topk of the sum.
+void shard_rade(cen_job *job, int32_t *R_out, int32_t *b) {
+  build_incidence(job);
+  mcera_prepare(job, 1);
+  cudaStream_t st = job->st;
+  const int32_t n = job->g->n;
+  const int t = job->t;
+  CEN_CK(cudaMemsetAsync(job->R.p, 0, 4 * (size_t)n * t, st));
+  launch(&job->stats, K_RADE, st, [&] {
+    k_rade<<<grid_for((size_t)n * 32, 256, sm_count() * 64), 256, 0, st>>>(
+        n, t, job->nw, job->noff.as<int64_t>(), job->nsamp.as<int32_t>(), job->sign.as<uint32_t>(),
+        job->R.as<int32_t>(), (unsigned long long *)(job->stats.d_units + K_RADE));
+  });
+  CEN_CK(cudaMemcpyAsync(job->R.as<int32_t>() + (size_t)n * t, job->c.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  CEN_CK(cudaMemcpyAsync(R_out, job->R.p, 4 * (size_t)n * (t + 1), cudaMemcpyDeviceToDevice, st));
+  int32_t *h = (int32_t *)host_staging(job, 4);
+  *h = 0;
+  if (job->m) CEN_CK(cudaMemcpyAsync(h, job->bmax.p, 4, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  *b = job->m ? *h : 0;
+}
+
+// Sums of the <= k largest positive entries of each of nrows rows of length n
+// (the job's graph's n) of a device matrix, with the job's select workspace.
+void shard_topk(cen_job *job, const int32_t *vals, int32_t nrows, int32_t k, int64_t *out) {
+  CEN_REQUIRE(nrows >= 1 && k >= 1, CEN_EINVAL, "cen_shard_topk: need nrows >= 1 and k >= 1");
+  cudaStream_t st = job->st;
+  job->selst.ensure(sizeof(SelRow) * (size_t)nrows, st);
+  job->selh.ensure((size_t)nrows * 256 * (4 + 8), st);
+  SelRow *h = (SelRow *)host_staging(job, sizeof(SelRow) * (size_t)nrows);
+  topk_enqueue(job, vals, job->g->n, nrows, k, st, h);
+  CEN_CK(cudaStreamSynchronize(st));
+  for (int r = 0; r < nrows; ++r) out[r] = h[r].sum;
+}
+
 void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b) {
   CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_mcera: k must be >= 1");
   Range range("cen_mcera");

@@ -208,6 +208,11 @@ static void apply_param(cen_job *job, int32_t param, double value) {
       job->bidir_table = h;
       break;
     }
+    case CEN_PARAM_BIDIR_WARPS:
+      CEN_REQUIRE(value == -1 || value == 0 || value == 1, CEN_EINVAL,
+                  "cen_job_set_param: warp searches must be -1, 0 or 1");
+      job->bidir_warps = (int)value;
+      break;
     case CEN_PARAM_BIDIR_QUEUE:
       CEN_REQUIRE(value >= 16 && value <= (double)(1 << 27), CEN_EINVAL,
                   "cen_job_set_param: bidirectional queue must be in [16, 2^27]");
@@ -356,7 +361,7 @@ int cen_job_create_space(const cen_graph *g, uint64_t seed, int32_t t, int32_t s
     const int w = atoi(e);
     if (w >= 1 && w <= 8) job->wave_streams = w;
   }
-  for (int p = 1; p <= 8; ++p)  // the graph's tuned defaults override the environment
+  for (int p = 1; p <= 9; ++p)  // the graph's tuned defaults override the environment
     if (g->param_set[p]) apply_param(job, p, g->param[p]);
   try {
     job->stats.init(job->st);
@@ -633,21 +638,73 @@ int cen_release_cached(void) {
   CEN_API_END
 }
 
+int cen_job_set_ids(cen_job *job, uint64_t stride, uint64_t offset) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && stride >= 1, CEN_EINVAL, "cen_job_set_ids: null job or stride 0");
+  CEN_REQUIRE(job->m == 0, CEN_EINVAL, "cen_job_set_ids: the job already holds samples");
+  job->id_stride = stride;
+  job->id_offset = offset;
+  CEN_API_END
+}
+
+int cen_shard_greedy_begin(cen_job *job) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job, CEN_EINVAL, "cen_shard_greedy_begin: null job");
+  cen::shard_greedy_begin(job);
+  CEN_API_END
+}
+
+int cen_shard_gains(const cen_job *job, int32_t *gains) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && gains, CEN_EINVAL, "cen_shard_gains: null argument");
+  cen::shard_gains(job, gains);
+  CEN_API_END
+}
+
+int cen_shard_pick(cen_job *job, const int32_t *gains, int32_t *u, int32_t *gain) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && gains && u && gain, CEN_EINVAL, "cen_shard_pick: null argument");
+  cen::shard_pick(job, gains, u, gain);
+  CEN_API_END
+}
+
+int cen_shard_apply(cen_job *job, int32_t u, uint64_t *newly_covered) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && newly_covered, CEN_EINVAL, "cen_shard_apply: null argument");
+  cen::shard_apply(job, u, newly_covered);
+  CEN_API_END
+}
+
+int cen_shard_rade(cen_job *job, int32_t *R, int32_t *b) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && R && b, CEN_EINVAL, "cen_shard_rade: null argument");
+  cen::shard_rade(job, R, b);
+  CEN_API_END
+}
+
+int cen_shard_topk(cen_job *job, const int32_t *vals, int32_t nrows, int32_t k, int64_t *out) {
+  CEN_API_BEGIN
+  CEN_REQUIRE(job && vals && out, CEN_EINVAL, "cen_shard_topk: null argument");
+  cen::shard_topk(job, vals, nrows, k, out);
+  CEN_API_END
+}
+
 int cen_job_sampler_info(const cen_job *job, uint64_t *deferred_search, uint64_t *deferred_walk, uint64_t *migrated,
-                         int32_t *slots) {
+                         int32_t *slots, uint64_t *escalated) {
   CEN_API_BEGIN
   CEN_REQUIRE(job, CEN_EINVAL, "cen_job_sampler_info: null job");
   if (deferred_search) *deferred_search = job->bidir_deferred_search;
   if (deferred_walk) *deferred_walk = job->bidir_deferred_walk;
   if (migrated) *migrated = job->bidir_migrated;
   if (slots) *slots = job->bws ? job->bws->nslots : 0;
+  if (escalated) *escalated = job->bidir_escalated;
   CEN_API_END
 }
 
 int cen_graph_set_param(cen_graph *g, int32_t param, double value) {
   CEN_API_BEGIN
   CEN_REQUIRE(g, CEN_EINVAL, "cen_graph_set_param: null graph");
-  CEN_REQUIRE(param >= 1 && param <= 8, CEN_EINVAL, "cen_graph_set_param: unknown parameter");
+  CEN_REQUIRE(param >= 1 && param <= 9, CEN_EINVAL, "cen_graph_set_param: unknown parameter");
   cen_job probe;  // validates the value with the job rules
   apply_param(&probe, param, value);
   g->param[param] = value;

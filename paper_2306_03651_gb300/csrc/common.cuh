@@ -145,6 +145,15 @@ __device__ __forceinline__ uint4 philox_block(uint64_t seed, uint64_t j, uint32_
                 make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
+// A job's Philox key and its map from store positions to sample ids:
+// position p holds sample id p * stride + offset (stride 1 and offset 0 unless
+// the job holds one shard of a sample split over several GPUs).  Every draw of
+// a sample is keyed by its id, so a sample does not depend on where it is stored.
+struct SampleKey {
+  uint64_t seed, stride, offset;
+  __host__ __device__ __forceinline__ uint64_t id(uint64_t p) const { return p * stride + offset; }
+};
+
 typedef unsigned __int128 u128;
 
 // Uniform integer in [0, B), 1 <= B <= 2^64 - 1: bitmask rejection with
@@ -307,11 +316,14 @@ struct cen_graph {
   cudaStream_t st = nullptr;
   cen::DevBuf off, col, roff, rcol;  // roff/rcol empty when undirected (alias off/col)
   cen::ChunkTable out_chunks, in_chunks_own;  // in_chunks_own used only when directed
-  double param[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // tuning defaults for jobs on this graph
-  bool param_set[9] = {};                           // which of them were set
+  double param[10] = {};   // tuning defaults for jobs on this graph, by CEN_PARAM_* id
+  bool param_set[10] = {};  // which of them were set
   // Set once most bidirectional searches on this graph outgrew their node
   // table: later jobs (without an explicit table size) use the large table only.
   mutable std::atomic<bool> bidir_table_off{false};
+  // Set once a call handed more than 30% of its warp searches on to CTAs:
+  // later jobs (without an explicit setting) search with whole CTAs only.
+  mutable std::atomic<bool> bidir_warps_off{false};
   // Triangle ranks (triangle space): exclusive prefix of per-arc counts, built once.
   std::mutex tri_mu;
   cen::DevBuf tri_off;

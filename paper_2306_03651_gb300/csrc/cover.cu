@@ -237,6 +237,95 @@ void greedy_result(const void *h, int32_t *S, int32_t *S_size, uint64_t *covered
   for (int i = 0; i < hc->size; ++i) S[i] = hc->S[i];
 }
 
+// ------------------------------------------- greedyCover one pick at a time
+// For a sample split over several GPUs (shards): every shard keeps its own
+// gains and covered bits; the caller sums the shards' gains, takes the pick
+// (shard_pick, the same key as k_greedy_all: largest gain, lowest id) and
+// applies it to every shard.  A shard's newly covered samples are exactly its
+// part of the pick's summed gain.
+
+// Warp per incident sample of u, as k_greedy_update; counts the samples it
+// newly covers.
+__global__ void __launch_bounds__(256) k_shard_apply(const int64_t *__restrict__ noff,
+                                                     const int32_t *__restrict__ nsamp,
+                                                     const int64_t *__restrict__ hoff,
+                                                     const int32_t *__restrict__ hmem, int32_t *gain,
+                                                     uint32_t *covered, int32_t u, unsigned long long *newly) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t r0 = noff[u], r1 = noff[u + 1];
+  unsigned long long mine = 0;
+  for (int64_t q = r0 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); q < r1; q += nwarps) {
+    const int32_t j = nsamp[q];
+    const uint32_t mask = 1u << (j & 31);
+    if (covered[j >> 5] & mask) continue;  // j occurs once in row u: only this warp can set its bit now
+    if (lane == 0) {
+      atomicOr(&covered[j >> 5], mask);
+      ++mine;
+    }
+    for (int64_t e = hoff[j] + lane; e < hoff[j + 1]; e += 32) atomicSub(&gain[hmem[e]], 1);
+  }
+  if (lane == 0 && mine) atomicAdd(newly, mine);
+}
+
+void shard_greedy_begin(cen_job *job) {
+  build_incidence(job);
+  greedy_prepare(job, 1);
+  cudaStream_t st = job->st;
+  const int32_t n = job->g->n;
+  CEN_CK(cudaMemsetAsync(job->covered.p, 0, 4 * ((job->m + 31) / 32 + 1), st));
+  launch(&job->stats, K_GREEDY, st,
+         [&] { k_gain_init<<<grid_for(n, 256), 256, 0, st>>>(job->c.as<int32_t>(), job->gain.as<int32_t>(), n); });
+  CEN_CK(cudaStreamSynchronize(st));
+  job->shard_greedy_m = (int64_t)job->m;
+}
+
+static void require_shard_greedy(const cen_job *job, const char *what) {
+  CEN_REQUIRE(job->shard_greedy_m == (int64_t)job->m, CEN_EINVAL,
+              std::string(what) + ": call cen_shard_greedy_begin after the last cen_sample");
+}
+
+void shard_gains(const cen_job *job, int32_t *dst) {
+  require_shard_greedy(job, "cen_shard_gains");
+  CEN_CK(cudaMemcpyAsync(dst, job->gain.p, 4 * (size_t)job->g->n, cudaMemcpyDeviceToDevice, job->st));
+  CEN_CK(cudaStreamSynchronize(job->st));
+}
+
+void shard_pick(cen_job *job, const int32_t *gains, int32_t *u, int32_t *gain) {
+  cudaStream_t st = job->st;
+  const int32_t n = job->g->n;
+  job->gctl.ensure(greedy_result_bytes(1), st);
+  GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
+  CEN_CK(cudaMemsetAsync(ctl, 0, sizeof(GreedyCtl), st));
+  launch(&job->stats, K_GREEDY, st, [&] {
+    k_greedy_argmax<<<grid_for((size_t)n, 256, sm_count() * 4), 256, 0, st>>>(gains, n, ctl, 0);
+  });
+  unsigned long long *h = (unsigned long long *)host_staging(job, 8);
+  CEN_CK(cudaMemcpyAsync(h, &ctl->key[0], 8, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  const unsigned long long key = *h;
+  *gain = (int32_t)(uint32_t)(key >> 32);
+  *u = key ? (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu)) : -1;
+}
+
+void shard_apply(cen_job *job, int32_t u, uint64_t *newly) {
+  require_shard_greedy(job, "cen_shard_apply");
+  CEN_REQUIRE(u >= 0 && u < job->g->n, CEN_EINVAL, "cen_shard_apply: node out of range");
+  cudaStream_t st = job->st;
+  GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
+  CEN_CK(cudaMemsetAsync(&ctl->covered, 0, 8, st));
+  launch(&job->stats, K_GREEDY, st, [&] {
+    k_shard_apply<<<sm_count() * 4, 256, 0, st>>>(job->noff.as<int64_t>(), job->nsamp.as<int32_t>(),
+                                                  job->hoff.as<int64_t>(), job->hmem.as<int32_t>(),
+                                                  job->gain.as<int32_t>(), job->covered.as<uint32_t>(), u,
+                                                  &ctl->covered);
+  });
+  unsigned long long *h = (unsigned long long *)host_staging(job, 8);
+  CEN_CK(cudaMemcpyAsync(h, &ctl->covered, 8, cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  *newly = *h;
+}
+
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered) {
   CEN_REQUIRE(k >= 1, CEN_EINVAL, "cen_greedy_cover: k must be >= 1");
   Range range("cen_greedy_cover");

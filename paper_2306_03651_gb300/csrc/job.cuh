@@ -60,21 +60,26 @@ struct BiCtl {
   unsigned long long nsearch;  // samples left whole to the bit-parallel sampler
   unsigned long long nwalk;    // samples whose walk is left to it (distance known)
   unsigned long long nmigrate; // searches that outgrew the small table
+  unsigned long long nbig;     // warp searches handed on to the CTA launch
+  unsigned long long bignext;  // next of them for the CTA launch
   int err;
   int pad;
 };
 struct BiWS {
   DevBuf tab1, tab2, lists, sig, epochs, ctl, aoff, dsearch, dwalk, arena;
+  DevBuf tabw, epw;        // warp searches: node tables and epochs (none when WQ = 0)
+  DevBuf big;              // ids the warp searches hand on to the CTA searches
   int nslots = 0;
   int64_t QC = 0;
   int64_t H1 = 0;
   int64_t H2 = 0;
+  int64_t WQ = 0;          // entries of each list of a warp search; 0: CTA searches only
   int dev = -1;
 };
 // A finished job's workspace is kept for the next job of the same shape on the
 // same device (its state words stay valid under the persisting epochs, so it
 // is not cleared again); at most a few are kept.
-std::unique_ptr<BiWS> bidir_take(int dev, int64_t QC, int64_t H1, int slots);
+std::unique_ptr<BiWS> bidir_take(int dev, int64_t QC, int64_t H1, int slots, int64_t WQ);
 void bidir_give(std::unique_ptr<BiWS> w);
 void bidir_drop_cached();
 // Lets the current device's stream-ordered pool keep freed memory for reuse.
@@ -108,6 +113,10 @@ struct AuxStream {
 struct cen_job {
   const cen_graph *g = nullptr;
   uint64_t seed = 0;
+  // store position p holds sample id p * id_stride + id_offset (cen_job_set_ids)
+  uint64_t id_stride = 1, id_offset = 0;
+  int64_t shard_greedy_m = -1;  // m when cen_shard_greedy_begin last ran
+  cen::SampleKey key() const { return cen::SampleKey{seed, id_stride, id_offset}; }
   int32_t t = 0;
   int32_t nw = 0;  // sign words per sample = ceil(t / 32)
   cudaStream_t st = nullptr;
@@ -143,9 +152,11 @@ struct cen_job {
   size_t bidir_budget = (size_t)16 << 30;   // bytes of per-slot workspace
   int64_t bidir_queue = (int64_t)1 << 16;   // entries per ball / cone list
   int64_t bidir_table = -1;                 // small-table entries per CTA (-1: sized for L2, 0: none)
+  int bidir_warps = -1;  // 1: warp searches, what they hand on by CTAs; 0: CTAs only; -1: by the graph's record
   uint64_t bidir_deferred_search = 0;       // samples it left whole to the bit-parallel sampler
   uint64_t bidir_deferred_walk = 0;         // samples whose walk it left (distance known)
   uint64_t bidir_migrated = 0;              // searches that outgrew the small table
+  uint64_t bidir_escalated = 0;             // warp searches handed to their CTA
   // hyper-edge space (CEN_SPACE_*) and the kappa of the kappa-path space
   int32_t space = 0;
   int32_t kappa = 0;
@@ -155,6 +166,9 @@ struct cen_job {
 namespace cen {
 void sample_append(cen_job *job, uint64_t m_new);
 void bidir_launch(cen_job *job, uint64_t j0, uint64_t count, int64_t arena_cap);
+// Entries of each list of a warp search for a CTA queue of QC entries (0: warp searches off).
+int64_t bidir_warp_queue(int64_t QC);
+size_t bidir_warp_bytes_per_slot();
 void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out, const int64_t *hoff);
 int64_t triangle_index(cen_job *job);
 void triangle_sample(cen_job *job, uint64_t j0, uint64_t count);
@@ -163,6 +177,12 @@ int bidir_resident_slots();
 void build_incidence(cen_job *job);
 void greedy_cover(cen_job *job, int32_t k, int32_t *S, int32_t *S_size, uint64_t *covered);
 void mcera(cen_job *job, int32_t k, int64_t *Rnum, int64_t *Wnum, int32_t *b);
+void shard_greedy_begin(cen_job *job);
+void shard_gains(const cen_job *job, int32_t *dst);
+void shard_pick(cen_job *job, const int32_t *gains, int32_t *u, int32_t *gain);
+void shard_apply(cen_job *job, int32_t u, uint64_t *newly);
+void shard_rade(cen_job *job, int32_t *R_out, int32_t *b);
+void shard_topk(cen_job *job, const int32_t *vals, int32_t nrows, int32_t k, int64_t *out);
 size_t greedy_result_bytes(int32_t k);
 void greedy_prepare(cen_job *job, int32_t k);
 void greedy_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst);

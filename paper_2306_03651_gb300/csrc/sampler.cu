@@ -80,7 +80,7 @@ __device__ __forceinline__ void block_publish(uint64_t alive, unsigned long long
 }
 
 // --------------------------------------------------------------- init
-__global__ void k_wave_init(int count, uint64_t jbase, const uint64_t *__restrict__ jlist, int32_t n, uint64_t seed,
+__global__ void k_wave_init(int count, uint64_t jbase, const uint64_t *__restrict__ jlist, int32_t n, SampleKey key,
                             int G, int W, uint64_t *slot_j, int32_t *slot_s, int32_t *slot_t, int32_t *slot_d,
                             uint64_t *lev0, uint64_t *vis, const int64_t *__restrict__ off, Ctl *ctl) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < W; b += gridDim.x * blockDim.x) {
@@ -90,8 +90,8 @@ __global__ void k_wave_init(int count, uint64_t jbase, const uint64_t *__restric
     }
     const uint64_t j = jlist ? jlist[b] : jbase + (uint64_t)b;
     // Sec. 5: s uniform over V; t uniform over V \ {s} (Sec. 3.1 pairs u != v)
-    const int32_t s = (int32_t)uniform_below64(seed, j, kPurposeS, (uint64_t)n);
-    const int32_t tt = (int32_t)uniform_below64(seed, j, kPurposeT, (uint64_t)(n - 1));
+    const int32_t s = (int32_t)uniform_below64(key.seed, key.id(j), kPurposeS, (uint64_t)n);
+    const int32_t tt = (int32_t)uniform_below64(key.seed, key.id(j), kPurposeT, (uint64_t)(n - 1));
     const int32_t t = tt + (tt >= s);
     slot_j[b] = j;
     slot_s[b] = s;
@@ -782,7 +782,7 @@ __global__ void k_walk(int count, int G, SigIdx ix, const uint64_t *__restrict__
                        const int64_t *__restrict__ roff, const int32_t *__restrict__ rcol,
                        const uint64_t *const *__restrict__ levs, const T *__restrict__ sig,
                        const uint64_t *__restrict__ ovf, const int64_t *__restrict__ slot_off,
-                       const int64_t *__restrict__ hoff, int32_t *out, uint64_t seed, Ctl *ctl,
+                       const int64_t *__restrict__ hoff, int32_t *out, SampleKey key, Ctl *ctl,
                        unsigned long long *units) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -810,7 +810,7 @@ __global__ void k_walk(int count, int G, SigIdx ix, const uint64_t *__restrict__
     uint32_t step = 0;
     int L = d;
     while (L >= 2) {
-      const T r = draw_below(seed, j, kPurposeWalk0 + step, sv);
+      const T r = draw_below(key.seed, key.id(j), kPurposeWalk0 + step, sv);
       const uint64_t *lp = levs[L - 1];
       T cum = 0;
       int32_t pick = -1;
@@ -864,13 +864,13 @@ __global__ void k_walk(int count, int G, SigIdx ix, const uint64_t *__restrict__
 // --------------------------------------------------------------- sign words
 // Alg. 1 "sampleRadeVars", extended by the new columns j: word w of sample j
 // is word w%4 of Philox block (j, SIGN, w/4); bits >= t are cleared.
-__global__ void k_sign(uint64_t j0, uint64_t count, int t, int nw, uint64_t seed, uint32_t *sign) {
+__global__ void k_sign(uint64_t j0, uint64_t count, int t, int nw, SampleKey key, uint32_t *sign) {
   const int nblk = (nw + 3) / 4;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < count * nblk;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t j = j0 + idx / nblk;
     const int blk = (int)(idx % nblk);
-    const uint4 x = philox_block(seed, j, kPurposeSign, (uint32_t)blk);
+    const uint4 x = philox_block(key.seed, key.id(j), kPurposeSign, (uint32_t)blk);
     const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -993,7 +993,7 @@ struct Sampler {
     const int64_t *roff = g->in_off();
     const int32_t *rcol = g->in_col();
     launch(S, K_PAIRS, st, [&] {
-      k_wave_init<<<grid_for(W, 256), 256, 0, st>>>(count, jbase, jlist, n, job->seed, G, W, slot_j, slot_s, slot_t,
+      k_wave_init<<<grid_for(W, 256), 256, 0, st>>>(count, jbase, jlist, n, job->key(), G, W, slot_j, slot_s, slot_t,
                                                     slot_d, lev0, vis, off, ctl);
     });
     fetch_ctl_head();
@@ -1169,7 +1169,7 @@ struct Sampler {
     launch(S, K_WALK, st, [&] {
       k_walk<T><<<grid_for((size_t)count * 32, 256), 256, 0, st>>>(
           count, G, ix, slot_j, slot_t, slot_d, roff, rcol, ws().lev_ptrs.as<const uint64_t *>(), sig, ovf, slot_off,
-          job->hoff.as<int64_t>(), out, job->seed, ctl, units(K_WALK));
+          job->hoff.as<int64_t>(), out, job->key(), ctl, units(K_WALK));
     });
   }
 };
@@ -1291,7 +1291,11 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
   const int64_t QC = std::max<int64_t>(16, std::min<int64_t>(n, job->bidir_queue));
   int64_t H2 = 1024;
   while (H2 < 4 * QC) H2 *= 2;
-  auto per_slot = [&](int64_t h1) { return 8 * (size_t)h1 + 16 * (size_t)H2 + 7 * 4 * (size_t)QC; };
+  const bool warps = job->bidir_warps > 0 || (job->bidir_warps < 0 && !job->g->bidir_warps_off.load());
+  const int64_t WQ = warps ? bidir_warp_queue(QC) : 0;
+  auto per_slot = [&](int64_t h1) {
+    return 8 * (size_t)h1 + 16 * (size_t)H2 + 7 * 4 * (size_t)QC + (WQ ? bidir_warp_bytes_per_slot() : 0);
+  };
   const size_t res = (size_t)bidir_resident_slots();
   int slots = (int)std::min<size_t>(res, std::max<size_t>(1, job->bidir_budget / per_slot(0)));
   int64_t H1 = 0;
@@ -1305,12 +1309,12 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
   int dev = 0;
   CEN_CK(cudaGetDevice(&dev));
   BiWS *cur = job->bws.get();
-  if (!(cur && cur->QC == QC && cur->H1 == H1 && cur->nslots == slots && cur->dev == dev)) {
+  if (!(cur && cur->QC == QC && cur->H1 == H1 && cur->nslots == slots && cur->WQ == WQ && cur->dev == dev)) {
     if (cur && cur->nslots) {  // another shape: keep this one for later jobs, once idle
       CEN_CK(cudaStreamSynchronize(st));
       bidir_give(std::move(job->bws));
     }
-    job->bws = bidir_take(dev, QC, H1, slots);
+    job->bws = bidir_take(dev, QC, H1, slots, WQ);
     if (!job->bws) job->bws.reset(new BiWS());
   }
   BiWS &wk = *job->bws;
@@ -1324,17 +1328,38 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
     if (H1) CEN_CK(cudaMemsetAsync(wk.tab1.p, 0, 8 * (size_t)H1 * slots, st));
     CEN_CK(cudaMemsetAsync(wk.tab2.p, 0, 8 * (size_t)H2 * slots, st));
     CEN_CK(cudaMemsetAsync(wk.epochs.p, 0, 8 * (size_t)slots, st));
+    if (WQ) {
+      const size_t wb = bidir_warp_bytes_per_slot() * (size_t)slots;
+      const size_t eb = 8 * 4 * (size_t)slots;  // two epochs of each of the four warps
+      wk.tabw.ensure_exact(wb - eb, st);
+      wk.epw.ensure_exact(eb, st);
+      CEN_CK(cudaMemsetAsync(wk.tabw.p, 0, wb - eb, st));
+      CEN_CK(cudaMemsetAsync(wk.epw.p, 0, eb, st));
+    }
     wk.QC = QC;
+    wk.WQ = WQ;
     wk.H1 = H1;
     wk.H2 = H2;
     wk.nslots = slots;
     wk.dev = dev;
   }
-  for (DevBuf *b : {&wk.tab1, &wk.tab2, &wk.lists, &wk.sig, &wk.epochs}) b->st = st;
+  for (DevBuf *b : {&wk.tab1, &wk.tab2, &wk.lists, &wk.sig, &wk.epochs, &wk.tabw, &wk.epw}) b->st = st;
   wk.ctl.ensure(sizeof(BiCtl), st);
+  wk.big.ensure(8 * (size_t)m_new, st);
   wk.aoff.ensure(8 * (size_t)m_new, st);
   wk.dsearch.ensure(8 * (size_t)m_new, st);
   wk.dwalk.ensure(8 * (size_t)m_new, st);
+}
+
+// The control block of the last bidir_launch.
+static BiCtl bidir_finish(cen_job *job) {
+  BiWS &bw = *job->bws;
+  cudaStream_t st = job->st;
+  CEN_CK(cudaMemcpyAsync(host_staging(job, sizeof(BiCtl)), bw.ctl.p, sizeof(BiCtl), cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  const BiCtl h = *(const BiCtl *)host_staging(job, sizeof(BiCtl));
+  CEN_REQUIRE(h.err == 0, h.err, "cen_sample: inconsistent path counts in the bidirectional walk");
+  return h;
 }
 
 // Bidirectional form: one CTA per sample writes its members to an arena;
@@ -1348,24 +1373,20 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   int64_t cap = (int64_t)((double)m_new * std::max(8.0, 2.0 * mean)) + ((int64_t)1 << 20);
   bw.arena.ensure(4 * (size_t)cap, st);
   bidir_launch(job, m0, m_new, cap);
-  BiCtl *hc = (BiCtl *)host_staging(job, sizeof(BiCtl));
-  CEN_CK(cudaMemcpyAsync(hc, bw.ctl.p, sizeof(BiCtl), cudaMemcpyDeviceToHost, st));
-  CEN_CK(cudaStreamSynchronize(st));
-  CEN_REQUIRE(hc->err == 0, hc->err, "cen_sample: inconsistent path counts in the bidirectional walk");
-  if ((int64_t)hc->cursor > cap) {
+  BiCtl h = bidir_finish(job);
+  if ((int64_t)h.cursor > cap) {
     // The arena was short (long paths in a job's first round, where no mean
     // is known yet): the cursor has counted every walk's members, so size the
     // arena to it and run the samples again (they are functions of their ids)
     // instead of leaving those walks to the bit-parallel sampler.
-    cap = (int64_t)hc->cursor + ((int64_t)1 << 20);
+    cap = (int64_t)h.cursor + ((int64_t)1 << 20);
     bw.arena.ensure(4 * (size_t)cap, st);
     bidir_launch(job, m0, m_new, cap);
-    CEN_CK(cudaMemcpyAsync(hc, bw.ctl.p, sizeof(BiCtl), cudaMemcpyDeviceToHost, st));
-    CEN_CK(cudaStreamSynchronize(st));
-    CEN_REQUIRE(hc->err == 0, hc->err, "cen_sample: inconsistent path counts in the bidirectional walk");
+    h = bidir_finish(job);
   }
-  const BiCtl h = *hc;
   if (job->bidir_table < 0 && m_new >= 1024 && 2 * h.nmigrate > m_new) job->g->bidir_table_off.store(true);
+  // warp searches pay off when few outgrow a warp; each one handed on is searched twice
+  if (job->bidir_warps < 0 && bw.WQ && m_new >= 1024 && 10 * h.nbig > 3 * m_new) job->g->bidir_warps_off.store(true);
   std::vector<uint64_t> search(h.nsearch), walk(h.nwalk);
   if (h.nsearch)
     CEN_CK(cudaMemcpyAsync(search.data(), bw.dsearch.p, 8 * h.nsearch, cudaMemcpyDeviceToHost, st));
@@ -1412,6 +1433,7 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   job->bidir_deferred_search += h.nsearch;
   job->bidir_deferred_walk += walk.size();
   job->bidir_migrated += h.nmigrate;
+  job->bidir_escalated += h.nbig;
   return total;
 }
 
@@ -1602,7 +1624,7 @@ void sample_append(cen_job *job, uint64_t m_new) {
   {
     const int nblk = (job->nw + 3) / 4;
     launch(&job->stats, K_SIGN, st, [&] {
-      k_sign<<<grid_for(m_new * nblk, 256), 256, 0, st>>>(m0, m_new, job->t, job->nw, job->seed,
+      k_sign<<<grid_for(m_new * nblk, 256), 256, 0, st>>>(m0, m_new, job->t, job->nw, job->key(),
                                                           job->sign.as<uint32_t>());
     });
   }

@@ -28,7 +28,7 @@ constexpr int kMaxKappa = 1024;
 // it, 32 arcs at a time, and takes the r-th of them.
 __global__ void __launch_bounds__(32 * kWalkWarps) k_kpath(uint64_t j0, uint64_t count, int32_t n, int kappa,
                                                            const int64_t *__restrict__ off,
-                                                           const int32_t *__restrict__ col, uint64_t seed,
+                                                           const int32_t *__restrict__ col, SampleKey key,
                                                            int32_t *ps, int32_t *pt, int32_t *pd, int32_t *out,
                                                            const int64_t *__restrict__ hoff, int *bmax,
                                                            unsigned long long *units) {
@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_kpath(uint64_t j0, uint64_t
   int mymax = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * kWalkWarps + wib; i < count; i += nw) {
     const uint64_t j = j0 + i;
-    const int32_t s = (int32_t)uniform_below64(seed, j, kPurposeS, (uint64_t)n);
-    const int32_t l = 1 + (int32_t)uniform_below64(seed, j, kPurposeT, (uint64_t)kappa);
+    const int32_t s = (int32_t)uniform_below64(key.seed, key.id(j), kPurposeS, (uint64_t)n);
+    const int32_t l = 1 + (int32_t)uniform_below64(key.seed, key.id(j), kPurposeT, (uint64_t)kappa);
     int32_t cur = s, len = 0;
     for (int32_t step = 0; step < l; ++step) {
       const int64_t e0 = off[cur], e1 = off[cur + 1];
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(32 * kWalkWarps) k_kpath(uint64_t j0, uint64_t
       }
       arcs += (unsigned long long)(e1 - e0);
       if (nfree == 0) break;
-      unsigned long long r = uniform_below64(seed, j, kPurposeWalk0 + (uint32_t)step, nfree);
+      unsigned long long r = uniform_below64(key.seed, key.id(j), kPurposeWalk0 + (uint32_t)step, nfree);
       int32_t next = -1;
       for (int64_t b = e0; b < e1 && next < 0; b += 32) {
         const int64_t e = b + lane;
@@ -166,12 +166,12 @@ __global__ void k_tri_count(int32_t n, const int64_t *__restrict__ off, const in
 // Thread per sample: rank r -> arc e (the last with tri_off[e] <= r) -> (u, v)
 // -> the common neighbour of rank r - tri_off[e].
 __global__ void k_tri_sample(uint64_t j0, uint64_t count, int32_t n, int64_t nnz, const int64_t *__restrict__ off,
-                             const int32_t *__restrict__ col, const int64_t *__restrict__ tri_off, uint64_t seed,
+                             const int32_t *__restrict__ col, const int64_t *__restrict__ tri_off, SampleKey key,
                              int32_t *ps, int32_t *pt, int32_t *pd, const int64_t *__restrict__ hoff, int32_t *hmem) {
   const uint64_t T = (uint64_t)tri_off[nnz];
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t j = j0 + i;
-    const int64_t r = (int64_t)uniform_below64(seed, j, kPurposeS, T);
+    const int64_t r = (int64_t)uniform_below64(key.seed, key.id(j), kPurposeS, T);
     int64_t lo = 0, hi = nnz + 1;  // upper bound of r in tri_off[0 .. nnz], minus one
     while (lo < hi) {
       const int64_t mid = lo + ((hi - lo) >> 1);
@@ -212,7 +212,7 @@ void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out, const
   const size_t smem = sizeof(int32_t) * (size_t)job->kappa * kWalkWarps;
   launch(&job->stats, K_SPACE, st, [&] {
     k_kpath<<<grid_for(count, kWalkWarps, sm_count() * 16), 32 * kWalkWarps, smem, st>>>(
-        j0, count, g->n, job->kappa, g->off.as<int64_t>(), g->col.as<int32_t>(), job->seed, job->ps.as<int32_t>(),
+        j0, count, g->n, job->kappa, g->off.as<int64_t>(), g->col.as<int32_t>(), job->key(), job->ps.as<int32_t>(),
         job->pt.as<int32_t>(), job->pd.as<int32_t>(), out, hoff, job->bmax.as<int>(),
         (unsigned long long *)(job->stats.d_units + K_SPACE));
   });
@@ -249,7 +249,7 @@ void triangle_sample(cen_job *job, uint64_t j0, uint64_t count) {
   cudaStream_t st = job->st;
   launch(&job->stats, K_SPACE, st, [&] {
     k_tri_sample<<<grid_for(count, 256), 256, 0, st>>>(j0, count, g->n, g->nnz, g->off.as<int64_t>(),
-                                                         g->col.as<int32_t>(), g->tri_off.as<int64_t>(), job->seed,
+                                                         g->col.as<int32_t>(), g->tri_off.as<int64_t>(), job->key(),
                                                          job->ps.as<int32_t>(), job->pt.as<int32_t>(),
                                                          job->pd.as<int32_t>(), job->hoff.as<int64_t>(),
                                                          job->hmem.as<int32_t>());

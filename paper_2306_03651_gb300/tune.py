@@ -1,7 +1,8 @@
 """Autotuner for the sampler's launch parameters.
 
 The sampler choice (bidirectional with the bit-parallel fallback, or
-bit-parallel waves only), the bidirectional sampler's node-table size, and
+bit-parallel waves only), the bidirectional sampler's node-table size and
+search granularity (warps, or whole CTAs), and
 the wave parameters (wave width, wave pipelines in flight, top-down/bottom-up
 switch) only change speed and memory: every configuration yields the same
 samples.  ``autotune`` times one probe round per
@@ -23,7 +24,9 @@ from . import cen as P
 DEFAULT_GRID = dict(sampler=(0, 1), bidir_table=(-1, 0, 8192), wave_streams=(1, 4))
 PARAM_IDS = {"wave_words": P.PARAM_WAVE_WORDS, "wave_streams": P.PARAM_WAVE_STREAMS, "push_ratio": P.PARAM_PUSH_RATIO,
              "level_budget": P.PARAM_LEVEL_BUDGET, "sampler": P.PARAM_SAMPLER, "bidir_budget": P.PARAM_BIDIR_BUDGET,
-             "bidir_queue": P.PARAM_BIDIR_QUEUE, "bidir_table": P.PARAM_BIDIR_TABLE}
+             "bidir_queue": P.PARAM_BIDIR_QUEUE, "bidir_table": P.PARAM_BIDIR_TABLE, "bidir_warps": P.PARAM_BIDIR_WARPS}
+# the bidirectional sampler's own choices, for tuning many graphs (the batched form)
+SAMPLER_GRID = dict(bidir_warps=(0, 1), bidir_table=(-1, 0))
 
 
 def _digest(h: dict) -> str:

@@ -7,9 +7,11 @@ range in spawned worker processes and merged; samples are functions of their ind
 At this size the select runs many blocks per row (multi-block histogram merge) and the
 cooperative greedy contends across all SMs.  The same store is checked with the
 bidirectional sampler forced through its other paths: the smallest node table (many
-searches move to the large table), no small table, and a short queue (searches handed
-to the bit-parallel sampler).  Epoch wrap: five CTAs draw 90,000 searches each on a
-small graph, so the 16-bit epochs of both node tables wrap and the tables are cleared.
+searches move to the large table), no small table, a short queue (searches handed
+to the bit-parallel sampler), and whole-CTA searches only, with and without the
+smallest node table.  Epoch wrap: a few CTAs draw more than
+65,535 searches per search group on a small graph, so the 16-bit epochs of the node
+tables wrap and the tables are cleared.
 """
 import math
 
@@ -47,6 +49,7 @@ def test_rmat18_whole_round_against_the_oracle(rmat18):
     job = P.Job(P.Graph.of(g), wl.seed, wl.t)
     job.sample(M18)
     store_equal(job.samples(), ref)
+    assert job.sampler_info()["escalated"] > 0
     oR, oc = ojob.rade_matrix()
     for k in (50, 100):
         S, cov, Rnum, Wnum, b = job.cover_and_mcera(k)
@@ -67,32 +70,34 @@ def test_rmat18_whole_round_against_the_oracle(rmat18):
     assert len(S) == 100 and cov > 0
 
 
-@pytest.mark.parametrize("table,queue", [(1024, 0), (0, 0), (0, 2048)])
-def test_rmat18_store_through_every_sampler_path(rmat18, table, queue):
+@pytest.mark.parametrize("table,queue,warps", [(1024, 0, 1), (0, 0, 1), (0, 2048, 1), (-1, 0, 0), (1024, 0, 0)])
+def test_rmat18_store_through_every_sampler_path(rmat18, table, queue, warps):
     wl, _, ref = rmat18
     job = P.Job(P.Graph.of(wl.graph), wl.seed, wl.t)
-    job.tune(bidir_table=table, bidir_queue=queue or None)
+    job.tune(bidir_table=table, bidir_queue=queue or None, bidir_warps=warps)
     job.sample(M18)
     store_equal(job.samples(), ref)
     info = job.sampler_info()
+    assert (info["escalated"] > 0) == (warps != 0)  # warp searches that outgrew a warp went to a CTA
     if table == 1024:
         assert info["migrated"] > 0  # searches that filled half of the small table moved to the large one
     if queue:
         assert info["deferred_search"] > 0  # balls beyond the queue went to the bit-parallel sampler
 
 
-@pytest.mark.parametrize("table", [0, 1024])
-def test_epoch_wrap_of_the_node_tables(table):
-    """Five CTAs (a 1 MiB workspace budget) draw 450,000 searches between them, so each
-    passes 65,535 searches and its table epoch wraps (table 0: the large table's epoch
-    advances per search; table 1024: the small table's)."""
+@pytest.mark.parametrize("table,warps,m", [(0, 0, 450_000), (1024, 0, 450_000), (1024, 1, 1_400_000)])
+def test_epoch_wrap_of_the_node_tables(table, warps, m):
+    """A 1 MiB workspace budget leaves four or five CTAs, whose search groups draw more
+    than 65,535 searches each, so their 16-bit table epochs wrap and the tables are
+    cleared: whole-CTA searches in the large table only (table 0) or in the small table
+    (table 1024), and warp searches in the warps' own tables (four groups per CTA)."""
     g = I.ba(2000, 4, 1)
-    m = 450_000
     job = P.Job(P.Graph.of(g), 3, 4)
-    job.tune(bidir_budget=1 << 20, bidir_queue=2000, bidir_table=table)
+    job.tune(bidir_budget=1 << 20, bidir_queue=2000, bidir_table=table, bidir_warps=warps)
     job.sample(m)
     info = job.sampler_info()
-    assert 1 <= info["slots"] <= 5 and m / info["slots"] > 1.3 * 65535
+    groups = info["slots"] * (4 if warps else 1)
+    assert 1 <= info["slots"] <= 5 and m / groups > 1.1 * 65535, info
     assert info["deferred_search"] == 0
     with shards.Pool(g) as pool:
         ref = pool.job(3, 4, m).hypergraph()

@@ -111,16 +111,38 @@ def test_bidirectional_node_table_and_direct_words(name, table):
     assert info["migrated"] == 0 if table == 0 else (name != "grid_rewired" or info["migrated"] > 0)
 
 
-def test_bidirectional_level_cap_deferral():
-    """A 5000-cycle: pairs far apart need more levels on one side than the per-side level
-    cap (255) and are searched by the bit-parallel sampler."""
+@pytest.mark.parametrize("warps", [0, 1])
+@pytest.mark.parametrize("name", ["ba2000", "rmat12_dir", "grid_rewired", "rmat12_lcc"])
+def test_bidirectional_warp_searches(name, warps):
+    """Samples searched by single warps, and by a second launch of whole CTAs when a level, the
+    node count or the depth is too large for a warp (1), or searched by whole CTAs only (0):
+    the oracle's samples either way, over two calls."""
+    g = GRAPHS[name]
+    _, _, ref = oracle_samples(g, 31, 2600)
+    job = P.Job(P.Graph.of(g), 31, 10)
+    job.set_param(P.PARAM_BIDIR_WARPS, warps)
+    job.sample(1300)
+    job.sample(1300)
+    assert_same_samples(job.samples(), ref)
+    if warps == 0:
+        assert job.sampler_info()["escalated"] == 0
+
+
+@pytest.mark.parametrize("warps", [0, 1])
+def test_bidirectional_level_cap_deferral(warps):
+    """A 5000-cycle: pairs far apart need more than a warp search's 64 levels on one side
+    (handed to the CTA) and more than a CTA search's level cap (255), and are searched by the
+    bit-parallel sampler."""
     n = 5000
     g = I.from_edges(n, np.arange(n), (np.arange(n) + 1) % n, False)
     _, _, ref = oracle_samples(g, 2, 300)
     job = P.Job(P.Graph.of(g), 2, 10)
+    job.set_param(P.PARAM_BIDIR_WARPS, warps)
     job.sample(300)
     assert_same_samples(job.samples(), ref)
-    assert job.sampler_info()["deferred_search"] > 0
+    info = job.sampler_info()
+    assert info["deferred_search"] > 0
+    assert info["escalated"] >= info["deferred_search"] if warps else info["escalated"] == 0
     assert ref["d"].max() > 2 * 255
 
 
