@@ -433,15 +433,32 @@ def oracle_rate(wl, seconds: float, seed: int = 424242):
     Rn, Wn, b = job.mcera(wl.k)
     O.bounds(cov, count, int(Rn.sum()), wl.t, Wn, b, wl.eps, wl.delta, 1)
     el = time.perf_counter() - t0
+    LAST_ORACLE_WORK[:] = [count, *job.work().tolist()]
     return count / el, count, el
+
+
+# the oracle's work tallies of the last oracle_rate sample: pairs, then nodes reached
+# before the target's level, arcs scanned out of them, in-arcs scanned by the walks,
+# path members written
+LAST_ORACLE_WORK: list = []
+
+
+def oracle_bytes_per_pair(work) -> float:
+    """Algorithmic bytes per pair of the forward search the oracle states (SURVEY-style
+    count): 16 per node reached before the target's level (distance and count), 16 per arc
+    scanned out of those levels (the arc, the head's distance check and count add), 16 per
+    in-arc the walk scans, 4 per member written."""
+    pairs, nodes, arcs, walk, members = work
+    return (16 * nodes + 16 * arcs + 16 * walk + 4 * members) / max(pairs, 1)
 
 
 def run_batch_mode(args):
     """Time to certified eps of the batched workload, every job to certification:
     the plain form (one job at a time, each sample searched by a whole CTA), the same
     sequence with the library's default sampler settings, and the batched form
-    (cen_run_batch: jobs concurrently on worker streams, sampler settings autotuned
-    per graph beforehand, tuning timed apart); all three give identical results."""
+    (cen_run_batch: jobs concurrently on worker streams) with the default settings and
+    with settings autotuned per graph beforehand (tuning timed apart); all four give
+    identical results."""
     import torch
     import paper_2306_03651_gb300 as P
     from paper_2306_03651_gb300 import tune
@@ -465,11 +482,14 @@ def run_batch_mode(args):
     plain_default = P.run_batch(jobs, nworkers=1)
     t_plain_default = time.perf_counter() - t0
     t0 = time.perf_counter()
+    batched = P.run_batch(jobs, nworkers=args.batch_workers)
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
     tuned = [tune.autotune(g, t=32, probe_pairs=8192, grid=tune.SAMPLER_GRID)["best"] for g in graphs]
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
-    batched = P.run_batch(jobs, nworkers=args.batch_workers)
-    t_batch = time.perf_counter() - t0
+    batched_tuned = P.run_batch(jobs, nworkers=args.batch_workers)
+    t_batch_tuned = time.perf_counter() - t0
     clk = clocks.stop()
 
     def same(a, b):
@@ -482,9 +502,10 @@ def run_batch_mode(args):
         "config": {"workload": f"{args.batch_jobs} BA jobs, n log-uniform in [1e4, 5e5], 2-8 edges per node, "
                                f"k in {{10,50,100}}, eps=0.01, delta=0.1, t=32, m0=1000 doubling",
                    "batched_workers": args.batch_workers},
-        "plain_s": t_plain, "plain_default_s": t_plain_default, "batched_s": t_batch, "tuning_s": t_tune,
+        "plain_s": t_plain, "plain_default_s": t_plain_default, "batched_s": t_batch,
+        "batched_tuned_s": t_batch_tuned, "tuning_s": t_tune,
         "speedup": t_plain / t_batch, "speedup_vs_plain_default": t_plain_default / t_batch,
-        "identical_results": same(plain, batched) and same(plain_default, batched),
+        "identical_results": same(plain, batched) and same(plain_default, batched) and same(batched_tuned, batched),
         "certified": sum(1 for r in batched if r["status"] == P.OK), "samples_total": samples,
         "paths_per_s_batched": samples / t_batch, "paths_per_s_plain": samples / t_plain,
         "tuned_warp_searches": sum(1 for c in tuned if c["bidir_warps"] == 1), "clocks": clk,
@@ -606,23 +627,31 @@ def run_serve_mode(args):
     reqs = [SV.Request(rid=i, graph=names[int(rng.integers(len(names)))], k=int(rng.integers(10, 201)),
                        eps=float(eps_list[int(rng.integers(len(eps_list)))]), delta=0.1, t=10, seed=5000 + i,
                        m_cap=1 << 27) for i in range(N)]
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
     srv = SV.Server(graphs, workers=args.serve_workers)
     res = srv.serve(reqs)
     cap = SV.summarize(res)
+    cap.update(peak_running=srv.peak_running, round_waits=srv.waits)
     rows = {"capacity": cap}
+    print(json.dumps({"pass": "capacity", **cap}), file=sys.stderr, flush=True)
     for frac in (0.5, 0.7, 0.9):
         arr = SV.poisson_arrivals(N, frac * cap["jobs_per_s"], seed=int(frac * 100))
         for r, a in zip(reqs, arr):
             r.arrival_s = a
-        res = SV.Server(graphs, workers=args.serve_workers).serve(reqs)
+        srv = SV.Server(graphs, workers=args.serve_workers)
+        res = srv.serve(reqs)
         rows[f"lambda_{frac}"] = SV.summarize(res)
+        rows[f"lambda_{frac}"].update(peak_running=srv.peak_running, round_waits=srv.waits)
+        print(json.dumps({"pass": f"lambda_{frac}", **rows[f"lambda_{frac}"]}), file=sys.stderr, flush=True)
+    clk = clocks.stop()
     print(json.dumps({
         "metric": "jobs/s", "value": rows["lambda_0.9"]["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1,
         "higher_is_better": True, "data": "synthetic",
         "config": {"workload": f"{N} requests, graphs {names}, k ~ U[10,200], eps in {eps_list}, delta=0.1, t=10",
                    "workers": args.serve_workers},
         "p50_latency_s": rows["lambda_0.9"]["p50_latency_s"], "p99_latency_s": rows["lambda_0.9"]["p99_latency_s"],
-        "runs": rows,
+        "runs": rows, "clocks": clk,
     }))
 
 
@@ -705,6 +734,16 @@ def main():
             r, c, e = oracle_rate(wl, args.cpu_seconds)
             out["cpu_baseline"] = {"value": r, "unit": "paths/s", "cores": 1, "kind": "oracle",
                                    "sample": f"{c} pairs of the same workload, one oracle round ({e:.1f} s)"}
+            roof = out.get("roofline")
+            if roof and roof.get("kernel") == "bidir" and roof.get("launches") == out["steps"] and args.space == 0:
+                # the oracle's count of a forward search's bytes, at the kernel's launch time
+                bpp = oracle_bytes_per_pair(LAST_ORACLE_WORK)
+                gbps = bpp * args.m / (roof["avg_launch_ms"] / 1e3) / 1e9
+                roof["oracle_basis"] = {"bytes_per_pair": bpp, "achieved": gbps, "frac": gbps / roof["peak"],
+                                        "pairs_sampled": LAST_ORACLE_WORK[0],
+                                        "note": "bytes a forward search needs per pair (counted by the oracle on "
+                                                "its sample) over the measured kernel time; the bidirectional "
+                                                "search scans fewer arcs, so this exceeds its own count"}
             procs = os.cpu_count() or 1
             if procs > 1:
                 cnt = max(procs, int(r * args.cpu_seconds / 2) * procs)

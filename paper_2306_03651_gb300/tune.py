@@ -6,7 +6,8 @@ search granularity (warps, or whole CTAs), and
 the wave parameters (wave width, wave pipelines in flight, top-down/bottom-up
 switch) only change speed and memory: every configuration yields the same
 samples.  ``autotune`` times one probe round per
-configuration on the caller's graph, checks that all configurations produced
+configuration on the caller's graph (after an untimed call that sizes that
+configuration's workspace), checks that all configurations produced
 identical hyper-edges, and stores the fastest as the graph's default
 (``cen_graph_set_param``) so that later jobs, ``run``, ``run_batch`` and the
 serving loop use it.
@@ -45,6 +46,10 @@ def autotune(graph: "P.Graph", t: int = 10, probe_pairs: int = 8192, seed: int =
     table, digests = [], set()
     for combo in itertools.product(*(grid[k] for k in keys)):
         cfg = dict(zip(keys, combo))
+        warm = P.Job(graph, seed + 1, t)  # untimed: sizes this configuration's workspace (kept for reuse)
+        warm.tune(**cfg)
+        warm.sample(min(probe_pairs, 2048))
+        warm.close()
         job = P.Job(graph, seed, t)
         job.tune(**cfg)
         torch.cuda.synchronize()
