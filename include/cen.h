@@ -296,6 +296,14 @@ typedef struct cen_job_result {
   double start_s, end_s;
 } cen_job_result;
 int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t nworkers, cen_job_result *results);
+/* One run of Algorithm 1 with its arguments and results in the two structs
+ * above: the same as cen_run_ex(spec->graph, spec->k, spec->eps, ..., &spec->opts,
+ * stream, out->S, &out->S_size, &out->covered, &out->m_final, &out->rounds,
+ * out->log, out->max_rounds), with out->status set to its return value and
+ * start_s / end_s to 0 and the run's seconds.  Caller-owned: out->S (capacity
+ * spec->k), out->log (optional).  Returns CEN_OK, CEN_ENOTCERTIFIED or an
+ * error (CEN_EINVAL for a null spec, out or out->S). */
+int cen_run_result(const cen_job_spec *spec, void *stream, cen_job_result *out);
 
 /* Allocation-free sum of the <= k largest positive entries of each row: the
  * per-vector sup that cen_mcera computes (Rnum), for callers that supply their

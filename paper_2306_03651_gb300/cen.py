@@ -104,6 +104,7 @@ def _load():
         "cen_job_reset_stats": ([vp], ip),
         "cen_topk_positive_sum_noalloc": ([vp, i64, i32, i32, vp, vp], ip),
         "cen_run_batch": ([vp, i32, i32, vp], ip),
+        "cen_run_result": ([vp, vp, vp], ip),
         "cen_job_set_param": ([vp, i32, dbl], ip),
         "cen_graph_set_param": ([vp, i32, dbl], ip),
         "cen_debug_fail_alloc": ([i64], ip),
@@ -474,3 +475,24 @@ def run_batch(jobs, nworkers: int = 8, max_rounds: int = 64) -> list[dict]:
                         rounds=r.rounds, log=log[: min(r.rounds, max_rounds)].copy(), start_s=r.start_s,
                         end_s=r.end_s))
     return out
+
+
+def run_result(job: dict, stream=None, max_rounds: int = 64) -> dict:
+    """``cen_run_result``: one run from a spec dict (as for ``run_batch``) into the result struct;
+    returns dict(status, S, covered, m_final, rounds, log, seconds)."""
+    g = job["graph"]
+    spec = cen_job_spec(g.h, job["k"], job["t"], job["eps"], job["delta"], job["seed"], job.get("m0", 1000),
+                        job.get("m_cap", 1 << 30),
+                        cen_run_opts(job.get("schedule", 0), job.get("rule", 0), job.get("alpha", 1.2),
+                                     job.get("space", 0), job.get("kappa", 0)))
+    S = np.empty(job["k"], np.int32)
+    log = np.zeros((max_rounds, 16), np.float64)
+    res = cen_job_result()
+    res.S = S.ctypes.data
+    res.log = log.ctypes.data
+    res.max_rounds = max_rounds
+    rc = _lib.cen_run_result(ctypes.byref(spec), stream if stream is not None else g.stream, ctypes.byref(res))
+    if rc not in (OK, ENOTCERTIFIED):
+        _check(rc, "cen_run_result")
+    return dict(status=rc, S=S[: res.S_size].copy(), covered=res.covered, m_final=res.m_final, rounds=res.rounds,
+                log=log[: min(res.rounds, max_rounds)].copy(), seconds=res.end_s)

@@ -16,6 +16,20 @@
 
 #include "job.cuh"
 
+extern "C" int cen_run_result(const cen_job_spec *spec, void *stream, cen_job_result *out) {
+  if (!spec || !out || !out->S) {
+    cen::set_last_error("cen_run_result: null spec, result or S buffer");
+    return CEN_EINVAL;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  out->start_s = 0.0;
+  out->status = cen_run_ex(spec->graph, spec->k, spec->eps, spec->delta, spec->t, spec->seed, spec->m0, spec->m_cap,
+                           &spec->opts, stream, out->S, &out->S_size, &out->covered, &out->m_final, &out->rounds,
+                           out->log, out->log ? out->max_rounds : 0);
+  out->end_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return out->status;
+}
+
 extern "C" int cen_run_batch(const cen_job_spec *specs, int32_t njobs, int32_t nworkers, cen_job_result *results) {
   try {
     CEN_REQUIRE(specs && results && njobs >= 0 && nworkers >= 1, CEN_EINVAL, "cen_run_batch: bad arguments");

@@ -171,10 +171,9 @@ struct BiSh {
   // arc-balanced scan (warp searches only, W = 1): first arc of each row of a
   // chunk and the total, the rows' nodes and their first arcs in the CSR
   static constexpr int kBal = W == 1 ? 32 : 1;
-  int bpre[kBal + 1];
+  long long bpre[kBal + 1];
   int bv[kBal];
   long long be0[kBal];
-  int bwt[W];
   unsigned long long sum, sum2, arcs;
   int added, nheavy, ccount[2], ncross;
   int hcount, hfull;  // small-table entries of this search; set once it is half full
@@ -345,49 +344,39 @@ __device__ void bi_scan_rows(const uint32_t *list, int cnt, const int64_t *__res
   gsync<T>();
 }
 
-// As bi_scan_rows, with the arcs of the rows of at most kBiHeavy arcs dealt
-// evenly to the group: the rows are taken T at a time, a scan of their
-// lengths gives each row's first arc within the chunk, and thread i takes
-// arcs i, i + T, ... of the chunk, finding each arc's row by binary search,
-// so that no lane waits on a long row of its subgroup.  Longer rows are
-// queued in `heavy` and scanned by the whole group.  Called by the whole group.
+// As bi_scan_rows for a warp search, with every row's arcs dealt evenly to
+// the warp's lanes: the rows are taken 32 at a time, a scan of their lengths
+// gives each row's first arc within the chunk, and lane i takes arcs i,
+// i + 32, ... of the chunk, finding each arc's row by binary search, so that
+// no lane waits on a long row of its subgroup and a long row needs no pass of
+// its own.  Called by the whole warp.
 template <int T, class SH, class F>
 __device__ void bi_scan_rows_bal(const uint32_t *list, int cnt, const int64_t *__restrict__ o,
-                                 const int32_t *__restrict__ c, uint32_t *heavy, SH &sh, F &&f) {
-  const int tid = gtid<T>(), lane = tid & 31;
-  if (tid == 0) sh.nheavy = 0;
-  gsync<T>();
+                                 const int32_t *__restrict__ c, SH &sh, F &&f) {
+  static_assert(T == 32, "the even deal is the warp searches' scan");
+  const int lane = gtid<T>();
   unsigned long long arcs = 0;
   for (int c0 = 0; c0 < cnt; c0 += T) {
-    int v = 0, len = 0;
-    long long e0 = 0;
-    if (c0 + tid < cnt) {
-      v = (int)list[c0 + tid];
+    int v = 0;
+    long long e0 = 0, len = 0;
+    if (c0 + lane < cnt) {
+      v = (int)list[c0 + lane];
       e0 = o[v];
-      const long long e1 = o[v + 1];
-      if (e1 - e0 > kBiHeavy)
-        heavy[atomicAdd(&sh.nheavy, 1)] = (uint32_t)v;
-      else
-        len = (int)(e1 - e0);
+      len = o[v + 1] - e0;
     }
     arcs += (unsigned long long)len;
-    int x = len;  // inclusive scan of the lengths within the warp
+    long long x = len;  // inclusive scan of the lengths
     for (int d = 1; d < 32; d <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      const long long y = __shfl_up_sync(0xffffffffu, x, d);
       if (lane >= d) x += y;
     }
-    if (T > 32) {
-      if (lane == 31) sh.bwt[tid >> 5] = x;
-      gsync<T>();
-      for (int w = 0; w < (tid >> 5); ++w) x += sh.bwt[w];
-    }
-    sh.bpre[tid] = x - len;
-    sh.bv[tid] = v;
-    sh.be0[tid] = e0;
-    if (tid == T - 1) sh.bpre[T] = x;
-    gsync<T>();
-    const int total = sh.bpre[T];
-    for (int a = tid; a < total; a += T) {
+    sh.bpre[lane] = x - len;
+    sh.bv[lane] = v;
+    sh.be0[lane] = e0;
+    if (lane == T - 1) sh.bpre[T] = x;
+    __syncwarp();
+    const long long total = sh.bpre[T];
+    for (long long a = lane; a < total; a += T) {
       int lo = 0, hi = T - 1;  // the last row starting at or before arc a
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -398,17 +387,23 @@ __device__ void bi_scan_rows_bal(const uint32_t *list, int cnt, const int64_t *_
       }
       f(sh.bv[lo], c[sh.be0[lo] + (a - sh.bpre[lo])]);
     }
-    gsync<T>();  // the next chunk overwrites the shared rows
-  }
-  const int nh = sh.nheavy;
-  for (int h = 0; h < nh; ++h) {
-    const int v = (int)heavy[h];
-    const int64_t e0 = o[v], e1 = o[v + 1];
-    for (int64_t e = e0 + tid; e < e1; e += T) f(v, c[e]);
-    if (tid == 0) arcs += (unsigned long long)(e1 - e0);
+    __syncwarp();  // the next chunk overwrites the shared rows
   }
   if (arcs) atomicAdd(&sh.arcs, arcs);
-  gsync<T>();
+  __syncwarp();
+}
+
+// The row scan of a search group: a warp deals every row's arcs evenly to its
+// lanes (measured faster for warps, 1.1-1.35x on BA graphs); a CTA gives rows
+// to lane groups of gs and long rows to the whole CTA (the even deal was no
+// faster for CTAs).
+template <int T, class SH, class F>
+__device__ __forceinline__ void bi_scan(const uint32_t *list, int cnt, const int64_t *__restrict__ o,
+                                        const int32_t *__restrict__ c, int gs, uint32_t *heavy, SH &sh, F &&f) {
+  if constexpr (T == 32)
+    bi_scan_rows_bal<T>(list, cnt, o, c, sh, f);
+  else
+    bi_scan_rows<T>(list, cnt, o, c, gs, heavy, sh, f);
 }
 
 __device__ __forceinline__ void add_carry(unsigned long long &acc, unsigned long long v, int &ovf) {
@@ -677,12 +672,7 @@ __device__ __forceinline__ int bi_search(const BiArgs &A, BiSh<LV, T / 32> &sh, 
         }
       }
     };
-    // a warp deals the level's arcs evenly to its lanes; a CTA gives rows to lane groups
-    // (measured: the even deal pays for warps, 1.1-1.35x on BA graphs, and not for CTAs)
-    if constexpr (kWarp)
-      bi_scan_rows_bal<T>(qx + f0, f1 - f0, o, c, heavy, sh, visit);
-    else
-      bi_scan_rows<T>(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, visit);
+    bi_scan<T>(qx + f0, f1 - f0, o, c, bi_group(fcost, f1 - f0), heavy, sh, visit);
     if (sh.met) {
       if (tid == 0) sh.d = sh.lvl[0] + sh.lvl[1] + 1;
       break;
@@ -783,7 +773,7 @@ __device__ __forceinline__ int bi_search(const BiArgs &A, BiSh<LV, T / 32> &sh, 
       gsync<T>();
     } else {
       const int f0 = sh.lo[0][ls], f1 = sh.lo[0][ls + 1];
-      bi_scan_rows<T>(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][ls], f1 - f0), heavy, sh,
+      bi_scan<T>(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][ls], f1 - f0), heavy, sh,
                       [&](int v, int w) {
                         const uint64_t sw = bi_find(M, w);
                         if (sw && st_side(sw) == 1 && st_level(sw) == lb) {
@@ -805,13 +795,13 @@ __device__ __forceinline__ int bi_search(const BiArgs &A, BiSh<LV, T / 32> &sh, 
       const int a = sh.cs[0][L], b = sh.ce[0][L];
       const unsigned long long in_cone = bi_row_sum<T>(cl[0] + a, b - a, A.roff, sh);
       if (in_cone <= sh.hcost[0][L - 1]) {
-        bi_scan_rows<T>(cl[0] + a, b - a, A.roff, A.rcol, 8, heavy, sh, [&](int, int u) {
+        bi_scan<T>(cl[0] + a, b - a, A.roff, A.rcol, 8, heavy, sh, [&](int, int u) {
           const uint64_t su = bi_find(M, u);
           if (su && st_side(su) == 0 && st_level(su) == L - 1) bi_mark(M, sg, cl[0], 0, QC, sh, u);
         });
       } else {
         const int f0 = sh.lo[0][L - 1], f1 = sh.lo[0][L];
-        bi_scan_rows<T>(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][L - 1], f1 - f0), heavy, sh,
+        bi_scan<T>(q[0] + f0, f1 - f0, A.off, A.col, bi_group(sh.hcost[0][L - 1], f1 - f0), heavy, sh,
                         [&](int u, int w) {
                           const uint64_t sw = bi_find(M, w);
                           if (sw && st_cone(sw) && st_side(sw) == 0 && st_level(sw) == L)
@@ -830,13 +820,13 @@ __device__ __forceinline__ int bi_search(const BiArgs &A, BiSh<LV, T / 32> &sh, 
       const int a = sh.cs[1][L], b = sh.ce[1][L];
       const unsigned long long out_cone = bi_row_sum<T>(cl[1] + a, b - a, A.off, sh);
       if (out_cone <= sh.hcost[1][L - 1]) {
-        bi_scan_rows<T>(cl[1] + a, b - a, A.off, A.col, 8, heavy, sh, [&](int, int y) {
+        bi_scan<T>(cl[1] + a, b - a, A.off, A.col, 8, heavy, sh, [&](int, int y) {
           const uint64_t sy = bi_find(M, y);
           if (sy && st_side(sy) == 1 && st_level(sy) == L - 1) bi_mark(M, sg, cl[1], 1, QC, sh, y);
         });
       } else {
         const int f0 = sh.lo[1][L - 1], f1 = sh.lo[1][L];
-        bi_scan_rows<T>(q[1] + f0, f1 - f0, A.roff, A.rcol, bi_group(sh.hcost[1][L - 1], f1 - f0), heavy, sh,
+        bi_scan<T>(q[1] + f0, f1 - f0, A.roff, A.rcol, bi_group(sh.hcost[1][L - 1], f1 - f0), heavy, sh,
                         [&](int y, int xv) {
                           const uint64_t sx = bi_find(M, xv);
                           if (sx && st_cone(sx) && st_side(sx) == 1 && st_level(sx) == L)
@@ -894,7 +884,7 @@ __device__ __forceinline__ int bi_search(const BiArgs &A, BiSh<LV, T / 32> &sh, 
       if (pull <= push) {
         bi_sigma_pull<T>(cur, ncur, D, d, M, sg, A.roff, A.rcol, 8, heavy, sh);
       } else {
-        bi_scan_rows<T>(prev, nprev, A.off, A.col, bi_group(push, nprev), heavy, sh, [&](int u, int w) {
+        bi_scan<T>(prev, nprev, A.off, A.col, bi_group(push, nprev), heavy, sh, [&](int u, int w) {
           int64_t iw = 0;
           const uint64_t sw = bi_find(M, w, iw);
           if (sw && st_cone(sw) && st_dist(sw, d) == D) {

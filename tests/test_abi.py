@@ -102,3 +102,21 @@ def test_new_entry_points_check_arguments_before_any_device_work():
     # an allocator needs both functions; restoring the default needs none
     assert P.cen_set_allocator(ctypes.cast(P._ALLOC_FN(lambda n, s, c: None), ctypes.c_void_p), None, None) == P.EINVAL
     assert P.cen_set_allocator(None, None, None) == P.OK
+
+
+def test_shard_and_result_entry_points_check_arguments_before_any_device_work():
+    out = np.zeros(4, np.int64)
+    u, g, b = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    newly = ctypes.c_uint64()
+    assert P.cen_job_set_ids(None, 2, 0) == P.EINVAL
+    assert P.cen_shard_greedy_begin(None) == P.EINVAL
+    assert P.cen_shard_gains(None, None) == P.EINVAL
+    assert P.cen_shard_pick(None, None, ctypes.byref(u), ctypes.byref(g)) == P.EINVAL
+    assert P.cen_shard_apply(None, 0, ctypes.byref(newly)) == P.EINVAL
+    assert P.cen_shard_rade(None, None, ctypes.byref(b)) == P.EINVAL
+    assert P.cen_shard_topk(None, None, 2, 3, out.ctypes.data) == P.EINVAL
+    res = P.cen_job_result()
+    assert P.cen_run_result(None, None, ctypes.byref(res)) == P.EINVAL
+    spec = P.cen_job_spec()
+    assert P.cen_run_result(ctypes.byref(spec), None, ctypes.byref(res)) == P.EINVAL  # no S buffer
+    assert "null" in P.last_error()

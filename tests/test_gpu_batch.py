@@ -36,3 +36,11 @@ def test_batch_equals_individual_runs():
 def test_batch_rejects_bad_arguments():
     with pytest.raises(P.CenError):
         P.run_batch([], nworkers=0)
+
+
+def test_run_result_struct_equals_run():
+    for j in specs()[:3]:
+        r = P.run_result(j)
+        a = P.run(j["graph"], j["k"], j["eps"], j["delta"], j["t"], j["seed"], m0=j["m0"])
+        same(a, r)
+        assert r["status"] == a["status"] and r["seconds"] > 0
