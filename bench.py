@@ -736,14 +736,14 @@ def main():
                                    "sample": f"{c} pairs of the same workload, one oracle round ({e:.1f} s)"}
             roof = out.get("roofline")
             if roof and roof.get("kernel") == "bidir" and roof.get("launches") == out["steps"] and args.space == 0:
-                # the oracle's count of a forward search's bytes, at the kernel's launch time
+                # the oracle's count of a forward search's bytes against the kernel's own count
                 bpp = oracle_bytes_per_pair(LAST_ORACLE_WORK)
-                gbps = bpp * args.m / (roof["avg_launch_ms"] / 1e3) / 1e9
-                roof["oracle_basis"] = {"bytes_per_pair": bpp, "achieved": gbps, "frac": gbps / roof["peak"],
-                                        "pairs_sampled": LAST_ORACLE_WORK[0],
-                                        "note": "bytes a forward search needs per pair (counted by the oracle on "
-                                                "its sample) over the measured kernel time; the bidirectional "
-                                                "search scans fewer arcs, so this exceeds its own count"}
+                counted = roof["algorithmic_bytes_per_launch"] / args.m
+                roof["oracle_basis"] = {"forward_bytes_per_pair": bpp, "counted_bytes_per_pair": counted,
+                                        "work_ratio": bpp / counted, "pairs_sampled": LAST_ORACLE_WORK[0],
+                                        "note": "bytes a forward search to d(s,t) needs per pair (the oracle's "
+                                                "tallies on its sample) against the bytes the bidirectional "
+                                                "kernel counts per pair; the roofline uses the kernel's count"}
             procs = os.cpu_count() or 1
             if procs > 1:
                 cnt = max(procs, int(r * args.cpu_seconds / 2) * procs)
