@@ -1103,7 +1103,9 @@ int64_t bidir_warp_queue(int64_t QC) {
   return wq >= 256 ? wq : 0;
 }
 
-size_t bidir_warp_bytes_per_slot() { return (size_t)kBiWarps * (8 * (size_t)kWarpTable + 8); }
+size_t bidir_warp_table_bytes_per_slot() { return (size_t)kBiWarps * 8 * (size_t)kWarpTable; }
+size_t bidir_warp_epoch_bytes_per_slot() { return (size_t)kBiWarps * 8; }  // two u32 epochs per warp
+size_t bidir_warp_bytes_per_slot() { return bidir_warp_table_bytes_per_slot() + bidir_warp_epoch_bytes_per_slot(); }
 
 namespace {
 constexpr size_t kBiCacheMax = 4;

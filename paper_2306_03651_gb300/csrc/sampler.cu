@@ -1329,11 +1329,11 @@ void bidir_setup(cen_job *job, uint64_t m_new) {
     CEN_CK(cudaMemsetAsync(wk.tab2.p, 0, 8 * (size_t)H2 * slots, st));
     CEN_CK(cudaMemsetAsync(wk.epochs.p, 0, 8 * (size_t)slots, st));
     if (WQ) {
-      const size_t wb = bidir_warp_bytes_per_slot() * (size_t)slots;
-      const size_t eb = 8 * 4 * (size_t)slots;  // two epochs of each of the four warps
-      wk.tabw.ensure_exact(wb - eb, st);
+      const size_t tb = bidir_warp_table_bytes_per_slot() * (size_t)slots;
+      const size_t eb = bidir_warp_epoch_bytes_per_slot() * (size_t)slots;
+      wk.tabw.ensure_exact(tb, st);
       wk.epw.ensure_exact(eb, st);
-      CEN_CK(cudaMemsetAsync(wk.tabw.p, 0, wb - eb, st));
+      CEN_CK(cudaMemsetAsync(wk.tabw.p, 0, tb, st));
       CEN_CK(cudaMemsetAsync(wk.epw.p, 0, eb, st));
     }
     wk.QC = QC;
