@@ -485,7 +485,8 @@ def run_batch_mode(args):
     batched = P.run_batch(jobs, nworkers=args.batch_workers)
     t_batch = time.perf_counter() - t0
     t0 = time.perf_counter()
-    tuned = [tune.autotune(g, t=32, probe_pairs=8192, grid=tune.SAMPLER_GRID)["best"] for g in graphs]
+    # probes of a full round: smaller ones time one wave of the warp kernel, not its throughput
+    tuned = [tune.autotune(g, t=32, probe_pairs=65536, grid=tune.SAMPLER_GRID)["best"] for g in graphs]
     t_tune = time.perf_counter() - t0
     t0 = time.perf_counter()
     batched_tuned = P.run_batch(jobs, nworkers=args.batch_workers)

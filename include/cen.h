@@ -365,9 +365,11 @@ int cen_job_copy_signs(const cen_job *job, uint32_t *words);
                                     node table, and a second launch searches with whole CTAs those it
                                     hands on (a level of more than 2,048 arcs to expand, more than 512
                                     nodes, or more than 64 levels a side); 0: every sample is searched
-                                    by a whole CTA; -1 (default): 1 until a call of 1,024 or more
-                                    samples hands more than 30% on, then 0 for later jobs on the
-                                    graph.  Queues of fewer than 1,024 nodes use CTA searches only */
+                                    by a whole CTA; -1 (default): 0 on graphs whose degrees have
+                                    E[d^2]/E[d] > 256 (frontiers that soon outgrow a warp), else 1
+                                    until a call of 1,024 or more samples hands more than 30% on,
+                                    then 0 for later jobs on the graph.  Queues of fewer than 1,024
+                                    nodes use CTA searches only */
 int cen_job_set_param(cen_job *job, int32_t param, double value);
 /* Releases the device memory the library keeps for reuse once jobs end: idle
  * bidirectional-sampler workspaces (up to four, each as large as

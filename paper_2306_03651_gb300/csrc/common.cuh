@@ -324,6 +324,10 @@ struct cen_graph {
   // Set once a call handed more than 30% of its warp searches on to CTAs:
   // later jobs (without an explicit setting) search with whole CTAs only.
   mutable std::atomic<bool> bidir_warps_off{false};
+  // E[d^2] / E[d] over the out- and in-degrees (the larger): how many arcs a
+  // frontier node's neighbour has on average; computed once, on first use.
+  mutable std::mutex branching_mu;
+  mutable double branching = -1.0;
   // Triangle ranks (triangle space): exclusive prefix of per-arc counts, built once.
   std::mutex tri_mu;
   cen::DevBuf tri_off;

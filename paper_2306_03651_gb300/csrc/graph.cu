@@ -187,6 +187,40 @@ void graph_canonicalize(cen_graph *g, const int64_t *off, const int32_t *col, in
   g->nnz = kept;
 }
 
+// Sums of d and d^2 over the rows of off (one pass, double sums).
+__global__ void k_degree_moments(const int64_t *__restrict__ off, int32_t n, double *sums) {
+  double a = 0.0, b = 0.0;
+  for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const double d = (double)(off[v + 1] - off[v]);
+    a += d;
+    b += d * d;
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+  }
+}
+
+double graph_branching(const cen_graph *g, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g->branching_mu);
+  if (g->branching >= 0.0) return g->branching;
+  DevBuf sums;
+  sums.ensure(4 * sizeof(double), st);
+  CEN_CK(cudaMemsetAsync(sums.p, 0, 4 * sizeof(double), st));
+  const int blocks = grid_for((size_t)g->n, 256, sm_count() * 4);
+  k_degree_moments<<<blocks, 256, 0, st>>>(g->off.as<int64_t>(), g->n, sums.as<double>());
+  if (g->directed) k_degree_moments<<<blocks, 256, 0, st>>>(g->in_off(), g->n, sums.as<double>() + 2);
+  CEN_CK(cudaGetLastError());
+  double h[4] = {0, 0, 0, 0};
+  CEN_CK(cudaMemcpyAsync(h, sums.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+  CEN_CK(cudaStreamSynchronize(st));
+  const double out = h[0] > 0 ? h[1] / h[0] : 0.0, in = h[2] > 0 ? h[3] / h[2] : 0.0;
+  g->branching = out > in ? out : in;
+  return g->branching;
+}
+
 void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_device, Stats *S) {
   cudaStream_t st = g->st;
   const int32_t n = g->n;

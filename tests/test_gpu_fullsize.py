@@ -49,7 +49,7 @@ def test_rmat18_whole_round_against_the_oracle(rmat18):
     job = P.Job(P.Graph.of(g), wl.seed, wl.t)
     job.sample(M18)
     store_equal(job.samples(), ref)
-    assert job.sampler_info()["escalated"] > 0
+    assert job.sampler_info()["escalated"] == 0  # by default a hub-heavy graph starts with whole-CTA searches
     oR, oc = ojob.rade_matrix()
     for k in (50, 100):
         S, cov, Rnum, Wnum, b = job.cover_and_mcera(k)
