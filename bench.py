@@ -156,9 +156,10 @@ class ClockSampler:
 DRAM_PROFILES = {"expand_pull": ("expand_pull_dram.md", "sampler.cu"), "bidir": ("bidir_dram.md", "bidir.cu")}
 
 
-def dram_traffic(kernel_class: str):
+def dram_traffic(kernel_class: str, workload: str, pairs_per_step: int):
     """DRAM bytes per launch of `kernel_class` from the committed ncu summary, or None when there
-    is none for the class or its source changed since the counters were taken."""
+    is none for the class, its source changed since the counters were taken, or the summary's
+    launch is another workload or step size (the traffic of a launch depends on both)."""
     import hashlib
     if kernel_class not in DRAM_PROFILES:
         return None
@@ -171,7 +172,8 @@ def dram_traffic(kernel_class: str):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if kv.get("kernel_class") == kernel_class and kv.get("source_sha256_16") == sha:
+        if (kv.get("kernel_class") == kernel_class and kv.get("source_sha256_16") == sha
+                and kv.get("workload") == workload and int(kv.get("pairs_per_step", -1)) == pairs_per_step):
             return float(kv["traffic_bytes_per_launch"])
     except (OSError, KeyError, ValueError):
         pass
@@ -210,13 +212,20 @@ def cover_and_mcera(job, k):
     return job.cover_and_mcera(k)
 
 
-def gpu_step(P, graph, wl, M, seed):
+def gpu_step(P, graph, wl, M, seed, events=None):
+    """One Algorithm-1 round on a new job: sample M pairs, greedyCover and the AMCERA, bounds.
+    `events` (start, end), when given, are recorded on the job's stream around the round alone:
+    the job's creation, its statistics and its release are not part of it."""
     job = P.Job(graph, seed, wl.t, space=SPACE["space"], kappa=SPACE["kappa"])
     job.set_timing(True)
+    if events:
+        events[0].record()
     job.sample(M)
-    SAMPLER_INFO.append(job.sampler_info())
     S, cov, Rnum, Wnum, b = cover_and_mcera(job, wl.k)
     stop, bd = P.bounds(cov, M, int(Rnum.sum()), wl.t, Wnum, b, wl.eps, wl.delta, 1)
+    if events:
+        events[1].record()
+    SAMPLER_INFO.append(job.sampler_info())
     st = job.stats()
     job.close()
     return st, (S, cov, Rnum, Wnum, b, stop, bd)
@@ -313,9 +322,7 @@ def run_gpu(args, rank, world):
     for s in range(args.steps):
         flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        st, _ = gpu_step(P, graph, wl, M, seed0 + 1000 + s)
-        b.record()
+        st, _ = gpu_step(P, graph, wl, M, seed0 + 1000 + s, (a, b))
         b.synchronize()
         times.append(a.elapsed_time(b))
         merge_stats(stats, st)
@@ -377,9 +384,11 @@ def run_gpu(args, rank, world):
         per_launch_bytes = stats[dom]["units"] / max(stats[dom]["launches"], 1)
         achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9 if dom in byte_classes else None
         counted = sum(stats[k]["units"] for k in byte_classes if k in stats)
-        traffic = dram_traffic(dom)
+        sampler_default = (not args.sampler and not args.bidir_budget and not args.bidir_queue
+                           and args.bidir_table == -2 and args.bidir_warps < 0)
+        traffic = dram_traffic(dom, args.workload, M) if sampler_default and args.space == 0 else None
         ratio = (f"DRAM traffic {traffic / per_launch_bytes:.2f}x the counted bytes, from an ncu DRAM capture"
-                 if traffic and per_launch_bytes else "DRAM traffic not profiled for this source")
+                 if traffic and per_launch_bytes else "DRAM traffic not profiled for this source and workload")
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else peak_src,
@@ -402,6 +411,7 @@ def run_gpu(args, rank, world):
         "config": {"workload": f"{args.workload}: {desc}; one Algorithm-1 round per step at m={M} pairs, "
                                f"k={wl.k}, t={wl.t}, eps={wl.eps}, delta={wl.delta}",
                    "n": g.n, "arcs": g.nnz, "pairs_per_step": M, "l2": "flushed (256 MB write) between steps",
+                   "timed": "the round (sample, greedyCover and AMCERA, bounds) on a job created just before it",
                    "space": ["set betweenness", f"kappa-path (kappa={args.kappa})", "triangle"][args.space],
                    "parallelism": f"replicas x{world}",
                    "round": ("greedyCover then AMCERA (two calls)" if args.serial_round

@@ -1259,8 +1259,9 @@ void rerun_in_place(cen_job *job, std::vector<uint64_t> ids) {
   }
 }
 
-// hoff of the new samples from their distances; returns their member total.
-int64_t offsets_from_distances(cen_job *job, uint64_t m0, uint64_t m_new) {
+// hoff of the new samples from their distances; returns their member total
+// (known_total, when the caller has counted it, saves reading it back).
+int64_t offsets_from_distances(cen_job *job, uint64_t m0, uint64_t m_new, int64_t known_total = -1) {
   cudaStream_t st = job->st;
   Stats *S = &job->stats;
   WaveWS &w0 = wave_ws0(job);
@@ -1274,6 +1275,7 @@ int64_t offsets_from_distances(cen_job *job, uint64_t m0, uint64_t m_new) {
   launch(S, K_APPEND, st, [&] {
     k_hoff_add<<<grid_for(m_new, 256), 256, 0, st>>>(job->hoff.as<int64_t>(), m0, m_new, w0.exoff.as<int64_t>());
   });
+  if (known_total >= 0) return known_total;  // the caller counted the members already
   int64_t *h = (int64_t *)host_staging(job, 8);
   CEN_CK(cudaMemcpyAsync(h, w0.exoff.as<int64_t>() + m_new, 8, cudaMemcpyDeviceToHost, st));
   CEN_CK(cudaStreamSynchronize(st));
@@ -1398,7 +1400,7 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
   if (h.nsearch)
     CEN_CK(cudaMemcpyAsync(search.data(), bw.dsearch.p, 8 * h.nsearch, cudaMemcpyDeviceToHost, st));
   if (h.nwalk) CEN_CK(cudaMemcpyAsync(walk.data(), bw.dwalk.p, 8 * h.nwalk, cudaMemcpyDeviceToHost, st));
-  CEN_CK(cudaStreamSynchronize(st));
+  if (h.nsearch || h.nwalk) CEN_CK(cudaStreamSynchronize(st));
   std::sort(search.begin(), search.end());
 
   // whole samples the CTAs could not search: bit-parallel, members into the arena
@@ -1427,7 +1429,10 @@ int64_t append_bidir(cen_job *job, uint64_t m0, uint64_t m_new) {
       q0 += (size_t)count;
     }
   }
-  const int64_t total = offsets_from_distances(job, m0, m_new);
+  // Without searches on the bit-parallel sampler, every sample with d >= 2
+  // reserved its d - 1 members in the arena (walked or deferred), so the
+  // cursor is the new members' total and the offsets need no read-back.
+  const int64_t total = offsets_from_distances(job, m0, m_new, search.empty() ? (int64_t)h.cursor : -1);
   job->hmem.ensure(4 * (size_t)(job->members + total + 1), st, 4 * (size_t)job->members);
   launch(&job->stats, K_APPEND, st, [&] {
     k_gather_arena<<<grid_for(m_new * 32, 256), 256, 0, st>>>(m_new, m0, bw.aoff.as<int64_t>(),

@@ -11,28 +11,32 @@ import bench
 from paper_2306_03651_gb300 import serve
 
 
-def test_dram_traffic_is_guarded_by_the_source_hash(tmp_path, monkeypatch):
+def test_dram_traffic_is_guarded_by_the_source_hash_and_workload(tmp_path, monkeypatch):
     src = tmp_path / "kernel.cu"
     src.write_text("// a kernel\n")
     sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
     prof_dir = tmp_path / "profiles"
     prof_dir.mkdir()
-    (prof_dir / "k_dram.md").write_text(f"# t\n\ntraffic_bytes_per_launch: 1234\nkernel_class: k\nsource_sha256_16: {sha}\n")
+    (prof_dir / "k_dram.md").write_text(f"# t\n\ntraffic_bytes_per_launch: 1234\nkernel_class: k\n"
+                                          f"workload: w\npairs_per_step: 64\nsource_sha256_16: {sha}\n")
     csrc = tmp_path / "paper_2306_03651_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (csrc / "kernel.cu").write_bytes(src.read_bytes())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "DRAM_PROFILES", {"k": ("k_dram.md", "kernel.cu")})
-    assert bench.dram_traffic("k") == 1234.0
-    assert bench.dram_traffic("other") is None
+    assert bench.dram_traffic("k", "w", 64) == 1234.0
+    assert bench.dram_traffic("other", "w", 64) is None
+    assert bench.dram_traffic("k", "w2", 64) is None  # another workload's launch
+    assert bench.dram_traffic("k", "w", 128) is None  # another step size
     (csrc / "kernel.cu").write_text("// changed\n")
-    assert bench.dram_traffic("k") is None
+    assert bench.dram_traffic("k", "w", 64) is None
 
 
 def test_committed_profiles_name_their_class_and_source():
     for cls, (prof, src) in bench.DRAM_PROFILES.items():
         text = open(os.path.join(bench.ROOT, "profiles", prof)).read()
         assert f"kernel_class: {cls}" in text and "source_sha256_16:" in text and "traffic_bytes_per_launch:" in text
+        assert "workload:" in text and "pairs_per_step:" in text
         assert os.path.exists(os.path.join(bench.ROOT, "paper_2306_03651_gb300", "csrc", src))
 
 

@@ -52,6 +52,8 @@ def oracle_samples(g, seed, m, t=10):
 
 
 def assert_same_samples(a, b):
+    for x in (a, b):  # the offsets end at the member total the job counted
+        assert x["hoff"][-1] == len(x["hmem"])
     for key in ("hoff", "s", "t", "d"):
         assert np.array_equal(a[key], b[key]), key
     assert np.array_equal(a["hmem"], b["hmem"])
@@ -193,6 +195,60 @@ def test_long_paths_in_the_first_round_fill_the_arena_without_deferral():
     job.sample(m2)
     assert job.sampler_info()["deferred_walk"] == 0
     assert_same_samples(job.samples(), ref)
+
+
+def hub_layers(directed: bool):
+    """Layers Z0 -> P -> M -> H -> Z2 and Z1 -> M: sources in Z0 or Z1 reach Z2 through one of
+    8 hubs H whose rows (about 1,040 arcs: 40 from M, 1,000 from Z2) are far longer than 8 times
+    the cone level of M they draw from (33 or more nodes), so the walk takes its step at a hub
+    over those cone nodes.  Directed: the hubs' long rows are in-rows (arcs Z2 -> H), and a
+    candidate's arc into the hub is found in its out-row."""
+    rng = np.random.default_rng(11)
+    nZ0, nZ1, nP, nM, nH, nZ2 = 600, 600, 40, 64, 8, 2000
+    Z0 = np.arange(nZ0)
+    Z1 = nZ0 + np.arange(nZ1)
+    Pl = nZ0 + nZ1 + np.arange(nP)
+    M = Pl[-1] + 1 + np.arange(nM)
+    H = M[-1] + 1 + np.arange(nH)
+    Z2 = H[-1] + 1 + np.arange(nZ2)
+    src, dst = [], []
+
+    def link(a, b, k):
+        for x in a:
+            for y in rng.choice(b, size=k, replace=False):
+                src.append(x)
+                dst.append(y)
+    link(Z0, Pl, 3)
+    link(Z1, M, 40)
+    link(Pl, M, 40)
+    link(M, H, 5)
+    for z in Z2:  # hub -> z for 4 hubs, and (directed) z -> 4 hubs
+        for h in rng.choice(H, size=4, replace=False):
+            src.append(h)
+            dst.append(z)
+        if directed:
+            for h in rng.choice(H, size=4, replace=False):
+                src.append(z)
+                dst.append(h)
+    n = int(Z2[-1]) + 1
+    return I.from_edges(n, np.array(src), np.array(dst), directed), int(Z1[-1]) + 1, int(Z2[0])
+
+
+@pytest.mark.parametrize("directed", [False, True])
+def test_walk_step_over_the_cone_nodes_at_a_hub(directed):
+    """Walk steps at hubs whose rows are much longer than the cone level they draw from: the
+    step looks up the cone nodes' arcs into the hub and picks by the running path count in
+    ascending id order, the oracle's pick for every sample."""
+    g, left_end, right_start = hub_layers(directed)
+    seed, m = 17, 4000
+    _, _, ref = oracle_samples(g, seed, m)
+    through_hub = np.sum((ref["s"] < left_end) & (ref["t"] >= right_start) & (ref["d"] >= 3))
+    assert through_hub > 300
+    for warps in (0, 1):
+        job = P.Job(P.Graph.of(g), seed, 10)
+        job.set_param(P.PARAM_BIDIR_WARPS, warps)
+        job.sample(m)
+        assert_same_samples(job.samples(), ref)
 
 
 def test_path_counts_beyond_64_bits():
