@@ -86,43 +86,66 @@ __global__ void __launch_bounds__(256) k_sel_hist(const int32_t *__restrict__ va
   }
 }
 
-// One thread per row: walk digits from the top, take whole buckets while
-// they fit in krem, descend into the bucket that crosses krem.
-__global__ void k_sel_step(int nrows, int shift, SelRow *rows, unsigned int *hcnt, unsigned long long *hsum) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+// One block of 256 threads per row, thread i on digit 255 - i: scans of the
+// bucket counts and sums from the top digit down give, for each digit, what
+// the buckets above it hold.  Whole buckets are taken while their running
+// count stays below krem; the first bucket whose running count reaches krem
+// is descended into (its digit joins the prefix).  If every matching value
+// fits in krem, all are taken.  Clears the row's buckets for the next digit.
+__global__ void __launch_bounds__(256) k_sel_step(int nrows, int shift, SelRow *rows, unsigned int *hcnt,
+                                                  unsigned long long *hsum) {
+  __shared__ long long wc[8], ws[8];
+  const int r = blockIdx.x, i = threadIdx.x, lane = i & 31, w = i >> 5;
   if (r >= nrows) return;
-  SelRow row = rows[r];
-  if (!row.done) {
-    long long total = 0;
-    for (int d = 0; d < 256; ++d) total += hcnt[r * 256 + d];
-    if (total <= row.krem) {  // every matching value is in
-      for (int d = 0; d < 256; ++d) row.sum += (long long)hsum[r * 256 + d];
-      row.krem = 0;
-      row.done = 1;
-    } else {
-      for (int d = 255; d >= 0; --d) {
-        const int c = (int)hcnt[r * 256 + d];
-        if (c < row.krem) {
-          row.krem -= c;
-          row.sum += (long long)hsum[r * 256 + d];
-        } else {
-          row.prefix |= (uint32_t)d << shift;
-          row.mask |= 255u << shift;
-          break;
-        }
-      }
-      if (shift == 0) {  // prefix is now the exact k-th value; krem copies of it remain
-        row.sum += (long long)row.krem * (long long)row.prefix;
-        row.krem = 0;
-        row.done = 1;
-      }
+  const SelRow row = rows[r];  // every thread reads it before thread 0 may rewrite it
+  if (row.done) return;        // the histogram pass skipped the row: its buckets are zero
+  const int d = 255 - i;
+  const long long c = (long long)hcnt[r * 256 + d];
+  const long long sv = (long long)hsum[r * 256 + d];
+  long long ci = c, si = sv;  // inclusive scans over digits 255 .. d
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long yc = __shfl_up_sync(0xffffffffu, ci, o), ys = __shfl_up_sync(0xffffffffu, si, o);
+    if (lane >= o) {
+      ci += yc;
+      si += ys;
     }
-    rows[r] = row;
   }
-  for (int d = 0; d < 256; ++d) {
-    hcnt[r * 256 + d] = 0;
-    hsum[r * 256 + d] = 0;
+  if (lane == 31) {
+    wc[w] = ci;
+    ws[w] = si;
   }
+  __syncthreads();
+  long long total = 0, stotal = 0;
+  for (int q = 0; q < 8; ++q) {
+    if (q < w) {
+      ci += wc[q];
+      si += ws[q];
+    }
+    total += wc[q];
+    stotal += ws[q];
+  }
+  hcnt[r * 256 + d] = 0;
+  hsum[r * 256 + d] = 0;
+  SelRow out = row;
+  if (total <= row.krem) {  // every matching value is in
+    if (i != 0) return;
+    out.sum += stotal;
+    out.krem = 0;
+    out.done = 1;
+  } else {
+    const long long ce = ci - c, se = si - sv;  // the buckets above digit d
+    if (!(ci >= row.krem && ce < row.krem)) return;  // not the bucket that reaches krem
+    out.krem = row.krem - (int32_t)ce;
+    out.sum += se;
+    out.prefix |= (uint32_t)d << shift;
+    out.mask |= 255u << shift;
+    if (shift == 0) {  // prefix is now the exact k-th value; krem copies of it remain
+      out.sum += (long long)out.krem * (long long)out.prefix;
+      out.krem = 0;
+      out.done = 1;
+    }
+  }
+  rows[r] = out;
 }
 
 // Enqueues on `run` the sums of the <= k largest positive entries of each of
@@ -141,7 +164,7 @@ static void topk_enqueue(cen_job *job, const int32_t *vals, int64_t n, int nrows
     launch(S, K_SELECT, run, [&] {
       k_sel_hist<<<dim3(bx, nrows), 256, 0, run>>>(vals, n, nrows, shift, rows, hcnt, hsum);
     });
-    launch(S, K_SELECT, run, [&] { k_sel_step<<<grid_for(nrows, 64), 64, 0, run>>>(nrows, shift, rows, hcnt, hsum); });
+    launch(S, K_SELECT, run, [&] { k_sel_step<<<nrows, 256, 0, run>>>(nrows, shift, rows, hcnt, hsum); });
   }
   CEN_CK(cudaMemcpyAsync(hdst, rows, sizeof(SelRow) * (size_t)nrows, cudaMemcpyDeviceToHost, run));
 }
@@ -336,7 +359,7 @@ extern "C" int cen_topk_positive_sum_noalloc(const int32_t *vals, int64_t n, int
         k_sel_hist<<<dim3(bx, nrows), 256, 0, st>>>(vals, n, nrows, shift, sc->rows, sc->hcnt, sc->hsum);
       });
       launch(nullptr, K_SELECT, st,
-             [&] { k_sel_step<<<grid_for(nrows, 64), 64, 0, st>>>(nrows, shift, sc->rows, sc->hcnt, sc->hsum); });
+             [&] { k_sel_step<<<nrows, 256, 0, st>>>(nrows, shift, sc->rows, sc->hcnt, sc->hsum); });
     }
     SelRow h[kNoAllocMaxRows];
     CEN_CK(cudaMemcpyAsync(h, sc->rows, sizeof(SelRow) * (size_t)nrows, cudaMemcpyDeviceToHost, st));

@@ -1,6 +1,8 @@
 // Node -> sample incidence and greedyCover(k, H) (Sec. 3.1; Alg. 1 line "greedyCover").
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 #include "job.cuh"
 
 namespace cg = cooperative_groups;
@@ -175,7 +177,125 @@ __global__ void __launch_bounds__(256) k_greedy_all(const int64_t *__restrict__ 
   }
 }
 
+// All k iterations in one thread-block cluster of kGreedyCluster CTAs, the
+// gains held in the CTAs' shared memory (CTA r owns nodes [r per, (r+1) per)).
+// Per iteration: each CTA takes the largest key of its nodes (the same key as
+// k_greedy_all: largest gain, lowest id), a cluster barrier, every CTA reads
+// the others' keys through distributed shared memory and so picks the same
+// u*; then a thread per incident sample of u* sets the sample's covered bit
+// and, if it was not set, decrements the gains of the sample's members in
+// their owners' shared memory; another cluster barrier.  The picks and counts
+// are those of k_greedy_all.  A cluster is launched only when all of its CTAs
+// are resident at once, so the barriers always complete.
+constexpr int kGreedyCluster = 8;
+constexpr int kGreedyThreads = 1024;
+
+__global__ void __launch_bounds__(kGreedyThreads, 1)
+    k_greedy_cluster(const int32_t *__restrict__ c, const int64_t *__restrict__ noff,
+                     const int32_t *__restrict__ nsamp, const int64_t *__restrict__ hoff,
+                     const int32_t *__restrict__ hmem, int32_t n, int32_t per, uint32_t *covered, GreedyCtl *ctl,
+                     int k) {
+  extern __shared__ int32_t s_gain[];
+  __shared__ unsigned long long s_wbest[kGreedyThreads / 32];
+  __shared__ unsigned long long s_best, s_key;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int32_t u0 = rank * per, u1 = min(n, u0 + per);
+  for (int32_t u = u0 + tid; u < u1; u += kGreedyThreads) s_gain[u - u0] = c[u];
+  cl.sync();
+  const int64_t gt = (int64_t)rank * kGreedyThreads + tid;
+  const int64_t nthreads = (int64_t)kGreedyCluster * kGreedyThreads;
+  for (int it = 0; it < k; ++it) {
+    unsigned long long best = 0;
+    for (int32_t u = u0 + tid; u < u1; u += kGreedyThreads) {
+      const unsigned long long key = ((unsigned long long)(uint32_t)s_gain[u - u0] << 32) | (0xFFFFFFFFu - (uint32_t)u);
+      best = key > best ? key : best;
+    }
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+      best = y > best ? y : best;
+    }
+    if (lane == 0) s_wbest[wid] = best;
+    __syncthreads();
+    if (wid == 0) {
+      best = s_wbest[lane];
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+        best = y > best ? y : best;
+      }
+      if (lane == 0) s_best = best;
+    }
+    cl.sync();  // every CTA's key is in place
+    if (wid == 0) {
+      unsigned long long key = lane < kGreedyCluster ? *cl.map_shared_rank(&s_best, lane) : 0ull;
+      for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
+        key = y > key ? y : key;
+      }
+      if (lane == 0) s_key = key;
+    }
+    __syncthreads();
+    const unsigned long long key = s_key;
+    const uint32_t g = (uint32_t)(key >> 32);
+    if (g == 0) break;  // every CTA holds the same key: all leave together
+    const int32_t u = (int32_t)(0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFFu));
+    if (rank == 0 && tid == 0) {
+      ctl->S[it] = u;
+      ctl->size = it + 1;
+      ctl->covered += g;
+    }
+    const int64_t r0 = noff[u], r1 = noff[u + 1];
+    for (int64_t q = r0 + gt; q < r1; q += nthreads) {
+      const int32_t j = nsamp[q];
+      const uint32_t mask = 1u << (j & 31);
+      if (atomicOr(&covered[j >> 5], mask) & mask) continue;  // covered by an earlier pick
+      for (int64_t e = hoff[j]; e < hoff[j + 1]; ++e) {
+        const int32_t w = hmem[e];
+        const int owner = w / per;
+        atomicSub(cl.map_shared_rank(s_gain + (w - owner * per), owner), 1);
+      }
+    }
+    cl.sync();  // every gain update has landed before the next argmax
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+// Nodes per CTA the cluster form can hold (the rest of the shared memory is
+// the kernel's own).
+constexpr int64_t kGreedyClusterMaxPer = (227 * 1024 - 2048) / 4;
+
 size_t greedy_result_bytes(int32_t k) { return sizeof(GreedyCtl) + 4 * (size_t)k; }
+
+// Whether a cluster of k_greedy_cluster with `smem` bytes of gains can be
+// resident on this device (the kernel's shared-memory limit is raised, once,
+// to the most it may ask for).
+static bool greedy_cluster_ready(size_t smem) {
+  static std::mutex mu;
+  static int dev_ok = -1;
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev_ok < 0) {
+    dev_ok = cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(kGreedyClusterMaxPer * 4)) == cudaSuccess;
+    cudaGetLastError();
+  }
+  if (!dev_ok) return false;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kGreedyCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(kGreedyCluster);
+  cfg.blockDim = dim3(kGreedyThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  const bool ok = cudaOccupancyMaxActiveClusters(&clusters, k_greedy_cluster, &cfg) == cudaSuccess && clusters >= 1;
+  cudaGetLastError();
+  return ok;
+}
 
 // Sizes the greedy workspace for k picks (allocations ordered on the job's
 // stream).  The incidence must be current.
@@ -196,6 +316,29 @@ void greedy_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
   CEN_CK(cudaMemsetAsync(job->covered.p, 0, 4 * ((job->m + 31) / 32 + 1), run));
   CEN_CK(cudaMemsetAsync(job->gctl.p, 0, cbytes, run));
   GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
+  const int64_t per = ((int64_t)n + kGreedyCluster - 1) / kGreedyCluster;
+  if (per <= kGreedyClusterMaxPer && greedy_cluster_ready((size_t)per * 4)) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kGreedyCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(kGreedyCluster);
+    cfg.blockDim = dim3(kGreedyThreads);
+    cfg.dynamicSmemBytes = (size_t)per * 4;
+    cfg.stream = run;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    launch(St, K_GREEDY, run, [&] {
+      CEN_CK(cudaLaunchKernelEx(&cfg, k_greedy_cluster, (const int32_t *)job->c.as<int32_t>(),
+                                (const int64_t *)job->noff.as<int64_t>(), (const int32_t *)job->nsamp.as<int32_t>(),
+                                (const int64_t *)job->hoff.as<int64_t>(), (const int32_t *)job->hmem.as<int32_t>(), n,
+                                (int32_t)per, job->covered.as<uint32_t>(), ctl, (int)k));
+    });
+    CEN_CK(cudaMemcpyAsync(hdst, ctl, cbytes, cudaMemcpyDeviceToHost, run));
+    return;
+  }
   launch(St, K_GREEDY, run,
          [&] { k_gain_init<<<grid_for(n, 256), 256, 0, run>>>(job->c.as<int32_t>(), job->gain.as<int32_t>(), n); });
   const int coop = cooperative_grid((const void *)k_greedy_all, 256);
