@@ -12,11 +12,15 @@
 namespace cen {
 
 // Warp per node u with c_u > 0: lanes take 32 incident samples at a time; for
-// each sign word the warp ballots bit q across the 32 samples and lane q adds
-// the popcount.
+// each sign word the warp ballots bit q across the 32 samples (the word's
+// rows only) and lane q adds the popcount.  The block sums its scanned
+// incidences before one atomic.
 __global__ void __launch_bounds__(256) k_rade(int32_t n, int t, int nw, const int64_t *__restrict__ noff,
                                               const int32_t *__restrict__ nsamp, const uint32_t *__restrict__ sign,
                                               int32_t *R, unsigned long long *units) {
+  __shared__ unsigned long long s_scanned;
+  if (threadIdx.x == 0) s_scanned = 0;
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long scanned = 0;
@@ -25,12 +29,13 @@ __global__ void __launch_bounds__(256) k_rade(int32_t n, int t, int nw, const in
     const int32_t cu = (int32_t)(r1 - r0);
     if (cu == 0) continue;  // R rows are zero-filled
     for (int w = 0; w < nw; ++w) {
+      const int qn = min(32, t - 32 * w);  // rows of this word
       int32_t P = 0;
       for (int64_t base = r0; base < r1; base += 32) {
         const int64_t i = base + lane;
         const uint32_t x = i < r1 ? sign[(int64_t)nsamp[i] * nw + w] : 0u;
 #pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
+        for (int q = 0; q < qn; ++q) {
           const int c = __popc(__ballot_sync(0xffffffffu, (x >> q) & 1u));
           if (lane == q) P += c;
         }
@@ -40,7 +45,9 @@ __global__ void __launch_bounds__(256) k_rade(int32_t n, int t, int nw, const in
     }
     scanned += (unsigned long long)cu;
   }
-  if (lane == 0 && scanned) atomicAdd(units, scanned);
+  if (lane == 0 && scanned) atomicAdd(&s_scanned, scanned);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_scanned) atomicAdd(units, s_scanned);
 }
 
 // ------------------------------------------------------------ radix select

@@ -187,7 +187,10 @@ __global__ void __launch_bounds__(256) k_greedy_all(const int64_t *__restrict__ 
 // their owners' shared memory; another cluster barrier.  The picks and counts
 // are those of k_greedy_all.  A cluster is launched only when all of its CTAs
 // are resident at once, so the barriers always complete.
-constexpr int kGreedyCluster = 8;
+#ifndef CEN_GREEDY_CLUSTER
+#define CEN_GREEDY_CLUSTER 8
+#endif
+constexpr int kGreedyCluster = CEN_GREEDY_CLUSTER;  // 8: the portable cluster size
 constexpr int kGreedyThreads = 1024;
 
 __global__ void __launch_bounds__(kGreedyThreads, 1)
@@ -249,8 +252,9 @@ __global__ void __launch_bounds__(kGreedyThreads, 1)
     for (int64_t q = r0 + gt; q < r1; q += nthreads) {
       const int32_t j = nsamp[q];
       const uint32_t mask = 1u << (j & 31);
+      const int64_t e0 = hoff[j], e1 = hoff[j + 1];  // loaded alongside the covered bit
       if (atomicOr(&covered[j >> 5], mask) & mask) continue;  // covered by an earlier pick
-      for (int64_t e = hoff[j]; e < hoff[j + 1]; ++e) {
+      for (int64_t e = e0; e < e1; ++e) {
         const int32_t w = hmem[e];
         const int owner = w / per;
         atomicSub(cl.map_shared_rank(s_gain + (w - owner * per), owner), 1);
@@ -277,6 +281,9 @@ static bool greedy_cluster_ready(size_t smem) {
   if (dev_ok < 0) {
     dev_ok = cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(kGreedyClusterMaxPer * 4)) == cudaSuccess;
+    if (kGreedyCluster > 8)
+      dev_ok = dev_ok && cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                             cudaSuccess;
     cudaGetLastError();
   }
   if (!dev_ok) return false;
