@@ -315,7 +315,11 @@ struct cen_graph {
   int directed = 0;
   cudaStream_t st = nullptr;
   cen::DevBuf off, col, roff, rcol;  // roff/rcol empty when undirected (alias off/col)
-  cen::ChunkTable out_chunks, in_chunks_own;  // in_chunks_own used only when directed
+  // Chunk tables of the bit-parallel sampler (in_chunks_own only when
+  // directed), built on first use (graph_out_chunks / graph_in_chunks).
+  mutable std::mutex chunks_mu;
+  mutable bool chunks_built = false;
+  mutable cen::ChunkTable out_chunks, in_chunks_own;
   double param[10] = {};   // tuning defaults for jobs on this graph, by CEN_PARAM_* id
   bool param_set[10] = {};  // which of them were set
   // Set once most bidirectional searches on this graph outgrew their node
@@ -325,7 +329,7 @@ struct cen_graph {
   // later jobs (without an explicit setting) search with whole CTAs only.
   mutable std::atomic<bool> bidir_warps_off{false};
   // E[d^2] / E[d] over the out- and in-degrees (the larger): how many arcs a
-  // frontier node's neighbour has on average; computed once, on first use.
+  // frontier node's neighbour has on average; computed when the graph loads.
   mutable std::mutex branching_mu;
   mutable double branching = -1.0;
   // Triangle ranks (triangle space): exclusive prefix of per-arc counts, built once.
@@ -334,5 +338,4 @@ struct cen_graph {
   int64_t tri_total = -1;
   const int64_t *in_off() const { return directed ? roff.as<int64_t>() : off.as<int64_t>(); }
   const int32_t *in_col() const { return directed ? rcol.as<int32_t>() : col.as<int32_t>(); }
-  const cen::ChunkTable &in_chunks() const { return directed ? in_chunks_own : out_chunks; }
 };

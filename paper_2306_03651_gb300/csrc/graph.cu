@@ -203,6 +203,27 @@ __global__ void k_degree_moments(const int64_t *__restrict__ off, int32_t n, dou
   }
 }
 
+// The chunk tables of the bit-parallel sampler's long rows, built on their
+// first use (on `st`, synchronized; released later on the graph's stream).
+static void graph_chunks_ready(const cen_graph *g, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g->chunks_mu);
+  if (g->chunks_built) return;
+  build_chunks(g->off.as<int64_t>(), g->n, g->out_chunks, st, nullptr);
+  if (g->directed) build_chunks(g->roff.as<int64_t>(), g->n, g->in_chunks_own, st, nullptr);
+  for (DevBuf *b : {&g->out_chunks.w, &g->out_chunks.beg, &g->in_chunks_own.w, &g->in_chunks_own.beg}) b->st = g->st;
+  g->chunks_built = true;
+}
+
+const ChunkTable &graph_out_chunks(const cen_graph *g, cudaStream_t st) {
+  graph_chunks_ready(g, st);
+  return g->out_chunks;
+}
+
+const ChunkTable &graph_in_chunks(const cen_graph *g, cudaStream_t st) {
+  graph_chunks_ready(g, st);
+  return g->directed ? g->in_chunks_own : g->out_chunks;
+}
+
 double graph_branching(const cen_graph *g, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g->branching_mu);
   if (g->branching >= 0.0) return g->branching;
@@ -232,26 +253,37 @@ void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_d
     CEN_CK(cudaMemcpyAsync(g->off.p, off, sizeof(int64_t) * ((size_t)n + 1), kind, st));
     if (nnz) CEN_CK(cudaMemcpyAsync(g->col.p, col, sizeof(int32_t) * (size_t)nnz, kind, st));
   }
-  DevBuf bad;
-  bad.ensure(sizeof(int), st);
-  CEN_CK(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+  // the validation flag and the degree moments (sums of d and d^2 over the
+  // out-rows, then the in-rows) come back in one copy
+  struct Check {
+    double sums[4];
+    int bad;
+  };
+  DevBuf chk;
+  chk.ensure(sizeof(Check), st);
+  CEN_CK(cudaMemsetAsync(chk.p, 0, sizeof(Check), st));
+  Check *dchk = chk.as<Check>();
   launch(S, K_GRAPH, st, [&] {
     k_validate_csr<<<grid_for((size_t)n, 8), 256, 0, st>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), n, nnz,
-                                                          bad.as<int>());
+                                                          &dchk->bad);
   });
-  int hbad = 0;
-  CEN_CK(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  const int mblocks = grid_for((size_t)n, 256, sm_count() * 4);
+  launch(S, K_GRAPH, st,
+         [&] { k_degree_moments<<<mblocks, 256, 0, st>>>(g->off.as<int64_t>(), n, dchk->sums); });
+  Check h{};
+  CEN_CK(cudaMemcpyAsync(&h, chk.p, sizeof(Check), cudaMemcpyDeviceToHost, st));
   CEN_CK(cudaStreamSynchronize(st));
-  CEN_REQUIRE(hbad == 0, CEN_EINVAL,
+  CEN_REQUIRE(h.bad == 0, CEN_EINVAL,
               "cen_graph_load: CSR is not canonical (offsets, ids in [0,n), no self-loops, rows strictly ascending)");
-  build_chunks(g->off.as<int64_t>(), n, g->out_chunks, st, S);
+  const double bout = h.sums[0] > 0 ? h.sums[1] / h.sums[0] : 0.0;
   if (!g->directed || nnz == 0) {
     if (g->directed) {  // no arcs: in-CSR is all zeros
       g->roff.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
       CEN_CK(cudaMemsetAsync(g->roff.p, 0, sizeof(int64_t) * ((size_t)n + 1), st));
       g->rcol.ensure(4, st);
-      build_chunks(g->roff.as<int64_t>(), n, g->in_chunks_own, st, S);
+      CEN_CK(cudaStreamSynchronize(st));
     }
+    g->branching = bout;
     return;
   }
   DevBuf key, val, k2, v2, hist, tmp, indeg;
@@ -270,8 +302,12 @@ void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_d
   counts_to_offsets(indeg.as<int32_t>(), g->roff.as<int64_t>(), (size_t)n, tmp, st, S);
   g->rcol.ensure(4 * (size_t)nnz, st);
   CEN_CK(cudaMemcpyAsync(g->rcol.p, val.p, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
-  build_chunks(g->roff.as<int64_t>(), n, g->in_chunks_own, st, S);
+  launch(S, K_GRAPH, st,
+         [&] { k_degree_moments<<<mblocks, 256, 0, st>>>(g->roff.as<int64_t>(), n, dchk->sums + 2); });
+  CEN_CK(cudaMemcpyAsync(&h, chk.p, sizeof(Check), cudaMemcpyDeviceToHost, st));
   CEN_CK(cudaStreamSynchronize(st));
+  const double bin = h.sums[2] > 0 ? h.sums[3] / h.sums[2] : 0.0;
+  g->branching = bout > bin ? bout : bin;
 }
 
 }  // namespace cen

@@ -171,6 +171,10 @@ int64_t bidir_warp_queue(int64_t QC);
 size_t bidir_warp_bytes_per_slot();
 // E[d^2] / E[d] of the graph's degrees (out and in, the larger), computed once.
 double graph_branching(const cen_graph *g, cudaStream_t st);
+// The bit-parallel sampler's chunk tables of the graph's long out- and in-rows
+// (built on first use, on st).
+const ChunkTable &graph_out_chunks(const cen_graph *g, cudaStream_t st);
+const ChunkTable &graph_in_chunks(const cen_graph *g, cudaStream_t st);
 size_t bidir_warp_table_bytes_per_slot();
 size_t bidir_warp_epoch_bytes_per_slot();
 void kpath_sample(cen_job *job, uint64_t j0, uint64_t count, int32_t *out, const int64_t *hoff);

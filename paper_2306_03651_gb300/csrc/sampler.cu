@@ -1013,7 +1013,7 @@ struct Sampler {
           k_expand_push<<<resident_grid((const void *)k_expand_push, 256), 256, 0, st>>>(off, col, n, G, gshift, cur,
                                                                                          nxt, ctl, units(K_PUSH));
         });
-        const ChunkTable &oc = g->out_chunks;
+        const ChunkTable &oc = graph_out_chunks(g, st);
         if (oc.count)
           launch(S, K_PUSH, st, [&] {
             k_expand_push_heavy<<<grid_for((size_t)oc.count * 32, 256, sm_count() * 64), 256, 0, st>>>(
@@ -1028,7 +1028,7 @@ struct Sampler {
           k_expand_pull<<<resident_grid((const void *)k_expand_pull, 256), 256, 0, st>>>(
               roff, rcol, off, n, G, gshift, cur, nxt, vis, ctl, units(K_PULL));
         });
-        const ChunkTable &ic = g->in_chunks();
+        const ChunkTable &ic = graph_in_chunks(g, st);
         if (ic.count)
           launch(S, K_PULL, st, [&] {
             k_expand_pull_heavy<<<resident_grid((const void *)k_expand_pull_heavy, 256), 256, 0, st>>>(
@@ -1062,7 +1062,7 @@ struct Sampler {
     uint64_t *any = w.any.as<uint64_t>();
     CEN_CK(cudaMemsetAsync(any, 0, words * 8, st));
     const ArcLog log{w.arcs.as<ConeArc>(), count, (unsigned long long)w.arc_cap};
-    const ChunkTable &ic = g->in_chunks();
+    const ChunkTable &ic = graph_in_chunks(g, st);
     for (int L = Lmax; L >= 1; --L) {
       uint64_t *lev = level(L);
       uint64_t *cone = w.tmp.as<uint64_t>();
