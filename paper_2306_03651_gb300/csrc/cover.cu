@@ -1,6 +1,7 @@
 // Node -> sample incidence and greedyCover(k, H) (Sec. 3.1; Alg. 1 line "greedyCover").
 #include <cooperative_groups.h>
 
+#include <cstdlib>
 #include <mutex>
 
 #include "job.cuh"
@@ -324,7 +325,9 @@ void greedy_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
   CEN_CK(cudaMemsetAsync(job->gctl.p, 0, cbytes, run));
   GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
   const int64_t per = ((int64_t)n + kGreedyCluster - 1) / kGreedyCluster;
-  if (per <= kGreedyClusterMaxPer && greedy_cluster_ready((size_t)per * 4)) {
+  const char *grid_env = getenv("CEN_GREEDY_GRID");  // diagnostic: "1" keeps the cooperative grid form
+  const bool grid_form = grid_env && grid_env[0] == '1';
+  if (!grid_form && per <= kGreedyClusterMaxPer && greedy_cluster_ready((size_t)per * 4)) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;

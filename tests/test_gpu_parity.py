@@ -298,8 +298,20 @@ def incidence_rows(h, n):
     return rows
 
 
+@pytest.fixture(params=["cluster", "grid"])
+def greedy_form(request, monkeypatch):
+    """greedyCover as one thread-block cluster (the default for these sizes) or, with the
+    diagnostic CEN_GREEDY_GRID=1, as the cooperative grid kernel that graphs over 462,848
+    nodes use."""
+    if request.param == "grid":
+        monkeypatch.setenv("CEN_GREEDY_GRID", "1")
+    else:
+        monkeypatch.delenv("CEN_GREEDY_GRID", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("name", ["ba2000", "rmat12_dir", "grid_rewired"])
-def test_greedy_incidence_mcera_parity(name):
+def test_greedy_incidence_mcera_parity(name, greedy_form):
     g = GRAPHS[name]
     m, t = 3000, 40
     og, ojob, ref = oracle_samples(g, 9, m, t)
