@@ -30,16 +30,26 @@ __global__ void k_validate_csr(const int64_t *off, const int32_t *col, int32_t n
 }
 
 // Arc list in CSR order: key = head, value = tail.
-__global__ void k_arcs_by_tail(const int64_t *off, const int32_t *col, int32_t n, uint32_t *key, uint32_t *val,
-                               int32_t *indeg) {
+__global__ void k_arcs_by_tail(const int64_t *off, const int32_t *col, int32_t n, uint32_t *key, uint32_t *val) {
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
     for (int64_t i = off[v] + lane; i < off[v + 1]; i += 32) {
       key[i] = (uint32_t)col[i];
       val[i] = (uint32_t)v;
-      atomicAdd(&indeg[col[i]], 1);
     }
+  }
+}
+
+// In-CSR offsets from the heads sorted ascending (nnz >= 1): roff[w] is the
+// first position whose head is >= w.  Position i sets it for the heads w in
+// (key[i-1], key[i]], with key[-1] = -1 and key[nnz] = n, so every w in
+// [0, n] is set exactly once (roff[n] = nnz).
+__global__ void k_in_offsets(const uint32_t *__restrict__ key, int64_t nnz, int32_t n, int64_t *roff) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= nnz; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t lo = i == 0 ? -1 : (int64_t)key[i - 1];
+    const int64_t hi = i == nnz ? (int64_t)n : (int64_t)key[i];
+    for (int64_t w = lo + 1; w <= hi; ++w) roff[w] = i;
   }
 }
 
@@ -286,22 +296,23 @@ void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_d
     g->branching = bout;
     return;
   }
-  DevBuf key, val, k2, v2, hist, tmp, indeg;
+  // arcs (head, tail) in CSR order, stably sorted by head: the tails of each
+  // head stay ascending, so rcol rows are ascending; the tails are sorted in
+  // place in rcol
+  DevBuf key, k2, v2, hist, tmp;
   key.ensure(4 * (size_t)nnz, st);
-  val.ensure(4 * (size_t)nnz, st);
-  indeg.ensure(4 * (size_t)n, st);
-  CEN_CK(cudaMemsetAsync(indeg.p, 0, 4 * (size_t)n, st));
+  g->rcol.ensure(4 * (size_t)nnz, st);
   launch(S, K_GRAPH, st, [&] {
     k_arcs_by_tail<<<grid_for((size_t)n, 8), 256, 0, st>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), n,
-                                                           key.as<uint32_t>(), val.as<uint32_t>(), indeg.as<int32_t>());
+                                                           key.as<uint32_t>(), g->rcol.as<uint32_t>());
   });
   int bits = 1;
   while (bits < 31 && (1u << bits) < (uint32_t)n) ++bits;
-  radix_sort_pairs(key.as<uint32_t>(), val.as<uint32_t>(), (size_t)nnz, bits, k2, v2, hist, tmp, st, S);
+  radix_sort_pairs(key.as<uint32_t>(), g->rcol.as<uint32_t>(), (size_t)nnz, bits, k2, v2, hist, tmp, st, S);
   g->roff.ensure(sizeof(int64_t) * ((size_t)n + 1), st);
-  counts_to_offsets(indeg.as<int32_t>(), g->roff.as<int64_t>(), (size_t)n, tmp, st, S);
-  g->rcol.ensure(4 * (size_t)nnz, st);
-  CEN_CK(cudaMemcpyAsync(g->rcol.p, val.p, 4 * (size_t)nnz, cudaMemcpyDeviceToDevice, st));
+  launch(S, K_GRAPH, st, [&] {
+    k_in_offsets<<<grid_for((size_t)nnz + 1, 256), 256, 0, st>>>(key.as<uint32_t>(), nnz, n, g->roff.as<int64_t>());
+  });
   launch(S, K_GRAPH, st,
          [&] { k_degree_moments<<<mblocks, 256, 0, st>>>(g->roff.as<int64_t>(), n, dchk->sums + 2); });
   CEN_CK(cudaMemcpyAsync(&h, chk.p, sizeof(Check), cudaMemcpyDeviceToHost, st));
