@@ -6,26 +6,51 @@
 
 namespace cen {
 
-// One warp per row: offsets monotone and in range, heads in [0, n), no
-// self-loop, strictly ascending.  bad |= 1 on any violation.
-__global__ void k_validate_csr(const int64_t *off, const int32_t *col, int32_t n, int64_t nnz, int *bad) {
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// Canonical-CSR validation in three passes (each *bad |= 1 on a violation):
+// offsets that rise from 0 to nnz, with the first arc of every non-empty row
+// marked; every head in [0, n) and above the arc before it unless it starts
+// its row (so rows are strictly ascending: no repeats); and no row that holds
+// its own node (a binary search, exact once the rows are ascending).
+__global__ void k_mark_starts(const int64_t *__restrict__ off, int32_t n, int64_t nnz, uint8_t *start, int *bad) {
   if (blockIdx.x == 0 && threadIdx.x == 0)
     if (off[0] != 0 || off[n] != nnz) atomicOr(bad, 1);
-  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += nwarps) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = off[v], e = off[v + 1];
-    if (b > e || b < 0 || e > nnz) {
-      if (lane == 0) atomicOr(bad, 1);
-      continue;
+    if (b > e || b < 0 || e > nnz)
+      atomicOr(bad, 1);
+    else if (b < e)
+      start[b] = 1;
+  }
+}
+
+__global__ void k_check_arcs(const int32_t *__restrict__ col, int32_t n, int64_t nnz,
+                             const uint8_t *__restrict__ start, int *bad) {
+  bool ok = true;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = col[i];
+    ok &= c >= 0 && c < n;
+    if (i > 0 && !start[i]) ok &= col[i - 1] < c;
+  }
+  if (!__all_sync(0xffffffffu, ok) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+__global__ void k_check_loops(const int64_t *__restrict__ off, const int32_t *__restrict__ col, int32_t n,
+                              int64_t nnz, int *bad) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = off[v], hi = off[v + 1];
+    if (lo < 0 || hi > nnz || lo >= hi) continue;  // bad offsets are flagged by k_mark_starts
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      const int32_t c = col[mid];
+      if (c == (int32_t)v) {
+        atomicOr(bad, 1);
+        break;
+      }
+      if (c < (int32_t)v)
+        lo = mid + 1;
+      else
+        hi = mid;
     }
-    bool ok = true;
-    for (int64_t i = b + lane; i < e; i += 32) {
-      const int32_t c = col[i];
-      ok &= (c >= 0 && c < n && c != (int32_t)v);
-      if (i > b) ok &= (col[i - 1] < c);
-    }
-    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(bad, 1);
   }
 }
 
@@ -273,9 +298,21 @@ void graph_build(cen_graph *g, const int64_t *off, const int32_t *col, bool on_d
   chk.ensure(sizeof(Check), st);
   CEN_CK(cudaMemsetAsync(chk.p, 0, sizeof(Check), st));
   Check *dchk = chk.as<Check>();
+  DevBuf start;
+  start.ensure((size_t)(nnz > 0 ? nnz : 1), st);
+  CEN_CK(cudaMemsetAsync(start.p, 0, (size_t)(nnz > 0 ? nnz : 1), st));
   launch(S, K_GRAPH, st, [&] {
-    k_validate_csr<<<grid_for((size_t)n, 8), 256, 0, st>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), n, nnz,
-                                                          &dchk->bad);
+    k_mark_starts<<<grid_for((size_t)n, 256), 256, 0, st>>>(g->off.as<int64_t>(), n, nnz, start.as<uint8_t>(),
+                                                           &dchk->bad);
+  });
+  if (nnz)
+    launch(S, K_GRAPH, st, [&] {
+      k_check_arcs<<<grid_for((size_t)nnz, 256), 256, 0, st>>>(g->col.as<int32_t>(), n, nnz, start.as<uint8_t>(),
+                                                                &dchk->bad);
+    });
+  launch(S, K_GRAPH, st, [&] {
+    k_check_loops<<<grid_for((size_t)n, 256), 256, 0, st>>>(g->off.as<int64_t>(), g->col.as<int32_t>(), n, nnz,
+                                                           &dchk->bad);
   });
   const int mblocks = grid_for((size_t)n, 256, sm_count() * 4);
   launch(S, K_GRAPH, st,

@@ -455,6 +455,57 @@ def test_graph_load_rejects_malformed_and_accepts_device_arrays():
     assert_same_samples(job.samples(), ref)
 
 
+def _csr(n, rows):
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([c for r in rows for c in r], np.int32)
+    return off, col
+
+
+@pytest.mark.parametrize("case", ["ok", "ok_empty_rows", "id_high", "id_negative", "repeat", "descending",
+                                  "self_loop_inside", "self_loop_first", "off_not_rising", "off0", "off_end"])
+def test_graph_load_validation_cases(case):
+    """A canonical CSR (rows strictly ascending, ids in [0, n), no self-loop, offsets rising from 0
+    to nnz) loads; each single violation is rejected with CEN_EINVAL, wherever it sits."""
+    n = 9
+    rows = [[1, 4, 7], [], [0, 5], [], [1, 2, 6, 8], [0], [], [3, 8], [2]]
+    off, col = _csr(n, rows)
+    if case == "ok_empty_rows":
+        rows = [[], [], [5], [], [], [], [], [], []]
+        off, col = _csr(n, rows)
+    elif case == "id_high":
+        col[4] = n
+    elif case == "id_negative":
+        col[0] = -1
+    elif case == "repeat":
+        rows[4] = [1, 2, 2, 8]
+        off, col = _csr(n, rows)
+    elif case == "descending":
+        rows[0] = [1, 7, 4]
+        off, col = _csr(n, rows)
+    elif case == "self_loop_inside":
+        rows[4] = [1, 2, 4, 8]  # sorted, holds its own node
+        off, col = _csr(n, rows)
+    elif case == "self_loop_first":
+        rows[2] = [2, 5]
+        off, col = _csr(n, rows)
+    elif case == "off_not_rising":
+        off[2] = off[3] + 1  # row 2 ends before it starts
+    elif case == "off0":
+        off[0] = 1
+    elif case == "off_end":
+        off[-1] = off[-2] - 1  # the last row ends before it starts (nnz is taken from off[n])
+    if case.startswith("ok"):
+        gg = P.Graph(n, off, col, True)
+        assert gg.nnz == len(col)
+        roff, rcol = gg.csr()  # the graph as loaded
+        assert np.array_equal(roff, off) and np.array_equal(rcol, col)
+        return
+    with pytest.raises(P.CenError) as ei:
+        P.Graph(n, off, col, True)
+    assert ei.value.rc == P.EINVAL
+
+
 def test_stats_and_timing():
     g = GRAPHS["ba2000"]
     job = P.Job(P.Graph.of(g), 1, 10)
