@@ -140,7 +140,7 @@ int cen_sample(cen_job *job, uint64_t m_new);
  * count is 0.  S_out[k] (host) receives the picks in order, *S_size their
  * number, *covered = |{j : h_j meets S}| = m * C_H(S).  Runs as one
  * thread-block cluster holding the gains in shared memory when they fit
- * (n <= 462,848), else as one cooperative grid launch; the environment
+ * (n <= 460,800), else as one cooperative grid launch; the environment
  * variable CEN_GREEDY_GRID=1 keeps the grid form (a diagnostic: the picks
  * are the same). */
 int cen_greedy_cover(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered);

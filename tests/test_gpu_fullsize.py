@@ -65,7 +65,7 @@ def test_rmat18_whole_round_against_the_oracle(rmat18):
         S2, cov2 = job.greedy_cover(k)
         R2, W2, b2 = job.mcera(k)
         assert S2.tolist() == oS.tolist() and cov2 == ocov and np.array_equal(R2, oRnum) and W2 == oWnum
-        # and greedyCover in the cooperative grid form (graphs over 462,848 nodes use it)
+        # and greedyCover in the cooperative grid form (graphs over 460,800 nodes use it)
         os.environ["CEN_GREEDY_GRID"] = "1"
         try:
             S3, cov3 = job.greedy_cover(k)

@@ -301,7 +301,7 @@ def incidence_rows(h, n):
 @pytest.fixture(params=["cluster", "grid"])
 def greedy_form(request, monkeypatch):
     """greedyCover as one thread-block cluster (the default for these sizes) or, with the
-    diagnostic CEN_GREEDY_GRID=1, as the cooperative grid kernel that graphs over 462,848
+    diagnostic CEN_GREEDY_GRID=1, as the cooperative grid kernel that graphs over 460,800
     nodes use."""
     if request.param == "grid":
         monkeypatch.setenv("CEN_GREEDY_GRID", "1")
