@@ -139,10 +139,11 @@ int cen_sample(cen_job *job, uint64_t m_new);
  * most still-uncovered samples (lowest id on ties); stop early when that
  * count is 0.  S_out[k] (host) receives the picks in order, *S_size their
  * number, *covered = |{j : h_j meets S}| = m * C_H(S).  Runs as one
- * thread-block cluster holding the gains in shared memory when they fit
- * (n <= 460,800), else as one cooperative grid launch; the environment
- * variable CEN_GREEDY_GRID=1 keeps the grid form (a diagnostic: the picks
- * are the same). */
+ * thread-block cluster holding the gains in shared memory when they fit (16
+ * CTAs, n <= 921,600, where the device allows such clusters; else 8 CTAs,
+ * n <= 460,800), otherwise as one cooperative grid launch.  Diagnostics (the
+ * picks are the same): the environment variable CEN_GREEDY_CLUSTER=8 keeps
+ * 8-CTA clusters, CEN_GREEDY_GRID=1 the grid form. */
 int cen_greedy_cover(cen_job *job, int32_t k, int32_t *S_out, int32_t *S_size, uint64_t *covered);
 
 /* AMCERA numerators (Sec. 4.1, Alg. 1 lines computing r_j^u and r_j), all

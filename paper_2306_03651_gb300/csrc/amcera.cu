@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) k_sel_step(int nrows, int shift, SelRow *
 // `nrows` rows of length n (select state sized beforehand, see mcera_prepare);
 // the per-row results reach hdst (pinned, nrows SelRow) once `run` drains.
 static void topk_enqueue(cen_job *job, const int32_t *vals, int64_t n, int nrows, int32_t k, cudaStream_t run,
-                         SelRow *hdst) {
+                         SelRow *hdst, int64_t vmax = INT32_MAX) {
   Stats *S = &job->stats;
   SelRow *rows = job->selst.as<SelRow>();
   unsigned int *hcnt = job->selh.as<unsigned int>();
@@ -167,7 +167,11 @@ static void topk_enqueue(cen_job *job, const int32_t *vals, int64_t n, int nrows
   CEN_CK(cudaMemsetAsync(job->selh.p, 0, (size_t)nrows * 256 * 12, run));
   launch(S, K_SELECT, run, [&] { k_sel_init<<<grid_for(nrows, 128), 128, 0, run>>>(rows, nrows, k); });
   const int bx = grid_for((size_t)n, 256 * 8, 512);
-  for (int shift = 24; shift >= 0; shift -= 8) {
+  // digits above the highest one a value <= vmax can have are 0 for every
+  // value, so their passes would only descend into digit 0
+  int top = 24;
+  while (top > 0 && (vmax >> top) == 0) top -= 8;
+  for (int shift = top; shift >= 0; shift -= 8) {
     launch(S, K_SELECT, run, [&] {
       k_sel_hist<<<dim3(bx, nrows), 256, 0, run>>>(vals, n, nrows, shift, rows, hcnt, hsum);
     });
@@ -207,7 +211,8 @@ void mcera_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
   CEN_CK(cudaMemcpyAsync(job->R.as<int32_t>() + (size_t)n * t, job->c.p, 4 * (size_t)n, cudaMemcpyDeviceToDevice,
                          run));
   SelRow *hrows = (SelRow *)hdst;
-  topk_enqueue(job, job->R.as<int32_t>(), n, t + 1, k, run, hrows);
+  // |R_q^u| <= c_u <= m: every value the select ranks is at most m
+  topk_enqueue(job, job->R.as<int32_t>(), n, t + 1, k, run, hrows, (int64_t)job->m);
   if (job->m) CEN_CK(cudaMemcpyAsync(hrows + t + 1, job->bmax.p, 4, cudaMemcpyDeviceToHost, run));  // b_H = 0 if m = 0
 }
 

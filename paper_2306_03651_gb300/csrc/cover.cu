@@ -178,8 +178,9 @@ __global__ void __launch_bounds__(256) k_greedy_all(const int64_t *__restrict__ 
   }
 }
 
-// All k iterations in one thread-block cluster of kGreedyCluster CTAs, the
-// gains held in the CTAs' shared memory (CTA r owns nodes [r per, (r+1) per)).
+// All k iterations in one thread-block cluster of C CTAs (16 where the device
+// allows clusters that large, else 8), the gains held in the CTAs' shared
+// memory (CTA r owns nodes [r per, (r+1) per)).
 // Per iteration: each CTA takes the largest key of its nodes (the same key as
 // k_greedy_all: largest gain, lowest id), a cluster barrier, every CTA reads
 // the others' keys through distributed shared memory and so picks the same
@@ -188,11 +189,10 @@ __global__ void __launch_bounds__(256) k_greedy_all(const int64_t *__restrict__ 
 // their owners' shared memory; another cluster barrier.  The picks and counts
 // are those of k_greedy_all.  A cluster is launched only when all of its CTAs
 // are resident at once, so the barriers always complete.
-#ifndef CEN_GREEDY_CLUSTER
-#define CEN_GREEDY_CLUSTER 8
-#endif
-constexpr int kGreedyCluster = CEN_GREEDY_CLUSTER;  // 8: the portable cluster size
-constexpr int kGreedyThreads = 1024;
+constexpr int kGreedyClusterMax = 16;  // non-portable; 8 is the portable size
+// 512 threads: cheaper barriers per pick than 1,024 (measured 0.215 vs 0.23 ms per R-MAT 18
+// round with 16 CTAs; 0.24 vs 0.25 ms with 8)
+constexpr int kGreedyThreads = 512;
 
 __global__ void __launch_bounds__(kGreedyThreads, 1)
     k_greedy_cluster(const int32_t *__restrict__ c, const int64_t *__restrict__ noff,
@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(kGreedyThreads, 1)
   for (int32_t u = u0 + tid; u < u1; u += kGreedyThreads) s_gain[u - u0] = c[u];
   cl.sync();
   const int64_t gt = (int64_t)rank * kGreedyThreads + tid;
-  const int64_t nthreads = (int64_t)kGreedyCluster * kGreedyThreads;
+  const int C = (int)cl.num_blocks();
+  const int64_t nthreads = (int64_t)C * kGreedyThreads;
   for (int it = 0; it < k; ++it) {
     unsigned long long best = 0;
     for (int32_t u = u0 + tid; u < u1; u += kGreedyThreads) {
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kGreedyThreads, 1)
     if (lane == 0) s_wbest[wid] = best;
     __syncthreads();
     if (wid == 0) {
-      best = s_wbest[lane];
+      best = lane < kGreedyThreads / 32 ? s_wbest[lane] : 0ull;
       for (int o = 16; o; o >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
         best = y > best ? y : best;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kGreedyThreads, 1)
     }
     cl.sync();  // every CTA's key is in place
     if (wid == 0) {
-      unsigned long long key = lane < kGreedyCluster ? *cl.map_shared_rank(&s_best, lane) : 0ull;
+      unsigned long long key = lane < C ? *cl.map_shared_rank(&s_best, lane) : 0ull;
       for (int o = 16; o; o >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, key, o);
         key = y > key ? y : key;
@@ -272,29 +273,28 @@ constexpr int64_t kGreedyClusterMaxPer = (227 * 1024 - 2048) / 4;
 
 size_t greedy_result_bytes(int32_t k) { return sizeof(GreedyCtl) + 4 * (size_t)k; }
 
-// Whether a cluster of k_greedy_cluster with `smem` bytes of gains can be
-// resident on this device (the kernel's shared-memory limit is raised, once,
-// to the most it may ask for).
-static bool greedy_cluster_ready(size_t smem) {
+// Whether a cluster of C CTAs of k_greedy_cluster with `smem` bytes of gains
+// can be resident on this device (the kernel's shared-memory limit is raised,
+// and clusters over 8 allowed, once per process).
+static bool greedy_cluster_ready(int C, size_t smem) {
   static std::mutex mu;
-  static int dev_ok = -1;
+  static int attr_ok = -1, big_ok = -1;
   std::lock_guard<std::mutex> lk(mu);
-  if (dev_ok < 0) {
-    dev_ok = cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(kGreedyClusterMaxPer * 4)) == cudaSuccess;
-    if (kGreedyCluster > 8)
-      dev_ok = dev_ok && cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                             cudaSuccess;
+  if (attr_ok < 0) {
+    attr_ok = cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(kGreedyClusterMaxPer * 4)) == cudaSuccess;
+    cudaGetLastError();
+    big_ok = cudaFuncSetAttribute(k_greedy_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
     cudaGetLastError();
   }
-  if (!dev_ok) return false;
+  if (!attr_ok || (C > 8 && !big_ok)) return false;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kGreedyCluster;
+  attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(kGreedyCluster);
+  cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(kGreedyThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.attrs = attr;
@@ -324,17 +324,26 @@ void greedy_enqueue(cen_job *job, int32_t k, cudaStream_t run, void *hdst) {
   CEN_CK(cudaMemsetAsync(job->covered.p, 0, 4 * ((job->m + 31) / 32 + 1), run));
   CEN_CK(cudaMemsetAsync(job->gctl.p, 0, cbytes, run));
   GreedyCtl *ctl = job->gctl.as<GreedyCtl>();
-  const int64_t per = ((int64_t)n + kGreedyCluster - 1) / kGreedyCluster;
-  const char *grid_env = getenv("CEN_GREEDY_GRID");  // diagnostic: "1" keeps the cooperative grid form
+  // diagnostics: CEN_GREEDY_GRID=1 keeps the cooperative grid form, CEN_GREEDY_CLUSTER=8 the
+  // portable cluster size
+  const char *grid_env = getenv("CEN_GREEDY_GRID");
+  const char *size_env = getenv("CEN_GREEDY_CLUSTER");
   const bool grid_form = grid_env && grid_env[0] == '1';
-  if (!grid_form && per <= kGreedyClusterMaxPer && greedy_cluster_ready((size_t)per * 4)) {
+  int C = 0;
+  for (int c : {kGreedyClusterMax, 8}) {
+    if (grid_form || C || (c > 8 && size_env && atoi(size_env) == 8)) continue;
+    const int64_t per_c = ((int64_t)n + c - 1) / c;
+    if (per_c <= kGreedyClusterMaxPer && greedy_cluster_ready(c, (size_t)per_c * 4)) C = c;
+  }
+  if (C) {
+    const int64_t per = ((int64_t)n + C - 1) / C;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kGreedyCluster;
+    attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(kGreedyCluster);
+    cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kGreedyThreads);
     cfg.dynamicSmemBytes = (size_t)per * 4;
     cfg.stream = run;

@@ -65,13 +65,15 @@ def test_rmat18_whole_round_against_the_oracle(rmat18):
         S2, cov2 = job.greedy_cover(k)
         R2, W2, b2 = job.mcera(k)
         assert S2.tolist() == oS.tolist() and cov2 == ocov and np.array_equal(R2, oRnum) and W2 == oWnum
-        # and greedyCover in the cooperative grid form (graphs over 460,800 nodes use it)
-        os.environ["CEN_GREEDY_GRID"] = "1"
-        try:
-            S3, cov3 = job.greedy_cover(k)
-        finally:
-            del os.environ["CEN_GREEDY_GRID"]
-        assert S3.tolist() == oS.tolist() and cov3 == ocov
+        # and greedyCover as an 8-CTA cluster and in the cooperative grid form (graphs over
+        # 921,600 nodes use it)
+        for var, val in (("CEN_GREEDY_CLUSTER", "8"), ("CEN_GREEDY_GRID", "1")):
+            os.environ[var] = val
+            try:
+                S3, cov3 = job.greedy_cover(k)
+            finally:
+                del os.environ[var]
+            assert S3.tolist() == oS.tolist() and cov3 == ocov, var
         for i in (1, 4):
             st, bd = P.bounds(cov, M18, int(Rnum.sum()), wl.t, Wnum, b, wl.eps, wl.delta, i)
             ost, obd = O.bounds(ocov, M18, int(oRnum.sum()), wl.t, oWnum, ob, wl.eps, wl.delta, i)

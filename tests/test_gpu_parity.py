@@ -298,15 +298,18 @@ def incidence_rows(h, n):
     return rows
 
 
-@pytest.fixture(params=["cluster", "grid"])
+@pytest.fixture(params=["cluster", "cluster8", "grid"])
 def greedy_form(request, monkeypatch):
-    """greedyCover as one thread-block cluster (the default for these sizes) or, with the
-    diagnostic CEN_GREEDY_GRID=1, as the cooperative grid kernel that graphs over 460,800
-    nodes use."""
+    """greedyCover as one thread-block cluster (16 CTAs where the device allows it, the default
+    for these sizes), with the diagnostic CEN_GREEDY_CLUSTER=8 as one 8-CTA cluster (the
+    portable size), or with CEN_GREEDY_GRID=1 as the cooperative grid kernel that graphs over
+    921,600 nodes use."""
+    monkeypatch.delenv("CEN_GREEDY_GRID", raising=False)
+    monkeypatch.delenv("CEN_GREEDY_CLUSTER", raising=False)
     if request.param == "grid":
         monkeypatch.setenv("CEN_GREEDY_GRID", "1")
-    else:
-        monkeypatch.delenv("CEN_GREEDY_GRID", raising=False)
+    elif request.param == "cluster8":
+        monkeypatch.setenv("CEN_GREEDY_CLUSTER", "8")
     return request.param
 
 
